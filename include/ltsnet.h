@@ -1,0 +1,236 @@
+/*
+ * ltsnet.h -- C ABI of the GB300 L-tsNET library (libltsnet.so).
+ *
+ * L-tsNET (Meidiana, Hong, Ma, "BH-tsNET, FIt-tsNET, L-tsNET: Fast tsNET
+ * Algorithms for Large Graph Drawing", arXiv 2509.19785) lays out a graph by
+ * minimising the tsNET cost (Eq. 1) of a 2-D layout Y.  Alg. 3 takes a graph,
+ * a perplexity u, a number of intervals I and a number of interpolation points
+ * P and returns the layout; the calls below follow that statement.
+ *
+ * Conventions shared by every call:
+ *  - Pointers are DEVICE pointers unless the comment says "host".
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy default
+ *    stream) and is asynchronous unless the comment says "synchronous".
+ *  - The library never allocates or frees device memory.  The caller owns
+ *    every buffer, including the workspace `ws` (`ws_bytes` long, 256-byte
+ *    aligned), whose size the matching *_workspace_size call returns.
+ *  - Every call returns an ltsnet_status.  Argument errors are detected on the
+ *    host and returned before anything is enqueued.  Errors found by a kernel
+ *    (a vertex id out of range, a non-finite coordinate, a loop that hit its
+ *    iteration cap) are recorded in a status word inside the workspace; the
+ *    synchronous calls return it, and ltsnet_poll_status reads it for the
+ *    asynchronous ones.  No kernel traps.
+ *  - Layout Y is row-major float[n][2] (x_i, y_i); gradients use the same
+ *    layout.  Graphs are CSR with int64 row offsets and int32 column ids, both
+ *    directions of every undirected edge stored; self-loops and duplicate
+ *    entries are allowed and ignored.
+ */
+#ifndef LTSNET_H
+#define LTSNET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ltsnet_stream; /* = cudaStream_t */
+
+typedef enum {
+    LTSNET_OK = 0,
+    LTSNET_WARN_NOT_CONVERGED = 1, /* some rows missed the perplexity target (the "perplexity too low" case of Sec. 4.1) */
+    LTSNET_ERR_INVALID_ARG = -1,
+    LTSNET_ERR_WORKSPACE = -2,     /* workspace or output capacity too small */
+    LTSNET_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+    LTSNET_ERR_DEVICE_TIMEOUT = -4,/* a device loop reached its iteration cap */
+    LTSNET_ERR_NONFINITE = -5,     /* NaN/Inf in the layout or the gradient */
+    LTSNET_ERR_BAD_GRAPH = -6      /* a column id outside [0, n) */
+} ltsnet_status;
+
+/* One descent stage.  Sec. 2.1: the multipliers lambda_KL, lambda_c, lambda_r
+ * of the three cost terms (Eq. 1) change between stages; the paper gives no
+ * values.  `exaggeration` multiplies P in the attractive term (1 = none);
+ * `momentum` is the optimiser's momentum for the stage. */
+typedef struct {
+    int32_t iters;
+    float lambda_kl;
+    float lambda_c;
+    float lambda_r;
+    float exaggeration;
+    float momentum;
+} ltsnet_stage;
+
+/* Method parameters.  ltsnet_default_params() fills every field. */
+typedef struct {
+    float perplexity;      /* u of Eq. 3; k = ceil(3u) neighbours per vertex (Sec. 3.1) */
+    float eps;             /* entropy kernel regulariser, 1/20 (Sec. 3.3) */
+    int32_t nodes_per_box; /* P of Alg. 3, interpolation nodes per interval: 2, 3, 4 or 5 (default 3) */
+    float box_width_max;   /* grid rule: I = max(min_boxes, ceil(extent / box_width_max)) ... */
+    int32_t min_boxes;     /* ... rounded up to a 5-smooth size ... */
+    int32_t max_boxes;     /* ... and capped here (the cap widens the boxes); default 640;
+                              2 * nodes_per_box * max_boxes (the FFT length) <= 4096 */
+    float learning_rate;   /* <= 0: max(200, n/12) */
+    int32_t beta_max_steps;/* beta search cap (default 100) */
+    double beta_tol;       /* |H_i - ln u| tolerance (default 1e-5) */
+    int32_t n_stages;      /* stage schedule; stages is a HOST pointer */
+    const ltsnet_stage* stages;
+    int32_t flags;         /* LTSNET_FLAG_* */
+} ltsnet_params;
+
+/* flags: LTSNET_FLAG_PLAIN selects the unfused FP32 baseline form of the loop
+ * (atomic spread in input order, separate gather/attraction/update kernels)
+ * instead of the optimised form (box-sorted deterministic spread, fused
+ * gather + attraction + compression + update). */
+#define LTSNET_FLAG_PLAIN 1
+
+/* Largest supported k (partial BFS neighbours per vertex). */
+#define LTSNET_MAX_K 4096
+
+/* Defaults: perplexity 30, eps 1/20, P = 3, box_width_max 1, min_boxes 50,
+ * max_boxes 640, automatic learning rate, beta search 100 steps / 1e-5, the
+ * two-stage schedule of ltsnet_default_stages (1000 iterations). */
+ltsnet_params ltsnet_default_params(void);
+
+/* Writes the default schedule for `total_iters` iterations into `out` (host,
+ * room for 2) and returns the number of stages: 250 iterations of
+ * (lambda_KL, lambda_c, lambda_r) = (1, 1.2, 0) with momentum 0.5, then the
+ * rest with (1, 0.01, 0.6) and momentum 0.8. */
+int32_t ltsnet_default_stages(int32_t total_iters, ltsnet_stage* out);
+
+const char* ltsnet_status_string(ltsnet_status s);
+
+/* Host: text of the last CUDA runtime failure seen by this library on the
+ * calling thread (name, description and source location), "" if none.  The
+ * string is owned by the library and valid until the thread's next failure. */
+const char* ltsnet_last_cuda_error(void);
+
+/* Synchronous: waits for `stream`, returns the status word recorded in `ws`
+ * by earlier asynchronous calls and clears it. */
+ltsnet_status ltsnet_poll_status(void* ws, size_t ws_bytes, ltsnet_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * C0 step 1 -- partial BFS k-nearest neighbours (Sec. 3.1, "partial BFS";
+ * Alg. 3 preprocessing loop).  For every source s: breadth-first search in
+ * FIFO order over the adjacency lists in their stored order, a vertex counting
+ * as visited when first reached, stopping as soon as k vertices other than s
+ * are visited.  The paper breaks ties randomly; this library breaks them by
+ * that deterministic discovery order, so the output is a function of the CSR.
+ *   row_ptr int64[n+1], col int32[row_ptr[n]]       graph (device)
+ *   nbr  int32[n][k]   neighbours of s in discovery order, -1 padded
+ *   hop  uint16[n][k]  their hop distances (non-decreasing along a row), 0 pad
+ *   cnt  int32[n]      neighbours found, = min(k, |component(s)| - 1)
+ * 1 <= k <= LTSNET_MAX_K.  A column id outside [0, n) is skipped and recorded
+ * as LTSNET_ERR_BAD_GRAPH in the workspace status word.  ws >= 256 bytes.
+ * ------------------------------------------------------------------------- */
+ltsnet_status ltsnet_knn_bfs(const int64_t* row_ptr, const int32_t* col, int32_t n, int32_t k,
+                             int32_t* nbr, uint16_t* hop, int32_t* cnt,
+                             void* ws, size_t ws_bytes, ltsnet_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * C0 step 2 -- perplexity calibration (Eq. 3 and the definition of the
+ * perplexity u beneath it).  Per row i, with d_ij the hop distance:
+ *   p_{j|i} = exp(-beta_i d_ij^2) / sum_l exp(-beta_i d_il^2),
+ *   beta_i = 1/(2 sigma_i^2) chosen so that -sum_j p_{j|i} ln p_{j|i} = ln u.
+ * Search in FP64: beta = 1; raise it (double, or bisect once bracketed) while
+ * the entropy is above ln u, lower it (halve, or bisect) while below; stop at
+ * |H - ln u| < tol or after max_steps evaluations; p is evaluated at the final
+ * beta.
+ *   beta       f64[n]        converged u8[n] (1 iff the tolerance was met)
+ *   pcond      f64[n][k]     p_{j|i} aligned with nbr/hop, 0 beyond cnt
+ * Rows with no neighbours get beta = 1, converged = 0.
+ * ------------------------------------------------------------------------- */
+ltsnet_status ltsnet_calibrate(const uint16_t* hop, const int32_t* cnt, int32_t n, int32_t k,
+                               double perplexity, double tol, int32_t max_steps,
+                               double* beta, double* pcond, uint8_t* converged,
+                               ltsnet_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * C0 step 3 -- symmetrisation (Eq. 2): p_ij = (p_{j|i} + p_{i|j}) / (2n) over
+ * the union of the supports of the conditional rows, as CSR with every row's
+ * columns ascending.  The sum and the division are done in FP64 and rounded
+ * once to FP32.  Synchronous (returns nnz on the host).
+ *   P_row int64[n+1], P_col int32[cap], P_val f32[cap]; cap >= nnz, and
+ *   nnz <= ltsnet_symmetrize_max_nnz(n, k).  *nnz_out (host) gets nnz.
+ * Returns LTSNET_ERR_WORKSPACE if cap < nnz (P_row is still complete).
+ * ------------------------------------------------------------------------- */
+int64_t ltsnet_symmetrize_max_nnz(int32_t n, int32_t k);
+size_t ltsnet_symmetrize_workspace_size(int32_t n, int32_t k);
+ltsnet_status ltsnet_symmetrize(const int32_t* nbr, const int32_t* cnt, const double* pcond,
+                                int32_t n, int32_t k,
+                                int64_t* P_row, int32_t* P_col, float* P_val, int64_t cap,
+                                int64_t* nnz_out, void* ws, size_t ws_bytes, ltsnet_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * One gradient of the tsNET cost at Y (Alg. 3 loop body without the move):
+ *   dC/dX_i = 4 lambda_KL (alpha A_i - (S/Z) R_i) + (lambda_c/n) X_i
+ *             - (lambda_r/n^2) E_i
+ *   A_i = sum_{j in row i} p_ij (X_i - X_j)/(1 + d_ij^2)   sparse, exact (Eq. 6)
+ *   R_i = sum_j (X_i - X_j)/(1 + d_ij^2)^2                  interpolated (Sec. 2.3)
+ *   E_i = sum_j (X_i - X_j)/(eps + d_ij^2) = X_i h1 - (h2,h3) interpolated (Eq. 8)
+ *   Z   = sum_{i != j} 1/(1 + d_ij^2)                       from the grid, FP64
+ *   S   = sum of P_val (1 for a normalised P), alpha = stage exaggeration.
+ * The interpolation: lo/hi = min/max over all coordinates, I boxes per
+ * dimension by the grid rule of ltsnet_params, nodes_per_box Lagrange nodes
+ * per box, charges (1, x, y, x^2+y^2) in coordinates centred on the domain,
+ * kernels (1+d^2)^-2 and 1/(eps+d^2) convolved on the node grid by FFT.
+ *   grad  f32[n][2]       (device)
+ *   parts f32[n][6] or NULL: (A_i, R_i, E_i) unscaled, for per-term checks
+ *   terms f64[8] or NULL: Z, S, I, h, lo, centre, M, 0
+ * ------------------------------------------------------------------------- */
+size_t ltsnet_gradient_workspace_size(int32_t n, const ltsnet_params* p);
+ltsnet_status ltsnet_gradient(const int64_t* P_row, const int32_t* P_col, const float* P_val,
+                              int32_t n, const float* Y, const ltsnet_stage* stage,
+                              const ltsnet_params* p, float* grad, float* parts, double* terms,
+                              void* ws, size_t ws_bytes, ltsnet_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * The descent loop (Alg. 3, "for iterations": gradient, then move every
+ * vertex).  Runs iterations [start_iter, start_iter + n_iter) of the stage
+ * schedule in `p`, updating Y, update (the previous step) and gains in place:
+ *   gain <- gain + 0.2 where sign(g) != sign(update), else gain * 0.8;
+ *   gain >= 0.01; update <- momentum*update - lr*gain*g; Y <- Y + update.
+ * (The paper does not name its optimiser; this is the t-SNE optimiser of van
+ * der Maaten and Hinton, which its C++ code base derives from.)  Start with
+ * update = 0, gains = 1.  Resuming from start_iter > 0 with the saved
+ * (Y, update, gains) gives the same result as an uninterrupted run.
+ * ------------------------------------------------------------------------- */
+size_t ltsnet_optimize_workspace_size(int32_t n, const ltsnet_params* p);
+ltsnet_status ltsnet_optimize(const int64_t* P_row, const int32_t* P_col, const float* P_val,
+                              int32_t n, const ltsnet_params* p, float* Y, float* update,
+                              float* gains, int32_t start_iter, int32_t n_iter,
+                              void* ws, size_t ws_bytes, ltsnet_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Whole method (Alg. 3 without the Pivot-MDS initialisation): C0 on the graph,
+ * then every iteration of the schedule.  Y holds the initial layout on entry
+ * and the final layout on return.  Synchronous; returns the first error, or
+ * LTSNET_WARN_NOT_CONVERGED if some rows missed the perplexity target.
+ * ltsnet_run_host takes HOST pointers for the graph and Y and does the
+ * host<->device copies itself (through the workspace).
+ * ------------------------------------------------------------------------- */
+size_t ltsnet_run_workspace_size(int32_t n, int64_t nnz_graph, const ltsnet_params* p);
+ltsnet_status ltsnet_run(const int64_t* row_ptr, const int32_t* col, int32_t n,
+                         const ltsnet_params* p, float* Y, void* ws, size_t ws_bytes,
+                         ltsnet_stream stream);
+ltsnet_status ltsnet_run_host(const int64_t* row_ptr_host, const int32_t* col_host, int32_t n,
+                              const ltsnet_params* p, float* Y_host, void* ws, size_t ws_bytes,
+                              ltsnet_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Instrumentation (host side, not part of the method).
+ * ltsnet_launch_count: kernels this library has launched in this process.
+ * ltsnet_profile_*: times every launch of one kernel with CUDA events on the
+ * stream it runs on; `kernel` is one of the LTSNET_KERNEL_* ids.
+ * ------------------------------------------------------------------------- */
+#define LTSNET_KERNEL_FUSED_UPDATE 1 /* gather + attraction + compression + update */
+#define LTSNET_KERNEL_SPREAD 2
+#define LTSNET_KERNEL_CONV 3
+int64_t ltsnet_launch_count(void);
+ltsnet_status ltsnet_profile_begin(int32_t kernel, int32_t max_launches);
+ltsnet_status ltsnet_profile_end(int32_t kernel, double* total_ms, int32_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LTSNET_H */

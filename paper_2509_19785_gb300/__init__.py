@@ -1,0 +1,357 @@
+"""GB300 L-tsNET: Python binding of libltsnet.so (include/ltsnet.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch supplies device memory (including the workspaces the
+library asks for) and the current CUDA stream.  There is no CPU fallback: if
+the library is missing or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass, field
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libltsnet.so")
+
+OK = 0
+WARN_NOT_CONVERGED = 1
+FLAG_PLAIN = 1
+MAX_K = 4096
+KERNEL_FUSED_UPDATE, KERNEL_SPREAD, KERNEL_CONV = 1, 2, 3
+
+# Every entry point declared in include/ltsnet.h.
+ABI_SYMBOLS = (
+    "ltsnet_default_params", "ltsnet_default_stages", "ltsnet_status_string", "ltsnet_last_cuda_error",
+    "ltsnet_poll_status",
+    "ltsnet_knn_bfs", "ltsnet_calibrate", "ltsnet_symmetrize_max_nnz", "ltsnet_symmetrize_workspace_size",
+    "ltsnet_symmetrize", "ltsnet_gradient_workspace_size", "ltsnet_gradient", "ltsnet_optimize_workspace_size",
+    "ltsnet_optimize", "ltsnet_run_workspace_size", "ltsnet_run", "ltsnet_run_host", "ltsnet_launch_count",
+    "ltsnet_profile_begin", "ltsnet_profile_end",
+)
+
+
+class LtsnetError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = f"{what}: {status_string(code)} ({code})"
+        if code == -3:
+            msg += f": {lib().ltsnet_last_cuda_error().decode()}"
+        super().__init__(msg)
+
+
+class CStage(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("lambda_kl", ctypes.c_float), ("lambda_c", ctypes.c_float),
+                ("lambda_r", ctypes.c_float), ("exaggeration", ctypes.c_float), ("momentum", ctypes.c_float)]
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [("perplexity", ctypes.c_float), ("eps", ctypes.c_float), ("nodes_per_box", ctypes.c_int32),
+                ("box_width_max", ctypes.c_float), ("min_boxes", ctypes.c_int32), ("max_boxes", ctypes.c_int32),
+                ("learning_rate", ctypes.c_float), ("beta_max_steps", ctypes.c_int32), ("beta_tol", ctypes.c_double),
+                ("n_stages", ctypes.c_int32), ("stages", ctypes.POINTER(CStage)), ("flags", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libltsnet.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libltsnet.so not built at {LIB_PATH}; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i32, i64, f64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+        pp = ctypes.POINTER(CParams)
+        L.ltsnet_default_params.restype = CParams
+        L.ltsnet_default_stages.argtypes = [i32, ctypes.POINTER(CStage)]
+        L.ltsnet_default_stages.restype = i32
+        L.ltsnet_status_string.argtypes = [i32]
+        L.ltsnet_status_string.restype = ctypes.c_char_p
+        L.ltsnet_last_cuda_error.restype = ctypes.c_char_p
+        L.ltsnet_poll_status.argtypes = [P, sz, P]
+        L.ltsnet_knn_bfs.argtypes = [P, P, i32, i32, P, P, P, P, sz, P]
+        L.ltsnet_calibrate.argtypes = [P, P, i32, i32, f64, f64, i32, P, P, P, P]
+        L.ltsnet_symmetrize_max_nnz.argtypes = [i32, i32]
+        L.ltsnet_symmetrize_max_nnz.restype = i64
+        L.ltsnet_symmetrize_workspace_size.argtypes = [i32, i32]
+        L.ltsnet_symmetrize_workspace_size.restype = sz
+        L.ltsnet_symmetrize.argtypes = [P, P, P, i32, i32, P, P, P, i64, ctypes.POINTER(i64), P, sz, P]
+        L.ltsnet_gradient_workspace_size.argtypes = [i32, pp]
+        L.ltsnet_gradient_workspace_size.restype = sz
+        L.ltsnet_gradient.argtypes = [P, P, P, i32, P, ctypes.POINTER(CStage), pp, P, P, P, P, sz, P]
+        L.ltsnet_optimize_workspace_size.argtypes = [i32, pp]
+        L.ltsnet_optimize_workspace_size.restype = sz
+        L.ltsnet_optimize.argtypes = [P, P, P, i32, pp, P, P, P, i32, i32, P, sz, P]
+        L.ltsnet_run_workspace_size.argtypes = [i32, i64, pp]
+        L.ltsnet_run_workspace_size.restype = sz
+        L.ltsnet_run.argtypes = [P, P, i32, pp, P, P, sz, P]
+        L.ltsnet_run_host.argtypes = [P, P, i32, pp, P, P, sz, P]
+        L.ltsnet_launch_count.restype = i64
+        L.ltsnet_profile_begin.argtypes = [i32, i32]
+        L.ltsnet_profile_end.argtypes = [i32, ctypes.POINTER(f64), ctypes.POINTER(i32)]
+        for name in ("ltsnet_poll_status", "ltsnet_knn_bfs", "ltsnet_calibrate", "ltsnet_symmetrize",
+                     "ltsnet_gradient", "ltsnet_optimize", "ltsnet_run", "ltsnet_run_host",
+                     "ltsnet_profile_begin", "ltsnet_profile_end"):
+            getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().ltsnet_status_string(int(code)).decode()
+
+
+def _check(rc: int, what: str, allow_warn: bool = True) -> int:
+    if rc < 0 or (rc > 0 and not allow_warn):
+        raise LtsnetError(rc, what)
+    return rc
+
+
+# --------------------------------------------------------------------------
+# Parameters
+# --------------------------------------------------------------------------
+@dataclass
+class Stage:
+    """One descent stage: the multipliers of the three cost terms (Eq. 1),
+    exaggeration of P in the attraction, optimiser momentum."""
+    iters: int
+    lambda_kl: float = 1.0
+    lambda_c: float = 1.2
+    lambda_r: float = 0.0
+    exaggeration: float = 1.0
+    momentum: float = 0.5
+
+    def to_c(self) -> CStage:
+        return CStage(int(self.iters), self.lambda_kl, self.lambda_c, self.lambda_r, self.exaggeration, self.momentum)
+
+
+def default_stages(total_iters: int = 1000) -> list[Stage]:
+    buf = (CStage * 2)()
+    k = lib().ltsnet_default_stages(int(total_iters), buf)
+    return [Stage(b.iters, b.lambda_kl, b.lambda_c, b.lambda_r, b.exaggeration, b.momentum) for b in buf[:k]]
+
+
+@dataclass
+class Params:
+    perplexity: float = 30.0
+    eps: float = 1.0 / 20.0
+    nodes_per_box: int = 3
+    box_width_max: float = 1.0
+    min_boxes: int = 50
+    max_boxes: int = 640
+    learning_rate: float = 0.0
+    beta_max_steps: int = 100
+    beta_tol: float = 1e-5
+    stages: list = field(default_factory=lambda: None)
+    plain: bool = False
+
+    @property
+    def k(self) -> int:
+        return int(math.ceil(3.0 * self.perplexity - 1e-9))
+
+    def schedule(self) -> list[Stage]:
+        return self.stages if self.stages is not None else default_stages(1000)
+
+    def to_c(self):
+        st = self.schedule()
+        arr = (CStage * max(1, len(st)))(*[s.to_c() for s in st])
+        p = CParams(self.perplexity, self.eps, self.nodes_per_box, self.box_width_max, self.min_boxes,
+                    self.max_boxes, self.learning_rate, self.beta_max_steps, self.beta_tol, len(st),
+                    ctypes.cast(arr, ctypes.POINTER(CStage)), FLAG_PLAIN if self.plain else 0)
+        p._keep = arr  # keep the stage array alive with the struct
+        return p
+
+
+# --------------------------------------------------------------------------
+# torch plumbing
+# --------------------------------------------------------------------------
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA device is required (no CPU fallback)")
+    return torch
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _workspace(nbytes: int, device=None):
+    torch = _torch()
+    # torch's caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def _dev(t, dtype):
+    torch = _torch()
+    t = torch.as_tensor(t)
+    return t.to(device="cuda", dtype=dtype).contiguous()
+
+
+def knn_bfs(row_ptr, col, k: int):
+    """Partial BFS neighbours (Sec. 3.1).  Returns (nbr int32 [n,k], hop
+    uint16 [n,k], cnt int32 [n]) on the GPU."""
+    torch = _torch()
+    row_ptr = _dev(row_ptr, torch.int64)
+    col = _dev(col, torch.int32)
+    n = row_ptr.numel() - 1
+    nbr = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    hop = torch.empty((n, k), dtype=torch.uint16, device="cuda")
+    cnt = torch.empty((n,), dtype=torch.int32, device="cuda")
+    ws = _workspace(256)
+    ws.zero_()
+    _check(lib().ltsnet_knn_bfs(_ptr(row_ptr), _ptr(col), n, k, _ptr(nbr), _ptr(hop), _ptr(cnt), _ptr(ws),
+                                ws.numel(), _stream()), "ltsnet_knn_bfs")
+    _check(lib().ltsnet_poll_status(_ptr(ws), ws.numel(), _stream()), "ltsnet_knn_bfs (device)")
+    return nbr, hop, cnt
+
+
+def calibrate(hop, cnt, perplexity: float, tol: float = 1e-5, max_steps: int = 100):
+    """Beta search (Eq. 3).  Returns (beta f64 [n], pcond f64 [n,k],
+    converged uint8 [n])."""
+    torch = _torch()
+    n, k = hop.shape
+    beta = torch.empty((n,), dtype=torch.float64, device="cuda")
+    pcond = torch.empty((n, k), dtype=torch.float64, device="cuda")
+    conv = torch.empty((n,), dtype=torch.uint8, device="cuda")
+    _check(lib().ltsnet_calibrate(_ptr(hop), _ptr(cnt), n, k, float(perplexity), float(tol), int(max_steps),
+                                  _ptr(beta), _ptr(pcond), _ptr(conv), _stream()), "ltsnet_calibrate")
+    return beta, pcond, conv
+
+
+def symmetrize(nbr, cnt, pcond):
+    """Eq. 2.  Returns (P_row int64 [n+1], P_col int32 [nnz], P_val f32 [nnz])."""
+    torch = _torch()
+    n, k = nbr.shape
+    cap = int(lib().ltsnet_symmetrize_max_nnz(n, k))
+    P_row = torch.empty((n + 1,), dtype=torch.int64, device="cuda")
+    P_col = torch.empty((max(cap, 1),), dtype=torch.int32, device="cuda")
+    P_val = torch.empty((max(cap, 1),), dtype=torch.float32, device="cuda")
+    ws = _workspace(lib().ltsnet_symmetrize_workspace_size(n, k))
+    nnz = ctypes.c_int64(0)
+    _check(lib().ltsnet_symmetrize(_ptr(nbr), _ptr(cnt), _ptr(pcond), n, k, _ptr(P_row), _ptr(P_col), _ptr(P_val),
+                                   cap, ctypes.byref(nnz), _ptr(ws), ws.numel(), _stream()), "ltsnet_symmetrize")
+    m = nnz.value
+    return P_row, P_col[:m].clone(), P_val[:m].clone()
+
+
+def affinities(row_ptr, col, perplexity: float, tol: float = 1e-5, max_steps: int = 100):
+    """C0 of Alg. 3 on the GPU: partial BFS, calibration, symmetrisation."""
+    k = int(math.ceil(3.0 * perplexity - 1e-9))
+    nbr, hop, cnt = knn_bfs(row_ptr, col, k)
+    beta, pcond, conv = calibrate(hop, cnt, perplexity, tol, max_steps)
+    P = symmetrize(nbr, cnt, pcond)
+    return dict(nbr=nbr, hop=hop, cnt=cnt, beta=beta, pcond=pcond, converged=conv, P=P)
+
+
+def gradient(P, Y, stage: Stage, params: Params | None = None, parts: bool = False, ws=None):
+    """One gradient of the tsNET cost at Y.  Returns (grad [n,2] f32,
+    parts [n,6] f32 or None, terms [8] f64)."""
+    torch = _torch()
+    params = params or Params()
+    P_row, P_col, P_val = P
+    Y = Y.contiguous()
+    n = Y.shape[0]
+    cp = params.to_c()
+    grad = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+    pt = torch.empty((n, 6), dtype=torch.float32, device="cuda") if parts else None
+    terms = torch.empty((8,), dtype=torch.float64, device="cuda")
+    need = lib().ltsnet_gradient_workspace_size(n, ctypes.byref(cp))
+    if need == 0:
+        raise LtsnetError(-1, "ltsnet_gradient_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need)
+    st = stage.to_c()
+    _check(lib().ltsnet_gradient(_ptr(P_row), _ptr(P_col), _ptr(P_val), n, _ptr(Y), ctypes.byref(st),
+                                 ctypes.byref(cp), _ptr(grad), _ptr(pt), _ptr(terms), _ptr(ws), ws.numel(),
+                                 _stream()), "ltsnet_gradient")
+    _check(lib().ltsnet_poll_status(_ptr(ws), ws.numel(), _stream()), "ltsnet_gradient (device)")
+    return grad, pt, terms
+
+
+def optimize(P, Y, update, gains, start_iter: int, n_iter: int, params: Params | None = None, ws=None,
+             sync: bool = True):
+    """Runs iterations [start_iter, start_iter+n_iter) of the schedule in
+    place on (Y, update, gains)."""
+    params = params or Params()
+    P_row, P_col, P_val = P
+    n = Y.shape[0]
+    cp = params.to_c()
+    need = lib().ltsnet_optimize_workspace_size(n, ctypes.byref(cp))
+    if need == 0:
+        raise LtsnetError(-1, "ltsnet_optimize_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need)
+    _check(lib().ltsnet_optimize(_ptr(P_row), _ptr(P_col), _ptr(P_val), n, ctypes.byref(cp), _ptr(Y), _ptr(update),
+                                 _ptr(gains), int(start_iter), int(n_iter), _ptr(ws), ws.numel(), _stream()),
+           "ltsnet_optimize")
+    if sync:
+        _check(lib().ltsnet_poll_status(_ptr(ws), ws.numel(), _stream()), "ltsnet_optimize (device)")
+    return ws
+
+
+def run_workspace(n: int, nnz_graph: int, params: Params):
+    cp = params.to_c()
+    need = lib().ltsnet_run_workspace_size(n, nnz_graph, ctypes.byref(cp))
+    if need == 0:
+        raise LtsnetError(-1, "ltsnet_run_workspace_size")
+    return _workspace(need)
+
+
+def run(row_ptr, col, Y0, params: Params | None = None, ws=None):
+    """Alg. 3 (without Pivot-MDS): C0 then the whole schedule.  Y0 is a
+    [n,2] float32 CUDA tensor; returns the final layout (a new tensor)."""
+    torch = _torch()
+    params = params or Params()
+    row_ptr = _dev(row_ptr, torch.int64)
+    col = _dev(col, torch.int32)
+    Y = Y0.to(device="cuda", dtype=torch.float32).contiguous().clone()
+    n = Y.shape[0]
+    cp = params.to_c()
+    if ws is None:
+        ws = run_workspace(n, col.numel(), params)
+    rc = lib().ltsnet_run(_ptr(row_ptr), _ptr(col), n, ctypes.byref(cp), _ptr(Y), _ptr(ws), ws.numel(), _stream())
+    _check(rc, "ltsnet_run")
+    return Y, rc
+
+
+def run_host(row_ptr, col, Y, params: Params | None = None, ws=None):
+    """Same as run() with HOST numpy arrays (the library copies them in and the
+    layout back); Y (float32 [n,2], C-contiguous) is updated in place."""
+    import numpy as np
+    params = params or Params()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    assert Y.dtype == np.float32 and Y.flags["C_CONTIGUOUS"]
+    n = Y.shape[0]
+    cp = params.to_c()
+    if ws is None:
+        ws = run_workspace(n, col.size, params)
+    rc = lib().ltsnet_run_host(row_ptr.ctypes.data_as(ctypes.c_void_p), col.ctypes.data_as(ctypes.c_void_p), n,
+                               ctypes.byref(cp), Y.ctypes.data_as(ctypes.c_void_p), _ptr(ws), ws.numel(), _stream())
+    _check(rc, "ltsnet_run_host")
+    return Y, rc
+
+
+def launch_count() -> int:
+    return int(lib().ltsnet_launch_count())
+
+
+def profile_begin(kernel: int, max_launches: int):
+    _check(lib().ltsnet_profile_begin(kernel, max_launches), "ltsnet_profile_begin")
+
+
+def profile_end(kernel: int):
+    ms = ctypes.c_double(0)
+    cnt = ctypes.c_int32(0)
+    _check(lib().ltsnet_profile_end(kernel, ctypes.byref(ms), ctypes.byref(cnt)), "ltsnet_profile_end")
+    return ms.value, cnt.value

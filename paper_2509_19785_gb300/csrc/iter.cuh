@@ -1,0 +1,129 @@
+// Internal: per-iteration device state of the interpolation grid and the
+// launch helpers shared by grid.cu (spread, FFT convolution, Z) and
+// iterate.cu (fused gather + attraction + compression + update).
+#pragma once
+#include "common.cuh"
+
+namespace lt {
+
+constexpr int kLMax = 4096;     // longest FFT line (L = 2 * P * I)
+constexpr int kMaxRadix = 16;   // FFT stages
+constexpr int kTileNodes = 48;  // spread tile edge in nodes (tile = 48/P boxes)
+constexpr int kFieldStride = 8; // floats per grid node in the field array
+
+// Written by k_setup every iteration from the layout bounds.  All integer
+// decisions (I, box) are FP32 and match the oracle's grid rule bit for bit.
+struct GridDev {
+    float lo, hi, ext, h, s, c;  // domain [lo, lo+ext], box width h, node spacing s, centre c
+    int32_t I, M, L;             // boxes per dim, nodes per dim (I*P), FFT length (2M)
+    int32_t P;                   // nodes per box
+    int32_t tb, tiles;           // boxes per spread tile edge, tiles per dim
+    int32_t nst;                 // FFT stages
+    int32_t radix[kMaxRadix];
+    double fx[4], ifx[4];        // fixed-point scale per charge and its inverse (powers of 2)
+    double Z;                    // sum_{i != j} 1/(1+d^2), from the grid
+    double S;                    // sum of P values
+    int32_t nitems;              // spread work items
+    int32_t ticket;              // last-block counter for the Z reduction
+};
+
+struct Stage {
+    float lambda_kl, lambda_c, lambda_r, exaggeration, momentum, lr;
+};
+
+// Device buffers of one gradient/optimize call, carved from the workspace.
+struct IterWs {
+    StatusBlock* st;
+    GridDev* g;
+    int32_t* bounds;     // [2 parities][2] ordered ints (min, max)
+    float2* tw;          // twiddles e^{-2 pi i t/L}, kLMax
+    int32_t* tile_cnt;   // tiles_max^2
+    int32_t* tile_off;   // tiles_max^2 + 1
+    int32_t* tile_cur;   // tiles_max^2
+    int4* items;         // spread work items (tile, begin, end, 0)
+    float2* binned;      // n points, binned by tile
+    long long* wfix;     // M_max^2 * 4 fixed-point charges
+    float4* wflt;        // M_max^2 float charges (plain form)
+    float2* krow;        // 3 * L_max * H kernel row transforms (H = L_max/2 + 1)
+    float* khat;         // 5 * L_max * H kernel spectra (K2, Ke, K1, Im K2dx, Im Kedx)
+    float2* srow;        // 4 * M_max * H row half spectra of S0, S1x, S1y, S2
+    float2* ucol;        // 6 * M_max * H column results
+    float* fields;       // M_max^2 * 8
+    double* zblk;        // per-block Z partials
+    double* sblk;        // per-block sum(P) partials
+    float2* yalt;        // n, ping-pong layout
+    float* phi;          // n * 8 (plain form gather output)
+    float2* attr;        // n (plain form attraction output)
+};
+
+struct IterShape {
+    int32_t n;
+    int32_t P;
+    int32_t max_boxes;
+    int32_t Mmax, Lmax, tiles_max;
+    int64_t items_max;
+};
+
+IterShape iter_shape(int32_t n, const ltsnet_params* p);
+IterWs iter_carve(Carve& c, const IterShape& sh);
+
+// Box of coordinate x (FP32, the same operations as the oracle's grid rule).
+__device__ __forceinline__ int box_of(float x, float lo, float h, int I)
+{
+    int b = (int)floorf(__fdiv_rn(__fsub_rn(x, lo), h));
+    return b < 0 ? 0 : (b > I - 1 ? I - 1 : b);
+}
+
+// Lagrange weights at local coordinate u (in node spacings from the box's
+// lower edge) for the P nodes of a box at u_a = a + 1/2.
+template <int P>
+__device__ __forceinline__ void lagrange(float u, float* w)
+{
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+        float num = 1.0f, den = 1.0f;
+#pragma unroll
+        for (int b = 0; b < P; ++b) {
+            if (b == a) continue;
+            num *= u - ((float)b + 0.5f);
+            den *= (float)(a - b);
+        }
+        w[a] = num / den;
+    }
+}
+
+// (x - lo) / s - base to FP32 accuracy of the result itself, although
+// (x - lo) / s can be in the thousands: x - lo is split exactly into
+// d_hi + d_lo (TwoSum), the quotient's remainder d_hi - q s is exact (FMA),
+// and q - base is exact (Sterbenz: base <= q <= 2 base, or base = 0).
+__device__ __forceinline__ float local_u(float x, float lo, float s, int base)
+{
+    const float d_hi = __fsub_rn(x, lo);
+    const float bb = __fsub_rn(d_hi, x);
+    const float d_lo = __fadd_rn(__fsub_rn(x, __fsub_rn(d_hi, bb)), __fsub_rn(-lo, bb));
+    const float q = __fdiv_rn(d_hi, s);
+    const float r = __fmaf_rn(-q, s, d_hi);
+    const float t_lo = __fdiv_rn(__fadd_rn(r, d_lo), s);
+    return __fadd_rn(__fsub_rn(q, (float)base), t_lo);
+}
+
+// Box of a point and its local coordinates inside the box, in node spacings
+// (u in [0, P]; the box's nodes sit at u = a + 1/2).
+__device__ __forceinline__ void local_coords(float2 p, const GridDev* G, int& bx, int& by, float& ux, float& uy)
+{
+    const float lo = G->lo, h = G->h, s = G->s;
+    const int I = G->I, P = G->P;
+    bx = box_of(p.x, lo, h, I);
+    by = box_of(p.y, lo, h, I);
+    ux = local_u(p.x, lo, s, P * bx);
+    uy = local_u(p.y, lo, s, P * by);
+}
+
+// grid.cu
+cudaError_t launch_bounds_init(const IterWs& w, const float2* Y, int32_t n, int parity, cudaStream_t s);
+cudaError_t launch_psum(const IterWs& w, const int64_t* P_row, int32_t n, const float* P_val, cudaStream_t s);
+cudaError_t grid_set_smem_attrs(const IterShape& sh);
+cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet_params* p, const float2* Y,
+                              int parity, bool plain, cudaStream_t s);
+
+}  // namespace lt

@@ -1,0 +1,701 @@
+// The per-iteration gradient and the descent loop (Alg. 3 loop body).
+//
+// k_fused (optimised form): one warp per 32 consecutive vertices.
+//   Attraction (Eq. 6, first term): the warp walks the 32 CSR rows in turn,
+//   each lane reading 4 consecutive (col, p) entries with 16-byte loads, and
+//   the row sum is reduced across the warp and handed to the row's lane.
+//   Then every lane, for its own vertex: gathers the interpolated repulsion
+//   sum R_i (Sec. 2.3) and entropy sum E_i (Eq. 8, repulsive reading) from
+//   the P x P nodes of its box, adds the compression (lambda_c/n) X_i
+//   (Eq. 1), assembles the gradient and applies the momentum/gain step,
+//   writing the new layout to the other ping-pong buffer and folding it into
+//   the bounds of the next grid.
+// Plain form: the same arithmetic split into a gather kernel, an attraction
+// kernel and an update kernel with intermediates in global memory.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "iter.cuh"
+#include "prims.cuh"
+
+namespace lt {
+namespace {
+
+struct Coeffs {
+    float a_att;   // 4 lambda_KL alpha
+    float a_rep;   // 4 lambda_KL S / Z
+    float a_cmp;   // lambda_c / n
+    float a_ent;   // lambda_r / n^2
+};
+
+__device__ __forceinline__ Coeffs coeffs(const GridDev* G, const Stage& st, int32_t n)
+{
+    Coeffs k;
+    k.a_att = 4.0f * st.lambda_kl * st.exaggeration;
+    k.a_rep = (float)(4.0 * (double)st.lambda_kl * G->S / G->Z);
+    k.a_cmp = (float)((double)st.lambda_c / (double)n);
+    k.a_ent = (float)((double)st.lambda_r / ((double)n * (double)n));
+    return k;
+}
+
+// Sum over CSR row [s0, e0) of p_ij (X_i - X_j) / (1 + |X_i - X_j|^2) by one
+// warp: lane l handles entries eb + 4l .. eb + 4l + 3 for eb from s0 rounded
+// down to a multiple of 4, so the int4/float4 loads are aligned.
+__device__ __forceinline__ float2 warp_row_attraction(const int32_t* __restrict__ P_col,
+                                                      const float* __restrict__ P_val, int64_t nnz, int64_t s0,
+                                                      int64_t e0, float xi, float yi, const float2* __restrict__ Y,
+                                                      int32_t n, int lane, StatusBlock* status)
+{
+    float ax = 0.f, ay = 0.f;
+    for (int64_t eb = s0 & ~(int64_t)3; eb < e0; eb += 128) {
+        const int64_t e = eb + 4 * lane;
+        if (e < e0) {
+            int cj[4];
+            float pv[4];
+            if (e + 3 < nnz) {
+                const int4 c4 = __ldg((const int4*)(P_col + e));
+                const float4 v4 = __ldg((const float4*)(P_val + e));
+                cj[0] = c4.x; cj[1] = c4.y; cj[2] = c4.z; cj[3] = c4.w;
+                pv[0] = v4.x; pv[1] = v4.y; pv[2] = v4.z; pv[3] = v4.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    cj[q] = (e + q < nnz) ? P_col[e + q] : 0;
+                    pv[q] = (e + q < nnz) ? P_val[e + q] : 0.f;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t idx = e + q;
+                if (idx >= s0 && idx < e0) {
+                    if ((unsigned)cj[q] >= (unsigned)n) {
+                        record_error(status, LTSNET_ERR_BAD_GRAPH, cj[q]);
+                        continue;
+                    }
+                    const float2 yj = __ldg(Y + cj[q]);
+                    const float dx = xi - yj.x, dy = yi - yj.y;
+                    const float w = pv[q] / (1.0f + dx * dx + dy * dy);
+                    ax += w * dx;
+                    ay += w * dy;
+                }
+            }
+        }
+    }
+    return make_float2(warp_sum(ax), warp_sum(ay));
+}
+
+// Interpolated repulsion and entropy sums of one point (node-local form):
+//   R = s sum_ab L_a L_b [e . F0 + V],  E = s sum_ab L_a L_b [e . Fe0 + Ve]
+// with e the point's offset from node (a, b) in node spacings.
+struct Sums {
+    float2 R, E;
+};
+
+template <int P>
+__device__ __forceinline__ Sums gather_sums(float2 p, const GridDev* G, const float* __restrict__ fields)
+{
+    const int M = G->M;
+    int bx, by;
+    float ux, uy;
+    local_coords(p, G, bx, by, ux, uy);
+    float wx[P], wy[P];
+    lagrange<P>(ux, wx);
+    lagrange<P>(uy, wy);
+    float rx = 0.f, ry = 0.f, ex = 0.f, ey = 0.f;
+#pragma unroll
+    for (int b = 0; b < P; ++b)
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            const float w = wx[a] * wy[b];
+            const float dx = ux - ((float)a + 0.5f), dy = uy - ((float)b + 0.5f);
+            const float4* nd = (const float4*)(fields + ((int64_t)(P * by + b) * M + (P * bx + a)) * kFieldStride);
+            const float4 u = __ldg(nd), v = __ldg(nd + 1);  // (F0, Vx, Vy, Fe0), (Vex, Vey, -, -)
+            rx += w * (dx * u.x + u.y);
+            ry += w * (dy * u.x + u.z);
+            ex += w * (dx * u.w + v.x);
+            ey += w * (dy * u.w + v.y);
+        }
+    const float s = G->s;
+    Sums r;
+    r.R = make_float2(s * rx, s * ry);
+    r.E = make_float2(s * ex, s * ey);
+    return r;
+}
+
+__device__ __forceinline__ float sgn(float v) { return (float)((v > 0.f) - (v < 0.f)); }
+
+// Gradient of vertex i and (optionally) its momentum/gain step.
+struct PointOut {
+    float2 g, A, R, E;
+};
+
+__device__ __forceinline__ PointOut point_gradient(float2 p, float2 A, const Sums& F, const Coeffs& k)
+{
+    PointOut o;
+    o.A = A;
+    o.R = F.R;
+    o.E = F.E;
+    o.g.x = k.a_att * A.x - k.a_rep * o.R.x + k.a_cmp * p.x - k.a_ent * o.E.x;
+    o.g.y = k.a_att * A.y - k.a_rep * o.R.y + k.a_cmp * p.y - k.a_ent * o.E.y;
+    return o;
+}
+
+__device__ __forceinline__ float2 step(float2 p, float2 g, float2& u, float2& gn, const Stage& st)
+{
+    gn.x = (sgn(g.x) != sgn(u.x)) ? gn.x + 0.2f : gn.x * 0.8f;
+    gn.y = (sgn(g.y) != sgn(u.y)) ? gn.y + 0.2f : gn.y * 0.8f;
+    gn.x = fmaxf(gn.x, 0.01f);
+    gn.y = fmaxf(gn.y, 0.01f);
+    u.x = st.momentum * u.x - st.lr * gn.x * g.x;
+    u.y = st.momentum * u.y - st.lr * gn.y * g.y;
+    return make_float2(p.x + u.x, p.y + u.y);
+}
+
+__device__ __forceinline__ void block_bounds(float mn, float mx, int32_t* bounds_next)
+{
+    __shared__ float smn[32], smx[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(FULL, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        smn[w] = mn;
+        smx[w] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+            mn = fminf(mn, smn[i]);
+            mx = fmaxf(mx, smx[i]);
+        }
+        if (mn <= mx) {
+            atomicMin(&bounds_next[0], f2ord(mn));
+            atomicMax(&bounds_next[1], f2ord(mx));
+        }
+    }
+}
+
+constexpr int kFusedThreads = 256;
+
+template <int P, bool UPDATE>
+__global__ void __launch_bounds__(kFusedThreads)
+    k_fused(const int64_t* __restrict__ P_row, const int32_t* __restrict__ P_col, const float* __restrict__ P_val,
+            int32_t n, const float2* __restrict__ Y, float2* __restrict__ Ynew, float2* __restrict__ upd,
+            float2* __restrict__ gains, const GridDev* __restrict__ G, const float* __restrict__ fields, Stage st,
+            int32_t* __restrict__ bounds_next, float2* __restrict__ grad_out, float* __restrict__ parts,
+            StatusBlock* status)
+{
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int64_t nnz = P_row[n];
+    const Coeffs k = coeffs(G, st, n);
+    float mn = INFINITY, mx = -INFINITY;
+    for (int64_t g0 = ((int64_t)blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; g0 < n;
+         g0 += (int64_t)gridDim.x * wpb * 32) {
+        const int64_t row = g0 + lane;
+        const bool has = row < n;
+        const float2 yi = has ? Y[row] : make_float2(0.f, 0.f);
+        const int64_t rs = has ? P_row[row] : 0;
+        const int64_t re = has ? P_row[row + 1] : 0;
+        const int nrows = (int)min((int64_t)32, (int64_t)n - g0);
+        float2 A = make_float2(0.f, 0.f);
+        for (int rr = 0; rr < nrows; ++rr) {
+            const int64_t s0 = __shfl_sync(FULL, rs, rr), e0 = __shfl_sync(FULL, re, rr);
+            const float xi = __shfl_sync(FULL, yi.x, rr), yv = __shfl_sync(FULL, yi.y, rr);
+            const float2 a = warp_row_attraction(P_col, P_val, nnz, s0, e0, xi, yv, Y, n, lane, status);
+            if (lane == rr) A = a;
+        }
+        if (has) {
+            const Sums F = gather_sums<P>(yi, G, fields);
+            const PointOut o = point_gradient(yi, A, F, k);
+            if (UPDATE) {
+                float2 u = upd[row], gn = gains[row];
+                const float2 yn = step(yi, o.g, u, gn, st);
+                upd[row] = u;
+                gains[row] = gn;
+                Ynew[row] = yn;
+                if (!(isfinite(yn.x) && isfinite(yn.y))) record_error(status, LTSNET_ERR_NONFINITE, (int32_t)row);
+                mn = fminf(mn, fminf(yn.x, yn.y));
+                mx = fmaxf(mx, fmaxf(yn.x, yn.y));
+            } else {
+                grad_out[row] = o.g;
+                if (!(isfinite(o.g.x) && isfinite(o.g.y))) record_error(status, LTSNET_ERR_NONFINITE, (int32_t)row);
+                if (parts) {
+                    float* q = parts + row * 6;
+                    q[0] = o.A.x; q[1] = o.A.y; q[2] = o.R.x; q[3] = o.R.y; q[4] = o.E.x; q[5] = o.E.y;
+                }
+            }
+        }
+    }
+    if (UPDATE) block_bounds(mn, mx, bounds_next);
+}
+
+// ---- plain form ------------------------------------------------------------
+template <int P>
+__global__ void k_plain_gather(const float2* __restrict__ Y, int32_t n, const GridDev* __restrict__ G,
+                               const float* __restrict__ fields, float* __restrict__ phi)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const Sums F = gather_sums<P>(Y[i], G, fields);
+        *(float4*)(phi + i * 8) = make_float4(F.R.x, F.R.y, F.E.x, F.E.y);
+    }
+}
+
+__global__ void k_plain_attract(const int64_t* __restrict__ P_row, const int32_t* __restrict__ P_col,
+                                const float* __restrict__ P_val, int32_t n, const float2* __restrict__ Y,
+                                float2* __restrict__ attr, StatusBlock* status)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nnz = P_row[n];
+    for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < n;
+         row += (int64_t)gridDim.x * (blockDim.x >> 5)) {
+        const float2 yi = Y[row];
+        const float2 a =
+            warp_row_attraction(P_col, P_val, nnz, P_row[row], P_row[row + 1], yi.x, yi.y, Y, n, lane, status);
+        if (lane == 0) attr[row] = a;
+    }
+}
+
+template <bool UPDATE>
+__global__ void k_plain_update(int32_t n, const float2* __restrict__ Y, float2* __restrict__ Ynew,
+                               float2* __restrict__ upd, float2* __restrict__ gains, const GridDev* __restrict__ G,
+                               const float* __restrict__ phi, const float2* __restrict__ attr, Stage st,
+                               int32_t* __restrict__ bounds_next, float2* __restrict__ grad_out,
+                               float* __restrict__ parts, StatusBlock* status)
+{
+    const Coeffs k = coeffs(G, st, n);
+    float mn = INFINITY, mx = -INFINITY;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 p = Y[i];
+        Sums F;
+        const float4 a = *(const float4*)(phi + i * 8);
+        F.R = make_float2(a.x, a.y);
+        F.E = make_float2(a.z, a.w);
+        const PointOut o = point_gradient(p, attr[i], F, k);
+        if (UPDATE) {
+            float2 u = upd[i], gn = gains[i];
+            const float2 yn = step(p, o.g, u, gn, st);
+            upd[i] = u;
+            gains[i] = gn;
+            Ynew[i] = yn;
+            if (!(isfinite(yn.x) && isfinite(yn.y))) record_error(status, LTSNET_ERR_NONFINITE, (int32_t)i);
+            mn = fminf(mn, fminf(yn.x, yn.y));
+            mx = fmaxf(mx, fmaxf(yn.x, yn.y));
+        } else {
+            grad_out[i] = o.g;
+            if (!(isfinite(o.g.x) && isfinite(o.g.y))) record_error(status, LTSNET_ERR_NONFINITE, (int32_t)i);
+            if (parts) {
+                float* q = parts + i * 6;
+                q[0] = o.A.x; q[1] = o.A.y; q[2] = o.R.x; q[3] = o.R.y; q[4] = o.E.x; q[5] = o.E.y;
+            }
+        }
+    }
+    if (UPDATE) block_bounds(mn, mx, bounds_next);
+}
+
+__global__ void k_terms(const GridDev* __restrict__ G, double* __restrict__ terms)
+{
+    terms[0] = G->Z;
+    terms[1] = G->S;
+    terms[2] = (double)G->I;
+    terms[3] = (double)G->h;
+    terms[4] = (double)G->lo;
+    terms[5] = (double)G->c;
+    terms[6] = (double)G->M;
+    terms[7] = 0.0;
+}
+
+__global__ void k_init_state(float2* __restrict__ upd, float2* __restrict__ gains, int32_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        upd[i] = make_float2(0.f, 0.f);
+        gains[i] = make_float2(1.f, 1.f);
+    }
+}
+
+__global__ void k_count_unconverged(const uint8_t* __restrict__ conv, const int32_t* __restrict__ cnt, int32_t n,
+                                    StatusBlock* st)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!conv[i] && cnt[i] > 0) atomicOr(&st->warn, 1);
+}
+
+int fused_blocks(int32_t n)
+{
+    const int64_t groups = ((int64_t)n + 31) / 32;
+    const int64_t wpb = kFusedThreads / 32;
+    int64_t b = (groups + wpb - 1) / wpb;
+    const int64_t cap = (int64_t)kSMs * 8;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+int flat_blocks(int64_t n, int per_sm = 8)
+{
+    int64_t b = (n + 255) / 256;
+    const int64_t cap = (int64_t)kSMs * per_sm;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <bool UPDATE>
+cudaError_t launch_point_phase(const int64_t* P_row, const int32_t* P_col, const float* P_val, int32_t n,
+                               const float2* Y, float2* Ynew, float2* upd, float2* gains, const IterWs& w,
+                               const IterShape& sh, const Stage& st, int parity, float2* grad, float* parts,
+                               bool plain, cudaStream_t s)
+{
+    int32_t* bn = w.bounds + 2 * (parity ^ 1);
+    profile_start(LTSNET_KERNEL_FUSED_UPDATE, s);
+    if (!plain) {
+        const int nb = fused_blocks(n);
+#define LT_FUSED(PP)                                                                                          \
+    k_fused<PP, UPDATE><<<nb, kFusedThreads, 0, s>>>(P_row, P_col, P_val, n, Y, Ynew, upd, gains, w.g, w.fields, \
+                                                     st, bn, grad, parts, w.st)
+        switch (sh.P) {
+            case 2: LT_FUSED(2); break;
+            case 3: LT_FUSED(3); break;
+            case 4: LT_FUSED(4); break;
+            default: LT_FUSED(5); break;
+        }
+#undef LT_FUSED
+        count_launches(1);
+    } else {
+        const int nb = flat_blocks(n);
+        switch (sh.P) {
+            case 2: k_plain_gather<2><<<nb, 256, 0, s>>>(Y, n, w.g, w.fields, w.phi); break;
+            case 3: k_plain_gather<3><<<nb, 256, 0, s>>>(Y, n, w.g, w.fields, w.phi); break;
+            case 4: k_plain_gather<4><<<nb, 256, 0, s>>>(Y, n, w.g, w.fields, w.phi); break;
+            default: k_plain_gather<5><<<nb, 256, 0, s>>>(Y, n, w.g, w.fields, w.phi); break;
+        }
+        int64_t ab = ((int64_t)n + 7) / 8;
+        if (ab > kSMs * 16) ab = kSMs * 16;
+        if (ab < 1) ab = 1;
+        k_plain_attract<<<(unsigned)ab, 256, 0, s>>>(P_row, P_col, P_val, n, Y, w.attr, w.st);
+        k_plain_update<UPDATE><<<nb, 256, 0, s>>>(n, Y, Ynew, upd, gains, w.g, w.phi, w.attr, st, bn, grad, parts,
+                                                  w.st);
+        count_launches(3);
+    }
+    profile_stop(LTSNET_KERNEL_FUSED_UPDATE, s);
+    return cudaGetLastError();
+}
+
+bool params_ok(const ltsnet_params* p)
+{
+    if (!p) return false;
+    if (!(p->perplexity > 0.f) || !(p->eps > 0.f) || !(p->box_width_max > 0.f)) return false;
+    if (p->nodes_per_box < 2 || p->nodes_per_box > 5) return false;
+    if (p->min_boxes < 1 || p->max_boxes < p->min_boxes) return false;
+    if ((int64_t)2 * p->nodes_per_box * p->max_boxes > kLMax) return false;
+    if (p->n_stages < 1 || !p->stages) return false;
+    for (int i = 0; i < p->n_stages; ++i)
+        if (p->stages[i].iters < 0) return false;
+    return true;
+}
+
+Stage make_stage(const ltsnet_stage& s, float lr)
+{
+    Stage st;
+    st.lambda_kl = s.lambda_kl;
+    st.lambda_c = s.lambda_c;
+    st.lambda_r = s.lambda_r;
+    st.exaggeration = s.exaggeration;
+    st.momentum = s.momentum;
+    st.lr = lr;
+    return st;
+}
+
+float learning_rate(const ltsnet_params* p, int32_t n)
+{
+    if (p->learning_rate > 0.f) return p->learning_rate;
+    const float a = (float)n / 12.0f;
+    return a > 200.f ? a : 200.f;
+}
+
+// Stage of global iteration t: walk the schedule; past its end, the last stage.
+const ltsnet_stage& stage_at(const ltsnet_params* p, int64_t t)
+{
+    int64_t acc = 0;
+    for (int i = 0; i < p->n_stages; ++i) {
+        acc += p->stages[i].iters;
+        if (t < acc) return p->stages[i];
+    }
+    return p->stages[p->n_stages - 1];
+}
+
+int64_t schedule_length(const ltsnet_params* p)
+{
+    int64_t acc = 0;
+    for (int i = 0; i < p->n_stages; ++i) acc += p->stages[i].iters;
+    return acc;
+}
+
+size_t iter_ws_bytes(int32_t n, const ltsnet_params* p)
+{
+    Carve c(nullptr, 0);
+    iter_carve(c, iter_shape(n, p));
+    return align_up(c.off, 256);
+}
+
+cudaError_t ensure_attrs(const IterShape& sh)
+{
+    static int done_lmax = -1;
+    if (sh.Lmax <= done_lmax) return cudaSuccess;
+    // Attributes for the largest shape seen so far cover every smaller one.
+    cudaError_t e = grid_set_smem_attrs(sh);
+    if (e == cudaSuccess) done_lmax = sh.Lmax;
+    return e;
+}
+
+ltsnet_status read_status(StatusBlock* st, cudaStream_t s)
+{
+    StatusBlock h;
+    LT_CUDA(cudaMemcpyAsync(&h, st, sizeof(StatusBlock), cudaMemcpyDeviceToHost, s));
+    LT_CUDA(cudaStreamSynchronize(s));
+    if (h.code != 0) return (ltsnet_status)h.code;
+    if (h.warn & 1) return LTSNET_WARN_NOT_CONVERGED;
+    return LTSNET_OK;
+}
+
+// The loop over iterations [t0, t0 + niter) on a carved iteration workspace.
+ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const float* P_val, int32_t n,
+                            const ltsnet_params* p, float2* Y, float2* upd, float2* gains, int32_t t0, int32_t niter,
+                            const IterWs& w, const IterShape& sh, cudaStream_t s)
+{
+    const bool plain = (p->flags & LTSNET_FLAG_PLAIN) != 0;
+    const float lr = learning_rate(p, n);
+    LT_CUDA(ensure_attrs(sh));
+    LT_CUDA(launch_psum(w, P_row, n, P_val, s));
+    LT_CUDA(launch_bounds_init(w, Y, n, 0, s));
+    float2* cur = Y;
+    float2* nxt = w.yalt;
+    for (int32_t i = 0; i < niter; ++i) {
+        const int parity = i & 1;
+        const Stage st = make_stage(stage_at(p, (int64_t)t0 + i), lr);
+        LT_CUDA(launch_grid_phase(w, sh, p, cur, parity, plain, s));
+        LT_CUDA(launch_point_phase<true>(P_row, P_col, P_val, n, cur, nxt, upd, gains, w, sh, st, parity, nullptr,
+                                         nullptr, plain, s));
+        float2* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    if (cur != Y) LT_CUDA(cudaMemcpyAsync(Y, cur, sizeof(float2) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    return LTSNET_OK;
+}
+
+struct RunWs {
+    StatusBlock* st;
+    int32_t* nbr;
+    uint16_t* hop;
+    int32_t* cnt;
+    double* beta;
+    double* pcond;
+    uint8_t* conv;
+    int64_t* P_row;
+    int32_t* P_col;
+    float* P_val;
+    float2* upd;
+    float2* gains;
+    int64_t* row_ptr;  // host-input copies (ltsnet_run_host)
+    int32_t* col;
+    float2* Y;
+    void* sym;
+    size_t sym_bytes;
+    void* iter;
+    size_t iter_bytes;
+};
+
+int32_t k_of(const ltsnet_params* p) { return (int32_t)ceil(3.0 * (double)p->perplexity - 1e-9); }
+
+RunWs run_carve(Carve& c, int32_t n, int64_t m2, const ltsnet_params* p, bool host_inputs)
+{
+    RunWs r;
+    const int32_t k = k_of(p);
+    const int64_t nk = (int64_t)n * k;
+    r.st = c.take<StatusBlock>(1);
+    r.nbr = c.take<int32_t>(nk);
+    r.hop = c.take<uint16_t>(nk);
+    r.cnt = c.take<int32_t>(n);
+    r.beta = c.take<double>(n);
+    r.pcond = c.take<double>(nk);
+    r.conv = c.take<uint8_t>(n);
+    r.P_row = c.take<int64_t>((int64_t)n + 1);
+    r.P_col = c.take<int32_t>(2 * nk);
+    r.P_val = c.take<float>(2 * nk);
+    r.upd = c.take<float2>(n);
+    r.gains = c.take<float2>(n);
+    r.row_ptr = host_inputs ? c.take<int64_t>((int64_t)n + 1) : nullptr;
+    r.col = host_inputs ? c.take<int32_t>(m2) : nullptr;
+    r.Y = host_inputs ? c.take<float2>(n) : nullptr;
+    r.sym_bytes = ltsnet_symmetrize_workspace_size(n, k);
+    r.sym = c.take<char>(r.sym_bytes);
+    r.iter_bytes = iter_ws_bytes(n, p);
+    r.iter = c.take<char>(r.iter_bytes);
+    return r;
+}
+
+ltsnet_status run_core(const int64_t* row_ptr, const int32_t* col, int32_t n, const ltsnet_params* p, float2* Y,
+                       const RunWs& r, cudaStream_t s)
+{
+    const int32_t k = k_of(p);
+    ltsnet_status rc = ltsnet_knn_bfs(row_ptr, col, n, k, r.nbr, r.hop, r.cnt, r.st, sizeof(StatusBlock), s);
+    if (rc != LTSNET_OK) return rc;
+    rc = ltsnet_calibrate(r.hop, r.cnt, n, k, p->perplexity, p->beta_tol, p->beta_max_steps, r.beta, r.pcond, r.conv,
+                          s);
+    if (rc != LTSNET_OK) return rc;
+    k_count_unconverged<<<flat_blocks(n), 256, 0, s>>>(r.conv, r.cnt, n, r.st);
+    count_launches(1);
+    LT_CHECK_LAUNCH();
+    int64_t nnz = 0;
+    rc = ltsnet_symmetrize(r.nbr, r.cnt, r.pcond, n, k, r.P_row, r.P_col, r.P_val, 2 * (int64_t)n * k, &nnz, r.sym,
+                           r.sym_bytes, s);
+    if (rc != LTSNET_OK) return rc;
+    k_init_state<<<flat_blocks(n), 256, 0, s>>>(r.upd, r.gains, n);
+    count_launches(1);
+    LT_CHECK_LAUNCH();
+    const IterShape sh = iter_shape(n, p);
+    Carve ic(r.iter, r.iter_bytes);
+    const IterWs w = iter_carve(ic, sh);
+    LT_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StatusBlock), s));
+    LT_CUDA(cudaMemsetAsync(w.wfix, 0, sizeof(long long) * 4 * (size_t)sh.Mmax * sh.Mmax, s));
+    LT_CUDA(cudaMemsetAsync(w.wflt, 0, sizeof(float4) * (size_t)sh.Mmax * sh.Mmax, s));
+    const int64_t total = schedule_length(p);
+    rc = optimize_core(r.P_row, r.P_col, r.P_val, n, p, Y, r.upd, r.gains, 0, (int32_t)total, w, sh, s);
+    if (rc != LTSNET_OK) return rc;
+    ltsnet_status a = read_status(w.st, s);
+    ltsnet_status b = read_status(r.st, s);
+    if (a < 0) return a;
+    if (b < 0) return b;
+    return b;
+}
+
+}  // namespace
+}  // namespace lt
+
+using namespace lt;
+
+extern "C" size_t ltsnet_gradient_workspace_size(int32_t n, const ltsnet_params* p)
+{
+    if (n < 0 || !params_ok(p)) return 0;
+    return iter_ws_bytes(n, p);
+}
+
+extern "C" size_t ltsnet_optimize_workspace_size(int32_t n, const ltsnet_params* p)
+{
+    return ltsnet_gradient_workspace_size(n, p);
+}
+
+static bool aligned16(const void* a, const void* b, const void* c)
+{
+    return (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c) & 15) == 0;
+}
+
+static ltsnet_status prepare_iter(int32_t n, const ltsnet_params* p, void* ws, size_t ws_bytes, IterShape& sh,
+                                  IterWs& w, cudaStream_t s)
+{
+    if ((uintptr_t)ws & 255) return LTSNET_ERR_WORKSPACE;
+    sh = iter_shape(n, p);
+    Carve c(ws, ws_bytes);
+    w = iter_carve(c, sh);
+    if (!c.ok()) return LTSNET_ERR_WORKSPACE;
+    LT_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StatusBlock), s));
+    LT_CUDA(cudaMemsetAsync(w.wfix, 0, sizeof(long long) * 4 * (size_t)sh.Mmax * sh.Mmax, s));
+    LT_CUDA(cudaMemsetAsync(w.wflt, 0, sizeof(float4) * (size_t)sh.Mmax * sh.Mmax, s));
+    return LTSNET_OK;
+}
+
+extern "C" ltsnet_status ltsnet_gradient(const int64_t* P_row, const int32_t* P_col, const float* P_val, int32_t n,
+                                         const float* Y, const ltsnet_stage* stage, const ltsnet_params* p,
+                                         float* grad, float* parts, double* terms, void* ws, size_t ws_bytes,
+                                         ltsnet_stream stream)
+{
+    if (n < 1 || !P_row || !P_col || !P_val || !Y || !stage || !grad || !ws || !params_ok(p))
+        return LTSNET_ERR_INVALID_ARG;
+    if (!aligned16(P_col, P_val, Y) || ((uintptr_t)grad & 7)) return LTSNET_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    IterShape sh;
+    IterWs w;
+    ltsnet_status rc = prepare_iter(n, p, ws, ws_bytes, sh, w, s);
+    if (rc != LTSNET_OK) return rc;
+    LT_CUDA(ensure_attrs(sh));
+    const bool plain = (p->flags & LTSNET_FLAG_PLAIN) != 0;
+    const Stage st = make_stage(*stage, learning_rate(p, n));
+    LT_CUDA(launch_psum(w, P_row, n, P_val, s));
+    LT_CUDA(launch_bounds_init(w, (const float2*)Y, n, 0, s));
+    LT_CUDA(launch_grid_phase(w, sh, p, (const float2*)Y, 0, plain, s));
+    LT_CUDA(launch_point_phase<false>(P_row, P_col, P_val, n, (const float2*)Y, nullptr, nullptr, nullptr, w, sh, st,
+                                      0, (float2*)grad, parts, plain, s));
+    if (terms) {
+        k_terms<<<1, 1, 0, s>>>(w.g, terms);
+        count_launches(1);
+        LT_CHECK_LAUNCH();
+    }
+    return LTSNET_OK;
+}
+
+extern "C" ltsnet_status ltsnet_optimize(const int64_t* P_row, const int32_t* P_col, const float* P_val, int32_t n,
+                                         const ltsnet_params* p, float* Y, float* update, float* gains,
+                                         int32_t start_iter, int32_t n_iter, void* ws, size_t ws_bytes,
+                                         ltsnet_stream stream)
+{
+    if (n < 1 || !P_row || !P_col || !P_val || !Y || !update || !gains || !ws || !params_ok(p) || start_iter < 0 ||
+        n_iter < 0)
+        return LTSNET_ERR_INVALID_ARG;
+    if (!aligned16(P_col, P_val, Y) || (((uintptr_t)update | (uintptr_t)gains) & 7)) return LTSNET_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    IterShape sh;
+    IterWs w;
+    ltsnet_status rc = prepare_iter(n, p, ws, ws_bytes, sh, w, s);
+    if (rc != LTSNET_OK) return rc;
+    return optimize_core(P_row, P_col, P_val, n, p, (float2*)Y, (float2*)update, (float2*)gains, start_iter, n_iter,
+                         w, sh, s);
+}
+
+extern "C" size_t ltsnet_run_workspace_size(int32_t n, int64_t nnz_graph, const ltsnet_params* p)
+{
+    if (n < 1 || nnz_graph < 0 || !params_ok(p)) return 0;
+    Carve c(nullptr, 0);
+    run_carve(c, n, nnz_graph, p, true);
+    return align_up(c.off, 256);
+}
+
+extern "C" ltsnet_status ltsnet_run(const int64_t* row_ptr, const int32_t* col, int32_t n, const ltsnet_params* p,
+                                    float* Y, void* ws, size_t ws_bytes, ltsnet_stream stream)
+{
+    if (n < 1 || !row_ptr || !col || !Y || !ws || !params_ok(p)) return LTSNET_ERR_INVALID_ARG;
+    if (k_of(p) > LTSNET_MAX_K) return LTSNET_ERR_INVALID_ARG;
+    if ((uintptr_t)ws & 255) return LTSNET_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    Carve c(ws, ws_bytes);
+    RunWs r = run_carve(c, n, 0, p, false);
+    if (!c.ok()) return LTSNET_ERR_WORKSPACE;
+    LT_CUDA(cudaMemsetAsync(r.st, 0, sizeof(StatusBlock), s));
+    return run_core(row_ptr, col, n, p, (float2*)Y, r, s);
+}
+
+extern "C" ltsnet_status ltsnet_run_host(const int64_t* row_ptr_host, const int32_t* col_host, int32_t n,
+                                         const ltsnet_params* p, float* Y_host, void* ws, size_t ws_bytes,
+                                         ltsnet_stream stream)
+{
+    if (n < 1 || !row_ptr_host || !col_host || !Y_host || !ws || !params_ok(p)) return LTSNET_ERR_INVALID_ARG;
+    if (k_of(p) > LTSNET_MAX_K) return LTSNET_ERR_INVALID_ARG;
+    if ((uintptr_t)ws & 255) return LTSNET_ERR_WORKSPACE;
+    const int64_t m2 = row_ptr_host[n];
+    if (m2 < 0) return LTSNET_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Carve c(ws, ws_bytes);
+    RunWs r = run_carve(c, n, m2, p, true);
+    if (!c.ok()) return LTSNET_ERR_WORKSPACE;
+    LT_CUDA(cudaMemsetAsync(r.st, 0, sizeof(StatusBlock), s));
+    LT_CUDA(cudaMemcpyAsync(r.row_ptr, row_ptr_host, sizeof(int64_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s));
+    if (m2 > 0) LT_CUDA(cudaMemcpyAsync(r.col, col_host, sizeof(int32_t) * (size_t)m2, cudaMemcpyHostToDevice, s));
+    LT_CUDA(cudaMemcpyAsync(r.Y, Y_host, sizeof(float2) * (size_t)n, cudaMemcpyHostToDevice, s));
+    ltsnet_status rc = run_core(r.row_ptr, r.col, n, p, r.Y, r, s);
+    if (rc < 0) return rc;
+    LT_CUDA(cudaMemcpyAsync(Y_host, r.Y, sizeof(float2) * (size_t)n, cudaMemcpyDeviceToHost, s));
+    LT_CUDA(cudaStreamSynchronize(s));
+    return rc;
+}

@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads without a GPU and exports every function
+declared in include/ltsnet.h; host-only calls behave as documented."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2509_19785_gb300 as lt
+
+    return lt
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "ltsnet.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(ltsnet_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("ltsnet_knn_bfs", "ltsnet_calibrate", "ltsnet_symmetrize", "ltsnet_gradient", "ltsnet_optimize",
+                 "ltsnet_run", "ltsnet_run_host"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True, text=True, check=True)
+    exported = set(re.findall(r"\bT (ltsnet_[a-z0-9_]+)", out.stdout))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    assert set(lib.ABI_SYMBOLS) <= set(declared_functions())
+
+
+def test_default_params_and_stages(lib):
+    p = lib.lib().ltsnet_default_params()
+    assert p.perplexity == 30.0 and abs(p.eps - 0.05) < 1e-9 and p.nodes_per_box == 3
+    assert p.n_stages == 2 and p.stages[0].iters == 250 and p.stages[1].iters == 750
+    st = lib.default_stages(100)
+    assert len(st) == 1 and st[0].iters == 100
+    st = lib.default_stages(1000)
+    assert [s.iters for s in st] == [250, 750] and abs(st[1].lambda_r - 0.6) < 1e-6
+
+
+def test_status_strings(lib):
+    for code in (0, 1, -1, -2, -3, -4, -5, -6):
+        assert lib.status_string(code) and "unknown" not in lib.status_string(code)
+    assert "unknown" in lib.status_string(42)
+
+
+def test_workspace_sizes_and_argument_checks(lib):
+    L = lib.lib()
+    cp = lib.Params().to_c()
+    assert L.ltsnet_gradient_workspace_size(1000, ctypes.byref(cp)) > 0
+    assert L.ltsnet_run_workspace_size(1000, 4000, ctypes.byref(cp)) > L.ltsnet_gradient_workspace_size(
+        1000, ctypes.byref(cp))
+    assert L.ltsnet_symmetrize_max_nnz(10, 3) == 60
+    bad = lib.Params(nodes_per_box=7).to_c()
+    assert L.ltsnet_gradient_workspace_size(1000, ctypes.byref(bad)) == 0
+    big = lib.Params(max_boxes=5000).to_c()
+    assert L.ltsnet_gradient_workspace_size(1000, ctypes.byref(big)) == 0
+    # argument errors are caught on the host before any CUDA call
+    null = ctypes.c_void_p(0)
+    assert L.ltsnet_knn_bfs(null, null, 10, 0, null, null, null, null, 0, null) == -1
+    assert L.ltsnet_knn_bfs(null, null, 10, 5000, null, null, null, null, 0, null) == -1
+    assert L.ltsnet_calibrate(null, null, 10, 3, -1.0, 1e-5, 10, null, null, null, null) == -1
+    assert L.ltsnet_gradient(null, null, null, 10, null, None, ctypes.byref(cp), null, null, null, null, 0,
+                             null) == -1

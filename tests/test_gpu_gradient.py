@@ -1,0 +1,206 @@
+"""GPU parity of the per-iteration gradient and of the descent loop against
+the FP64 oracle with the same interpolation, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5  # FP32 GPU gradient vs FP64 oracle of the same interpolation, rel. L2
+# Each term (attraction A, repulsion R, entropy E, Z) is compared on its own.
+# The assembled gradient is compared relative to the sum of its terms' norms:
+# near a stationary layout the gradient is a small difference of large terms
+# and its own norm is no scale for FP32 rounding.
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def grid32(ltlib):
+    g = synth.grid2d(32, 32)
+    aff = ltlib.affinities(g.row_ptr, g.col, 30.0)
+    P = aff["P"]
+    Pn = tuple(t.cpu().numpy() for t in P)
+    return g, P, Pn
+
+
+@pytest.fixture(scope="module")
+def snapshots(grid32):
+    """Layouts along an oracle run on the 32x32 grid (iterations 0, 60, 300)."""
+    g, P, Pn = grid32
+    stages = oracle.default_stages(1000)
+    Y = synth.initial_layout(g.n, 1).astype(np.float64)
+    upd = np.zeros_like(Y)
+    gains = np.ones_like(Y)
+    lr = oracle.auto_learning_rate(g.n)
+    out = {}
+    sched = []
+    for st in stages:
+        sched += [st] * st.iters
+    for it in range(301):
+        Y32 = Y.astype(np.float32)
+        if it in (0, 60, 300):
+            out[it] = Y32.copy()
+        gr, _ = oracle.interp_gradient(Y32, Pn[0], Pn[1], Pn[2].astype(np.float64), sched[it], oracle.GridParams())
+        Y, upd, gains = oracle.update(Y32.astype(np.float64), upd, gains, gr, sched[it].momentum, lr)
+    return out
+
+
+def _compare(lt, P, Pn, Y32, stage, params, gp, plain=False):
+    import torch
+
+    params.plain = plain
+    grad, parts, terms = lt.gradient(P, torch.from_numpy(Y32).cuda(), stage, params, parts=True)
+    ost = oracle.Stage(stage.iters, stage.lambda_kl, stage.lambda_c, stage.lambda_r, stage.exaggeration,
+                       stage.momentum)
+    gref, pr = oracle.interp_gradient(Y32, Pn[0], Pn[1], Pn[2].astype(np.float64), ost, gp)
+    grad = grad.cpu().numpy()
+    parts = parts.cpu().numpy()
+    terms = terms.cpu().numpy()
+    gi = pr["grid"]
+    assert int(terms[2]) == gi.I and float(terms[3]) == np.float32(gi.h)
+    n = Y32.shape[0]
+    scale = (np.linalg.norm(4 * ost.lambda_kl * ost.exaggeration * pr["A"])
+             + np.linalg.norm(4 * ost.lambda_kl * pr["S"] / pr["Z"] * pr["R"])
+             + np.linalg.norm(ost.lambda_c / n * Y32.astype(np.float64))
+             + np.linalg.norm(ost.lambda_r / n ** 2 * pr["E"]))
+    errs = dict(grad=float(np.linalg.norm(grad - gref) / scale), A=rel(parts[:, 0:2], pr["A"]),
+                R=rel(parts[:, 2:4], pr["R"]), E=rel(parts[:, 4:6], pr["E"]), Z=abs(terms[0] - pr["Z"]) / pr["Z"])
+    return errs
+
+
+@pytest.mark.parametrize("plain", [False, True])
+@pytest.mark.parametrize("which", ["init", "spread", 60, 300])
+def test_gradient_grid32(ltlib, grid32, snapshots, which, plain):
+    g, P, Pn = grid32
+    if which == "init":
+        Y = synth.initial_layout(g.n, 1)
+    elif which == "spread":
+        Y = (np.random.default_rng(0).standard_normal((g.n, 2)) * 10).astype(np.float32)
+    else:
+        Y = snapshots[which]
+    st = ltlib.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+    errs = _compare(ltlib, P, Pn, Y, st, ltlib.Params(), oracle.GridParams(), plain)
+    for key, v in errs.items():
+        assert v < TOL, f"{key}: {v:.3e} ({errs})"
+
+
+@pytest.mark.parametrize("P_nodes,bw,minb,maxb", [(2, 1.0, 20, 640), (4, 0.5, 10, 500), (5, 2.0, 7, 400),
+                                                  (3, 0.25, 3, 640)])
+def test_gradient_grid_settings(ltlib, grid32, P_nodes, bw, minb, maxb):
+    g, P, Pn = grid32
+    Y = (np.random.default_rng(3).standard_normal((g.n, 2)) * 4).astype(np.float32)
+    st = ltlib.Stage(1, 0.7, 0.3, 0.9, 4.0, 0.5)
+    params = ltlib.Params(nodes_per_box=P_nodes, box_width_max=bw, min_boxes=minb, max_boxes=maxb)
+    gp = oracle.GridParams(nodes_per_box=P_nodes, box_width_max=bw, min_boxes=minb, max_boxes=maxb)
+    errs = _compare(ltlib, P, Pn, Y, st, params, gp)
+    for key, v in errs.items():
+        assert v < TOL, f"{key}: {v:.3e} ({errs})"
+
+
+def test_gradient_max_boxes_cap(ltlib, grid32):
+    """An extent far above max_boxes * box_width_max: the cap widens the boxes."""
+    g, P, Pn = grid32
+    Y = (np.random.default_rng(5).standard_normal((g.n, 2)) * 40).astype(np.float32)
+    st = ltlib.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+    params = ltlib.Params(max_boxes=96)
+    gp = oracle.GridParams(max_boxes=96)
+    errs = _compare(ltlib, P, Pn, Y, st, params, gp)
+    for key, v in errs.items():
+        assert v < TOL, f"{key}: {v:.3e} ({errs})"
+
+
+def test_gradient_sbm20k(ltlib):
+    """n = 20,000 (several spread tiles and FFT lengths, ragged tail rows)."""
+    g = synth.sbm([8000, 6000, 3000, 2000, 1001], 12.0, 5000, seed=3)
+    aff = ltlib.affinities(g.row_ptr, g.col, 40.0)
+    P = aff["P"]
+    Pn = tuple(t.cpu().numpy() for t in P)
+    Y = (np.random.default_rng(1).standard_normal((g.n, 2)) * 15).astype(np.float32)
+    st = ltlib.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+    errs = _compare(ltlib, P, Pn, Y, st, ltlib.Params(perplexity=40.0), oracle.GridParams())
+    for key, v in errs.items():
+        assert v < TOL, f"{key}: {v:.3e} ({errs})"
+
+
+def test_gradient_tiny(ltlib):
+    """n = 2 and n = 3 (closed-form sized inputs), isolated vertex rows."""
+    import torch
+
+    for n in (2, 3, 5):
+        Y = np.array([[0.3, -0.2], [-0.5, 0.4], [1.0, 1.0], [2.0, -1.0], [-1.5, 0.0]][:n], np.float32)
+        P_row = np.array([0, 1, 2] + [2] * (n - 2), np.int64)[: n + 1]
+        P_col = np.array([1, 0], np.int32)
+        P_val = np.array([0.5, 0.5], np.float32)
+        P = (torch.from_numpy(P_row).cuda(), torch.from_numpy(P_col).cuda(), torch.from_numpy(P_val).cuda())
+        st = ltlib.Stage(1, 1.0, 0.5, 0.6, 1.0, 0.8)
+        errs = _compare(ltlib, P, (P_row, P_col, P_val), Y, st, ltlib.Params(), oracle.GridParams())
+        for key, v in errs.items():
+            assert v < TOL, f"n={n} {key}: {v:.3e} ({errs})"
+
+
+def _run_steps(lt, P, Y0, start, count, params, state=None):
+    import torch
+
+    Y = torch.from_numpy(Y0).cuda().clone() if state is None else state[0]
+    upd = torch.zeros_like(Y) if state is None else state[1]
+    gains = torch.ones_like(Y) if state is None else state[2]
+    lt.optimize(P, Y, upd, gains, start, count, params)
+    return Y, upd, gains
+
+
+def test_optimize_deterministic_and_resumable(ltlib, grid32):
+    g, P, Pn = grid32
+    Y0 = synth.initial_layout(g.n, 1)
+    params = ltlib.Params(stages=ltlib.default_stages(400))
+    a = _run_steps(ltlib, P, Y0, 0, 400, params)
+    b = _run_steps(ltlib, P, Y0, 0, 400, params)
+    assert all(np.array_equal(x.cpu().numpy(), y.cpu().numpy()) for x, y in zip(a, b))
+    c = _run_steps(ltlib, P, Y0, 0, 137, params)
+    c = _run_steps(ltlib, P, Y0, 137, 263, params, state=c)
+    assert all(np.array_equal(x.cpu().numpy(), y.cpu().numpy()) for x, y in zip(a, c))
+
+
+def test_optimize_first_steps_match_oracle(ltlib, grid32):
+    """Ten descent steps from the same start: FP32 GPU vs FP64 oracle."""
+    g, P, Pn = grid32
+    Y0 = synth.initial_layout(g.n, 2)
+    params = ltlib.Params(stages=ltlib.default_stages(1000))
+    Yg = _run_steps(ltlib, P, Y0, 0, 10, params)[0].cpu().numpy()
+    Yo = oracle.run(Y0, Pn[0], Pn[1], Pn[2].astype(np.float64), oracle.default_stages(1000), oracle.GridParams(),
+                    iters=10)
+    assert rel(Yg, Yo) < 1e-4
+
+
+def test_full_run_final_cost_grid32(ltlib, grid32):
+    """Whole method on the 32x32 grid (u = 30, 1000 iterations): the final
+    costs (exact FP64 cost of each final layout) agree within 1%."""
+    import torch
+
+    g, P, Pn = grid32
+    Y0 = synth.initial_layout(g.n, 1)
+    params = ltlib.Params(stages=ltlib.default_stages(1000))
+    Yg, rc = ltlib.run(g.row_ptr, g.col, torch.from_numpy(Y0), params)
+    Yg = Yg.cpu().numpy()
+    Pv = Pn[2].astype(np.float64)
+    Yo = oracle.run(Y0, Pn[0], Pn[1], Pv, oracle.default_stages(1000), oracle.GridParams())
+    st = oracle.default_stages(1000)[-1]
+    cg, _ = oracle.exact_cost(Yg.astype(np.float64), Pn[0], Pn[1], Pv, st)
+    co, _ = oracle.exact_cost(Yo, Pn[0], Pn[1], Pv, st)
+    assert abs(cg - co) / abs(co) < 0.01, (cg, co)
+
+
+def test_run_host_matches_device(ltlib, grid32):
+    import torch
+
+    g, P, Pn = grid32
+    Y0 = synth.initial_layout(g.n, 4)
+    params = ltlib.Params(stages=ltlib.default_stages(120))
+    Yd, _ = ltlib.run(g.row_ptr, g.col, torch.from_numpy(Y0), params)
+    Yh = Y0.copy()
+    ltlib.run_host(g.row_ptr, g.col, Yh, params)
+    assert np.array_equal(Yd.cpu().numpy(), Yh)
