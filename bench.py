@@ -1,0 +1,373 @@
+"""Benchmark of the L-tsNET hot path on GB300 (one JSON line on stdout).
+
+A step is one whole L-tsNET run on the workload -- partial BFS, perplexity
+calibration, symmetrisation, then every iteration of the schedule (gradient
++ move) -- with the graph and the initial layout already resident in HBM.
+The metric is gradient iterations per second of the whole job (the C0
+preprocessing amortised in), on a random geometric graph with n ~ 1e6.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ltsnet|reference]
+
+--impl reference times the FP64 CPU oracle on this machine's host cores
+instead (bounded sample; see the cpu_baseline key).  Under torchrun each rank
+runs an independent replica (the single-graph path does not shard without an
+exchange step); value = iterations of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "L-tsNET gradient iters/s at n=1M vs plain FP32 form; batched graphs/s"
+WORKLOAD = "rgg1m"
+PERPLEXITY = 30.0
+ITERS = 1000
+FUSED_PROFILE = os.path.join(ROOT, "profiles", "fused_update_rgg1m.md")
+KERNEL_SOURCES = ("paper_2509_19785_gb300/csrc/iterate.cu", "paper_2509_19785_gb300/csrc/iter.cuh")
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def ncu_traffic_per_launch():
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    if not os.path.exists(FUSED_PROFILE):
+        return None
+    text = open(FUSED_PROFILE).read()
+    m = re.search(r"traffic_bytes_per_launch\s*=\s*([0-9.eE+]+)", text)
+    k = re.search(r"kernel_source_hash\s*=\s*([0-9a-f]+)", text)
+    if not m or not k or k.group(1) != kernel_hash():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out = self.proc.communicate(timeout=5)[0]
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+        else:
+            self.out = ""
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload():
+    import synth
+
+    g = synth.config_graph(WORKLOAD)
+    return g
+
+
+def bench_ltsnet(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    import synth
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2509_19785_gb300 as lt
+
+    lt.lib()
+    g = workload()
+    n = g.n
+    params = lt.Params(perplexity=PERPLEXITY, stages=lt.default_stages(ITERS))
+    row_ptr = torch.from_numpy(g.row_ptr).cuda()
+    col = torch.from_numpy(g.col).cuda()
+    Y0 = torch.from_numpy(synth.initial_layout(n, 1 + rank)).cuda()
+    ws = lt.run_workspace(n, g.col.shape[0], params)
+    stream = torch.cuda.current_stream()
+
+    def step(p):
+        Y, rc = lt.run(row_ptr, col, Y0, p, ws=ws)
+        return Y
+
+    def timed(p, steps, warmup, profile=False):
+        for _ in range(warmup):
+            step(p)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        if profile:
+            lt.profile_begin(lt.KERNEL_FUSED_UPDATE, steps * ITERS)
+        l0 = lt.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            Y = step(p)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = lt.launch_count() - l0
+        prof = lt.profile_end(lt.KERNEL_FUSED_UPDATE) if profile else None
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, launches, prof, Y
+
+    # C0 alone (reported, part of every step)
+    aff = lt.affinities(g.row_ptr, g.col, PERPLEXITY)
+    nnz = int(aff["P"][1].numel())
+    torch.cuda.synchronize()
+    c0 = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lt.affinities(row_ptr, col, PERPLEXITY)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        c0.append(e0.elapsed_time(e1))
+    del aff
+
+    with ClockSampler(local) as clk:
+        ms, launches, prof, Y = timed(params, args.steps, args.warmup, profile=True)
+    clocks = clk.summary()
+    Yn = Y.cpu().numpy()
+    if not np.all(np.isfinite(Yn)):
+        raise RuntimeError("non-finite layout")
+    value = world * args.steps * ITERS / (ms / 1e3)
+
+    # plain FP32 form, same workload
+    plain = lt.Params(perplexity=PERPLEXITY, stages=lt.default_stages(ITERS), plain=True)
+    ms_plain, _, _, _ = timed(plain, max(1, args.steps // 2), 1)
+    value_plain = world * max(1, args.steps // 2) * ITERS / (ms_plain / 1e3)
+
+    # end to end through the C ABI with host buffers (copies inside the region)
+    Yh0 = synth.initial_layout(n, 1 + rank)
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        Yh = Yh0.copy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lt.run_host(g.row_ptr, g.col, Yh, params, ws=ws)
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_ms.append((t1 - t0) * 1e3)
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * args.steps * ITERS / (e2e_total / 1e3)
+
+    # roofline of the fused gather + attraction + compression + update kernel
+    peaks = measured_peaks()
+    bytes_per_launch = 8 * nnz + 8 * (n + 1) + 48 * n
+    fused_ms, fused_launches = prof
+    avg_s = fused_ms / 1e3 / max(1, fused_launches)
+    achieved = bytes_per_launch / avg_s / 1e9
+    roofline = {"kernel": "k_fused (gather + attraction + compression + update)", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": ncu_traffic_per_launch(),
+                "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": round(avg_s * 1e6, 2),
+                "launches_timed": fused_launches, "peak_source": peaks["source"]}
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return None
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "iters/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: random geometric graph, 1e6 points in the unit square, mean degree 8, "
+                               f"largest component n={n}, m={g.m}; perplexity {PERPLEXITY:g} (k=90), {ITERS} "
+                               f"iterations, 3 nodes/box, min 50 boxes",
+                   "n": n, "nnz_P": nnz, "iters_per_step": ITERS, "form": "optimised (fused, deterministic spread)",
+                   "step": "C0 (BFS + calibration + symmetrisation) + all iterations",
+                   "l2": "inputs larger than L2: P is 8 bytes x nnz ~ 0.8 GB", "parallelism": f"replicas{world}"},
+        "vertex_iters_per_s": round(value * n, 1),
+        "c0_ms": round(statistics.median(c0), 3),
+        "plain_fp32": {"value": round(value_plain, 2), "unit": "iters/s", "form": "unfused, atomic spread",
+                       "speedup_of_optimised": round(value / value_plain, 3)},
+        "roofline": roofline,
+        "e2e": {"value": round(e2e_value, 2), "unit": "iters/s",
+                "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes + 8 * n), "d2h_bytes_per_step": 8 * n},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+    }
+    line["cpu_baseline"] = cpu_baseline(g)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
+def oracle_affinities(g):
+    import oracle
+
+    return oracle.preprocess(g.row_ptr, g.col, PERPLEXITY)
+
+
+def oracle_iteration_time(g, aff, iters: int, lr: float):
+    """Seconds per oracle iteration (interpolated gradient + update) on the
+    full workload, starting from a spread layout (the loop's typical grid)."""
+    import numpy as np
+
+    import oracle
+
+    st = oracle.default_stages(ITERS)[-1]
+    Y = (np.random.default_rng(0).standard_normal((g.n, 2)) * 15).astype(np.float64)
+    upd = np.zeros_like(Y)
+    gains = np.ones_like(Y)
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        Y32 = Y.astype(np.float32)
+        gr, _ = oracle.interp_gradient(Y32, aff.P_row, aff.P_col, aff.P_val64, st, oracle.GridParams())
+        Y, upd, gains = oracle.update(Y32.astype(np.float64), upd, gains, gr, st.momentum, lr)
+    return (time.perf_counter() - t0) / iters
+
+
+def cpu_baseline(g, n_sample: int = 100_000, iters: int = 3):
+    """The oracle, as it stands, on a 100k-vertex instance of the same recipe
+    (C0 + a few iterations), scaled linearly in n (every step is O(n))."""
+    import oracle
+    import synth
+
+    gs = synth.rgg(n_sample)
+    t0 = time.perf_counter()
+    aff = oracle_affinities(gs)
+    c0_s = time.perf_counter() - t0
+    per_iter = oracle_iteration_time(gs, aff, iters, oracle.auto_learning_rate(gs.n))
+    scale = g.n / gs.n
+    run_s = scale * (c0_s + ITERS * per_iter)
+    return {"value": round(ITERS / run_s, 5), "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle on a {gs.n}-vertex RGG of the same recipe: C0 {c0_s:.1f} s + {iters} iterations "
+                      f"(interpolated gradient + update) {per_iter:.3f} s each, one {ITERS}-iteration run "
+                      f"scaled by n ({scale:.2f}x); single thread"}
+
+
+def bench_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    import synth
+
+    oracle.build()
+    g = workload()
+    t0 = time.perf_counter()
+    aff = oracle_affinities(g)
+    c0_s = time.perf_counter() - t0
+    lr = oracle.auto_learning_rate(g.n)
+    oracle_iteration_time(g, aff, args.warmup, lr)
+    per_iter = oracle_iteration_time(g, aff, args.steps, lr)
+    run_s = c0_s + ITERS * per_iter
+    value = ITERS / run_s
+    cb = {"value": round(value, 5), "unit": "iters/s", "cores": 1, "kind": "oracle",
+          "sample": f"oracle C0 on the full graph ({c0_s:.1f} s, once) + {args.steps} timed oracle iterations "
+                    f"({per_iter:.2f} s each, after {args.warmup} warm-up iterations), extrapolated to one "
+                    f"{ITERS}-iteration run; single thread"}
+    return {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(run_s * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: random geometric graph n={g.n}, perplexity {PERPLEXITY:g}, "
+                                   f"{ITERS} iterations", "n": g.n},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ltsnet", choices=["ltsnet", "reference"])
+    args = ap.parse_args()
+    line = bench_reference(args) if args.impl == "reference" else bench_ltsnet(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -300,55 +300,114 @@ __global__ void k_bin_scatter(const float2* __restrict__ Y, int32_t n, const Gri
     }
 }
 
+// One work item = one tile of tb x tb boxes and up to kSpreadChunk of its
+// points.  The points are counting-sorted by box in shared memory (their
+// local coordinates computed once on the way); then each thread takes one
+// node row b of a contiguous slice of the sorted points and accumulates that
+// row's P nodes x 4 charges in 64-bit fixed point in registers, adding them
+// to the global fixed-point grid only when the box changes.  Integer sums do
+// not depend on order, so the grid is the same bit for bit from run to run.
 template <int P>
 __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__ binned, const GridDev* __restrict__ G,
                                                       const int4* __restrict__ items, long long* __restrict__ wfix)
 {
-    extern __shared__ long long acc[];  // TN*TN nodes x 4 charges
-    const int M = G->M, tb = G->tb, tiles = G->tiles;
-    const int TN = tb * P;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int M = G->M, I = G->I, tb = G->tb, tiles = G->tiles, Pg = G->P;
+    const float lo = G->lo, h = G->h, s = G->s;
+    const int NB = tb * tb;
+    float2* su = (float2*)smraw;          // kSpreadChunk local coordinates (sorted by box)
+    int* slb = (int*)(su + kSpreadChunk);  // kSpreadChunk boxes (sorted)
+    int* off = slb + kSpreadChunk;         // NB + 1
+    int* cur = off + kMaxTileBoxes + 1;    // NB
     float fx[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) fx[q] = (float)G->fx[q];
+    const int nslice = blockDim.x / P;
     const int nitems = G->nitems;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int4 item = items[it];
         const int tx = item.x % tiles, ty = item.x / tiles;
         const int bx0 = tx * tb, by0 = ty * tb;
-        for (int i = threadIdx.x; i < TN * TN * 4; i += blockDim.x) acc[i] = 0;
+        const int cnt = item.z - item.y;
+        for (int i = threadIdx.x; i < NB; i += blockDim.x) cur[i] = 0;
         __syncthreads();
-        for (int j = item.y + threadIdx.x; j < item.z; j += blockDim.x) {
-            int bx, by;
-            float ux, uy;
-            local_coords(binned[j], G, bx, by, ux, uy);
-            float wx[P], wy[P];
-            lagrange<P>(ux, wx);
-            lagrange<P>(uy, wy);
-            const int lx0 = (bx - bx0) * P, ly0 = (by - by0) * P;
-#pragma unroll
-            for (int b = 0; b < P; ++b)
-#pragma unroll
-                for (int a = 0; a < P; ++a) {
-                    const float w = wx[a] * wy[b];
-                    const float ex = ux - ((float)a + 0.5f), ey = uy - ((float)b + 0.5f);
-                    const float q[4] = {w, w * ex, w * ey, w * (ex * ex + ey * ey)};
-                    long long* dst = acc + ((ly0 + b) * TN + (lx0 + a)) * 4;
-#pragma unroll
-                    for (int ch = 0; ch < 4; ++ch)
-                        atomicAdd((unsigned long long*)(dst + ch), (unsigned long long)__float2ll_rn(q[ch] * fx[ch]));
-                }
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+            const float2 p = binned[item.y + j];
+            const int lb = (box_of(p.y, lo, h, I) - by0) * tb + (box_of(p.x, lo, h, I) - bx0);
+            atomicAdd(&cur[lb], 1);
         }
         __syncthreads();
-        const bool single = item.w != 0;
-        for (int i = threadIdx.x; i < TN * TN * 4; i += blockDim.x) {
-            const long long v = acc[i];
-            if (v == 0) continue;
-            const int node = i >> 2, ch = i & 3;
-            const int gy = by0 * P + node / TN, gx = bx0 * P + node % TN;
-            if (gy >= M || gx >= M) continue;
-            long long* dst = wfix + ((int64_t)gy * M + gx) * 4 + ch;
-            if (single) *dst = v;
-            else atomicAdd((unsigned long long*)dst, (unsigned long long)v);
+        if (threadIdx.x < 32) {  // exclusive scan of the box counts by warp 0
+            int carry = 0;
+            for (int b0 = 0; b0 < NB; b0 += 32) {
+                const int b = b0 + threadIdx.x;
+                const int v = b < NB ? cur[b] : 0;
+                int inc = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(FULL, inc, o);
+                    if (threadIdx.x >= o) inc += t;
+                }
+                if (b < NB) {
+                    off[b] = carry + inc - v;
+                    cur[b] = carry + inc - v;
+                }
+                carry += __shfl_sync(FULL, inc, 31);
+            }
+            if (threadIdx.x == 0) off[NB] = carry;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+            const float2 p = binned[item.y + j];
+            const int bx = box_of(p.x, lo, h, I), by = box_of(p.y, lo, h, I);
+            const int lb = (by - by0) * tb + (bx - bx0);
+            const int pos = atomicAdd(&cur[lb], 1);
+            su[pos] = make_float2(local_u(p.x, lo, s, Pg * bx), local_u(p.y, lo, s, Pg * by));
+            slb[pos] = lb;
+        }
+        __syncthreads();
+        if (threadIdx.x < nslice * P) {
+            const int slice = threadIdx.x / P, bb = threadIdx.x - slice * P;
+            const int per = (cnt + nslice - 1) / nslice;
+            const int q0 = slice * per, q1 = min(cnt, q0 + per);
+            long long ra[P][4];
+            int cur_lb = -1;
+            for (int q = q0; q <= q1; ++q) {
+                const int lb = q < q1 ? slb[q] : -2;
+                if (lb != cur_lb) {
+                    if (cur_lb >= 0) {
+                        const int gy = (by0 + cur_lb / tb) * P + bb;
+                        const int gx0 = (bx0 + cur_lb % tb) * P;
+                        long long* dst = wfix + ((int64_t)gy * M + gx0) * 4;
+#pragma unroll
+                        for (int a = 0; a < P; ++a)
+#pragma unroll
+                            for (int ch = 0; ch < 4; ++ch)
+                                if (ra[a][ch] != 0)
+                                    atomicAdd((unsigned long long*)(dst + a * 4 + ch), (unsigned long long)ra[a][ch]);
+                    }
+                    if (q == q1) break;
+                    cur_lb = lb;
+#pragma unroll
+                    for (int a = 0; a < P; ++a)
+#pragma unroll
+                        for (int ch = 0; ch < 4; ++ch) ra[a][ch] = 0;
+                }
+                const float2 u = su[q];
+                float wx[P];
+                lagrange<P>(u.x, wx);
+                const float wyb = lagrange_one<P>(u.y, bb);
+                const float ey = u.y - ((float)bb + 0.5f);
+#pragma unroll
+                for (int a = 0; a < P; ++a) {
+                    const float w = wx[a] * wyb;
+                    const float ex = u.x - ((float)a + 0.5f);
+                    ra[a][0] += __float2ll_rn(w * fx[0]);
+                    ra[a][1] += __float2ll_rn((w * ex) * fx[1]);
+                    ra[a][2] += __float2ll_rn((w * ey) * fx[2]);
+                    ra[a][3] += __float2ll_rn((w * (ex * ex + ey * ey)) * fx[3]);
+                }
+            }
         }
         __syncthreads();
     }
@@ -569,6 +628,50 @@ __global__ void k_conv_rows_fwd(const GridDev* __restrict__ Gp, const float2* __
 // and, by Parseval over the half spectrum, the grid sum
 //   Z + n = sum [S0 (K1*S0) + 2 s^2 (S1 . (2 (K2 d)*S0 - K2*S1) + S2 (K2*S0))],
 // accumulated in FP64 and finished by the last block in a fixed order.
+__device__ __forceinline__ float odd_transposed(const float* __restrict__ Dh, int kx, int ky, int L, int H)
+{
+    // (K dy)^(kx, ky) = (K dx)^(ky, kx); stored half spectrum covers kx <= L/2,
+    // the rest by oddness in the first argument.
+    return ky <= L / 2 ? Dh[(int64_t)kx * H + ky] : -Dh[(int64_t)kx * H + (L - ky)];
+}
+
+// Z integrand at (kx, ky) from the four charge spectra (see k_conv_cols).
+__device__ __forceinline__ double z_term(float2 s0, float2 s1x, float2 s1y, float2 s2v, float k2, float k1, float d2x,
+                                         float d2y, float s2)
+{
+    const double gx_re = -2.0 * d2x * s0.y - k2 * s1x.x, gx_im = 2.0 * d2x * s0.x - k2 * s1x.y;
+    const double gy_re = -2.0 * d2y * s0.y - k2 * s1y.x, gy_im = 2.0 * d2y * s0.x - k2 * s1y.y;
+    double t = (double)k1 * ((double)s0.x * s0.x + (double)s0.y * s0.y);
+    const double c = (double)s1x.x * gx_re + (double)s1x.y * gx_im + (double)s1y.x * gy_re + (double)s1y.y * gy_im +
+                     (double)k2 * ((double)s2v.x * s0.x + (double)s2v.y * s0.y);
+    return t + 2.0 * (double)s2 * c;
+}
+
+// Product q at (kx, ky) for the inverse column transform (conjugated).
+__device__ __forceinline__ float2 conv_product(int q, float2 s0, float2 s1x, float2 s1y, const float* __restrict__ K2h,
+                                               const float* __restrict__ Keh, const float* __restrict__ D2h,
+                                               const float* __restrict__ Deh, int kx, int ky, int L, int H)
+{
+    const int64_t o = (int64_t)ky * H + kx;
+    float2 v;
+    if (q == 0) {
+        const float k = K2h[o];
+        v = make_float2(k * s0.x, k * s0.y);
+    } else if (q == 1) {
+        const float k = Keh[o];
+        v = make_float2(k * s0.x, k * s0.y);
+    } else {
+        const bool ent = q >= 4;
+        const bool ydir = (q & 1) != 0;
+        const float* Dh = ent ? Deh : D2h;
+        const float k = ent ? Keh[o] : K2h[o];
+        const float d = ydir ? odd_transposed(Dh, kx, ky, L, H) : Dh[o];
+        const float2 s1 = ydir ? s1y : s1x;
+        v = make_float2(-d * s0.y - k * s1.x, d * s0.x - k * s1.y);
+    }
+    return conj2(v);
+}
+
 __global__ void k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const float2* __restrict__ srow,
                             const float* __restrict__ khat, float2* __restrict__ ucol, double* __restrict__ zblk,
                             int32_t n, int sm_f2)
@@ -579,10 +682,7 @@ __global__ void k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const fl
     const GridDev& G = *Gp;
     const int L = G.L, M = G.M, H = L / 2 + 1;
     const float s2 = G.s * G.s;
-    const int cap = line_cap(sm_f2, L, 6);
     float2* stw = smf;
-    float2* buf[6];
-    for (int i = 0; i < 6; ++i) buf[i] = smf + L + (size_t)i * cap * L;
     load_tw(stw, tw, L);
     const int64_t MH = (int64_t)M * H, LH = (int64_t)L * H;
     const float* K2h = khat;
@@ -593,85 +693,94 @@ __global__ void k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const fl
     double zacc = 0.0;
     int beg, end;
     block_range(H, beg, end);
-    for (int k0 = beg; k0 < end; k0 += cap) {
-        const int nl = min(cap, end - k0);
-        // spectra of S0, S1x, S1y, S2 along y; slots assigned as results land
-        float2* spec[4];
-        float2* freeb[2];
-        float2* pool[6] = {buf[0], buf[1], buf[2], buf[3], buf[4], buf[5]};
-        int used = 0;
-        for (int gsel = 0; gsel < 4; ++gsel) {
-            float2* a = pool[used];
-            float2* b = pool[used + 1];
+    // Batched: 4 spectra + 6 products + 6 work lines per column, two FFT calls.
+    const int capb = (sm_f2 - L) / (16 * L);
+    if (capb >= 1) {
+        for (int k0 = beg; k0 < end; k0 += capb) {
+            const int nc = min(capb, end - k0);
+            float2* SP = smf + L;
+            float2* PR = SP + (size_t)4 * nc * L;
+            float2* PP = PR + (size_t)6 * nc * L;
             __syncthreads();
-            for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
-                const int y = idx / nl, line = idx - y * nl;
-                a[line * L + y] =
-                    y < M ? srow[(int64_t)gsel * MH + (int64_t)y * H + k0 + line] : make_float2(0.f, 0.f);
+            for (int idx = threadIdx.x; idx < 4 * nc * L; idx += blockDim.x) {
+                const int y = idx / (4 * nc), r = idx - y * (4 * nc);
+                const int gsel = r / nc, c = r - gsel * nc;
+                SP[r * L + y] = y < M ? srow[(int64_t)gsel * MH + (int64_t)y * H + k0 + c] : make_float2(0.f, 0.f);
             }
             __syncthreads();
-            float2* r = fft_lines(a, b, nl, L, G, stw);
-            spec[gsel] = r;
-            pool[used] = r;
-            pool[used + 1] = (r == a) ? b : a;
-            ++used;
-        }
-        freeb[0] = pool[4];
-        freeb[1] = pool[5];
-        // Z integrand over this batch of columns
-        for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
-            const int ky = idx / nl, line = idx - ky * nl;
-            const int kx = k0 + line;
-            const int64_t o = (int64_t)ky * H + kx;
-            const float k2 = K2h[o], k1 = K1h[o], d2x = D2h[o];
-            const float d2y = ky <= L / 2 ? D2h[(int64_t)kx * H + ky] : -D2h[(int64_t)kx * H + (L - ky)];
-            const float2 s0 = spec[0][line * L + ky], s1x = spec[1][line * L + ky];
-            const float2 s1y = spec[2][line * L + ky], s2v = spec[3][line * L + ky];
-            // 2 (K2 d)^ S0^ - K2^ S1^, with (K2 d)^ = i d
-            const double gx_re = -2.0 * d2x * s0.y - k2 * s1x.x, gx_im = 2.0 * d2x * s0.x - k2 * s1x.y;
-            const double gy_re = -2.0 * d2y * s0.y - k2 * s1y.x, gy_im = 2.0 * d2y * s0.x - k2 * s1y.y;
-            double t = (double)k1 * ((double)s0.x * s0.x + (double)s0.y * s0.y);
-            double c = (double)s1x.x * gx_re + (double)s1x.y * gx_im + (double)s1y.x * gy_re + (double)s1y.y * gy_im +
-                       (double)k2 * ((double)s2v.x * s0.x + (double)s2v.y * s0.y);
-            t += 2.0 * (double)s2 * c;
-            const double wgt = (kx == 0 || 2 * kx == L) ? 1.0 : 2.0;
-            zacc += wgt * t;
-        }
-        // products and inverse column transforms
-        for (int q = 0; q < 6; ++q) {
-            float2* a = freeb[0];
-            float2* b = freeb[1];
+            float2* R = fft_lines(SP, PP, 4 * nc, L, G, stw);
+            if (R != SP) {
+                for (int idx = threadIdx.x; idx < 4 * nc * L; idx += blockDim.x) SP[idx] = R[idx];
+                __syncthreads();
+            }
+            for (int idx = threadIdx.x; idx < nc * L; idx += blockDim.x) {
+                const int ky = idx / nc, c = idx - ky * nc;
+                const int kx = k0 + c;
+                const int64_t o = (int64_t)ky * H + kx;
+                const float2 s0 = SP[(0 * nc + c) * L + ky], s1x = SP[(1 * nc + c) * L + ky];
+                const float2 s1y = SP[(2 * nc + c) * L + ky], s2v = SP[(3 * nc + c) * L + ky];
+                const double wgt = (kx == 0 || 2 * kx == L) ? 1.0 : 2.0;
+                zacc += wgt * z_term(s0, s1x, s1y, s2v, K2h[o], K1h[o], D2h[o], odd_transposed(D2h, kx, ky, L, H), s2);
+#pragma unroll
+                for (int q = 0; q < 6; ++q)
+                    PR[(q * nc + c) * L + ky] = conv_product(q, s0, s1x, s1y, K2h, Keh, D2h, Deh, kx, ky, L, H);
+            }
             __syncthreads();
+            float2* R2 = fft_lines(PR, PP, 6 * nc, L, G, stw);
+            for (int idx = threadIdx.x; idx < 6 * nc * M; idx += blockDim.x) {
+                const int y = idx / (6 * nc), r = idx - y * (6 * nc);
+                const int q = r / nc, c = r - q * nc;
+                ucol[(int64_t)q * MH + (int64_t)y * H + k0 + c] = conj2(R2[r * L + y]);
+            }
+        }
+    } else {
+        // Long lines: four kept spectra + two work lines per column.
+        const int cap = line_cap(sm_f2, L, 6);
+        float2* buf[6];
+        for (int i = 0; i < 6; ++i) buf[i] = smf + L + (size_t)i * cap * L;
+        for (int k0 = beg; k0 < end; k0 += cap) {
+            const int nl = min(cap, end - k0);
+            float2* spec[4];
+            float2* pool[6] = {buf[0], buf[1], buf[2], buf[3], buf[4], buf[5]};
+            for (int gsel = 0; gsel < 4; ++gsel) {
+                float2* a = pool[gsel];
+                float2* b = pool[gsel + 1];
+                __syncthreads();
+                for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
+                    const int y = idx / nl, line = idx - y * nl;
+                    a[line * L + y] =
+                        y < M ? srow[(int64_t)gsel * MH + (int64_t)y * H + k0 + line] : make_float2(0.f, 0.f);
+                }
+                __syncthreads();
+                float2* r = fft_lines(a, b, nl, L, G, stw);
+                spec[gsel] = r;
+                pool[gsel] = r;
+                pool[gsel + 1] = (r == a) ? b : a;
+            }
+            float2* wa = pool[4];
+            float2* wb = pool[5];
             for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
                 const int ky = idx / nl, line = idx - ky * nl;
                 const int kx = k0 + line;
                 const int64_t o = (int64_t)ky * H + kx;
-                const float2 s0 = spec[0][line * L + ky];
-                float2 v;
-                if (q == 0) {
-                    const float k = K2h[o];
-                    v = make_float2(k * s0.x, k * s0.y);
-                } else if (q == 1) {
-                    const float k = Keh[o];
-                    v = make_float2(k * s0.x, k * s0.y);
-                } else {
-                    const bool ent = q >= 4;
-                    const bool ydir = (q & 1) != 0;
-                    const float* Dh = ent ? Deh : D2h;
-                    const float k = ent ? Keh[o] : K2h[o];
-                    float d;
-                    if (!ydir) d = Dh[o];
-                    else d = ky <= L / 2 ? Dh[(int64_t)kx * H + ky] : -Dh[(int64_t)kx * H + (L - ky)];
-                    const float2 s1 = spec[ydir ? 2 : 1][line * L + ky];
-                    v = make_float2(-d * s0.y - k * s1.x, d * s0.x - k * s1.y);
-                }
-                a[line * L + ky] = conj2(v);
+                const double wgt = (kx == 0 || 2 * kx == L) ? 1.0 : 2.0;
+                zacc += wgt * z_term(spec[0][line * L + ky], spec[1][line * L + ky], spec[2][line * L + ky],
+                                     spec[3][line * L + ky], K2h[o], K1h[o], D2h[o],
+                                     odd_transposed(D2h, kx, ky, L, H), s2);
             }
-            __syncthreads();
-            float2* r = fft_lines(a, b, nl, L, G, stw);
-            for (int idx = threadIdx.x; idx < nl * M; idx += blockDim.x) {
-                const int y = idx / nl, line = idx - y * nl;
-                ucol[(int64_t)q * MH + (int64_t)y * H + k0 + line] = conj2(r[line * L + y]);
+            for (int q = 0; q < 6; ++q) {
+                __syncthreads();
+                for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
+                    const int ky = idx / nl, line = idx - ky * nl;
+                    wa[line * L + ky] = conv_product(q, spec[0][line * L + ky], spec[1][line * L + ky],
+                                                     spec[2][line * L + ky], K2h, Keh, D2h, Deh, k0 + line, ky, L, H);
+                }
+                __syncthreads();
+                float2* r = fft_lines(wa, wb, nl, L, G, stw);
+                for (int idx = threadIdx.x; idx < nl * M; idx += blockDim.x) {
+                    const int y = idx / nl, line = idx - y * nl;
+                    ucol[(int64_t)q * MH + (int64_t)y * H + k0 + line] = conj2(r[line * L + y]);
+                }
             }
         }
     }
@@ -697,7 +806,11 @@ __global__ void k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const fl
             if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
             __syncthreads();
         }
-        if (threadIdx.x == 0) Gp->Z = red[0] - (double)n;
+        if (threadIdx.x == 0) {
+            const double Z = red[0] - (double)n;
+            Gp->Z = Z;
+            Gp->SoZ = (float)(Gp->S / Z);
+        }
     }
 }
 
@@ -832,6 +945,13 @@ __global__ void k_psum(const float* __restrict__ v, const int64_t* __restrict__ 
 constexpr int kFftThreads = 256;
 constexpr int kPsumBlocks = 304;
 
+// Shared memory of the spread: the fixed-point tile, the item's points and
+// their boxes, box offsets and cursors.
+size_t spread_smem_bytes()
+{
+    return (size_t)kSpreadChunk * (sizeof(float2) + sizeof(int)) + (size_t)(2 * kMaxTileBoxes + 1) * sizeof(int);
+}
+
 // Room for the twiddles plus six lines of the longest length (the column
 // pass keeps four spectra and two work lines), at least 64 KB.
 size_t fft_smem_bytes(int Lmax) { return std::max<size_t>(64 * 1024, (size_t)7 * Lmax * 8); }
@@ -931,17 +1051,16 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
         if (blocks < 1) blocks = 1;
         const size_t sm1 = (size_t)T * 4;
         k_bin_count<<<(unsigned)blocks, 256, sm1, s>>>(Y, n, w.g, w.tile_cnt);
-        const int32_t chunk = (int32_t)std::max<int64_t>(4096, ((int64_t)n + 2 * kSMs - 1) / (2 * kSMs));
-        k_bin_plan<<<1, 1024, 0, s>>>(w.g, w.tile_cnt, w.tile_off, w.tile_cur, w.items, chunk);
+        k_bin_plan<<<1, 1024, 0, s>>>(w.g, w.tile_cnt, w.tile_off, w.tile_cur, w.items, kSpreadChunk);
         int64_t sblocks = ((int64_t)n + 256 * 8 - 1) / (256 * 8);
         if (sblocks < 1) sblocks = 1;
         k_bin_scatter<<<(unsigned)sblocks, 256, 2 * sm1, s>>>(Y, n, w.g, w.tile_cur, w.binned);
-        const size_t sm2 = (size_t)kTileNodes * kTileNodes * 4 * sizeof(long long);
+        const size_t sm2 = spread_smem_bytes();
         switch (P) {
-            case 2: k_spread_tiles<2><<<kSMs * 2, 256, sm2, s>>>(w.binned, w.g, w.items, w.wfix); break;
-            case 3: k_spread_tiles<3><<<kSMs * 2, 256, sm2, s>>>(w.binned, w.g, w.items, w.wfix); break;
-            case 4: k_spread_tiles<4><<<kSMs * 2, 256, sm2, s>>>(w.binned, w.g, w.items, w.wfix); break;
-            default: k_spread_tiles<5><<<kSMs * 2, 256, sm2, s>>>(w.binned, w.g, w.items, w.wfix); break;
+            case 2: k_spread_tiles<2><<<kSMs * 4, 256, sm2, s>>>(w.binned, w.g, w.items, w.wfix); break;
+            case 3: k_spread_tiles<3><<<kSMs * 4, 256, sm2, s>>>(w.binned, w.g, w.items, w.wfix); break;
+            case 4: k_spread_tiles<4><<<kSMs * 4, 256, sm2, s>>>(w.binned, w.g, w.items, w.wfix); break;
+            default: k_spread_tiles<5><<<kSMs * 4, 256, sm2, s>>>(w.binned, w.g, w.items, w.wfix); break;
         }
         count_launches(4);
     }
@@ -962,23 +1081,26 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
     return cudaGetLastError();
 }
 
-cudaError_t grid_set_smem_attrs(const IterShape& sh)
+cudaError_t grid_set_smem_attrs()
 {
-    const size_t fsm = fft_smem_bytes(sh.Lmax);
+    const int fsm = (int)fft_smem_bytes(kLMax);
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_spec_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm))) return e;
-    if ((e = cudaFuncSetAttribute(k_spec_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm))) return e;
-    if ((e = cudaFuncSetAttribute(k_conv_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm))) return e;
-    if ((e = cudaFuncSetAttribute(k_conv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm))) return e;
-    if ((e = cudaFuncSetAttribute(k_conv_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm))) return e;
-    const int sm2 = kTileNodes * kTileNodes * 4 * (int)sizeof(long long);
+    if ((e = cudaFuncSetAttribute(k_spec_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
+    if ((e = cudaFuncSetAttribute(k_spec_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
+    if ((e = cudaFuncSetAttribute(k_conv_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
+    if ((e = cudaFuncSetAttribute(k_conv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
+    if ((e = cudaFuncSetAttribute(k_conv_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
+    const int sm2 = (int)spread_smem_bytes();
     if ((e = cudaFuncSetAttribute(k_spread_tiles<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2))) return e;
     if ((e = cudaFuncSetAttribute(k_spread_tiles<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2))) return e;
     if ((e = cudaFuncSetAttribute(k_spread_tiles<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2))) return e;
     if ((e = cudaFuncSetAttribute(k_spread_tiles<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2))) return e;
-    const int64_t T = (int64_t)sh.tiles_max * sh.tiles_max;
-    if ((e = cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(T * 4)))) return e;
-    if ((e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(T * 8)))) return e;
+    // binning: one int (count) or two (count, base) per tile; the most tiles
+    // any supported configuration has is with P = 5 at the largest max_boxes.
+    const int tiles = (kLMax / (2 * 5) + (kTileNodes / 5) - 1) / (kTileNodes / 5);
+    const int bins = tiles * tiles * 4;
+    if ((e = cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, bins))) return e;
+    if ((e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * bins))) return e;
     return cudaSuccess;
 }
 

@@ -10,6 +10,8 @@ constexpr int kLMax = 4096;     // longest FFT line (L = 2 * P * I)
 constexpr int kMaxRadix = 16;   // FFT stages
 constexpr int kTileNodes = 48;  // spread tile edge in nodes (tile = 48/P boxes)
 constexpr int kFieldStride = 8; // floats per grid node in the field array
+constexpr int kSpreadChunk = 2048; // points per spread work item
+constexpr int kMaxTileBoxes = (kTileNodes / 2) * (kTileNodes / 2);  // boxes per spread tile, P >= 2
 
 // Written by k_setup every iteration from the layout bounds.  All integer
 // decisions (I, box) are FP32 and match the oracle's grid rule bit for bit.
@@ -23,12 +25,19 @@ struct GridDev {
     double fx[4], ifx[4];        // fixed-point scale per charge and its inverse (powers of 2)
     double Z;                    // sum_{i != j} 1/(1+d^2), from the grid
     double S;                    // sum of P values
+    float SoZ;                   // S / Z rounded to FP32 (the repulsion scale)
     int32_t nitems;              // spread work items
     int32_t ticket;              // last-block counter for the Z reduction
 };
 
+// Per-iteration scalars of the gradient, precomputed on the host in FP64:
+// g = a_att A - a_rep (S/Z) R + a_cmp X - a_ent E.
 struct Stage {
-    float lambda_kl, lambda_c, lambda_r, exaggeration, momentum, lr;
+    float a_att;  // 4 lambda_KL alpha
+    float a_rep;  // 4 lambda_KL
+    float a_cmp;  // lambda_c / n
+    float a_ent;  // lambda_r / n^2
+    float momentum, lr;
 };
 
 // Device buffers of one gradient/optimize call, carved from the workspace.
@@ -92,6 +101,20 @@ __device__ __forceinline__ void lagrange(float u, float* w)
     }
 }
 
+// Lagrange basis function a alone at local coordinate u.
+template <int P>
+__device__ __forceinline__ float lagrange_one(float u, int a)
+{
+    float num = 1.0f, den = 1.0f;
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+        if (b == a) continue;
+        num *= u - ((float)b + 0.5f);
+        den *= (float)(a - b);
+    }
+    return num / den;
+}
+
 // (x - lo) / s - base to FP32 accuracy of the result itself, although
 // (x - lo) / s can be in the thousands: x - lo is split exactly into
 // d_hi + d_lo (TwoSum), the quotient's remainder d_hi - q s is exact (FMA),
@@ -122,7 +145,7 @@ __device__ __forceinline__ void local_coords(float2 p, const GridDev* G, int& bx
 // grid.cu
 cudaError_t launch_bounds_init(const IterWs& w, const float2* Y, int32_t n, int parity, cudaStream_t s);
 cudaError_t launch_psum(const IterWs& w, const int64_t* P_row, int32_t n, const float* P_val, cudaStream_t s);
-cudaError_t grid_set_smem_attrs(const IterShape& sh);
+cudaError_t grid_set_smem_attrs();
 cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet_params* p, const float2* Y,
                               int parity, bool plain, cudaStream_t s);
 

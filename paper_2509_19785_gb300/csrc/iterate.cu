@@ -24,19 +24,16 @@ namespace lt {
 namespace {
 
 struct Coeffs {
-    float a_att;   // 4 lambda_KL alpha
-    float a_rep;   // 4 lambda_KL S / Z
-    float a_cmp;   // lambda_c / n
-    float a_ent;   // lambda_r / n^2
+    float a_att, a_rep, a_cmp, a_ent;
 };
 
-__device__ __forceinline__ Coeffs coeffs(const GridDev* G, const Stage& st, int32_t n)
+__device__ __forceinline__ Coeffs coeffs(const GridDev* G, const Stage& st)
 {
     Coeffs k;
-    k.a_att = 4.0f * st.lambda_kl * st.exaggeration;
-    k.a_rep = (float)(4.0 * (double)st.lambda_kl * G->S / G->Z);
-    k.a_cmp = (float)((double)st.lambda_c / (double)n);
-    k.a_ent = (float)((double)st.lambda_r / ((double)n * (double)n));
+    k.a_att = st.a_att;
+    k.a_rep = st.a_rep * G->SoZ;
+    k.a_cmp = st.a_cmp;
+    k.a_ent = st.a_ent;
     return k;
 }
 
@@ -180,34 +177,147 @@ __device__ __forceinline__ void block_bounds(float mn, float mx, int32_t* bounds
 }
 
 constexpr int kFusedThreads = 256;
+constexpr int kRowLanes = 8;     // lanes per CSR row in the attraction pass
+constexpr int kWin = 128;        // CSR entries of a row staged per round
+constexpr int kFusedWarps = kFusedThreads / 32;
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Per warp and round: the CSR windows of 4 rows (one per 8-lane group).
+struct RoundBuf {
+    int32_t col[4][kWin];
+    float val[4][kWin];
+};
+
+// Stage the window [eb, eb + kWin) of a row (eb = s0 rounded down to a
+// multiple of 4, so every 16-byte copy is aligned); bytes past the row's end
+// are not read (the copy zero-fills them).
+__device__ __forceinline__ void stage_row(RoundBuf& b, int grp, int gl, const int32_t* __restrict__ P_col,
+                                          const float* __restrict__ P_val, int64_t eb, int64_t e0)
+{
+#pragma unroll
+    for (int u = 0; u < kWin / 32; ++u) {
+        const int j = 32 * u + 4 * gl;
+        const int64_t e = eb + j;
+        const int64_t left = e0 - e;
+        const int bytes = left >= 4 ? 16 : (left > 0 ? (int)left * 4 : 0);
+        const int64_t src = bytes > 0 ? e : 0;
+        cp_async16(&b.col[grp][j], P_col + src, bytes);
+        cp_async16(&b.val[grp][j], P_val + src, bytes);
+    }
+}
+
+// One warp per 32 consecutive vertices.  Attraction (Eq. 6, first term) in 8
+// rounds of 4 rows, one row per 8-lane group; the CSR windows of round r+1 are
+// copied into shared memory (cp.async) while round r gathers its neighbours'
+// coordinates and computes, so HBM streaming does not wait on the gathers.
+// Entries of rows longer than the window are read directly.  Row r's sum goes
+// to lane r, which then finishes its vertex: interpolated repulsion and
+// entropy (gather from the grid), compression, gradient, momentum/gain step,
+// bounds of the next grid.
 template <int P, bool UPDATE>
-__global__ void __launch_bounds__(kFusedThreads)
+__global__ void __launch_bounds__(kFusedThreads, 3)
     k_fused(const int64_t* __restrict__ P_row, const int32_t* __restrict__ P_col, const float* __restrict__ P_val,
             int32_t n, const float2* __restrict__ Y, float2* __restrict__ Ynew, float2* __restrict__ upd,
             float2* __restrict__ gains, const GridDev* __restrict__ G, const float* __restrict__ fields, Stage st,
             int32_t* __restrict__ bounds_next, float2* __restrict__ grad_out, float* __restrict__ parts,
             StatusBlock* status)
 {
-    const int lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
-    const int64_t nnz = P_row[n];
-    const Coeffs k = coeffs(G, st, n);
+    extern __shared__ __align__(16) unsigned char fsm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int grp = lane >> 3, gl = lane & 7;
+    const unsigned gmask = 0xffu << (grp * 8);
+    RoundBuf* rb = (RoundBuf*)fsm + 2 * wib;
+    const Coeffs k = coeffs(G, st);
     float mn = INFINITY, mx = -INFINITY;
-    for (int64_t g0 = ((int64_t)blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; g0 < n;
-         g0 += (int64_t)gridDim.x * wpb * 32) {
+    for (int64_t g0 = ((int64_t)blockIdx.x * kFusedWarps + wib) * 32; g0 < n;
+         g0 += (int64_t)gridDim.x * kFusedWarps * 32) {
         const int64_t row = g0 + lane;
         const bool has = row < n;
         const float2 yi = has ? Y[row] : make_float2(0.f, 0.f);
         const int64_t rs = has ? P_row[row] : 0;
         const int64_t re = has ? P_row[row + 1] : 0;
-        const int nrows = (int)min((int64_t)32, (int64_t)n - g0);
         float2 A = make_float2(0.f, 0.f);
-        for (int rr = 0; rr < nrows; ++rr) {
-            const int64_t s0 = __shfl_sync(FULL, rs, rr), e0 = __shfl_sync(FULL, re, rr);
-            const float xi = __shfl_sync(FULL, yi.x, rr), yv = __shfl_sync(FULL, yi.y, rr);
-            const float2 a = warp_row_attraction(P_col, P_val, nnz, s0, e0, xi, yv, Y, n, lane, status);
-            if (lane == rr) A = a;
+        {
+            const int src = grp;
+            const int64_t s0 = __shfl_sync(FULL, rs, src), e0 = __shfl_sync(FULL, re, src);
+            stage_row(rb[0], grp, gl, P_col, P_val, s0 & ~(int64_t)3, e0);
+            cp_async_commit();
+        }
+#pragma unroll 1
+        for (int rr = 0; rr < 8; ++rr) {
+            const int src = rr * 4 + grp;
+            const int64_t s0 = __shfl_sync(FULL, rs, src), e0 = __shfl_sync(FULL, re, src);
+            const float xi = __shfl_sync(FULL, yi.x, src), yv = __shfl_sync(FULL, yi.y, src);
+            if (rr < 7) {
+                const int nsrc = src + 4;
+                const int64_t ns0 = __shfl_sync(FULL, rs, nsrc), ne0 = __shfl_sync(FULL, re, nsrc);
+                stage_row(rb[(rr + 1) & 1], grp, gl, P_col, P_val, ns0 & ~(int64_t)3, ne0);
+                cp_async_commit();
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            const RoundBuf& b = rb[rr & 1];
+            const int64_t eb = s0 & ~(int64_t)3;
+            float ax = 0.f, ay = 0.f;
+            float2 yj[kWin / 32][4];
+            float pv[kWin / 32][4];
+#pragma unroll
+            for (int u = 0; u < kWin / 32; ++u) {
+                const int j = 32 * u + 4 * gl;
+                const int4 c4 = *(const int4*)&b.col[grp][j];
+                const float4 v4 = *(const float4*)&b.val[grp][j];
+                const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
+                const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int64_t idx = eb + j + q;
+                    const bool in = idx >= s0 && idx < e0;
+                    const bool okc = (unsigned)cc[q] < (unsigned)n;
+                    if (in && !okc) record_error(status, LTSNET_ERR_BAD_GRAPH, cc[q]);
+                    yj[u][q] = (in && okc) ? __ldg(Y + cc[q]) : make_float2(xi, yv);
+                    pv[u][q] = (in && okc) ? vv[q] : 0.f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kWin / 32; ++u)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float dx = xi - yj[u][q].x, dy = yv - yj[u][q].y;
+                    const float w = pv[u][q] * __frcp_rn(1.0f + dx * dx + dy * dy);
+                    ax += w * dx;
+                    ay += w * dy;
+                }
+            // entries past the window (rows longer than it)
+            for (int64_t e = eb + kWin + gl; e < e0; e += kRowLanes) {
+                const int c = __ldg(P_col + e);
+                if ((unsigned)c >= (unsigned)n) {
+                    record_error(status, LTSNET_ERR_BAD_GRAPH, c);
+                    continue;
+                }
+                const float2 q = __ldg(Y + c);
+                const float dx = xi - q.x, dy = yv - q.y;
+                const float w = __ldg(P_val + e) * __frcp_rn(1.0f + dx * dx + dy * dy);
+                ax += w * dx;
+                ay += w * dy;
+            }
+#pragma unroll
+            for (int o = kRowLanes / 2; o > 0; o >>= 1) {
+                ax += __shfl_xor_sync(gmask, ax, o);
+                ay += __shfl_xor_sync(gmask, ay, o);
+            }
+            const float sx = __shfl_sync(FULL, ax, (lane & 3) * 8);
+            const float sy = __shfl_sync(FULL, ay, (lane & 3) * 8);
+            if ((lane >> 2) == rr) A = make_float2(sx, sy);
+            __syncwarp();
         }
         if (has) {
             const Sums F = gather_sums<P>(yi, G, fields);
@@ -233,6 +343,8 @@ __global__ void __launch_bounds__(kFusedThreads)
     }
     if (UPDATE) block_bounds(mn, mx, bounds_next);
 }
+
+constexpr size_t kFusedSmem = sizeof(RoundBuf) * 2 * kFusedWarps;
 
 // ---- plain form ------------------------------------------------------------
 template <int P>
@@ -267,7 +379,7 @@ __global__ void k_plain_update(int32_t n, const float2* __restrict__ Y, float2* 
                                int32_t* __restrict__ bounds_next, float2* __restrict__ grad_out,
                                float* __restrict__ parts, StatusBlock* status)
 {
-    const Coeffs k = coeffs(G, st, n);
+    const Coeffs k = coeffs(G, st);
     float mn = INFINITY, mx = -INFINITY;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float2 p = Y[i];
@@ -353,7 +465,8 @@ cudaError_t launch_point_phase(const int64_t* P_row, const int32_t* P_col, const
     if (!plain) {
         const int nb = fused_blocks(n);
 #define LT_FUSED(PP)                                                                                          \
-    k_fused<PP, UPDATE><<<nb, kFusedThreads, 0, s>>>(P_row, P_col, P_val, n, Y, Ynew, upd, gains, w.g, w.fields, \
+    k_fused<PP, UPDATE><<<nb, kFusedThreads, kFusedSmem, s>>>(P_row, P_col, P_val, n, Y, Ynew, upd, gains, w.g,  \
+                                                              w.fields, \
                                                      st, bn, grad, parts, w.st)
         switch (sh.P) {
             case 2: LT_FUSED(2); break;
@@ -396,13 +509,13 @@ bool params_ok(const ltsnet_params* p)
     return true;
 }
 
-Stage make_stage(const ltsnet_stage& s, float lr)
+Stage make_stage(const ltsnet_stage& s, float lr, int32_t n)
 {
     Stage st;
-    st.lambda_kl = s.lambda_kl;
-    st.lambda_c = s.lambda_c;
-    st.lambda_r = s.lambda_r;
-    st.exaggeration = s.exaggeration;
+    st.a_att = (float)(4.0 * (double)s.lambda_kl * (double)s.exaggeration);
+    st.a_rep = (float)(4.0 * (double)s.lambda_kl);
+    st.a_cmp = (float)((double)s.lambda_c / (double)n);
+    st.a_ent = (float)((double)s.lambda_r / ((double)n * (double)n));
     st.momentum = s.momentum;
     st.lr = lr;
     return st;
@@ -440,14 +553,23 @@ size_t iter_ws_bytes(int32_t n, const ltsnet_params* p)
     return align_up(c.off, 256);
 }
 
-cudaError_t ensure_attrs(const IterShape& sh)
+cudaError_t ensure_attrs()
 {
-    static int done_lmax = -1;
-    if (sh.Lmax <= done_lmax) return cudaSuccess;
-    // Attributes for the largest shape seen so far cover every smaller one.
-    cudaError_t e = grid_set_smem_attrs(sh);
-    if (e == cudaSuccess) done_lmax = sh.Lmax;
-    return e;
+    // Every kernel's dynamic shared-memory limit is raised once to the most
+    // any supported configuration asks for.
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = grid_set_smem_attrs();
+    if (e != cudaSuccess) return e;
+    const int fs = (int)kFusedSmem;
+#define LT_ATTR(PP, UU)                                                                                  \
+    if ((e = cudaFuncSetAttribute(k_fused<PP, UU>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs))) \
+        return e;
+    LT_ATTR(2, true) LT_ATTR(3, true) LT_ATTR(4, true) LT_ATTR(5, true)
+    LT_ATTR(2, false) LT_ATTR(3, false) LT_ATTR(4, false) LT_ATTR(5, false)
+#undef LT_ATTR
+    done = true;
+    return cudaSuccess;
 }
 
 ltsnet_status read_status(StatusBlock* st, cudaStream_t s)
@@ -467,14 +589,14 @@ ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const fl
 {
     const bool plain = (p->flags & LTSNET_FLAG_PLAIN) != 0;
     const float lr = learning_rate(p, n);
-    LT_CUDA(ensure_attrs(sh));
+    LT_CUDA(ensure_attrs());
     LT_CUDA(launch_psum(w, P_row, n, P_val, s));
     LT_CUDA(launch_bounds_init(w, Y, n, 0, s));
     float2* cur = Y;
     float2* nxt = w.yalt;
     for (int32_t i = 0; i < niter; ++i) {
         const int parity = i & 1;
-        const Stage st = make_stage(stage_at(p, (int64_t)t0 + i), lr);
+        const Stage st = make_stage(stage_at(p, (int64_t)t0 + i), lr, n);
         LT_CUDA(launch_grid_phase(w, sh, p, cur, parity, plain, s));
         LT_CUDA(launch_point_phase<true>(P_row, P_col, P_val, n, cur, nxt, upd, gains, w, sh, st, parity, nullptr,
                                          nullptr, plain, s));
@@ -620,9 +742,9 @@ extern "C" ltsnet_status ltsnet_gradient(const int64_t* P_row, const int32_t* P_
     IterWs w;
     ltsnet_status rc = prepare_iter(n, p, ws, ws_bytes, sh, w, s);
     if (rc != LTSNET_OK) return rc;
-    LT_CUDA(ensure_attrs(sh));
+    LT_CUDA(ensure_attrs());
     const bool plain = (p->flags & LTSNET_FLAG_PLAIN) != 0;
-    const Stage st = make_stage(*stage, learning_rate(p, n));
+    const Stage st = make_stage(*stage, learning_rate(p, n), n);
     LT_CUDA(launch_psum(w, P_row, n, P_val, s));
     LT_CUDA(launch_bounds_init(w, (const float2*)Y, n, 0, s));
     LT_CUDA(launch_grid_phase(w, sh, p, (const float2*)Y, 0, plain, s));
