@@ -162,6 +162,26 @@ ltsnet_status ltsnet_symmetrize(const int32_t* nbr, const int32_t* cnt, const do
                                 int64_t* nnz_out, void* ws, size_t ws_bytes, ltsnet_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * ltsnet_symmetrize without a workspace argument (no counterpart in the
+ * paper; an interface for callers that cannot allocate device memory where
+ * they need this step, e.g. while capturing a stream into a CUDA graph, or in
+ * a host that forbids device allocation).  The scratch is a device array
+ * built into the library (about 10.6 MB on every GPU that loads it, held until
+ * the process exits); nothing is allocated by the call.  Limit:
+ * 2 * n * k <= ltsnet_symmetrize_static_max_entries() (2^18); larger inputs
+ * return LTSNET_ERR_WORKSPACE without touching the GPU.  The first call on a
+ * device looks up the array's device address there (cudaGetSymbolAddress),
+ * so make that first call before any stream capture.  All calls share the
+ * array: calls whose GPU work overlaps (other streams or threads) race.
+ * Synchronous, same arguments and results as ltsnet_symmetrize.
+ * ------------------------------------------------------------------------- */
+int64_t ltsnet_symmetrize_static_max_entries(void);
+ltsnet_status ltsnet_symmetrize_static(const int32_t* nbr, const int32_t* cnt, const double* pcond,
+                                       int32_t n, int32_t k,
+                                       int64_t* P_row, int32_t* P_col, float* P_val, int64_t cap,
+                                       int64_t* nnz_out, ltsnet_stream stream);
+
+/* ---------------------------------------------------------------------------
  * One gradient of the tsNET cost at Y (Alg. 3 loop body without the move):
  *   dC/dX_i = 4 lambda_KL (alpha A_i - (S/Z) R_i) + (lambda_c/n) X_i
  *             - (lambda_r/n^2) E_i

@@ -26,7 +26,8 @@ ABI_SYMBOLS = (
     "ltsnet_default_params", "ltsnet_default_stages", "ltsnet_status_string", "ltsnet_last_cuda_error",
     "ltsnet_poll_status",
     "ltsnet_knn_bfs", "ltsnet_calibrate", "ltsnet_symmetrize_max_nnz", "ltsnet_symmetrize_workspace_size",
-    "ltsnet_symmetrize", "ltsnet_gradient_workspace_size", "ltsnet_gradient", "ltsnet_optimize_workspace_size",
+    "ltsnet_symmetrize", "ltsnet_symmetrize_static_max_entries", "ltsnet_symmetrize_static",
+    "ltsnet_gradient_workspace_size", "ltsnet_gradient", "ltsnet_optimize_workspace_size",
     "ltsnet_optimize", "ltsnet_run_workspace_size", "ltsnet_run", "ltsnet_run_host", "ltsnet_launch_count",
     "ltsnet_profile_begin", "ltsnet_profile_end",
 )
@@ -79,6 +80,8 @@ def lib():
         L.ltsnet_symmetrize_workspace_size.argtypes = [i32, i32]
         L.ltsnet_symmetrize_workspace_size.restype = sz
         L.ltsnet_symmetrize.argtypes = [P, P, P, i32, i32, P, P, P, i64, ctypes.POINTER(i64), P, sz, P]
+        L.ltsnet_symmetrize_static_max_entries.restype = i64
+        L.ltsnet_symmetrize_static.argtypes = [P, P, P, i32, i32, P, P, P, i64, ctypes.POINTER(i64), P]
         L.ltsnet_gradient_workspace_size.argtypes = [i32, pp]
         L.ltsnet_gradient_workspace_size.restype = sz
         L.ltsnet_gradient.argtypes = [P, P, P, i32, P, ctypes.POINTER(CStage), pp, P, P, P, P, sz, P]
@@ -93,6 +96,7 @@ def lib():
         L.ltsnet_profile_begin.argtypes = [i32, i32]
         L.ltsnet_profile_end.argtypes = [i32, ctypes.POINTER(f64), ctypes.POINTER(i32)]
         for name in ("ltsnet_poll_status", "ltsnet_knn_bfs", "ltsnet_calibrate", "ltsnet_symmetrize",
+                     "ltsnet_symmetrize_static",
                      "ltsnet_gradient", "ltsnet_optimize", "ltsnet_run", "ltsnet_run_host",
                      "ltsnet_profile_begin", "ltsnet_profile_end"):
             getattr(L, name).restype = i32
@@ -240,6 +244,23 @@ def symmetrize(nbr, cnt, pcond):
     nnz = ctypes.c_int64(0)
     _check(lib().ltsnet_symmetrize(_ptr(nbr), _ptr(cnt), _ptr(pcond), n, k, _ptr(P_row), _ptr(P_col), _ptr(P_val),
                                    cap, ctypes.byref(nnz), _ptr(ws), ws.numel(), _stream()), "ltsnet_symmetrize")
+    m = nnz.value
+    return P_row, P_col[:m].clone(), P_val[:m].clone()
+
+
+def symmetrize_static(nbr, cnt, pcond):
+    """Same as symmetrize() but with the library's built-in scratch array
+    instead of a workspace (for callers that cannot allocate device memory
+    at that point; limit 2 n k <= 2^18).  The outputs are still the caller's."""
+    torch = _torch()
+    n, k = nbr.shape
+    cap = int(lib().ltsnet_symmetrize_max_nnz(n, k))
+    P_row = torch.empty((n + 1,), dtype=torch.int64, device="cuda")
+    P_col = torch.empty((max(cap, 1),), dtype=torch.int32, device="cuda")
+    P_val = torch.empty((max(cap, 1),), dtype=torch.float32, device="cuda")
+    nnz = ctypes.c_int64(0)
+    _check(lib().ltsnet_symmetrize_static(_ptr(nbr), _ptr(cnt), _ptr(pcond), n, k, _ptr(P_row), _ptr(P_col),
+                                          _ptr(P_val), cap, ctypes.byref(nnz), _stream()), "ltsnet_symmetrize_static")
     m = nnz.value
     return P_row, P_col[:m].clone(), P_val[:m].clone()
 
