@@ -83,6 +83,13 @@ typedef struct {
  * instead of the optimised form (box-sorted deterministic spread, fused
  * gather + attraction + compression + update). */
 #define LTSNET_FLAG_PLAIN 1
+/* flags: LTSNET_FLAG_NO_REORDER keeps the input's vertex numbering inside
+ * ltsnet_run / ltsnet_run_host.  By default those calls renumber the vertices
+ * in breadth-first order (Cuthill-McKee) after the partial BFS, so that the
+ * attraction pass reads neighbour coordinates from nearby memory; the result
+ * is returned in the input's numbering and differs only in floating-point
+ * summation order.  Graphs with more than 4096 BFS levels are not renumbered. */
+#define LTSNET_FLAG_NO_REORDER 2
 
 /* Largest supported k (partial BFS neighbours per vertex). */
 #define LTSNET_MAX_K 4096
@@ -180,6 +187,21 @@ ltsnet_status ltsnet_symmetrize_static(const int32_t* nbr, const int32_t* cnt, c
                                        int32_t n, int32_t k,
                                        int64_t* P_row, int32_t* P_col, float* P_val, int64_t cap,
                                        int64_t* nnz_out, ltsnet_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Breadth-first vertex renumbering (a memory-locality aid; no counterpart in
+ * the paper).  order[new] = old in the discovery order of a FIFO BFS that
+ * scans adjacency lists in stored order, starting at vertex 0 and restarting
+ * at the smallest unvisited vertex for each further component; inv is the
+ * inverse.  *reordered (host) = 0 and order/inv untouched if the graph has
+ * more than 4096 BFS levels.  Synchronous.  ltsnet_run applies it internally
+ * unless LTSNET_FLAG_NO_REORDER is set; callers of ltsnet_optimize can apply
+ * it to their own P (relabel rows and columns) for the same effect.
+ * ------------------------------------------------------------------------- */
+size_t ltsnet_bfs_order_workspace_size(int32_t n);
+ltsnet_status ltsnet_bfs_order(const int64_t* row_ptr, const int32_t* col, int32_t n,
+                               int32_t* order, int32_t* inv, int32_t* reordered,
+                               void* ws, size_t ws_bytes, ltsnet_stream stream);
 
 /* ---------------------------------------------------------------------------
  * One gradient of the tsNET cost at Y (Alg. 3 loop body without the move):

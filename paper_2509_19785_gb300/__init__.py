@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libltsnet.so")
 OK = 0
 WARN_NOT_CONVERGED = 1
 FLAG_PLAIN = 1
+FLAG_NO_REORDER = 2
 MAX_K = 4096
 KERNEL_FUSED_UPDATE, KERNEL_SPREAD, KERNEL_CONV = 1, 2, 3
 
@@ -27,7 +28,7 @@ ABI_SYMBOLS = (
     "ltsnet_poll_status",
     "ltsnet_knn_bfs", "ltsnet_calibrate", "ltsnet_symmetrize_max_nnz", "ltsnet_symmetrize_workspace_size",
     "ltsnet_symmetrize", "ltsnet_symmetrize_static_max_entries", "ltsnet_symmetrize_static",
-    "ltsnet_gradient_workspace_size", "ltsnet_gradient", "ltsnet_optimize_workspace_size",
+    "ltsnet_bfs_order_workspace_size", "ltsnet_bfs_order", "ltsnet_gradient_workspace_size", "ltsnet_gradient", "ltsnet_optimize_workspace_size",
     "ltsnet_optimize", "ltsnet_run_workspace_size", "ltsnet_run", "ltsnet_run_host", "ltsnet_launch_count",
     "ltsnet_profile_begin", "ltsnet_profile_end",
 )
@@ -82,6 +83,9 @@ def lib():
         L.ltsnet_symmetrize.argtypes = [P, P, P, i32, i32, P, P, P, i64, ctypes.POINTER(i64), P, sz, P]
         L.ltsnet_symmetrize_static_max_entries.restype = i64
         L.ltsnet_symmetrize_static.argtypes = [P, P, P, i32, i32, P, P, P, i64, ctypes.POINTER(i64), P]
+        L.ltsnet_bfs_order_workspace_size.argtypes = [i32]
+        L.ltsnet_bfs_order_workspace_size.restype = sz
+        L.ltsnet_bfs_order.argtypes = [P, P, i32, P, P, ctypes.POINTER(i32), P, sz, P]
         L.ltsnet_gradient_workspace_size.argtypes = [i32, pp]
         L.ltsnet_gradient_workspace_size.restype = sz
         L.ltsnet_gradient.argtypes = [P, P, P, i32, P, ctypes.POINTER(CStage), pp, P, P, P, P, sz, P]
@@ -96,7 +100,7 @@ def lib():
         L.ltsnet_profile_begin.argtypes = [i32, i32]
         L.ltsnet_profile_end.argtypes = [i32, ctypes.POINTER(f64), ctypes.POINTER(i32)]
         for name in ("ltsnet_poll_status", "ltsnet_knn_bfs", "ltsnet_calibrate", "ltsnet_symmetrize",
-                     "ltsnet_symmetrize_static",
+                     "ltsnet_symmetrize_static", "ltsnet_bfs_order",
                      "ltsnet_gradient", "ltsnet_optimize", "ltsnet_run", "ltsnet_run_host",
                      "ltsnet_profile_begin", "ltsnet_profile_end"):
             getattr(L, name).restype = i32
@@ -151,6 +155,7 @@ class Params:
     beta_tol: float = 1e-5
     stages: list = field(default_factory=lambda: None)
     plain: bool = False
+    reorder: bool = True
 
     @property
     def k(self) -> int:
@@ -164,7 +169,8 @@ class Params:
         arr = (CStage * max(1, len(st)))(*[s.to_c() for s in st])
         p = CParams(self.perplexity, self.eps, self.nodes_per_box, self.box_width_max, self.min_boxes,
                     self.max_boxes, self.learning_rate, self.beta_max_steps, self.beta_tol, len(st),
-                    ctypes.cast(arr, ctypes.POINTER(CStage)), FLAG_PLAIN if self.plain else 0)
+                    ctypes.cast(arr, ctypes.POINTER(CStage)),
+                    (FLAG_PLAIN if self.plain else 0) | (0 if self.reorder else FLAG_NO_REORDER))
         p._keep = arr  # keep the stage array alive with the struct
         return p
 
@@ -263,6 +269,22 @@ def symmetrize_static(nbr, cnt, pcond):
                                           _ptr(P_val), cap, ctypes.byref(nnz), _stream()), "ltsnet_symmetrize_static")
     m = nnz.value
     return P_row, P_col[:m].clone(), P_val[:m].clone()
+
+
+def bfs_order(row_ptr, col):
+    """Breadth-first renumbering.  Returns (order, inv, reordered): order[new]
+    = old, inv[old] = new (int32 CUDA tensors)."""
+    torch = _torch()
+    row_ptr = _dev(row_ptr, torch.int64)
+    col = _dev(col, torch.int32)
+    n = row_ptr.numel() - 1
+    order = torch.empty((n,), dtype=torch.int32, device="cuda")
+    inv = torch.empty((n,), dtype=torch.int32, device="cuda")
+    ws = _workspace(lib().ltsnet_bfs_order_workspace_size(n))
+    r = ctypes.c_int32(0)
+    _check(lib().ltsnet_bfs_order(_ptr(row_ptr), _ptr(col), n, _ptr(order), _ptr(inv), ctypes.byref(r), _ptr(ws),
+                                  ws.numel(), _stream()), "ltsnet_bfs_order")
+    return order, inv, bool(r.value)
 
 
 def affinities(row_ptr, col, perplexity: float, tol: float = 1e-5, max_steps: int = 100):

@@ -132,7 +132,16 @@ __device__ void compute_grid(const int32_t* bounds, float bwm, int min_boxes, in
     g.P = P;
     g.M = I * P;
     g.L = 2 * g.M;
-    g.tb = kTileNodes / P;
+    // Spread tiles of tb x tb boxes: about kSpreadChunk points per tile at the
+    // mean density, at most kMaxTiles tiles per dimension, at most 8 boxes
+    // per dimension unless the tile count forces more.
+    {
+        const double per_box = (double)n / ((double)I * (double)I);
+        int tb = (int)floor(sqrt((double)kSpreadChunk / (per_box > 1e-9 ? per_box : 1e-9)));
+        tb = tb < 1 ? 1 : (tb > 8 ? 8 : tb);
+        const int tmin = (I + kMaxTiles - 1) / kMaxTiles;
+        g.tb = tb < tmin ? tmin : tb;
+    }
     g.tiles = (I + g.tb - 1) / g.tb;
     int r = g.L, k = 0;
     while (r % 4 == 0) { g.radix[k++] = 4; r /= 4; }
@@ -172,9 +181,17 @@ __global__ void k_setup(const int32_t* __restrict__ bounds_cur, int32_t* __restr
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = tid; t < g.L; t += nth) {
-        double sn, cs;
-        sincospi(-2.0 * (double)t / (double)g.L, &sn, &cs);
-        tw[t] = make_float2((float)cs, (float)sn);
+        // e^{-2 pi i t/L} = (-i)^q e^{-(pi/2) i r/L} with 4t = q L + r, 0 <= r < L:
+        // the reduced argument r/L is in [0, 1) and correctly rounded.
+        const int q = (int)((4 * t) / g.L), r = (int)(4 * t - (int64_t)q * g.L);
+        float sn, cs;
+        sincospif(-0.5f * ((float)r / (float)g.L), &sn, &cs);
+        float2 v;
+        if (q == 0) v = make_float2(cs, sn);
+        else if (q == 1) v = make_float2(sn, -cs);
+        else if (q == 2) v = make_float2(-cs, -sn);
+        else v = make_float2(-sn, cs);
+        tw[t] = v;
     }
     for (int64_t t = tid; t < (int64_t)g.tiles * g.tiles; t += nth) tile_cnt[t] = 0;
 }
@@ -301,24 +318,28 @@ __global__ void k_bin_scatter(const float2* __restrict__ Y, int32_t n, const Gri
 }
 
 // One work item = one tile of tb x tb boxes and up to kSpreadChunk of its
-// points.  The points are counting-sorted by box in shared memory (their
-// local coordinates computed once on the way); then each thread takes one
-// node row b of a contiguous slice of the sorted points and accumulates that
-// row's P nodes x 4 charges in 64-bit fixed point in registers, adding them
-// to the global fixed-point grid only when the box changes.  Integer sums do
-// not depend on order, so the grid is the same bit for bit from run to run.
+// points (tiles are sized for about one item at the mean density).  The
+// points are counting-sorted by box in shared memory, their local
+// coordinates computed once on the way.  Each thread then takes one node row
+// of a contiguous slice of the sorted points and accumulates that row's P
+// nodes x 4 charges in 64-bit fixed point in registers, adding them into a
+// shared-memory tile when the box changes; the tile is stored to the global
+// fixed-point grid (added atomically when a dense tile has several items).
+// Integer sums do not depend on order, so the grid is the same bit for bit
+// from run to run.
 template <int P>
 __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__ binned, const GridDev* __restrict__ G,
                                                       const int4* __restrict__ items, long long* __restrict__ wfix)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int M = G->M, I = G->I, tb = G->tb, tiles = G->tiles, Pg = G->P;
+    const int M = G->M, I = G->I, tb = G->tb, tiles = G->tiles;
     const float lo = G->lo, h = G->h, s = G->s;
-    const int NB = tb * tb;
-    float2* su = (float2*)smraw;          // kSpreadChunk local coordinates (sorted by box)
-    int* slb = (int*)(su + kSpreadChunk);  // kSpreadChunk boxes (sorted)
-    int* off = slb + kSpreadChunk;         // NB + 1
-    int* cur = off + kMaxTileBoxes + 1;    // NB
+    const int NB = tb * tb, TN = tb * P;
+    long long* acc = (long long*)smraw;                      // TN * TN * 4
+    float2* su = (float2*)(acc + kMaxTileNodes * kMaxTileNodes * 4);  // kSpreadChunk
+    int* slb = (int*)(su + kSpreadChunk);                    // kSpreadChunk
+    int* off = slb + kSpreadChunk;                           // NB + 1
+    int* cur = off + kMaxTileBoxes + 1;                      // NB
     float fx[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) fx[q] = (float)G->fx[q];
@@ -329,6 +350,7 @@ __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__
         const int tx = item.x % tiles, ty = item.x / tiles;
         const int bx0 = tx * tb, by0 = ty * tb;
         const int cnt = item.z - item.y;
+        for (int i = threadIdx.x; i < TN * TN * 4; i += blockDim.x) acc[i] = 0;
         for (int i = threadIdx.x; i < NB; i += blockDim.x) cur[i] = 0;
         __syncthreads();
         for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
@@ -362,7 +384,7 @@ __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__
             const int bx = box_of(p.x, lo, h, I), by = box_of(p.y, lo, h, I);
             const int lb = (by - by0) * tb + (bx - bx0);
             const int pos = atomicAdd(&cur[lb], 1);
-            su[pos] = make_float2(local_u(p.x, lo, s, Pg * bx), local_u(p.y, lo, s, Pg * by));
+            su[pos] = make_float2(local_u(p.x, lo, s, P * bx), local_u(p.y, lo, s, P * by));
             slb[pos] = lb;
         }
         __syncthreads();
@@ -376,9 +398,8 @@ __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__
                 const int lb = q < q1 ? slb[q] : -2;
                 if (lb != cur_lb) {
                     if (cur_lb >= 0) {
-                        const int gy = (by0 + cur_lb / tb) * P + bb;
-                        const int gx0 = (bx0 + cur_lb % tb) * P;
-                        long long* dst = wfix + ((int64_t)gy * M + gx0) * 4;
+                        const int ly = (cur_lb / tb) * P + bb, lx0 = (cur_lb % tb) * P;
+                        long long* dst = acc + (ly * TN + lx0) * 4;
 #pragma unroll
                         for (int a = 0; a < P; ++a)
 #pragma unroll
@@ -408,6 +429,18 @@ __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__
                     ra[a][3] += __float2ll_rn((w * (ex * ex + ey * ey)) * fx[3]);
                 }
             }
+        }
+        __syncthreads();
+        const bool single = item.w != 0;
+        for (int i = threadIdx.x; i < TN * TN * 4; i += blockDim.x) {
+            const long long v = acc[i];
+            if (v == 0) continue;
+            const int node = i >> 2, ch = i & 3;
+            const int gy = by0 * P + node / TN, gx = bx0 * P + node % TN;
+            if (gy >= M || gx >= M) continue;
+            long long* dst = wfix + ((int64_t)gy * M + gx) * 4 + ch;
+            if (single) *dst = v;
+            else atomicAdd((unsigned long long*)dst, (unsigned long long)v);
         }
         __syncthreads();
     }
@@ -949,7 +982,8 @@ constexpr int kPsumBlocks = 304;
 // their boxes, box offsets and cursors.
 size_t spread_smem_bytes()
 {
-    return (size_t)kSpreadChunk * (sizeof(float2) + sizeof(int)) + (size_t)(2 * kMaxTileBoxes + 1) * sizeof(int);
+    return (size_t)kMaxTileNodes * kMaxTileNodes * 4 * sizeof(long long) +
+           (size_t)kSpreadChunk * (sizeof(float2) + sizeof(int)) + (size_t)(2 * kMaxTileBoxes + 1) * sizeof(int);
 }
 
 // Room for the twiddles plus six lines of the longest length (the column
@@ -966,9 +1000,8 @@ IterShape iter_shape(int32_t n, const ltsnet_params* p)
     sh.max_boxes = p->max_boxes;
     sh.Mmax = p->max_boxes * p->nodes_per_box;
     sh.Lmax = 2 * sh.Mmax;
-    const int tb = kTileNodes / sh.P;
-    sh.tiles_max = (p->max_boxes + tb - 1) / tb;
-    sh.items_max = (int64_t)sh.tiles_max * sh.tiles_max + (int64_t)n / 1024 + 2;
+    sh.tiles_max = kMaxTiles;
+    sh.items_max = (int64_t)kMaxTiles * kMaxTiles + (int64_t)n / kSpreadChunk + 2;
     return sh;
 }
 
@@ -1095,10 +1128,8 @@ cudaError_t grid_set_smem_attrs()
     if ((e = cudaFuncSetAttribute(k_spread_tiles<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2))) return e;
     if ((e = cudaFuncSetAttribute(k_spread_tiles<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2))) return e;
     if ((e = cudaFuncSetAttribute(k_spread_tiles<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2))) return e;
-    // binning: one int (count) or two (count, base) per tile; the most tiles
-    // any supported configuration has is with P = 5 at the largest max_boxes.
-    const int tiles = (kLMax / (2 * 5) + (kTileNodes / 5) - 1) / (kTileNodes / 5);
-    const int bins = tiles * tiles * 4;
+    // binning: one int (count) or two (count, base) per tile
+    const int bins = kMaxTiles * kMaxTiles * 4;
     if ((e = cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, bins))) return e;
     if ((e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * bins))) return e;
     return cudaSuccess;

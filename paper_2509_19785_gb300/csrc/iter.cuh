@@ -8,10 +8,14 @@ namespace lt {
 
 constexpr int kLMax = 4096;     // longest FFT line (L = 2 * P * I)
 constexpr int kMaxRadix = 16;   // FFT stages
-constexpr int kTileNodes = 48;  // spread tile edge in nodes (tile = 48/P boxes)
 constexpr int kFieldStride = 8; // floats per grid node in the field array
 constexpr int kSpreadChunk = 2048; // points per spread work item
-constexpr int kMaxTileBoxes = (kTileNodes / 2) * (kTileNodes / 2);  // boxes per spread tile, P >= 2
+constexpr int kMaxTiles = 64;        // spread tiles per dimension (at most)
+// Boxes per spread tile edge: at most 8, or ceil(I / kMaxTiles) when larger;
+// I <= kLMax / (2P) bounds that by 16 (P = 2), so tiles have at most 256
+// boxes and at most 40 nodes per edge (P = 5: 8 boxes).
+constexpr int kMaxTileBoxes = 256;
+constexpr int kMaxTileNodes = 40;
 
 // Written by k_setup every iteration from the layout bounds.  All integer
 // decisions (I, box) are FP32 and match the oracle's grid rule bit for bit.
@@ -141,6 +145,15 @@ __device__ __forceinline__ void local_coords(float2 p, const GridDev* G, int& bx
     ux = local_u(p.x, lo, s, P * bx);
     uy = local_u(p.y, lo, s, P * by);
 }
+
+// order.cu
+size_t order_ws_bytes(int32_t n);
+cudaError_t bfs_order(const int64_t* row_ptr, const int32_t* col, int32_t n, int32_t* order, int32_t* inv, void* ws,
+                      cudaStream_t s, bool* reordered);
+cudaError_t permute_conditional_rows(const int32_t* order, const int32_t* inv, const int32_t* nbr,
+                                     const double* pcond, const int32_t* cnt, int32_t n, int32_t k, int32_t* nbr2,
+                                     double* pcond2, int32_t* cnt2, cudaStream_t s);
+cudaError_t gather_rows2(const float2* src, const int32_t* idx, int32_t n, float2* dst, cudaStream_t s);
 
 // grid.cu
 cudaError_t launch_bounds_init(const IterWs& w, const float2* Y, int32_t n, int parity, cudaStream_t s);

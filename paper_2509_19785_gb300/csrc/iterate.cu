@@ -624,6 +624,14 @@ struct RunWs {
     int64_t* row_ptr;  // host-input copies (ltsnet_run_host)
     int32_t* col;
     float2* Y;
+    int32_t* order;    // breadth-first renumbering: order[new] = old, inv[old] = new
+    int32_t* inv;
+    int32_t* nbr2;     // conditional rows in the new numbering
+    double* pcond2;
+    int32_t* cnt2;
+    float2* Y2;
+    void* ord;
+    size_t ord_bytes;
     void* sym;
     size_t sym_bytes;
     void* iter;
@@ -652,6 +660,14 @@ RunWs run_carve(Carve& c, int32_t n, int64_t m2, const ltsnet_params* p, bool ho
     r.row_ptr = host_inputs ? c.take<int64_t>((int64_t)n + 1) : nullptr;
     r.col = host_inputs ? c.take<int32_t>(m2) : nullptr;
     r.Y = host_inputs ? c.take<float2>(n) : nullptr;
+    r.order = c.take<int32_t>(n);
+    r.inv = c.take<int32_t>(n);
+    r.nbr2 = c.take<int32_t>(nk);
+    r.pcond2 = c.take<double>(nk);
+    r.cnt2 = c.take<int32_t>(n);
+    r.Y2 = c.take<float2>(n);
+    r.ord_bytes = order_ws_bytes(n);
+    r.ord = c.take<char>(r.ord_bytes);
     r.sym_bytes = ltsnet_symmetrize_workspace_size(n, k);
     r.sym = c.take<char>(r.sym_bytes);
     r.iter_bytes = iter_ws_bytes(n, p);
@@ -671,9 +687,20 @@ ltsnet_status run_core(const int64_t* row_ptr, const int32_t* col, int32_t n, co
     k_count_unconverged<<<flat_blocks(n), 256, 0, s>>>(r.conv, r.cnt, n, r.st);
     count_launches(1);
     LT_CHECK_LAUNCH();
+    // Breadth-first renumbering for locality of the neighbour gathers: the
+    // conditional rows are relabelled before symmetrisation, so P is built
+    // directly in the new numbering; the layout is permuted in and out.
+    bool reordered = false;
+    if (!(p->flags & LTSNET_FLAG_NO_REORDER)) LT_CUDA(bfs_order(row_ptr, col, n, r.order, r.inv, r.ord, s, &reordered));
     int64_t nnz = 0;
-    rc = ltsnet_symmetrize(r.nbr, r.cnt, r.pcond, n, k, r.P_row, r.P_col, r.P_val, 2 * (int64_t)n * k, &nnz, r.sym,
-                           r.sym_bytes, s);
+    if (reordered) {
+        LT_CUDA(permute_conditional_rows(r.order, r.inv, r.nbr, r.pcond, r.cnt, n, k, r.nbr2, r.pcond2, r.cnt2, s));
+        rc = ltsnet_symmetrize(r.nbr2, r.cnt2, r.pcond2, n, k, r.P_row, r.P_col, r.P_val, 2 * (int64_t)n * k, &nnz,
+                               r.sym, r.sym_bytes, s);
+    } else {
+        rc = ltsnet_symmetrize(r.nbr, r.cnt, r.pcond, n, k, r.P_row, r.P_col, r.P_val, 2 * (int64_t)n * k, &nnz,
+                               r.sym, r.sym_bytes, s);
+    }
     if (rc != LTSNET_OK) return rc;
     k_init_state<<<flat_blocks(n), 256, 0, s>>>(r.upd, r.gains, n);
     count_launches(1);
@@ -685,8 +712,14 @@ ltsnet_status run_core(const int64_t* row_ptr, const int32_t* col, int32_t n, co
     LT_CUDA(cudaMemsetAsync(w.wfix, 0, sizeof(long long) * 4 * (size_t)sh.Mmax * sh.Mmax, s));
     LT_CUDA(cudaMemsetAsync(w.wflt, 0, sizeof(float4) * (size_t)sh.Mmax * sh.Mmax, s));
     const int64_t total = schedule_length(p);
-    rc = optimize_core(r.P_row, r.P_col, r.P_val, n, p, Y, r.upd, r.gains, 0, (int32_t)total, w, sh, s);
+    float2* Yw = Y;
+    if (reordered) {
+        LT_CUDA(gather_rows2(Y, r.order, n, r.Y2, s));
+        Yw = r.Y2;
+    }
+    rc = optimize_core(r.P_row, r.P_col, r.P_val, n, p, Yw, r.upd, r.gains, 0, (int32_t)total, w, sh, s);
     if (rc != LTSNET_OK) return rc;
+    if (reordered) LT_CUDA(gather_rows2(r.Y2, r.inv, n, Y, s));
     ltsnet_status a = read_status(w.st, s);
     ltsnet_status b = read_status(r.st, s);
     if (a < 0) return a;

@@ -204,3 +204,51 @@ def test_run_host_matches_device(ltlib, grid32):
     Yh = Y0.copy()
     ltlib.run_host(g.row_ptr, g.col, Yh, params)
     assert np.array_equal(Yd.cpu().numpy(), Yh)
+
+
+def _scipy_order(g):
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import breadth_first_order
+
+    A = csr_matrix((np.ones(g.col.shape[0]), g.col, g.row_ptr), shape=(g.n, g.n))
+    seen = np.zeros(g.n, bool)
+    out = []
+    for s in range(g.n):
+        if seen[s]:
+            continue
+        o = breadth_first_order(A, s, directed=True, return_predecessors=False)
+        seen[o] = True
+        out.append(o)
+    return np.concatenate(out)
+
+
+@pytest.mark.parametrize("gname", ["grid", "islands", "tree", "rgg"])
+def test_bfs_order_is_fifo_discovery_order(ltlib, gname):
+    """The renumbering is the discovery order of a FIFO BFS (scipy's
+    breadth_first_order), restarted at the smallest unvisited vertex."""
+    g = {"grid": synth.grid2d(40, 25),
+         "islands": synth.csr_from_edges(60, np.array([5, 6, 7, 30, 31, 40]), np.array([6, 7, 8, 31, 32, 41])),
+         "tree": synth.random_recursive_tree(5000, 3), "rgg": synth.rgg(20000, seed=7, lcc=False)}[gname]
+    order, inv, reordered = ltlib.bfs_order(g.row_ptr, g.col)
+    assert reordered
+    order = order.cpu().numpy()
+    inv = inv.cpu().numpy()
+    assert np.array_equal(order, _scipy_order(g))
+    assert np.array_equal(inv[order], np.arange(g.n))
+
+
+def test_run_with_and_without_reordering(ltlib, grid32):
+    """Renumbering changes only the floating-point summation order: the final
+    costs of the two runs agree within 1%."""
+    import torch
+
+    g, P, Pn = grid32
+    Y0 = synth.initial_layout(g.n, 5)
+    a, _ = ltlib.run(g.row_ptr, g.col, torch.from_numpy(Y0), ltlib.Params(stages=ltlib.default_stages(600)))
+    b, _ = ltlib.run(g.row_ptr, g.col, torch.from_numpy(Y0),
+                     ltlib.Params(stages=ltlib.default_stages(600), reorder=False))
+    st = oracle.default_stages(600)[-1]
+    Pv = Pn[2].astype(np.float64)
+    ca, _ = oracle.exact_cost(a.cpu().numpy().astype(np.float64), Pn[0], Pn[1], Pv, st)
+    cb, _ = oracle.exact_cost(b.cpu().numpy().astype(np.float64), Pn[0], Pn[1], Pv, st)
+    assert abs(ca - cb) / abs(cb) < 0.01, (ca, cb)
