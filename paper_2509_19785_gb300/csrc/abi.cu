@@ -40,6 +40,40 @@ void note_cuda_error(cudaError_t e, const char* where)
     snprintf(g_err, sizeof(g_err), "%s (%s) at %s", cudaGetErrorName(e), cudaGetErrorString(e), where);
 }
 
+bool profiling_active()
+{
+    std::lock_guard<std::mutex> lk(g_probe_mu);
+    for (int k = 1; k <= 3; ++k)
+        if (g_probe[k].on) return true;
+    return false;
+}
+
+namespace {
+std::mutex g_aux_mu;
+AuxStreams g_aux[64];
+}  // namespace
+
+// Internal non-blocking streams and events of the current device, created on
+// first use (they carry the kernel-spectrum branch and graph capture).
+cudaError_t aux_streams(AuxStreams** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_aux_mu);
+    AuxStreams& a = g_aux[dev];
+    if (!a.ready) {
+        if ((e = cudaStreamCreateWithFlags(&a.branch, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaStreamCreateWithFlags(&a.capture, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming)) != cudaSuccess) return e;
+        a.ready = true;
+    }
+    *out = &a;
+    return cudaSuccess;
+}
+
 void profile_start(int32_t kernel, cudaStream_t s)
 {
     if (kernel < 1 || kernel > 3) return;

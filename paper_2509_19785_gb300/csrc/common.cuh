@@ -53,6 +53,14 @@ __device__ __forceinline__ unsigned lanemask_lt()
 void count_launches(int64_t k);
 // Host: remember the last failing CUDA call of this thread (ltsnet_last_cuda_error).
 void note_cuda_error(cudaError_t e, const char* where);
+// Host: internal streams/events of a device (abi.cu).
+struct AuxStreams {
+    bool ready = false;
+    cudaStream_t branch = nullptr, capture = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+cudaError_t aux_streams(AuxStreams** out);
+bool profiling_active();
 // Host: per-kernel event timing hooks (no-ops unless profiling is enabled).
 void profile_start(int32_t kernel, cudaStream_t s);
 void profile_stop(int32_t kernel, cudaStream_t s);

@@ -16,13 +16,13 @@
 //
 //  k_setup        grid rule from the layout bounds (FP32, same decisions as
 //                 the oracle), FFT plan and twiddles, fixed-point scales.
-//  k_bin_count    points -> spread tiles (48x48 nodes), counts per tile.
-//  k_bin_plan     tile offsets and work items (tile, point range).
-//  k_bin_scatter  points copied into their tile's range.
-//  k_spread_tiles per work item: Lagrange weights x charges accumulated in a
-//                 shared-memory tile as 64-bit fixed point (integer sums are
-//                 order independent, so the grid is bit-identical from run to
-//                 run), then flushed to the global fixed-point grid.
+//  k_box_count    points per box (warp-aggregated atomics).
+//  k_box_scan     box offsets (one block).
+//  k_box_scatter  local coordinates and boxes of the points, in box order.
+//  k_box_spread   per run of 32 box-sorted points and node row: Lagrange
+//                 weights x charges summed in 64-bit fixed point (integer sums
+//                 are order independent, so the grid is bit-identical from run
+//                 to run), added to the global fixed-point grid per box.
 //  k_spread_atomic  the plain form: FP32 atomics straight into the grid.
 //  k_spec_rows/cols 2-D FFTs of the kernels (K2, Ke, K1 even; K2 dx, Ke dx
 //                 odd), three packed complex transforms, half spectra kept.
@@ -132,17 +132,6 @@ __device__ void compute_grid(const int32_t* bounds, float bwm, int min_boxes, in
     g.P = P;
     g.M = I * P;
     g.L = 2 * g.M;
-    // Spread tiles of tb x tb boxes: about kSpreadChunk points per tile at the
-    // mean density, at most kMaxTiles tiles per dimension, at most 8 boxes
-    // per dimension unless the tile count forces more.
-    {
-        const double per_box = (double)n / ((double)I * (double)I);
-        int tb = (int)floor(sqrt((double)kSpreadChunk / (per_box > 1e-9 ? per_box : 1e-9)));
-        tb = tb < 1 ? 1 : (tb > 8 ? 8 : tb);
-        const int tmin = (I + kMaxTiles - 1) / kMaxTiles;
-        g.tb = tb < tmin ? tmin : tb;
-    }
-    g.tiles = (I + g.tb - 1) / g.tb;
     int r = g.L, k = 0;
     while (r % 4 == 0) { g.radix[k++] = 4; r /= 4; }
     while (r % 2 == 0) { g.radix[k++] = 2; r /= 2; }
@@ -161,7 +150,7 @@ __device__ void compute_grid(const int32_t* bounds, float bwm, int min_boxes, in
 }
 
 __global__ void k_setup(const int32_t* __restrict__ bounds_cur, int32_t* __restrict__ bounds_next, GridDev* G,
-                        float2* __restrict__ tw, int32_t* __restrict__ tile_cnt, int32_t n, float bwm, int min_boxes,
+                        float2* __restrict__ tw, int32_t* __restrict__ bcnt, int32_t n, float bwm, int min_boxes,
                         int max_boxes, int P)
 {
     __shared__ GridDev g;
@@ -169,12 +158,11 @@ __global__ void k_setup(const int32_t* __restrict__ bounds_cur, int32_t* __restr
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         G->lo = g.lo; G->hi = g.hi; G->ext = g.ext; G->h = g.h; G->s = g.s; G->c = g.c;
-        G->I = g.I; G->M = g.M; G->L = g.L; G->P = g.P; G->tb = g.tb; G->tiles = g.tiles;
+        G->I = g.I; G->M = g.M; G->L = g.L; G->P = g.P;
         G->nst = g.nst;
         for (int i = 0; i < kMaxRadix; ++i) G->radix[i] = i < g.nst ? g.radix[i] : 0;
         for (int c = 0; c < 4; ++c) { G->fx[c] = g.fx[c]; G->ifx[c] = g.ifx[c]; }
         G->ticket = 0;
-        G->nitems = 0;
         bounds_next[0] = f2ord(INFINITY);
         bounds_next[1] = f2ord(-INFINITY);
     }
@@ -193,256 +181,261 @@ __global__ void k_setup(const int32_t* __restrict__ bounds_cur, int32_t* __restr
         else v = make_float2(-sn, cs);
         tw[t] = v;
     }
-    for (int64_t t = tid; t < (int64_t)g.tiles * g.tiles; t += nth) tile_cnt[t] = 0;
+    for (int64_t t = tid; t < (int64_t)g.I * g.I; t += nth) bcnt[t] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        G->nheavy = 0;
+        G->scan_ticket = 0;
+    }
 }
 
-__global__ void k_bin_count(const float2* __restrict__ Y, int32_t n, const GridDev* __restrict__ G,
-                            int32_t* __restrict__ tile_cnt)
+// ---- deterministic spread: box sort, then one owner per box ----
+// The Lagrange nodes a point feeds are those of its own box, so every node's
+// charges are sums over one box's points.  The points are counted per box
+// (warp-aggregated atomics), the counts scanned, and the points scattered
+// into box order with their local coordinates.  Then each box is summed by a
+// single owner -- a thread per (box, node row) for boxes of at most
+// kLightMax points, a warp per box for the rest -- in 64-bit fixed point,
+// whose sums do not depend on the order of the points within the box.  The
+// owner writes its nodes' final FP32 charges: every node is written every
+// iteration, with no atomics on the grid and no clearing pass, and the grid
+// is bit-identical from run to run.
+
+constexpr int kScanBlock = 1024;  // boxes per block of the box scan
+constexpr int kLightMax = 32;     // boxes with more points are summed by a warp
+
+__global__ void k_box_count(const float2* __restrict__ Y, int32_t n, const GridDev* __restrict__ G,
+                            int32_t* __restrict__ bcnt)
 {
-    extern __shared__ int32_t sh[];
     const float lo = G->lo, h = G->h;
-    const int I = G->I, tb = G->tb, tiles = G->tiles, T = tiles * tiles;
-    for (int t = threadIdx.x; t < T; t += blockDim.x) sh[t] = 0;
-    __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float2 p = Y[i];
-        const int bx = box_of(p.x, lo, h, I), by = box_of(p.y, lo, h, I);
-        atomicAdd(&sh[(by / tb) * tiles + bx / tb], 1);
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < T; t += blockDim.x)
-        if (sh[t]) atomicAdd(&tile_cnt[t], sh[t]);
-}
-
-// Single block: exclusive scan of the tile counts and the work-item list.
-__global__ void k_bin_plan(GridDev* G, const int32_t* __restrict__ tile_cnt, int32_t* __restrict__ tile_off,
-                           int32_t* __restrict__ tile_cur, int4* __restrict__ items, int32_t chunk)
-{
-    __shared__ int32_t wsum[33];
-    __shared__ int32_t carry_pts, carry_items;
-    const int T = G->tiles * G->tiles;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) {
-        carry_pts = 0;
-        carry_items = 0;
-    }
-    __syncthreads();
-    for (int t0 = 0; t0 < T; t0 += blockDim.x) {
-        const int t = t0 + threadIdx.x;
-        const int c = t < T ? tile_cnt[t] : 0;
-        const int ni = (c + chunk - 1) / chunk;
-        int vals[2] = {c, ni};
-        int excl[2], tot[2];
-        for (int k = 0; k < 2; ++k) {
-            int inc = vals[k];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int u = __shfl_up_sync(FULL, inc, o);
-                if (lane >= o) inc += u;
-            }
-            if (lane == 31) wsum[w] = inc;
-            __syncthreads();
-            if (w == 0) {
-                int x = lane < nw ? wsum[lane] : 0, xi = x;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int u = __shfl_up_sync(FULL, xi, o);
-                    if (lane >= o) xi += u;
-                }
-                if (lane < nw) wsum[lane] = xi - x;
-                if (lane == 31) wsum[32] = xi;
-            }
-            __syncthreads();
-            excl[k] = wsum[w] + inc - vals[k];
-            tot[k] = wsum[32];
-            __syncthreads();
-        }
-        if (t < T) {
-            const int off = carry_pts + excl[0];
-            tile_off[t] = off;
-            tile_cur[t] = off;
-            const int ib = carry_items + excl[1];
-            for (int q = 0; q < ni; ++q) {
-                const int b = off + q * chunk;
-                const int e = min(off + c, b + chunk);
-                items[ib + q] = make_int4(t, b, e, ni == 1 ? 1 : 0);
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            carry_pts += tot[0];
-            carry_items += tot[1];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        tile_off[T] = carry_pts;
-        G->nitems = carry_items;
-    }
-}
-
-__global__ void k_bin_scatter(const float2* __restrict__ Y, int32_t n, const GridDev* __restrict__ G,
-                              int32_t* __restrict__ tile_cur, float2* __restrict__ binned)
-{
-    extern __shared__ int32_t sh[];
-    const float lo = G->lo, h = G->h;
-    const int I = G->I, tb = G->tb, tiles = G->tiles, T = tiles * tiles;
-    int32_t* cnt = sh;
-    int32_t* base = sh + T;
-    constexpr int kItems = 8;
-    for (int t = threadIdx.x; t < T; t += blockDim.x) cnt[t] = 0;
-    __syncthreads();
-    const int64_t b0 = (int64_t)blockIdx.x * blockDim.x * kItems;
-    int tl[kItems], rk[kItems];
-#pragma unroll
-    for (int q = 0; q < kItems; ++q) {
-        const int64_t i = b0 + (int64_t)q * blockDim.x + threadIdx.x;
-        tl[q] = -1;
-        rk[q] = 0;
+    const int I = G->I;
+    const unsigned ltm = lanemask_lt();
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        int box = -1;
         if (i < n) {
             const float2 p = Y[i];
-            const int bx = box_of(p.x, lo, h, I), by = box_of(p.y, lo, h, I);
-            tl[q] = (by / tb) * tiles + bx / tb;
-            rk[q] = atomicAdd(&cnt[tl[q]], 1);
+            box = box_of(p.y, lo, h, I) * I + box_of(p.x, lo, h, I);
         }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < T; t += blockDim.x)
-        base[t] = cnt[t] ? atomicAdd(&tile_cur[t], cnt[t]) : 0;
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kItems; ++q) {
-        const int64_t i = b0 + (int64_t)q * blockDim.x + threadIdx.x;
-        if (tl[q] >= 0) binned[base[tl[q]] + rk[q]] = Y[i];
+        const unsigned peers = __match_any_sync(FULL, box);
+        if (box >= 0 && (peers & ltm) == 0) atomicAdd(&bcnt[box], __popc(peers));
     }
 }
 
-// One work item = one tile of tb x tb boxes and up to kSpreadChunk of its
-// points (tiles are sized for about one item at the mean density).  The
-// points are counting-sorted by box in shared memory, their local
-// coordinates computed once on the way.  Each thread then takes one node row
-// of a contiguous slice of the sorted points and accumulates that row's P
-// nodes x 4 charges in 64-bit fixed point in registers, adding them into a
-// shared-memory tile when the box changes; the tile is stored to the global
-// fixed-point grid (added atomically when a dense tile has several items).
-// Integer sums do not depend on order, so the grid is the same bit for bit
-// from run to run.
-template <int P>
-__global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__ binned, const GridDev* __restrict__ G,
-                                                      const int4* __restrict__ items, long long* __restrict__ wfix)
+// Block-wide exclusive scan of one value per thread (blockDim.x = kScanBlock).
+__device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const int M = G->M, I = G->I, tb = G->tb, tiles = G->tiles;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const int x = wsum[lane];
+        int xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(FULL, xi, o);
+            if (lane >= o) xi += u;
+        }
+        wsum[lane] = xi - x;
+        if (lane == 31) wsum[32] = xi;
+    }
+    __syncthreads();
+    const int r = wsum[w] + inc - v;
+    *total = wsum[32];
+    __syncthreads();
+    return r;
+}
+
+// Box offsets: block-local exclusive offsets into bcur (the scatter cursors),
+// block totals into btot, and, by the last block to finish, the exclusive
+// scan of the totals into bpre; a box's points start at
+// bpre[box / kScanBlock] + (local offset).  Boxes with more than kLightMax
+// points are listed in heavy[0 .. G->nheavy).
+__global__ void __launch_bounds__(kScanBlock) k_box_scan(GridDev* __restrict__ G, const int32_t* __restrict__ bcnt,
+                                                         int32_t* __restrict__ bcur, int32_t* __restrict__ btot,
+                                                         int32_t* __restrict__ bpre, int32_t* __restrict__ heavy)
+{
+    __shared__ int wsum[33];
+    __shared__ bool last;
+    const int NB = G->I * G->I;
+    const int b = blockIdx.x * kScanBlock + threadIdx.x;
+    const int v = b < NB ? bcnt[b] : 0;
+    int tot;
+    const int ex = block_exclusive_scan(v, wsum, &tot);
+    if (b < NB) bcur[b] = ex;
+    const bool hv = v > kLightMax;
+    const unsigned hm = __ballot_sync(FULL, hv);
+    if (hm) {
+        const int lane = threadIdx.x & 31, leader = __ffs(hm) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&G->nheavy, __popc(hm));
+        base = __shfl_sync(FULL, base, leader);
+        if (hv) heavy[base + __popc(hm & lanemask_lt())] = b;
+    }
+    if (threadIdx.x == 0) {
+        btot[blockIdx.x] = tot;
+        __threadfence();
+        last = atomicAdd(&G->scan_ticket, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int t = threadIdx.x < (int)gridDim.x ? ((volatile int32_t*)btot)[threadIdx.x] : 0;
+    int all;
+    const int pre = block_exclusive_scan(t, wsum, &all);
+    if (threadIdx.x < (int)gridDim.x) bpre[threadIdx.x] = pre;
+    if (threadIdx.x == 0) G->scan_ticket = 0;
+}
+
+__global__ void k_box_scatter(const float2* __restrict__ Y, int32_t n, const GridDev* __restrict__ G,
+                              int32_t* __restrict__ bcur, const int32_t* __restrict__ bpre, float2* __restrict__ su)
+{
     const float lo = G->lo, h = G->h, s = G->s;
-    const int NB = tb * tb, TN = tb * P;
-    long long* acc = (long long*)smraw;                      // TN * TN * 4
-    float2* su = (float2*)(acc + kMaxTileNodes * kMaxTileNodes * 4);  // kSpreadChunk
-    int* slb = (int*)(su + kSpreadChunk);                    // kSpreadChunk
-    int* off = slb + kSpreadChunk;                           // NB + 1
-    int* cur = off + kMaxTileBoxes + 1;                      // NB
-    float fx[4];
+    const int I = G->I, P = G->P;
+    const int lane = threadIdx.x & 31;
+    const unsigned ltm = lanemask_lt();
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        int box = -1, bx = 0, by = 0;
+        float2 p = make_float2(0.f, 0.f);
+        if (i < n) {
+            p = Y[i];
+            bx = box_of(p.x, lo, h, I);
+            by = box_of(p.y, lo, h, I);
+            box = by * I + bx;
+        }
+        const unsigned peers = __match_any_sync(FULL, box);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (box >= 0 && lane == leader) base = bpre[box / kScanBlock] + atomicAdd(&bcur[box], __popc(peers));
+        base = __shfl_sync(FULL, base, leader);
+        if (box >= 0)
+            su[base + __popc(peers & ltm)] = make_float2(local_u(p.x, lo, s, P * bx), local_u(p.y, lo, s, P * by));
+    }
+}
+
+// |v| < 2^63 to FP32 with integer operations only (two roundings, relative
+// error below 2^-22), then scaled by the power of two 1/fx.
+__device__ __forceinline__ float fix_to_float(long long v, float ifx)
+{
+    const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    const float f = __fmaf_rn((float)(unsigned)(a >> 32), 4294967296.0f, (float)(unsigned)a);
+    return (v < 0 ? -f : f) * ifx;
+}
+
+// Charges of one point on node row bb of its box, added to the fixed-point
+// sums ra[a][0..3] of the row's P nodes: (w, w ex, w ey, w |e|^2) with w the
+// tensor Lagrange weight and e the offset from the node in node spacings.
+template <int P>
+__device__ __forceinline__ void add_point_row(float2 u, int bb, const float* fx, long long (*ra)[4])
+{
+    float wx[P];
+    lagrange<P>(u.x, wx);
+    const float wyb = lagrange_one<P>(u.y, bb);
+    const float ey = u.y - ((float)bb + 0.5f);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) fx[q] = (float)G->fx[q];
-    const int nslice = blockDim.x / P;
-    const int nitems = G->nitems;
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const int4 item = items[it];
-        const int tx = item.x % tiles, ty = item.x / tiles;
-        const int bx0 = tx * tb, by0 = ty * tb;
-        const int cnt = item.z - item.y;
-        for (int i = threadIdx.x; i < TN * TN * 4; i += blockDim.x) acc[i] = 0;
-        for (int i = threadIdx.x; i < NB; i += blockDim.x) cur[i] = 0;
-        __syncthreads();
-        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-            const float2 p = binned[item.y + j];
-            const int lb = (box_of(p.y, lo, h, I) - by0) * tb + (box_of(p.x, lo, h, I) - bx0);
-            atomicAdd(&cur[lb], 1);
-        }
-        __syncthreads();
-        if (threadIdx.x < 32) {  // exclusive scan of the box counts by warp 0
-            int carry = 0;
-            for (int b0 = 0; b0 < NB; b0 += 32) {
-                const int b = b0 + threadIdx.x;
-                const int v = b < NB ? cur[b] : 0;
-                int inc = v;
+    for (int a = 0; a < P; ++a) {
+        const float w = wx[a] * wyb;
+        const float ex = u.x - ((float)a + 0.5f);
+        ra[a][0] += f2ll_rn(w * fx[0]);
+        ra[a][1] += f2ll_rn((w * ex) * fx[1]);
+        ra[a][2] += f2ll_rn((w * ey) * fx[2]);
+        ra[a][3] += f2ll_rn((w * (ex * ex + ey * ey)) * fx[3]);
+    }
+}
+
+// One thread per (box row by, node row bb, box column bx): consecutive
+// threads write consecutive nodes of a grid row.  Boxes with more than
+// kLightMax points are left to k_box_spread_heavy.
+template <int P>
+__global__ void __launch_bounds__(256) k_box_spread_light(const float2* __restrict__ su,
+                                                          const int32_t* __restrict__ bcnt,
+                                                          const int32_t* __restrict__ bcur,
+                                                          const int32_t* __restrict__ bpre,
+                                                          const GridDev* __restrict__ G, float4* __restrict__ wflt)
+{
+    const int I = G->I, M = G->M;
+    float fx[4], ifx[4];
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t = __shfl_up_sync(FULL, inc, o);
-                    if (threadIdx.x >= o) inc += t;
-                }
-                if (b < NB) {
-                    off[b] = carry + inc - v;
-                    cur[b] = carry + inc - v;
-                }
-                carry += __shfl_sync(FULL, inc, 31);
-            }
-            if (threadIdx.x == 0) off[NB] = carry;
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-            const float2 p = binned[item.y + j];
-            const int bx = box_of(p.x, lo, h, I), by = box_of(p.y, lo, h, I);
-            const int lb = (by - by0) * tb + (bx - bx0);
-            const int pos = atomicAdd(&cur[lb], 1);
-            su[pos] = make_float2(local_u(p.x, lo, s, P * bx), local_u(p.y, lo, s, P * by));
-            slb[pos] = lb;
-        }
-        __syncthreads();
-        if (threadIdx.x < nslice * P) {
-            const int slice = threadIdx.x / P, bb = threadIdx.x - slice * P;
-            const int per = (cnt + nslice - 1) / nslice;
-            const int q0 = slice * per, q1 = min(cnt, q0 + per);
+    for (int q = 0; q < 4; ++q) {
+        fx[q] = (float)G->fx[q];
+        ifx[q] = (float)G->ifx[q];
+    }
+    const int64_t total = (int64_t)I * I * P;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int bx = (int)(t % I);
+        const int r = (int)(t / I);
+        const int by = r / P, bb = r - by * P;
+        const int box = by * I + bx;
+        const int cnt = bcnt[box];
+        if (cnt > kLightMax) continue;
+        long long ra[P][4];
+#pragma unroll
+        for (int a = 0; a < P; ++a)
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) ra[a][ch] = 0;
+        const int start = bpre[box / kScanBlock] + bcur[box] - cnt;
+        for (int q = start; q < start + cnt; ++q) add_point_row<P>(su[q], bb, fx, ra);
+        float4* dst = wflt + (int64_t)(by * P + bb) * M + (int64_t)bx * P;
+#pragma unroll
+        for (int a = 0; a < P; ++a)
+            dst[a] = make_float4(fix_to_float(ra[a][0], ifx[0]), fix_to_float(ra[a][1], ifx[1]),
+                                 fix_to_float(ra[a][2], ifx[2]), fix_to_float(ra[a][3], ifx[3]));
+    }
+}
+
+// One warp per box of more than kLightMax points: per node row, the lanes sum
+// strided points and the fixed-point sums are reduced across the warp.
+template <int P>
+__global__ void __launch_bounds__(256) k_box_spread_heavy(const float2* __restrict__ su,
+                                                          const int32_t* __restrict__ bcnt,
+                                                          const int32_t* __restrict__ bcur,
+                                                          const int32_t* __restrict__ bpre,
+                                                          const int32_t* __restrict__ heavy,
+                                                          const GridDev* __restrict__ G, float4* __restrict__ wflt)
+{
+    const int I = G->I, M = G->M, nh = G->nheavy;
+    float fx[4], ifx[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        fx[q] = (float)G->fx[q];
+        ifx[q] = (float)G->ifx[q];
+    }
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)(gridDim.x * blockDim.x) >> 5;
+    for (int hb = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); hb < nh; hb += nw) {
+        const int box = heavy[hb];
+        const int cnt = bcnt[box];
+        const int start = bpre[box / kScanBlock] + bcur[box] - cnt;
+        const int by = box / I, bx = box - by * I;
+        for (int bb = 0; bb < P; ++bb) {
             long long ra[P][4];
-            int cur_lb = -1;
-            for (int q = q0; q <= q1; ++q) {
-                const int lb = q < q1 ? slb[q] : -2;
-                if (lb != cur_lb) {
-                    if (cur_lb >= 0) {
-                        const int ly = (cur_lb / tb) * P + bb, lx0 = (cur_lb % tb) * P;
-                        long long* dst = acc + (ly * TN + lx0) * 4;
 #pragma unroll
-                        for (int a = 0; a < P; ++a)
+            for (int a = 0; a < P; ++a)
 #pragma unroll
-                            for (int ch = 0; ch < 4; ++ch)
-                                if (ra[a][ch] != 0)
-                                    atomicAdd((unsigned long long*)(dst + a * 4 + ch), (unsigned long long)ra[a][ch]);
-                    }
-                    if (q == q1) break;
-                    cur_lb = lb;
+                for (int ch = 0; ch < 4; ++ch) ra[a][ch] = 0;
+            for (int q = start + lane; q < start + cnt; q += 32) add_point_row<P>(su[q], bb, fx, ra);
 #pragma unroll
-                    for (int a = 0; a < P; ++a)
+            for (int a = 0; a < P; ++a)
 #pragma unroll
-                        for (int ch = 0; ch < 4; ++ch) ra[a][ch] = 0;
-                }
-                const float2 u = su[q];
-                float wx[P];
-                lagrange<P>(u.x, wx);
-                const float wyb = lagrange_one<P>(u.y, bb);
-                const float ey = u.y - ((float)bb + 0.5f);
+                for (int ch = 0; ch < 4; ++ch)
 #pragma unroll
-                for (int a = 0; a < P; ++a) {
-                    const float w = wx[a] * wyb;
-                    const float ex = u.x - ((float)a + 0.5f);
-                    ra[a][0] += __float2ll_rn(w * fx[0]);
-                    ra[a][1] += __float2ll_rn((w * ex) * fx[1]);
-                    ra[a][2] += __float2ll_rn((w * ey) * fx[2]);
-                    ra[a][3] += __float2ll_rn((w * (ex * ex + ey * ey)) * fx[3]);
-                }
+                    for (int o = 16; o > 0; o >>= 1) ra[a][ch] += __shfl_xor_sync(FULL, ra[a][ch], o);
+            if (lane < P) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int a = 0; a < P; ++a)
+                    if (a == lane)
+                        v = make_float4(fix_to_float(ra[a][0], ifx[0]), fix_to_float(ra[a][1], ifx[1]),
+                                        fix_to_float(ra[a][2], ifx[2]), fix_to_float(ra[a][3], ifx[3]));
+                wflt[(int64_t)(by * P + bb) * M + (int64_t)bx * P + lane] = v;
             }
         }
-        __syncthreads();
-        const bool single = item.w != 0;
-        for (int i = threadIdx.x; i < TN * TN * 4; i += blockDim.x) {
-            const long long v = acc[i];
-            if (v == 0) continue;
-            const int node = i >> 2, ch = i & 3;
-            const int gy = by0 * P + node / TN, gx = bx0 * P + node % TN;
-            if (gy >= M || gx >= M) continue;
-            long long* dst = wfix + ((int64_t)gy * M + gx) * 4 + ch;
-            if (single) *dst = v;
-            else atomicAdd((unsigned long long*)dst, (unsigned long long)v);
-        }
-        __syncthreads();
     }
 }
 
@@ -595,21 +588,11 @@ __global__ void k_spec_cols(const GridDev* __restrict__ Gp, const float2* __rest
     }
 }
 
-__device__ __forceinline__ float4 load_charges(const long long* __restrict__ wfix, const float4* __restrict__ wflt,
-                                               int plain, const GridDev& G, int64_t node)
-{
-    if (plain) return wflt[node];
-    const long long* p = wfix + node * 4;
-    return make_float4((float)((double)p[0] * G.ifx[0]), (float)((double)p[1] * G.ifx[1]),
-                       (float)((double)p[2] * G.ifx[2]), (float)((double)p[3] * G.ifx[3]));
-}
-
 // Row FFTs of the charge grids S0, S1x, S1y, S2 (node-local moments), packed
 // two real rows per complex line (S0 + i S1x, S1y + i S2) and separated by
 // Hermitian symmetry into half spectra srow[g][ty][kx], kx in [0, L/2].
 __global__ void k_conv_rows_fwd(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
-                                const long long* __restrict__ wfix, const float4* __restrict__ wflt, int plain,
-                                float2* __restrict__ srow, int sm_f2)
+                                const float4* __restrict__ wflt, float2* __restrict__ srow, int sm_f2)
 {
     extern __shared__ float2 smf[];
     const GridDev& G = *Gp;
@@ -630,7 +613,7 @@ __global__ void k_conv_rows_fwd(const GridDev* __restrict__ Gp, const float2* __
             const int u = u0 + line, pr = u / M, row = u - pr * M;
             float2 v = make_float2(0.f, 0.f);
             if (x < M) {
-                const float4 w = load_charges(wfix, wflt, plain, G, (int64_t)row * M + x);
+                const float4 w = wflt[(int64_t)row * M + x];
                 v = pr == 0 ? make_float2(w.x, w.y) : make_float2(w.z, w.w);
             }
             A[line * L + x] = v;
@@ -850,10 +833,11 @@ __global__ void k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const fl
 // Inverse row FFTs, three packed lines per row (U0 + i U1, U2 + i U3,
 // U4 + i U5), each half spectrum extended by Hermitian symmetry.  Fields per
 // node: f0 = F0, f1 = Vx, f2 = Vy, f3 = Fe0, f4 = Vex, f5 = Vey, f6 = f7 = 0.
-// Also clears the charge grid (its readers have finished) for the next spread.
+// The plain (atomic) spread also needs the charge grid cleared for the next
+// iteration; its readers have finished, so that is done here.
 __global__ void k_conv_rows_inv(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
                                 const float2* __restrict__ ucol, float* __restrict__ fields,
-                                long long* __restrict__ wfix, float4* __restrict__ wflt, int plain, int sm_f2)
+                                float4* __restrict__ wflt, int plain, int sm_f2)
 {
     extern __shared__ float2 smf[];
     const GridDev& G = *Gp;
@@ -896,16 +880,10 @@ __global__ void k_conv_rows_inv(const GridDev* __restrict__ Gp, const float2* __
             else { f[4] = v.x; f[5] = v.y; }
         }
     }
+    if (!plain) return;
     for (int u = beg; u < end; ++u) {
         if (u >= M) break;  // units (0, row) cover every row once
-        for (int x = threadIdx.x; x < M; x += blockDim.x) {
-            const int64_t node = (int64_t)u * M + x;
-            if (plain) wflt[node] = make_float4(0.f, 0.f, 0.f, 0.f);
-            else {
-                long long* q = wfix + node * 4;
-                q[0] = 0; q[1] = 0; q[2] = 0; q[3] = 0;
-            }
-        }
+        for (int x = threadIdx.x; x < M; x += blockDim.x) wflt[(int64_t)u * M + x] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -978,14 +956,6 @@ __global__ void k_psum(const float* __restrict__ v, const int64_t* __restrict__ 
 constexpr int kFftThreads = 256;
 constexpr int kPsumBlocks = 304;
 
-// Shared memory of the spread: the fixed-point tile, the item's points and
-// their boxes, box offsets and cursors.
-size_t spread_smem_bytes()
-{
-    return (size_t)kMaxTileNodes * kMaxTileNodes * 4 * sizeof(long long) +
-           (size_t)kSpreadChunk * (sizeof(float2) + sizeof(int)) + (size_t)(2 * kMaxTileBoxes + 1) * sizeof(int);
-}
-
 // Room for the twiddles plus six lines of the longest length (the column
 // pass keeps four spectra and two work lines), at least 64 KB.
 size_t fft_smem_bytes(int Lmax) { return std::max<size_t>(64 * 1024, (size_t)7 * Lmax * 8); }
@@ -1000,26 +970,24 @@ IterShape iter_shape(int32_t n, const ltsnet_params* p)
     sh.max_boxes = p->max_boxes;
     sh.Mmax = p->max_boxes * p->nodes_per_box;
     sh.Lmax = 2 * sh.Mmax;
-    sh.tiles_max = kMaxTiles;
-    sh.items_max = (int64_t)kMaxTiles * kMaxTiles + (int64_t)n / kSpreadChunk + 2;
     return sh;
 }
 
 IterWs iter_carve(Carve& c, const IterShape& sh)
 {
     IterWs w;
-    const int64_t T = (int64_t)sh.tiles_max * sh.tiles_max;
     const int64_t MM = (int64_t)sh.Mmax * sh.Mmax;
     w.st = c.take<StatusBlock>(1);
     w.g = c.take<GridDev>(1);
     w.bounds = c.take<int32_t>(4);
     w.tw = c.take<float2>(kLMax);
-    w.tile_cnt = c.take<int32_t>(T);
-    w.tile_off = c.take<int32_t>(T + 1);
-    w.tile_cur = c.take<int32_t>(T);
-    w.items = c.take<int4>(sh.items_max);
-    w.binned = c.take<float2>(sh.n);
-    w.wfix = c.take<long long>(4 * MM);
+    const int64_t NB = (int64_t)sh.max_boxes * sh.max_boxes;
+    w.bcnt = c.take<int32_t>(NB);
+    w.bcur = c.take<int32_t>(NB);
+    w.heavy = c.take<int32_t>(NB);
+    w.btot = c.take<int32_t>(kScanBlock);
+    w.bpre = c.take<int32_t>(kScanBlock);
+    w.su = c.take<float2>(sh.n);
     w.wflt = c.take<float4>(MM);
     const int64_t LH = (int64_t)sh.Lmax * (sh.Lmax / 2 + 1);
     const int64_t MH = (int64_t)sh.Mmax * (sh.Lmax / 2 + 1);
@@ -1062,11 +1030,25 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
 {
     const int32_t n = sh.n;
     const int P = sh.P;
-    k_setup<<<16, 256, 0, s>>>(w.bounds + 2 * parity, w.bounds + 2 * (parity ^ 1), w.g, w.tw, w.tile_cnt, n,
+    k_setup<<<64, 256, 0, s>>>(w.bounds + 2 * parity, w.bounds + 2 * (parity ^ 1), w.g, w.tw, w.bcnt, n,
                                p->box_width_max, p->min_boxes, p->max_boxes, P);
     count_launches(1);
+    const size_t fsm = fft_smem_bytes(sh.Lmax);
+    const int f2 = (int)(fsm / sizeof(float2));
+    // The kernel spectra need only the grid parameters: unless kernels are
+    // being timed one by one, they run on a side stream next to the spread
+    // and join before the column pass.
+    AuxStreams* aux = nullptr;
+    const bool fork = !profiling_active() && aux_streams(&aux) == cudaSuccess;
+    if (fork) {
+        cudaError_t e2;
+        if ((e2 = cudaEventRecord(aux->fork, s)) != cudaSuccess) return e2;
+        if ((e2 = cudaStreamWaitEvent(aux->branch, aux->fork, 0)) != cudaSuccess) return e2;
+        k_spec_rows<<<kSMs, kFftThreads, fsm, aux->branch>>>(w.g, w.tw, p->eps, w.krow, f2);
+        k_spec_cols<<<kSMs, kFftThreads, fsm, aux->branch>>>(w.g, w.tw, w.krow, w.khat, f2);
+        if ((e2 = cudaEventRecord(aux->join, aux->branch)) != cudaSuccess) return e2;
+    }
     profile_start(LTSNET_KERNEL_SPREAD, s);
-    const int64_t T = (int64_t)sh.tiles_max * sh.tiles_max;
     if (plain) {
         int64_t blocks = ((int64_t)n + 255) / 256;
         if (blocks > kSMs * 8) blocks = kSMs * 8;
@@ -1080,35 +1062,44 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
         count_launches(1);
     } else {
         int64_t blocks = ((int64_t)n + 255) / 256;
-        if (blocks > kSMs * 4) blocks = kSMs * 4;
+        if (blocks > kSMs * 8) blocks = kSMs * 8;
         if (blocks < 1) blocks = 1;
-        const size_t sm1 = (size_t)T * 4;
-        k_bin_count<<<(unsigned)blocks, 256, sm1, s>>>(Y, n, w.g, w.tile_cnt);
-        k_bin_plan<<<1, 1024, 0, s>>>(w.g, w.tile_cnt, w.tile_off, w.tile_cur, w.items, kSpreadChunk);
-        int64_t sblocks = ((int64_t)n + 256 * 8 - 1) / (256 * 8);
-        if (sblocks < 1) sblocks = 1;
-        k_bin_scatter<<<(unsigned)sblocks, 256, 2 * sm1, s>>>(Y, n, w.g, w.tile_cur, w.binned);
-        const size_t sm2 = spread_smem_bytes();
+        k_box_count<<<(unsigned)blocks, 256, 0, s>>>(Y, n, w.g, w.bcnt);
+        const int nsb = (int)(((int64_t)sh.max_boxes * sh.max_boxes + kScanBlock - 1) / kScanBlock);
+        k_box_scan<<<nsb, kScanBlock, 0, s>>>(w.g, w.bcnt, w.bcur, w.btot, w.bpre, w.heavy);
+        k_box_scatter<<<(unsigned)blocks, 256, 0, s>>>(Y, n, w.g, w.bcur, w.bpre, w.su);
+        int64_t lb = ((int64_t)sh.max_boxes * sh.max_boxes * P + 255) / 256;
+        if (lb > kSMs * 16) lb = kSMs * 16;
         switch (P) {
-            case 2: k_spread_tiles<2><<<kSMs * 4, 256, sm2, s>>>(w.binned, w.g, w.items, w.wfix); break;
-            case 3: k_spread_tiles<3><<<kSMs * 4, 256, sm2, s>>>(w.binned, w.g, w.items, w.wfix); break;
-            case 4: k_spread_tiles<4><<<kSMs * 4, 256, sm2, s>>>(w.binned, w.g, w.items, w.wfix); break;
-            default: k_spread_tiles<5><<<kSMs * 4, 256, sm2, s>>>(w.binned, w.g, w.items, w.wfix); break;
+#define LT_SPREAD(PP)                                                                                          \
+    case PP:                                                                                                   \
+        k_box_spread_light<PP><<<(unsigned)lb, 256, 0, s>>>(w.su, w.bcnt, w.bcur, w.bpre, w.g, w.wflt);       \
+        k_box_spread_heavy<PP><<<kSMs * 4, 256, 0, s>>>(w.su, w.bcnt, w.bcur, w.bpre, w.heavy, w.g, w.wflt); \
+        break;
+            LT_SPREAD(2)
+            LT_SPREAD(3)
+            LT_SPREAD(4)
+            default: LT_SPREAD(5)
+#undef LT_SPREAD
         }
-        count_launches(4);
+        count_launches(5);
     }
     profile_stop(LTSNET_KERNEL_SPREAD, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
 
     profile_start(LTSNET_KERNEL_CONV, s);
-    const size_t fsm = fft_smem_bytes(sh.Lmax);
-    const int f2 = (int)(fsm / sizeof(float2));
-    k_spec_rows<<<kSMs, kFftThreads, fsm, s>>>(w.g, w.tw, p->eps, w.krow, f2);
-    k_spec_cols<<<kSMs, kFftThreads, fsm, s>>>(w.g, w.tw, w.krow, w.khat, f2);
-    k_conv_rows_fwd<<<kSMs, kFftThreads, fsm, s>>>(w.g, w.tw, w.wfix, w.wflt, plain ? 1 : 0, w.srow, f2);
+    if (!fork) {
+        k_spec_rows<<<kSMs, kFftThreads, fsm, s>>>(w.g, w.tw, p->eps, w.krow, f2);
+        k_spec_cols<<<kSMs, kFftThreads, fsm, s>>>(w.g, w.tw, w.krow, w.khat, f2);
+    }
+    k_conv_rows_fwd<<<kSMs, kFftThreads, fsm, s>>>(w.g, w.tw, w.wflt, w.srow, f2);
+    if (fork) {
+        cudaError_t e2 = cudaStreamWaitEvent(s, aux->join, 0);
+        if (e2 != cudaSuccess) return e2;
+    }
     k_conv_cols<<<kSMs, kFftThreads, fsm, s>>>(w.g, w.tw, w.srow, w.khat, w.ucol, w.zblk, n, f2);
-    k_conv_rows_inv<<<kSMs, kFftThreads, fsm, s>>>(w.g, w.tw, w.ucol, w.fields, w.wfix, w.wflt, plain ? 1 : 0, f2);
+    k_conv_rows_inv<<<kSMs, kFftThreads, fsm, s>>>(w.g, w.tw, w.ucol, w.fields, w.wflt, plain ? 1 : 0, f2);
     count_launches(5);
     profile_stop(LTSNET_KERNEL_CONV, s);
     return cudaGetLastError();
@@ -1123,15 +1114,6 @@ cudaError_t grid_set_smem_attrs()
     if ((e = cudaFuncSetAttribute(k_conv_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
     if ((e = cudaFuncSetAttribute(k_conv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
     if ((e = cudaFuncSetAttribute(k_conv_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
-    const int sm2 = (int)spread_smem_bytes();
-    if ((e = cudaFuncSetAttribute(k_spread_tiles<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2))) return e;
-    if ((e = cudaFuncSetAttribute(k_spread_tiles<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2))) return e;
-    if ((e = cudaFuncSetAttribute(k_spread_tiles<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2))) return e;
-    if ((e = cudaFuncSetAttribute(k_spread_tiles<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2))) return e;
-    // binning: one int (count) or two (count, base) per tile
-    const int bins = kMaxTiles * kMaxTiles * 4;
-    if ((e = cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, bins))) return e;
-    if ((e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * bins))) return e;
     return cudaSuccess;
 }
 

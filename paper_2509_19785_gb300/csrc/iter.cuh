@@ -9,13 +9,7 @@ namespace lt {
 constexpr int kLMax = 4096;     // longest FFT line (L = 2 * P * I)
 constexpr int kMaxRadix = 16;   // FFT stages
 constexpr int kFieldStride = 8; // floats per grid node in the field array
-constexpr int kSpreadChunk = 2048; // points per spread work item
-constexpr int kMaxTiles = 64;        // spread tiles per dimension (at most)
-// Boxes per spread tile edge: at most 8, or ceil(I / kMaxTiles) when larger;
-// I <= kLMax / (2P) bounds that by 16 (P = 2), so tiles have at most 256
-// boxes and at most 40 nodes per edge (P = 5: 8 boxes).
-constexpr int kMaxTileBoxes = 256;
-constexpr int kMaxTileNodes = 40;
+
 
 // Written by k_setup every iteration from the layout bounds.  All integer
 // decisions (I, box) are FP32 and match the oracle's grid rule bit for bit.
@@ -23,15 +17,15 @@ struct GridDev {
     float lo, hi, ext, h, s, c;  // domain [lo, lo+ext], box width h, node spacing s, centre c
     int32_t I, M, L;             // boxes per dim, nodes per dim (I*P), FFT length (2M)
     int32_t P;                   // nodes per box
-    int32_t tb, tiles;           // boxes per spread tile edge, tiles per dim
     int32_t nst;                 // FFT stages
     int32_t radix[kMaxRadix];
     double fx[4], ifx[4];        // fixed-point scale per charge and its inverse (powers of 2)
     double Z;                    // sum_{i != j} 1/(1+d^2), from the grid
     double S;                    // sum of P values
     float SoZ;                   // S / Z rounded to FP32 (the repulsion scale)
-    int32_t nitems;              // spread work items
     int32_t ticket;              // last-block counter for the Z reduction
+    int32_t scan_ticket;         // last-block counter of the box scan
+    int32_t nheavy;              // boxes summed by a warp
 };
 
 // Per-iteration scalars of the gradient, precomputed on the host in FP64:
@@ -50,12 +44,12 @@ struct IterWs {
     GridDev* g;
     int32_t* bounds;     // [2 parities][2] ordered ints (min, max)
     float2* tw;          // twiddles e^{-2 pi i t/L}, kLMax
-    int32_t* tile_cnt;   // tiles_max^2
-    int32_t* tile_off;   // tiles_max^2 + 1
-    int32_t* tile_cur;   // tiles_max^2
-    int4* items;         // spread work items (tile, begin, end, 0)
-    float2* binned;      // n points, binned by tile
-    long long* wfix;     // M_max^2 * 4 fixed-point charges
+    int32_t* bcnt;       // max_boxes^2 points per box
+    int32_t* bcur;       // max_boxes^2 block-local box offsets / scatter cursors
+    int32_t* heavy;      // boxes summed by a warp (G->nheavy of them)
+    int32_t* btot;       // totals of the box-scan blocks
+    int32_t* bpre;       // their exclusive scan
+    float2* su;          // n local coordinates, box-sorted
     float4* wflt;        // M_max^2 float charges (plain form)
     float2* krow;        // 3 * L_max * H kernel row transforms (H = L_max/2 + 1)
     float* khat;         // 5 * L_max * H kernel spectra (K2, Ke, K1, Im K2dx, Im Kedx)
@@ -73,8 +67,7 @@ struct IterShape {
     int32_t n;
     int32_t P;
     int32_t max_boxes;
-    int32_t Mmax, Lmax, tiles_max;
-    int64_t items_max;
+    int32_t Mmax, Lmax;
 };
 
 IterShape iter_shape(int32_t n, const ltsnet_params* p);
@@ -103,6 +96,27 @@ __device__ __forceinline__ void lagrange(float u, float* w)
         }
         w[a] = num / den;
     }
+}
+
+// Round a float to the nearest 64-bit integer (ties to even) with integer
+// operations only, from its sign, exponent and 24-bit significand.  Same
+// result as a hardware float-to-int64 conversion for |x| < 2^62, which on
+// this GPU would go through the narrow FP64 pipe.
+__device__ __forceinline__ long long f2ll_rn(float x)
+{
+    const unsigned bits = __float_as_uint(x);
+    const int e = (int)((bits >> 23) & 0xffu) - 127;  // unbiased exponent
+    if (e < -1) return 0;                              // |x| < 0.5 (and zeros, denormals)
+    const unsigned m = (bits & 0x7fffffu) | 0x800000u;  // significand, value = m * 2^(e - 23)
+    long long r;
+    if (e >= 23) {
+        r = (long long)m << (e - 23);
+    } else {
+        const int sh = 23 - e;  // 1 .. 24
+        const unsigned q = m >> sh, rem = m & ((1u << sh) - 1u), half = 1u << (sh - 1);
+        r = (long long)(q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u));
+    }
+    return (bits >> 31) ? -r : r;
 }
 
 // Lagrange basis function a alone at local coordinate u.

@@ -583,6 +583,32 @@ ltsnet_status read_status(StatusBlock* st, cudaStream_t s)
 }
 
 // The loop over iterations [t0, t0 + niter) on a carved iteration workspace.
+// One iteration i (local index; parity i & 1 picks the layout buffer and
+// the bounds slot): grid phase, then the point phase.
+cudaError_t one_iteration(const int64_t* P_row, const int32_t* P_col, const float* P_val, int32_t n,
+                          const ltsnet_params* p, float2* Y, float2* upd, float2* gains, const IterWs& w,
+                          const IterShape& sh, const Stage& st, int parity, bool plain, cudaStream_t s)
+{
+    float2* cur = parity ? w.yalt : Y;
+    float2* nxt = parity ? Y : w.yalt;
+    cudaError_t e = launch_grid_phase(w, sh, p, cur, parity, plain, s);
+    if (e != cudaSuccess) return e;
+    return launch_point_phase<true>(P_row, P_col, P_val, n, cur, nxt, upd, gains, w, sh, st, parity, nullptr, nullptr,
+                                    plain, s);
+}
+
+bool same_stage(const ltsnet_stage& a, const ltsnet_stage& b)
+{
+    return a.lambda_kl == b.lambda_kl && a.lambda_c == b.lambda_c && a.lambda_r == b.lambda_r &&
+           a.exaggeration == b.exaggeration && a.momentum == b.momentum;
+}
+
+// The loop over iterations [t0, t0 + niter).  Runs of iterations with the
+// same stage are replayed from a CUDA graph holding two iterations (one per
+// layout parity), captured on an internal stream and launched on `s`; the
+// graph's launches are counted as their kernels.  While kernels are being
+// timed one by one (ltsnet_profile_begin) every iteration is launched
+// directly.
 ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const float* P_val, int32_t n,
                             const ltsnet_params* p, float2* Y, float2* upd, float2* gains, int32_t t0, int32_t niter,
                             const IterWs& w, const IterShape& sh, cudaStream_t s)
@@ -592,19 +618,51 @@ ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const fl
     LT_CUDA(ensure_attrs());
     LT_CUDA(launch_psum(w, P_row, n, P_val, s));
     LT_CUDA(launch_bounds_init(w, Y, n, 0, s));
-    float2* cur = Y;
-    float2* nxt = w.yalt;
-    for (int32_t i = 0; i < niter; ++i) {
-        const int parity = i & 1;
-        const Stage st = make_stage(stage_at(p, (int64_t)t0 + i), lr, n);
-        LT_CUDA(launch_grid_phase(w, sh, p, cur, parity, plain, s));
-        LT_CUDA(launch_point_phase<true>(P_row, P_col, P_val, n, cur, nxt, upd, gains, w, sh, st, parity, nullptr,
-                                         nullptr, plain, s));
-        float2* t = cur;
-        cur = nxt;
-        nxt = t;
+    AuxStreams* aux = nullptr;
+    const bool graphs = !profiling_active() && aux_streams(&aux) == cudaSuccess;
+    int32_t i = 0;
+    while (i < niter) {
+        const ltsnet_stage& sg = stage_at(p, (int64_t)t0 + i);
+        int32_t run = 1;
+        while (i + run < niter && same_stage(stage_at(p, (int64_t)t0 + i + run), sg)) ++run;
+        const Stage st = make_stage(sg, lr, n);
+        int32_t done = 0;
+        if ((i & 1) && run > 0) {  // align to an even iteration
+            LT_CUDA(one_iteration(P_row, P_col, P_val, n, p, Y, upd, gains, w, sh, st, 1, plain, s));
+            done = 1;
+        }
+        const int32_t pairs = graphs ? (run - done) / 2 : 0;
+        if (pairs >= 2) {
+            const int64_t c0 = ltsnet_launch_count();
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            LT_CUDA(cudaStreamBeginCapture(aux->capture, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = one_iteration(P_row, P_col, P_val, n, p, Y, upd, gains, w, sh, st, 0, plain, aux->capture);
+            if (e == cudaSuccess)
+                e = one_iteration(P_row, P_col, P_val, n, p, Y, upd, gains, w, sh, st, 1, plain, aux->capture);
+            cudaError_t e2 = cudaStreamEndCapture(aux->capture, &graph);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                LT_CUDA(e != cudaSuccess ? e : e2);
+            }
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            LT_CUDA(e);
+            const int64_t per = ltsnet_launch_count() - c0;
+            for (int32_t q = 0; q < pairs; ++q) {
+                e = cudaGraphLaunch(exec, s);
+                if (e != cudaSuccess) break;
+            }
+            cudaGraphExecDestroy(exec);  // freed once its launches complete
+            LT_CUDA(e);
+            count_launches(per * (pairs - 1));
+            done += 2 * pairs;
+        }
+        for (; done < run; ++done)
+            LT_CUDA(one_iteration(P_row, P_col, P_val, n, p, Y, upd, gains, w, sh, st, (i + done) & 1, plain, s));
+        i += run;
     }
-    if (cur != Y) LT_CUDA(cudaMemcpyAsync(Y, cur, sizeof(float2) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    if (niter & 1) LT_CUDA(cudaMemcpyAsync(Y, w.yalt, sizeof(float2) * (size_t)n, cudaMemcpyDeviceToDevice, s));
     return LTSNET_OK;
 }
 
@@ -709,7 +767,6 @@ ltsnet_status run_core(const int64_t* row_ptr, const int32_t* col, int32_t n, co
     Carve ic(r.iter, r.iter_bytes);
     const IterWs w = iter_carve(ic, sh);
     LT_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StatusBlock), s));
-    LT_CUDA(cudaMemsetAsync(w.wfix, 0, sizeof(long long) * 4 * (size_t)sh.Mmax * sh.Mmax, s));
     LT_CUDA(cudaMemsetAsync(w.wflt, 0, sizeof(float4) * (size_t)sh.Mmax * sh.Mmax, s));
     const int64_t total = schedule_length(p);
     float2* Yw = Y;
@@ -757,7 +814,6 @@ static ltsnet_status prepare_iter(int32_t n, const ltsnet_params* p, void* ws, s
     w = iter_carve(c, sh);
     if (!c.ok()) return LTSNET_ERR_WORKSPACE;
     LT_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StatusBlock), s));
-    LT_CUDA(cudaMemsetAsync(w.wfix, 0, sizeof(long long) * 4 * (size_t)sh.Mmax * sh.Mmax, s));
     LT_CUDA(cudaMemsetAsync(w.wflt, 0, sizeof(float4) * (size_t)sh.Mmax * sh.Mmax, s));
     return LTSNET_OK;
 }
