@@ -16,13 +16,13 @@
 //
 //  k_setup        grid rule from the layout bounds (FP32, same decisions as
 //                 the oracle), FFT plan and twiddles, fixed-point scales.
-//  k_box_count    points per box (warp-aggregated atomics).
-//  k_box_scan     box offsets (one block).
-//  k_box_scatter  local coordinates and boxes of the points, in box order.
-//  k_box_spread   per run of 32 box-sorted points and node row: Lagrange
-//                 weights x charges summed in 64-bit fixed point (integer sums
-//                 are order independent, so the grid is bit-identical from run
-//                 to run), added to the global fixed-point grid per box.
+//  k_box_count    points per box (per-block hash aggregation, then global
+//                 atomics).
+//  k_box_scan     box offsets, heavy boxes and their segments.
+//  k_box_scatter  local coordinates of the points, in box order.
+//  k_box_spread   Lagrange weights x charges summed per box in integers and
+//                 written as the FP32 charge grid (bit-identical from run to
+//                 run).
 //  k_spread_atomic  the plain form: FP32 atomics straight into the grid.
 //  k_spec_rows/cols 2-D FFTs of the kernels (K2, Ke, K1 even; K2 dx, Ke dx
 //                 odd), three packed complex transforms, half spectra kept.
@@ -55,6 +55,115 @@ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 conj2(float2 a) { return make_float2(a.x, -a.y); }
 
+// Forward DFT of size R in place on v[0..R-1] (e^{-2 pi i rq / R}); the
+// radix-3 and radix-5 forms pair the inputs symmetrically so that only the
+// real constants cos(2 pi k / R), sin(2 pi k / R) appear.
+__device__ __forceinline__ float2 mul_mi(float2 z) { return make_float2(z.y, -z.x); }  // -i z
+
+template <int R>
+__device__ __forceinline__ void dft_small(float2* v);
+
+template <>
+__device__ __forceinline__ void dft_small<2>(float2* v)
+{
+    const float2 t = v[1];
+    v[1] = csub(v[0], t);
+    v[0] = cadd(v[0], t);
+}
+
+template <>
+__device__ __forceinline__ void dft_small<4>(float2* v)
+{
+    const float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    const float2 t2 = cadd(v[1], v[3]), t3 = mul_mi(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[2] = csub(t0, t2);
+    v[3] = csub(t1, t3);
+}
+
+template <>
+__device__ __forceinline__ void dft_small<3>(float2* v)
+{
+    const float s60 = 0.866025403784438647f;  // sin(2 pi / 3)
+    const float2 a = cadd(v[1], v[2]);
+    const float2 d = mul_mi(csub(v[1], v[2]));
+    const float2 m = make_float2(v[0].x - 0.5f * a.x, v[0].y - 0.5f * a.y);
+    v[0] = cadd(v[0], a);
+    v[1] = make_float2(m.x + s60 * d.x, m.y + s60 * d.y);
+    v[2] = make_float2(m.x - s60 * d.x, m.y - s60 * d.y);
+}
+
+template <>
+__device__ __forceinline__ void dft_small<5>(float2* v)
+{
+    const float c1 = 0.309016994374947424f, c2 = -0.809016994374947424f;  // cos(2 pi / 5), cos(4 pi / 5)
+    const float s1 = 0.951056516295153572f, s2 = 0.587785252292473129f;   // sin(2 pi / 5), sin(4 pi / 5)
+    const float2 a1 = cadd(v[1], v[4]), b1 = mul_mi(csub(v[1], v[4]));
+    const float2 a2 = cadd(v[2], v[3]), b2 = mul_mi(csub(v[2], v[3]));
+    const float2 m1 = make_float2(v[0].x + c1 * a1.x + c2 * a2.x, v[0].y + c1 * a1.y + c2 * a2.y);
+    const float2 m2 = make_float2(v[0].x + c2 * a1.x + c1 * a2.x, v[0].y + c2 * a1.y + c1 * a2.y);
+    const float2 n1 = make_float2(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y);
+    const float2 n2 = make_float2(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y);
+    v[0] = cadd(v[0], cadd(a1, a2));
+    v[1] = cadd(m1, n1);
+    v[4] = csub(m1, n1);
+    v[2] = cadd(m2, n2);
+    v[3] = csub(m2, n2);
+}
+
+// One radix-R Stockham stage on nl lines (stride ld): butterfly j of a line
+// reads a[j + r L/R] (r = 0..R-1), multiplies by the twiddles
+// e^{-2 pi i (j mod Ns) r / (Ns R)}, and writes b[(j - j mod Ns) R + j mod Ns
+// + q Ns].  When a line has fewer butterflies than the block has threads,
+// each thread keeps one j for several lines and loads its twiddles once.
+template <int R>
+__device__ __forceinline__ void fft_stage(const float2* a, float2* b, int nl, int ld, int L, int Ns,
+                                          const float2* tw)
+{
+    const int nbf = L / R;
+    const int ts = L / (Ns * R);
+    const int nt = blockDim.x;
+    if (nbf < nt) {
+        const int lpp = nt / nbf;
+        const int t0 = threadIdx.x / nbf;
+        if (t0 >= lpp) return;
+        const int j = threadIdx.x - t0 * nbf;
+        const int jm = j % Ns;
+        const int ob = (j - jm) * R + jm;
+        float2 w[R];
+#pragma unroll
+        for (int r = 1; r < R; ++r) w[r] = tw[jm * r * ts];
+        for (int line = t0; line < nl; line += lpp) {
+            const float2* in = a + line * ld;
+            float2* out = b + line * ld;
+            float2 v[R];
+            v[0] = in[j];
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(in[j + r * nbf], w[r]);
+            dft_small<R>(v);
+#pragma unroll
+            for (int q = 0; q < R; ++q) out[ob + q * Ns] = v[q];
+        }
+    } else {
+        for (int line = 0; line < nl; ++line) {
+            const float2* in = a + line * ld;
+            float2* out = b + line * ld;
+            for (int j = threadIdx.x; j < nbf; j += nt) {
+                const int jm = j % Ns;
+                const int ob = (j - jm) * R + jm;
+                float2 v[R];
+                v[0] = in[j];
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[r] = cmul(in[j + r * nbf], tw[jm * r * ts]);
+                dft_small<R>(v);
+#pragma unroll
+                for (int q = 0; q < R; ++q) out[ob + q * Ns] = v[q];
+            }
+        }
+    }
+}
+
 // Forward DFT (e^{-2 pi i jk/L}) of `nl` lines of length L (stride ld) held in
 // shared memory, mixed radix 4/2/3/5 Stockham autosort with ping-pong buffers
 // a, b.  Returns the buffer holding the result.  All threads of the block
@@ -65,36 +174,11 @@ __device__ float2* fft_lines(float2* a, float2* b, int nl, int ld, const GridDev
     int Ns = 1;
     for (int st = 0; st < g.nst; ++st) {
         const int R = g.radix[st];
-        const int nbf = L / R;
-        const int ts = L / (Ns * R);
-        const int wR = L / R;
-        for (int idx = threadIdx.x; idx < nl * nbf; idx += blockDim.x) {
-            const int line = idx / nbf;
-            const int j = idx - line * nbf;
-            const float2* in = a + line * ld;
-            float2* out = b + line * ld;
-            const int jm = j % Ns;
-            const int ob = (j - jm) * R + jm;
-            float2 v[5];
-            v[0] = in[j];
-            for (int r = 1; r < R; ++r) v[r] = cmul(in[j + r * nbf], tw[jm * r * ts]);
-            if (R == 4) {
-                const float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-                const float2 t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
-                out[ob] = cadd(t0, t2);
-                out[ob + Ns] = make_float2(t1.x + t3.y, t1.y - t3.x);
-                out[ob + 2 * Ns] = csub(t0, t2);
-                out[ob + 3 * Ns] = make_float2(t1.x - t3.y, t1.y + t3.x);
-            } else if (R == 2) {
-                out[ob] = cadd(v[0], v[1]);
-                out[ob + Ns] = csub(v[0], v[1]);
-            } else {
-                for (int q = 0; q < R; ++q) {
-                    float2 acc = v[0];
-                    for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(v[r], tw[((r * q) % R) * wR]));
-                    out[ob + q * Ns] = acc;
-                }
-            }
+        switch (R) {
+            case 4: fft_stage<4>(a, b, nl, ld, L, Ns, tw); break;
+            case 2: fft_stage<2>(a, b, nl, ld, L, Ns, tw); break;
+            case 3: fft_stage<3>(a, b, nl, ld, L, Ns, tw); break;
+            default: fft_stage<5>(a, b, nl, ld, L, Ns, tw); break;
         }
         __syncthreads();
         float2* t = a;
@@ -139,13 +223,29 @@ __device__ void compute_grid(const int32_t* bounds, float bwm, int min_boxes, in
     while (r % 5 == 0) { g.radix[k++] = 5; r /= 5; }
     g.nst = k;
     // node-local charges (1, ex, ey, ex^2 + ey^2) with |e| <= P in node units,
-    // Lagrange weight products <= 8 for P <= 5
+    // Lagrange weight products <= 8 for P <= 5: 64-bit fixed point with room
+    // for the sum over all n points
     const double qb[4] = {1.0, (double)P, (double)P, 2.0 * P * P};
     for (int c = 0; c < 4; ++c) {
         int ex;
         frexp((double)n * 8.0 * qb[c], &ex);
-        g.fx[c] = ldexp(1.0, 62 - ex);
-        g.ifx[c] = ldexp(1.0, ex - 62);
+        g.fx[c] = ldexpf(1.0f, 62 - ex);
+        g.ifx[c] = ldexpf(1.0f, ex - 62);
+    }
+    // Per-point 32-bit quantisation of the warp-summed (heavy) boxes: bounds
+    // of |w|, |w e|, |w e|, |w |e|^2| over local coordinates in
+    // [-0.05, P + 0.05] (tensor Lagrange weights w, offsets e from the nodes),
+    // scaled to at most 2^22 so that the round-to-integer by adding 1.5 * 2^23
+    // is exact and kSeg points sum below 2^31.
+    const float hb[4][4] = {{2.41f, 3.91f, 6.20f, 14.26f},
+                            {1.33f, 4.30f, 9.61f, 33.2f},
+                            {1.33f, 4.30f, 9.61f, 33.2f},
+                            {4.10f, 13.4f, 49.0f, 169.1f}};
+    for (int c = 0; c < 4; ++c) {
+        int ex;
+        frexpf(4194304.0f / hb[c][P - 2], &ex);
+        g.hf[c] = ldexpf(1.0f, ex - 1);
+        g.ihf[c] = ldexpf(1.0f, 1 - ex);
     }
 }
 
@@ -161,7 +261,12 @@ __global__ void k_setup(const int32_t* __restrict__ bounds_cur, int32_t* __restr
         G->I = g.I; G->M = g.M; G->L = g.L; G->P = g.P;
         G->nst = g.nst;
         for (int i = 0; i < kMaxRadix; ++i) G->radix[i] = i < g.nst ? g.radix[i] : 0;
-        for (int c = 0; c < 4; ++c) { G->fx[c] = g.fx[c]; G->ifx[c] = g.ifx[c]; }
+        for (int c = 0; c < 4; ++c) {
+            G->fx[c] = g.fx[c];
+            G->ifx[c] = g.ifx[c];
+            G->hf[c] = g.hf[c];
+            G->ihf[c] = g.ihf[c];
+        }
         G->ticket = 0;
         bounds_next[0] = f2ord(INFINITY);
         bounds_next[1] = f2ord(-INFINITY);
@@ -184,40 +289,93 @@ __global__ void k_setup(const int32_t* __restrict__ bounds_cur, int32_t* __restr
     for (int64_t t = tid; t < (int64_t)g.I * g.I; t += nth) bcnt[t] = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         G->nheavy = 0;
+        G->nitems = 0;
         G->scan_ticket = 0;
     }
 }
 
-// ---- deterministic spread: box sort, then one owner per box ----
+// ---- deterministic spread: box sort, then integer sums per box ----
 // The Lagrange nodes a point feeds are those of its own box, so every node's
-// charges are sums over one box's points.  The points are counted per box
-// (warp-aggregated atomics), the counts scanned, and the points scattered
-// into box order with their local coordinates.  Then each box is summed by a
-// single owner -- a thread per (box, node row) for boxes of at most
-// kLightMax points, a warp per box for the rest -- in 64-bit fixed point,
-// whose sums do not depend on the order of the points within the box.  The
-// owner writes its nodes' final FP32 charges: every node is written every
-// iteration, with no atomics on the grid and no clearing pass, and the grid
-// is bit-identical from run to run.
+// charges are sums over one box's points.  The points are counted per box,
+// the counts scanned, and the points scattered into box order with their
+// local coordinates.  Then every box is summed in integers -- a thread per
+// (box, node row) for boxes of at most kLightMax points, warps over segments
+// of kSeg points for the rest -- so the sums do not depend on the order of
+// the points within a box.  Every node's final FP32 charges are written once
+// per iteration, with no atomics on the grid and no clearing pass, and the
+// grid is bit-identical from run to run.
 
 constexpr int kScanBlock = 1024;  // boxes per block of the box scan
-constexpr int kLightMax = 32;     // boxes with more points are summed by a warp
+constexpr int kLightMax = 32;     // boxes with more points are summed by warps
+constexpr int kSeg = 256;         // points per warp work item of a heavy box
 
-__global__ void k_box_count(const float2* __restrict__ Y, int32_t n, const GridDev* __restrict__ G,
-                            int32_t* __restrict__ bcnt)
+// Points are taken in tiles of kBoxTile consecutive indices per block.  The
+// boxes a tile touches are aggregated in a shared-memory hash table (at most
+// kBoxTile keys in 2 kBoxTile slots, linear probing), so a box that holds
+// most of the points receives one global atomic per tile instead of one per
+// warp.
+constexpr int kBoxThreads = 256;
+constexpr int kBoxRounds = 4;
+constexpr int kBoxTile = kBoxThreads * kBoxRounds;
+constexpr int kBoxHash = 2 * kBoxTile;
+
+struct BoxHash {
+    int key[kBoxHash];
+    int val[kBoxHash];
+    int base[kBoxHash];
+};
+
+__device__ __forceinline__ void box_hash_clear(BoxHash& H)
 {
+    for (int i = threadIdx.x; i < kBoxHash; i += blockDim.x) {
+        H.key[i] = -1;
+        H.val[i] = 0;
+    }
+}
+
+// Slot of `box` (inserted if absent); the table never holds more than half
+// its slots, so the probe ends within kBoxHash steps.
+__device__ __forceinline__ int box_hash_slot(BoxHash& H, int box)
+{
+    int slot = (int)(((unsigned)box * 2654435761u) >> 21) & (kBoxHash - 1);
+    for (int k = 0; k < kBoxHash; ++k) {
+        const int old = atomicCAS(&H.key[slot], -1, box);
+        if (old == -1 || old == box) return slot;
+        slot = (slot + 1) & (kBoxHash - 1);
+    }
+    return -1;
+}
+
+__global__ void __launch_bounds__(kBoxThreads) k_box_count(const float2* __restrict__ Y, int32_t n,
+                                                           const GridDev* __restrict__ G,
+                                                           int32_t* __restrict__ bcnt)
+{
+    __shared__ BoxHash H;
     const float lo = G->lo, h = G->h;
     const int I = G->I;
-    const unsigned ltm = lanemask_lt();
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = i0 + threadIdx.x;
-        int box = -1;
-        if (i < n) {
-            const float2 p = Y[i];
-            box = box_of(p.y, lo, h, I) * I + box_of(p.x, lo, h, I);
+    const int lane = threadIdx.x & 31;
+    const int64_t ntiles = ((int64_t)n + kBoxTile - 1) / kBoxTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        box_hash_clear(H);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kBoxRounds; ++r) {
+            const int64_t i = tile * kBoxTile + r * kBoxThreads + threadIdx.x;
+            int box = -1;
+            if (i < n) {
+                const float2 p = Y[i];
+                box = box_of(p.y, lo, h, I) * I + box_of(p.x, lo, h, I);
+            }
+            const unsigned peers = __match_any_sync(FULL, box);
+            if (box >= 0 && lane == __ffs(peers) - 1) {
+                const int slot = box_hash_slot(H, box);
+                if (slot >= 0) atomicAdd(&H.val[slot], __popc(peers));
+            }
         }
-        const unsigned peers = __match_any_sync(FULL, box);
-        if (box >= 0 && (peers & ltm) == 0) atomicAdd(&bcnt[box], __popc(peers));
+        __syncthreads();
+        for (int k = threadIdx.x; k < kBoxHash; k += blockDim.x)
+            if (H.key[k] >= 0) atomicAdd(&bcnt[H.key[k]], H.val[k]);
+        __syncthreads();
     }
 }
 
@@ -255,67 +413,123 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total
 // block totals into btot, and, by the last block to finish, the exclusive
 // scan of the totals into bpre; a box's points start at
 // bpre[box / kScanBlock] + (local offset).  Boxes with more than kLightMax
-// points are listed in heavy[0 .. G->nheavy).
+// points are listed in heavy[0 .. G->nheavy), and their segments of kSeg
+// points in items[0 .. G->nitems) as (heavy index, segment).
 __global__ void __launch_bounds__(kScanBlock) k_box_scan(GridDev* __restrict__ G, const int32_t* __restrict__ bcnt,
                                                          int32_t* __restrict__ bcur, int32_t* __restrict__ btot,
-                                                         int32_t* __restrict__ bpre, int32_t* __restrict__ heavy)
+                                                         int32_t* __restrict__ bpre, int32_t* __restrict__ heavy,
+                                                         int2* __restrict__ items)
 {
     __shared__ int wsum[33];
     __shared__ bool last;
     const int NB = G->I * G->I;
+    const int nblk = (NB + kScanBlock - 1) / kScanBlock;  // blocks with boxes; the rest leave
+    if ((int)blockIdx.x >= nblk) return;
     const int b = blockIdx.x * kScanBlock + threadIdx.x;
     const int v = b < NB ? bcnt[b] : 0;
     int tot;
     const int ex = block_exclusive_scan(v, wsum, &tot);
     if (b < NB) bcur[b] = ex;
+    // heavy boxes: listed, and split into segments of kSeg points (the work
+    // items of k_box_spread), written by consecutive lanes
     const bool hv = v > kLightMax;
     const unsigned hm = __ballot_sync(FULL, hv);
     if (hm) {
         const int lane = threadIdx.x & 31, leader = __ffs(hm) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(&G->nheavy, __popc(hm));
-        base = __shfl_sync(FULL, base, leader);
-        if (hv) heavy[base + __popc(hm & lanemask_lt())] = b;
+        const int nseg = hv ? (v + kSeg - 1) / kSeg : 0;
+        int inc = nseg;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += u;
+        }
+        const int nall = __shfl_sync(FULL, inc, 31);
+        int hbase = 0, ibase = 0;
+        if (lane == leader) {
+            hbase = atomicAdd(&G->nheavy, __popc(hm));
+            ibase = atomicAdd(&G->nitems, nall);
+        }
+        hbase = __shfl_sync(FULL, hbase, leader);
+        ibase = __shfl_sync(FULL, ibase, leader);
+        if (hv) heavy[hbase + __popc(hm & lanemask_lt())] = b;
+        for (int k0 = 0; k0 < nall; k0 += 32) {
+            const int k = k0 + lane;
+            int owner = 0;  // first lane whose inclusive segment count exceeds k
+            for (int l = 0; l < 32; ++l) owner += __shfl_sync(FULL, inc, l) <= k ? 1 : 0;
+            owner = min(owner, 31);
+            const int ex = __shfl_sync(FULL, inc - nseg, owner);
+            if (k < nall) items[ibase + k] = make_int2(hbase + __popc(hm & ((1u << owner) - 1u)), k - ex);
+        }
     }
     if (threadIdx.x == 0) {
         btot[blockIdx.x] = tot;
         __threadfence();
-        last = atomicAdd(&G->scan_ticket, 1) == (int)gridDim.x - 1;
+        last = atomicAdd(&G->scan_ticket, 1) == nblk - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    const int t = threadIdx.x < (int)gridDim.x ? ((volatile int32_t*)btot)[threadIdx.x] : 0;
+    const int t = (int)threadIdx.x < nblk ? ((volatile int32_t*)btot)[threadIdx.x] : 0;
     int all;
     const int pre = block_exclusive_scan(t, wsum, &all);
-    if (threadIdx.x < (int)gridDim.x) bpre[threadIdx.x] = pre;
+    if ((int)threadIdx.x < nblk) bpre[threadIdx.x] = pre;
     if (threadIdx.x == 0) G->scan_ticket = 0;
 }
 
-__global__ void k_box_scatter(const float2* __restrict__ Y, int32_t n, const GridDev* __restrict__ G,
-                              int32_t* __restrict__ bcur, const int32_t* __restrict__ bpre, float2* __restrict__ su)
+// Same tiles and hash table as k_box_count: each box a tile touches reserves
+// its range once (one global atomic), and the tile's points of that box take
+// consecutive places in it.
+__global__ void __launch_bounds__(kBoxThreads) k_box_scatter(const float2* __restrict__ Y, int32_t n,
+                                                             const GridDev* __restrict__ G,
+                                                             int32_t* __restrict__ bcur,
+                                                             const int32_t* __restrict__ bpre,
+                                                             float2* __restrict__ su)
 {
+    __shared__ BoxHash H;
     const float lo = G->lo, h = G->h, s = G->s;
     const int I = G->I, P = G->P;
     const int lane = threadIdx.x & 31;
     const unsigned ltm = lanemask_lt();
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = i0 + threadIdx.x;
-        int box = -1, bx = 0, by = 0;
-        float2 p = make_float2(0.f, 0.f);
-        if (i < n) {
-            p = Y[i];
-            bx = box_of(p.x, lo, h, I);
-            by = box_of(p.y, lo, h, I);
-            box = by * I + bx;
+    const int64_t ntiles = ((int64_t)n + kBoxTile - 1) / kBoxTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        box_hash_clear(H);
+        __syncthreads();
+        float2 pt[kBoxRounds];
+        int slot[kBoxRounds], off[kBoxRounds];
+#pragma unroll
+        for (int r = 0; r < kBoxRounds; ++r) {
+            const int64_t i = tile * kBoxTile + r * kBoxThreads + threadIdx.x;
+            int box = -1;
+            pt[r] = make_float2(0.f, 0.f);
+            if (i < n) {
+                pt[r] = Y[i];
+                box = box_of(pt[r].y, lo, h, I) * I + box_of(pt[r].x, lo, h, I);
+            }
+            const unsigned peers = __match_any_sync(FULL, box);
+            const int leader = __ffs(peers) - 1;
+            int sl = -1, o = 0;
+            if (box >= 0 && lane == leader) {
+                sl = box_hash_slot(H, box);
+                if (sl >= 0) o = atomicAdd(&H.val[sl], __popc(peers));
+            }
+            sl = __shfl_sync(FULL, sl, leader);
+            o = __shfl_sync(FULL, o, leader);
+            slot[r] = box >= 0 ? sl : -1;
+            off[r] = o + __popc(peers & ltm);
         }
-        const unsigned peers = __match_any_sync(FULL, box);
-        const int leader = __ffs(peers) - 1;
-        int base = 0;
-        if (box >= 0 && lane == leader) base = bpre[box / kScanBlock] + atomicAdd(&bcur[box], __popc(peers));
-        base = __shfl_sync(FULL, base, leader);
-        if (box >= 0)
-            su[base + __popc(peers & ltm)] = make_float2(local_u(p.x, lo, s, P * bx), local_u(p.y, lo, s, P * by));
+        __syncthreads();
+        for (int k = threadIdx.x; k < kBoxHash; k += blockDim.x) {
+            const int key = H.key[k];
+            if (key >= 0) H.base[k] = bpre[key / kScanBlock] + atomicAdd(&bcur[key], H.val[k]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kBoxRounds; ++r) {
+            if (slot[r] < 0) continue;
+            const int bx = box_of(pt[r].x, lo, h, I), by = box_of(pt[r].y, lo, h, I);
+            su[H.base[slot[r]] + off[r]] = make_float2(local_u(pt[r].x, lo, s, P * bx), local_u(pt[r].y, lo, s, P * by));
+        }
+        __syncthreads();
     }
 }
 
@@ -349,22 +563,132 @@ __device__ __forceinline__ void add_point_row(float2 u, int bb, const float* fx,
     }
 }
 
-// One thread per (box row by, node row bb, box column bx): consecutive
-// threads write consecutive nodes of a grid row.  Boxes with more than
-// kLightMax points are left to k_box_spread_heavy.
+// Charges of one point on node row bb, quantised to integers of the scale
+// hf (|value| * hf < 2^22) by adding 1.5 * 2^23 -- the sum is then exactly
+// the rounded value plus that constant, whose bit pattern is accumulated and
+// removed once per lane at the end.
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+constexpr unsigned kMagicBits = 0x4B400000u;
+
 template <int P>
-__global__ void __launch_bounds__(256) k_box_spread_light(const float2* __restrict__ su,
-                                                          const int32_t* __restrict__ bcnt,
-                                                          const int32_t* __restrict__ bcur,
-                                                          const int32_t* __restrict__ bpre,
-                                                          const GridDev* __restrict__ G, float4* __restrict__ wflt)
+__device__ __forceinline__ void add_point_row_q(float2 u, int bb, const float* hf, unsigned (*ra)[4])
+{
+    float wx[P];
+    lagrange<P>(u.x, wx);
+    const float wyb = lagrange_one<P>(u.y, bb);
+    const float ey = u.y - ((float)bb + 0.5f);
+    const float ey2 = ey * ey;
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+        const float w = wx[a] * wyb;
+        const float ex = u.x - ((float)a + 0.5f);
+        ra[a][0] += __float_as_uint(__fmaf_rn(w, hf[0], kMagic));
+        ra[a][1] += __float_as_uint(__fmaf_rn(w * ex, hf[1], kMagic));
+        ra[a][2] += __float_as_uint(__fmaf_rn(w * ey, hf[2], kMagic));
+        ra[a][3] += __float_as_uint(__fmaf_rn(w * __fmaf_rn(ex, ex, ey2), hf[3], kMagic));
+    }
+}
+
+// The charge grid from the box-sorted points, every node written once.
+// (1) Boxes of more than kLightMax points, one warp per (segment of kSeg
+// points, node row): the lanes sum strided points in 32-bit integers and the
+// sums are reduced across the warp.  A box of one segment is written
+// directly; for the others the segments add their sums to the box's 64-bit
+// accumulator, and the warp that finishes last (a ticket per box) converts
+// it, writes the box's nodes and clears the accumulator and the ticket for
+// the next iteration.  (2) The other boxes, one thread per (box row, node
+// row, box column) -- consecutive threads write consecutive nodes of a grid
+// row -- with exact 64-bit fixed-point sums (empty boxes write zeros).
+// Integer sums make the grid independent of the order of the points within
+// a box and of which warp finishes when.
+template <int P>
+__global__ void __launch_bounds__(256) k_box_spread(const float2* __restrict__ su, const int32_t* __restrict__ bcnt,
+                                                    const int32_t* __restrict__ bcur,
+                                                    const int32_t* __restrict__ bpre,
+                                                    const int32_t* __restrict__ heavy,
+                                                    const int2* __restrict__ items, long long* __restrict__ hacc,
+                                                    int32_t* __restrict__ hticket, const GridDev* __restrict__ G,
+                                                    float4* __restrict__ wflt)
 {
     const int I = G->I, M = G->M;
+    const int nunits = G->nitems * P;
+    float hf[4], ihf[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        hf[q] = G->hf[q];
+        ihf[q] = G->ihf[q];
+    }
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)(gridDim.x * blockDim.x) >> 5;
+    for (int un = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); un < nunits; un += nw) {
+        const int it = un / P, bb = un - it * P;
+        const int2 item = items[it];
+        const int hb = item.x;
+        const int box = heavy[hb];
+        const int cnt = bcnt[box];
+        const int nseg = (cnt + kSeg - 1) / kSeg;
+        const int start = bpre[box / kScanBlock] + bcur[box] - cnt;
+        const int q0 = start + item.y * kSeg, q1 = min(start + cnt, q0 + kSeg);
+        const int by = box / I, bx = box - by * I;
+        unsigned ra[P][4];  // sums modulo 2^32; the true sums are below 2^31
+#pragma unroll
+        for (int a = 0; a < P; ++a)
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) ra[a][ch] = 0u;
+        unsigned m = 0;
+        for (int q = q0 + lane; q < q1; q += 32, ++m) add_point_row_q<P>(su[q], bb, hf, ra);
+        const unsigned bias = m * kMagicBits;
+        int mine = 0;
+#pragma unroll
+        for (int a = 0; a < P; ++a)
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) {
+                ra[a][ch] -= bias;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) ra[a][ch] += __shfl_xor_sync(FULL, ra[a][ch], o);
+                if (lane == a * 4 + ch) mine = (int)ra[a][ch];
+            }
+        if (nseg == 1) {
+            if (lane < P) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int a = 0; a < P; ++a)
+                    if (a == lane)
+                        v = make_float4((float)(int)ra[a][0] * ihf[0], (float)(int)ra[a][1] * ihf[1],
+                                        (float)(int)ra[a][2] * ihf[2], (float)(int)ra[a][3] * ihf[3]);
+                wflt[(int64_t)(by * P + bb) * M + (int64_t)bx * P + lane] = v;
+            }
+            continue;
+        }
+        long long* acc = hacc + (int64_t)hb * P * P * 4;
+        if (lane < P * 4 && mine != 0)
+            atomicAdd((unsigned long long*)(acc + bb * P * 4 + lane), (unsigned long long)(long long)mine);
+        __threadfence();
+        int last = 0;
+        if (lane == 0) last = atomicAdd(&hticket[hb], 1) == nseg * P - 1;
+        last = __shfl_sync(FULL, last, 0);
+        if (!last) continue;
+        __threadfence();
+        if (lane < P * P) {
+            const int nb = lane / P, a = lane - nb * P;
+            long long* q = acc + lane * 4;
+            const long long c0 = __ldcg(q + 0), c1 = __ldcg(q + 1), c2 = __ldcg(q + 2), c3 = __ldcg(q + 3);
+            wflt[(int64_t)(by * P + nb) * M + (int64_t)bx * P + a] =
+                make_float4(fix_to_float(c0, ihf[0]), fix_to_float(c1, ihf[1]), fix_to_float(c2, ihf[2]),
+                            fix_to_float(c3, ihf[3]));
+            q[0] = 0;
+            q[1] = 0;
+            q[2] = 0;
+            q[3] = 0;
+        }
+        if (lane == 0) hticket[hb] = 0;
+    }
+
     float fx[4], ifx[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        fx[q] = (float)G->fx[q];
-        ifx[q] = (float)G->ifx[q];
+        fx[q] = G->fx[q];
+        ifx[q] = G->ifx[q];
     }
     const int64_t total = (int64_t)I * I * P;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -386,56 +710,6 @@ __global__ void __launch_bounds__(256) k_box_spread_light(const float2* __restri
         for (int a = 0; a < P; ++a)
             dst[a] = make_float4(fix_to_float(ra[a][0], ifx[0]), fix_to_float(ra[a][1], ifx[1]),
                                  fix_to_float(ra[a][2], ifx[2]), fix_to_float(ra[a][3], ifx[3]));
-    }
-}
-
-// One warp per box of more than kLightMax points: per node row, the lanes sum
-// strided points and the fixed-point sums are reduced across the warp.
-template <int P>
-__global__ void __launch_bounds__(256) k_box_spread_heavy(const float2* __restrict__ su,
-                                                          const int32_t* __restrict__ bcnt,
-                                                          const int32_t* __restrict__ bcur,
-                                                          const int32_t* __restrict__ bpre,
-                                                          const int32_t* __restrict__ heavy,
-                                                          const GridDev* __restrict__ G, float4* __restrict__ wflt)
-{
-    const int I = G->I, M = G->M, nh = G->nheavy;
-    float fx[4], ifx[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        fx[q] = (float)G->fx[q];
-        ifx[q] = (float)G->ifx[q];
-    }
-    const int lane = threadIdx.x & 31;
-    const int nw = (int)(gridDim.x * blockDim.x) >> 5;
-    for (int hb = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); hb < nh; hb += nw) {
-        const int box = heavy[hb];
-        const int cnt = bcnt[box];
-        const int start = bpre[box / kScanBlock] + bcur[box] - cnt;
-        const int by = box / I, bx = box - by * I;
-        for (int bb = 0; bb < P; ++bb) {
-            long long ra[P][4];
-#pragma unroll
-            for (int a = 0; a < P; ++a)
-#pragma unroll
-                for (int ch = 0; ch < 4; ++ch) ra[a][ch] = 0;
-            for (int q = start + lane; q < start + cnt; q += 32) add_point_row<P>(su[q], bb, fx, ra);
-#pragma unroll
-            for (int a = 0; a < P; ++a)
-#pragma unroll
-                for (int ch = 0; ch < 4; ++ch)
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) ra[a][ch] += __shfl_xor_sync(FULL, ra[a][ch], o);
-            if (lane < P) {
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int a = 0; a < P; ++a)
-                    if (a == lane)
-                        v = make_float4(fix_to_float(ra[a][0], ifx[0]), fix_to_float(ra[a][1], ifx[1]),
-                                        fix_to_float(ra[a][2], ifx[2]), fix_to_float(ra[a][3], ifx[3]));
-                wflt[(int64_t)(by * P + bb) * M + (int64_t)bx * P + lane] = v;
-            }
-        }
     }
 }
 
@@ -652,15 +926,14 @@ __device__ __forceinline__ float odd_transposed(const float* __restrict__ Dh, in
 }
 
 // Z integrand at (kx, ky) from the four charge spectra (see k_conv_cols).
-__device__ __forceinline__ double z_term(float2 s0, float2 s1x, float2 s1y, float2 s2v, float k2, float k1, float d2x,
-                                         float d2y, float s2)
+__device__ __forceinline__ float z_term(float2 s0, float2 s1x, float2 s1y, float2 s2v, float k2, float k1, float d2x,
+                                        float d2y, float s2)
 {
-    const double gx_re = -2.0 * d2x * s0.y - k2 * s1x.x, gx_im = 2.0 * d2x * s0.x - k2 * s1x.y;
-    const double gy_re = -2.0 * d2y * s0.y - k2 * s1y.x, gy_im = 2.0 * d2y * s0.x - k2 * s1y.y;
-    double t = (double)k1 * ((double)s0.x * s0.x + (double)s0.y * s0.y);
-    const double c = (double)s1x.x * gx_re + (double)s1x.y * gx_im + (double)s1y.x * gy_re + (double)s1y.y * gy_im +
-                     (double)k2 * ((double)s2v.x * s0.x + (double)s2v.y * s0.y);
-    return t + 2.0 * (double)s2 * c;
+    const float gx_re = -2.0f * d2x * s0.y - k2 * s1x.x, gx_im = 2.0f * d2x * s0.x - k2 * s1x.y;
+    const float gy_re = -2.0f * d2y * s0.y - k2 * s1y.x, gy_im = 2.0f * d2y * s0.x - k2 * s1y.y;
+    const float t = k1 * (s0.x * s0.x + s0.y * s0.y);
+    const float c = s1x.x * gx_re + s1x.y * gx_im + s1y.x * gy_re + s1y.y * gy_im + k2 * (s2v.x * s0.x + s2v.y * s0.y);
+    return t + 2.0f * s2 * c;
 }
 
 // Product q at (kx, ky) for the inverse column transform (conjugated).
@@ -735,8 +1008,8 @@ __global__ void k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const fl
                 const int64_t o = (int64_t)ky * H + kx;
                 const float2 s0 = SP[(0 * nc + c) * L + ky], s1x = SP[(1 * nc + c) * L + ky];
                 const float2 s1y = SP[(2 * nc + c) * L + ky], s2v = SP[(3 * nc + c) * L + ky];
-                const double wgt = (kx == 0 || 2 * kx == L) ? 1.0 : 2.0;
-                zacc += wgt * z_term(s0, s1x, s1y, s2v, K2h[o], K1h[o], D2h[o], odd_transposed(D2h, kx, ky, L, H), s2);
+                const float wgt = (kx == 0 || 2 * kx == L) ? 1.0f : 2.0f;
+                zacc += (double)(wgt * z_term(s0, s1x, s1y, s2v, K2h[o], K1h[o], D2h[o], odd_transposed(D2h, kx, ky, L, H), s2));
 #pragma unroll
                 for (int q = 0; q < 6; ++q)
                     PR[(q * nc + c) * L + ky] = conv_product(q, s0, s1x, s1y, K2h, Keh, D2h, Deh, kx, ky, L, H);
@@ -779,10 +1052,10 @@ __global__ void k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const fl
                 const int ky = idx / nl, line = idx - ky * nl;
                 const int kx = k0 + line;
                 const int64_t o = (int64_t)ky * H + kx;
-                const double wgt = (kx == 0 || 2 * kx == L) ? 1.0 : 2.0;
-                zacc += wgt * z_term(spec[0][line * L + ky], spec[1][line * L + ky], spec[2][line * L + ky],
+                const float wgt = (kx == 0 || 2 * kx == L) ? 1.0f : 2.0f;
+                zacc += (double)(wgt * z_term(spec[0][line * L + ky], spec[1][line * L + ky], spec[2][line * L + ky],
                                      spec[3][line * L + ky], K2h[o], K1h[o], D2h[o],
-                                     odd_transposed(D2h, kx, ky, L, H), s2);
+                                     odd_transposed(D2h, kx, ky, L, H), s2));
             }
             for (int q = 0; q < 6; ++q) {
                 __syncthreads();
@@ -970,6 +1243,8 @@ IterShape iter_shape(int32_t n, const ltsnet_params* p)
     sh.max_boxes = p->max_boxes;
     sh.Mmax = p->max_boxes * p->nodes_per_box;
     sh.Lmax = 2 * sh.Mmax;
+    // boxes of more than kLightMax points: at most n / (kLightMax + 1)
+    sh.hcap = std::min<int64_t>((int64_t)sh.max_boxes * sh.max_boxes, (int64_t)n / (kLightMax + 1) + 1);
     return sh;
 }
 
@@ -984,7 +1259,13 @@ IterWs iter_carve(Carve& c, const IterShape& sh)
     const int64_t NB = (int64_t)sh.max_boxes * sh.max_boxes;
     w.bcnt = c.take<int32_t>(NB);
     w.bcur = c.take<int32_t>(NB);
-    w.heavy = c.take<int32_t>(NB);
+    // boxes of more than kLightMax points: at most n / (kLightMax + 1) of
+    // them, with at most n / kSeg + (their number) segments
+    const int64_t HC = sh.hcap;
+    w.heavy = c.take<int32_t>(HC);
+    w.hticket = c.take<int32_t>(HC);
+    w.hacc = c.take<long long>(HC * sh.P * sh.P * 4);
+    w.items = c.take<int2>(HC + (int64_t)sh.n / kSeg + 1);
     w.btot = c.take<int32_t>(kScanBlock);
     w.bpre = c.take<int32_t>(kScanBlock);
     w.su = c.take<float2>(sh.n);
@@ -1002,6 +1283,19 @@ IterWs iter_carve(Carve& c, const IterShape& sh)
     w.phi = c.take<float>((int64_t)sh.n * 8);
     w.attr = c.take<float2>(sh.n);
     return w;
+}
+
+// Clears what the iteration kernels expect cleared when a workspace is first
+// used: the status block, the charge grid (the plain spread accumulates into
+// it) and the heavy-box accumulators and tickets (cleared again by their
+// last user every iteration).
+cudaError_t iter_reset(const IterWs& w, const IterShape& sh, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(w.st, 0, sizeof(StatusBlock), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.wflt, 0, sizeof(float4) * (size_t)sh.Mmax * sh.Mmax, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.hticket, 0, sizeof(int32_t) * (size_t)sh.hcap, s)) != cudaSuccess) return e;
+    return cudaMemsetAsync(w.hacc, 0, sizeof(long long) * (size_t)sh.hcap * sh.P * sh.P * 4, s);
 }
 
 cudaError_t launch_bounds_init(const IterWs& w, const float2* Y, int32_t n, int parity, cudaStream_t s)
@@ -1050,7 +1344,7 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
     }
     profile_start(LTSNET_KERNEL_SPREAD, s);
     if (plain) {
-        int64_t blocks = ((int64_t)n + 255) / 256;
+        int64_t blocks = ((int64_t)n + kBoxTile - 1) / kBoxTile;
         if (blocks > kSMs * 8) blocks = kSMs * 8;
         if (blocks < 1) blocks = 1;
         switch (P) {
@@ -1061,20 +1355,18 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
         }
         count_launches(1);
     } else {
-        int64_t blocks = ((int64_t)n + 255) / 256;
+        int64_t blocks = ((int64_t)n + kBoxTile - 1) / kBoxTile;
         if (blocks > kSMs * 8) blocks = kSMs * 8;
         if (blocks < 1) blocks = 1;
-        k_box_count<<<(unsigned)blocks, 256, 0, s>>>(Y, n, w.g, w.bcnt);
+        k_box_count<<<(unsigned)blocks, kBoxThreads, 0, s>>>(Y, n, w.g, w.bcnt);
         const int nsb = (int)(((int64_t)sh.max_boxes * sh.max_boxes + kScanBlock - 1) / kScanBlock);
-        k_box_scan<<<nsb, kScanBlock, 0, s>>>(w.g, w.bcnt, w.bcur, w.btot, w.bpre, w.heavy);
-        k_box_scatter<<<(unsigned)blocks, 256, 0, s>>>(Y, n, w.g, w.bcur, w.bpre, w.su);
-        int64_t lb = ((int64_t)sh.max_boxes * sh.max_boxes * P + 255) / 256;
-        if (lb > kSMs * 16) lb = kSMs * 16;
+        k_box_scan<<<nsb, kScanBlock, 0, s>>>(w.g, w.bcnt, w.bcur, w.btot, w.bpre, w.heavy, w.items);
+        k_box_scatter<<<(unsigned)blocks, kBoxThreads, 0, s>>>(Y, n, w.g, w.bcur, w.bpre, w.su);
         switch (P) {
-#define LT_SPREAD(PP)                                                                                          \
-    case PP:                                                                                                   \
-        k_box_spread_light<PP><<<(unsigned)lb, 256, 0, s>>>(w.su, w.bcnt, w.bcur, w.bpre, w.g, w.wflt);       \
-        k_box_spread_heavy<PP><<<kSMs * 4, 256, 0, s>>>(w.su, w.bcnt, w.bcur, w.bpre, w.heavy, w.g, w.wflt); \
+#define LT_SPREAD(PP)                                                                                      \
+    case PP:                                                                                               \
+        k_box_spread<PP><<<kSMs * 4, 256, 0, s>>>(w.su, w.bcnt, w.bcur, w.bpre, w.heavy, w.items, w.hacc, \
+                                                   w.hticket, w.g, w.wflt);                               \
         break;
             LT_SPREAD(2)
             LT_SPREAD(3)
@@ -1082,7 +1374,7 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
             default: LT_SPREAD(5)
 #undef LT_SPREAD
         }
-        count_launches(5);
+        count_launches(4);
     }
     profile_stop(LTSNET_KERNEL_SPREAD, s);
     cudaError_t e = cudaGetLastError();

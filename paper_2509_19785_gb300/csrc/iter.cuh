@@ -19,13 +19,15 @@ struct GridDev {
     int32_t P;                   // nodes per box
     int32_t nst;                 // FFT stages
     int32_t radix[kMaxRadix];
-    double fx[4], ifx[4];        // fixed-point scale per charge and its inverse (powers of 2)
+    float fx[4], ifx[4];         // 64-bit fixed-point scale per charge and its inverse (powers of 2)
+    float hf[4], ihf[4];         // 32-bit per-point quantisation of warp-summed boxes
     double Z;                    // sum_{i != j} 1/(1+d^2), from the grid
     double S;                    // sum of P values
     float SoZ;                   // S / Z rounded to FP32 (the repulsion scale)
     int32_t ticket;              // last-block counter for the Z reduction
     int32_t scan_ticket;         // last-block counter of the box scan
-    int32_t nheavy;              // boxes summed by a warp
+    int32_t nheavy;              // boxes summed by warps
+    int32_t nitems;              // their segments
 };
 
 // Per-iteration scalars of the gradient, precomputed on the host in FP64:
@@ -46,7 +48,10 @@ struct IterWs {
     float2* tw;          // twiddles e^{-2 pi i t/L}, kLMax
     int32_t* bcnt;       // max_boxes^2 points per box
     int32_t* bcur;       // max_boxes^2 block-local box offsets / scatter cursors
-    int32_t* heavy;      // boxes summed by a warp (G->nheavy of them)
+    int32_t* heavy;      // boxes summed by warps (G->nheavy of them)
+    int32_t* hticket;    // per heavy box: segments finished
+    long long* hacc;     // per heavy box: P^2 x 4 fixed-point sums
+    int2* items;         // heavy-box segments (heavy index, segment)
     int32_t* btot;       // totals of the box-scan blocks
     int32_t* bpre;       // their exclusive scan
     float2* su;          // n local coordinates, box-sorted
@@ -68,10 +73,12 @@ struct IterShape {
     int32_t P;
     int32_t max_boxes;
     int32_t Mmax, Lmax;
+    int64_t hcap;  // capacity of the heavy-box lists
 };
 
 IterShape iter_shape(int32_t n, const ltsnet_params* p);
 IterWs iter_carve(Carve& c, const IterShape& sh);
+cudaError_t iter_reset(const IterWs& w, const IterShape& sh, cudaStream_t s);
 
 // Box of coordinate x (FP32, the same operations as the oracle's grid rule).
 __device__ __forceinline__ int box_of(float x, float lo, float h, int I)

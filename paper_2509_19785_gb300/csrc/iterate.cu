@@ -766,8 +766,7 @@ ltsnet_status run_core(const int64_t* row_ptr, const int32_t* col, int32_t n, co
     const IterShape sh = iter_shape(n, p);
     Carve ic(r.iter, r.iter_bytes);
     const IterWs w = iter_carve(ic, sh);
-    LT_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StatusBlock), s));
-    LT_CUDA(cudaMemsetAsync(w.wflt, 0, sizeof(float4) * (size_t)sh.Mmax * sh.Mmax, s));
+    LT_CUDA(iter_reset(w, sh, s));
     const int64_t total = schedule_length(p);
     float2* Yw = Y;
     if (reordered) {
@@ -813,8 +812,7 @@ static ltsnet_status prepare_iter(int32_t n, const ltsnet_params* p, void* ws, s
     Carve c(ws, ws_bytes);
     w = iter_carve(c, sh);
     if (!c.ok()) return LTSNET_ERR_WORKSPACE;
-    LT_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StatusBlock), s));
-    LT_CUDA(cudaMemsetAsync(w.wflt, 0, sizeof(float4) * (size_t)sh.Mmax * sh.Mmax, s));
+    LT_CUDA(iter_reset(w, sh, s));
     return LTSNET_OK;
 }
 
