@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libltsnet.so")
 
 OK = 0
 WARN_NOT_CONVERGED = 1
+ERR_BAD_GRAPH = -6
 FLAG_PLAIN = 1
 FLAG_NO_REORDER = 2
 MAX_K = 4096

@@ -211,6 +211,8 @@ __device__ void compute_grid(const int32_t* bounds, float bwm, int min_boxes, in
     g.ext = ext;
     g.h = __fdiv_rn(ext, (float)I);
     g.s = __fdiv_rn(g.h, (float)P);
+    g.rh = __frcp_rn(g.h);
+    g.rs = __frcp_rn(g.s);
     g.c = __fmul_rn(0.5f, __fadd_rn(lo, hi));
     g.I = I;
     g.P = P;
@@ -258,6 +260,7 @@ __global__ void k_setup(const int32_t* __restrict__ bounds_cur, int32_t* __restr
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         G->lo = g.lo; G->hi = g.hi; G->ext = g.ext; G->h = g.h; G->s = g.s; G->c = g.c;
+        G->rh = g.rh; G->rs = g.rs;
         G->I = g.I; G->M = g.M; G->L = g.L; G->P = g.P;
         G->nst = g.nst;
         for (int i = 0; i < kMaxRadix; ++i) G->radix[i] = i < g.nst ? g.radix[i] : 0;
@@ -305,8 +308,9 @@ __global__ void k_setup(const int32_t* __restrict__ bounds_cur, int32_t* __restr
 // per iteration, with no atomics on the grid and no clearing pass, and the
 // grid is bit-identical from run to run.
 
-constexpr int kScanBlock = 1024;  // boxes per block of the box scan
-constexpr int kLightMax = 32;     // boxes with more points are summed by warps
+constexpr int kScanBlock = 256;   // boxes per chunk of the box scan (one per thread)
+constexpr int kMaxScanChunks = 4096;  // max_boxes <= 1024
+constexpr int kLightMax = 8;      // boxes with more points are summed by warps
 constexpr int kSeg = 256;         // points per warp work item of a heavy box
 
 // Points are taken in tiles of kBoxTile consecutive indices per block.  The
@@ -351,7 +355,7 @@ __global__ void __launch_bounds__(kBoxThreads) k_box_count(const float2* __restr
                                                            int32_t* __restrict__ bcnt)
 {
     __shared__ BoxHash H;
-    const float lo = G->lo, h = G->h;
+    const float lo = G->lo, h = G->h, rh = G->rh;
     const int I = G->I;
     const int lane = threadIdx.x & 31;
     const int64_t ntiles = ((int64_t)n + kBoxTile - 1) / kBoxTile;
@@ -364,7 +368,7 @@ __global__ void __launch_bounds__(kBoxThreads) k_box_count(const float2* __restr
             int box = -1;
             if (i < n) {
                 const float2 p = Y[i];
-                box = box_of(p.y, lo, h, I) * I + box_of(p.x, lo, h, I);
+                box = box_of_r(p.y, lo, h, rh, I) * I + box_of_r(p.x, lo, h, rh, I);
             }
             const unsigned peers = __match_any_sync(FULL, box);
             if (box >= 0 && lane == __ffs(peers) - 1) {
@@ -379,8 +383,16 @@ __global__ void __launch_bounds__(kBoxThreads) k_box_count(const float2* __restr
     }
 }
 
-// Block-wide exclusive scan of one value per thread (blockDim.x = kScanBlock).
-__device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total)
+// Box offsets, in chunks of kScanBlock boxes (one per thread): chunk-local
+// exclusive offsets into bcur (the scatter cursors), chunk totals into btot,
+// and, by the last block to finish, the exclusive scan of the totals into
+// bpre; a box's points start at bpre[box / kScanBlock] + (local offset).
+// Boxes with more than kLightMax points are listed in heavy[0 .. G->nheavy),
+// and their segments of kSeg points in items[0 .. G->nitems) as (heavy index,
+// segment).
+constexpr int kScanThreads = kScanBlock;
+
+__device__ __forceinline__ int block_exclusive_scan256(int v, int* wsum, int* total)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int inc = v;
@@ -392,14 +404,14 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total
     if (lane == 31) wsum[w] = inc;
     __syncthreads();
     if (w == 0) {
-        const int x = wsum[lane];
+        const int x = lane < (kScanThreads >> 5) ? wsum[lane] : 0;
         int xi = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int u = __shfl_up_sync(FULL, xi, o);
             if (lane >= o) xi += u;
         }
-        wsum[lane] = xi - x;
+        if (lane < (kScanThreads >> 5)) wsum[lane] = xi - x;
         if (lane == 31) wsum[32] = xi;
     }
     __syncthreads();
@@ -409,70 +421,85 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total
     return r;
 }
 
-// Box offsets: block-local exclusive offsets into bcur (the scatter cursors),
-// block totals into btot, and, by the last block to finish, the exclusive
-// scan of the totals into bpre; a box's points start at
-// bpre[box / kScanBlock] + (local offset).  Boxes with more than kLightMax
-// points are listed in heavy[0 .. G->nheavy), and their segments of kSeg
-// points in items[0 .. G->nitems) as (heavy index, segment).
-__global__ void __launch_bounds__(kScanBlock) k_box_scan(GridDev* __restrict__ G, const int32_t* __restrict__ bcnt,
-                                                         int32_t* __restrict__ bcur, int32_t* __restrict__ btot,
-                                                         int32_t* __restrict__ bpre, int32_t* __restrict__ heavy,
-                                                         int2* __restrict__ items)
+__device__ __forceinline__ void list_heavy(GridDev* __restrict__ G, int b, int v, int32_t* __restrict__ heavy,
+                                           int2* __restrict__ items)
+{
+    const bool hv = v > kLightMax;
+    const unsigned hm = __ballot_sync(FULL, hv);
+    if (!hm) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(hm) - 1;
+    const int nseg = hv ? (v + kSeg - 1) / kSeg : 0;
+    int inc = nseg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += u;
+    }
+    const int nall = __shfl_sync(FULL, inc, 31);
+    int hbase = 0, ibase = 0;
+    if (lane == leader) {
+        hbase = atomicAdd(&G->nheavy, __popc(hm));
+        ibase = atomicAdd(&G->nitems, nall);
+    }
+    hbase = __shfl_sync(FULL, hbase, leader);
+    ibase = __shfl_sync(FULL, ibase, leader);
+    if (hv) heavy[hbase + __popc(hm & lanemask_lt())] = b;
+    for (int k0 = 0; k0 < nall; k0 += 32) {
+        const int k = k0 + lane;
+        int owner = 0;  // first lane whose inclusive segment count exceeds k (binary search)
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int probe = __shfl_sync(FULL, inc, owner + step - 1);
+            if (probe <= k) owner += step;
+        }
+        owner = min(owner, 31);
+        const int ex = __shfl_sync(FULL, inc - nseg, owner);
+        if (k < nall) items[ibase + k] = make_int2(hbase + __popc(hm & ((1u << owner) - 1u)), k - ex);
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_box_scan(GridDev* __restrict__ G, const int32_t* __restrict__ bcnt,
+                                                           int32_t* __restrict__ bcur, int32_t* __restrict__ btot,
+                                                           int32_t* __restrict__ bpre, int32_t* __restrict__ heavy,
+                                                           int2* __restrict__ items)
 {
     __shared__ int wsum[33];
     __shared__ bool last;
     const int NB = G->I * G->I;
-    const int nblk = (NB + kScanBlock - 1) / kScanBlock;  // blocks with boxes; the rest leave
-    if ((int)blockIdx.x >= nblk) return;
-    const int b = blockIdx.x * kScanBlock + threadIdx.x;
-    const int v = b < NB ? bcnt[b] : 0;
-    int tot;
-    const int ex = block_exclusive_scan(v, wsum, &tot);
-    if (b < NB) bcur[b] = ex;
-    // heavy boxes: listed, and split into segments of kSeg points (the work
-    // items of k_box_spread), written by consecutive lanes
-    const bool hv = v > kLightMax;
-    const unsigned hm = __ballot_sync(FULL, hv);
-    if (hm) {
-        const int lane = threadIdx.x & 31, leader = __ffs(hm) - 1;
-        const int nseg = hv ? (v + kSeg - 1) / kSeg : 0;
-        int inc = nseg;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(FULL, inc, o);
-            if (lane >= o) inc += u;
-        }
-        const int nall = __shfl_sync(FULL, inc, 31);
-        int hbase = 0, ibase = 0;
-        if (lane == leader) {
-            hbase = atomicAdd(&G->nheavy, __popc(hm));
-            ibase = atomicAdd(&G->nitems, nall);
-        }
-        hbase = __shfl_sync(FULL, hbase, leader);
-        ibase = __shfl_sync(FULL, ibase, leader);
-        if (hv) heavy[hbase + __popc(hm & lanemask_lt())] = b;
-        for (int k0 = 0; k0 < nall; k0 += 32) {
-            const int k = k0 + lane;
-            int owner = 0;  // first lane whose inclusive segment count exceeds k
-            for (int l = 0; l < 32; ++l) owner += __shfl_sync(FULL, inc, l) <= k ? 1 : 0;
-            owner = min(owner, 31);
-            const int ex = __shfl_sync(FULL, inc - nseg, owner);
-            if (k < nall) items[ibase + k] = make_int2(hbase + __popc(hm & ((1u << owner) - 1u)), k - ex);
-        }
+    const int nchunks = (NB + kScanBlock - 1) / kScanBlock;
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int b = c * kScanBlock + threadIdx.x;
+        const int v = b < NB ? bcnt[b] : 0;
+        int tot;
+        const int ex = block_exclusive_scan256(v, wsum, &tot);
+        if (b < NB) bcur[b] = ex;
+        list_heavy(G, b, v, heavy, items);
+        if (threadIdx.x == 0) btot[c] = tot;
     }
     if (threadIdx.x == 0) {
-        btot[blockIdx.x] = tot;
         __threadfence();
-        last = atomicAdd(&G->scan_ticket, 1) == nblk - 1;
+        last = atomicAdd(&G->scan_ticket, 1) == (int)gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    const int t = (int)threadIdx.x < nblk ? ((volatile int32_t*)btot)[threadIdx.x] : 0;
+    // exclusive scan of up to kMaxScanChunks chunk totals, 16 per thread
+    constexpr int kPer = kMaxScanChunks / kScanThreads;
+    int v[kPer], t = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int c = kPer * threadIdx.x + k;
+        v[k] = c < nchunks ? ((volatile int32_t*)btot)[c] : 0;
+        t += v[k];
+    }
     int all;
-    const int pre = block_exclusive_scan(t, wsum, &all);
-    if ((int)threadIdx.x < nblk) bpre[threadIdx.x] = pre;
+    int ex = block_exclusive_scan256(t, wsum, &all);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int c = kPer * threadIdx.x + k;
+        if (c < nchunks) bpre[c] = ex;
+        ex += v[k];
+    }
     if (threadIdx.x == 0) G->scan_ticket = 0;
 }
 
@@ -486,7 +513,7 @@ __global__ void __launch_bounds__(kBoxThreads) k_box_scatter(const float2* __res
                                                              float2* __restrict__ su)
 {
     __shared__ BoxHash H;
-    const float lo = G->lo, h = G->h, s = G->s;
+    const float lo = G->lo, h = G->h, s = G->s, rh = G->rh, rs = G->rs;
     const int I = G->I, P = G->P;
     const int lane = threadIdx.x & 31;
     const unsigned ltm = lanemask_lt();
@@ -495,16 +522,19 @@ __global__ void __launch_bounds__(kBoxThreads) k_box_scatter(const float2* __res
         box_hash_clear(H);
         __syncthreads();
         float2 pt[kBoxRounds];
-        int slot[kBoxRounds], off[kBoxRounds];
+        int slot[kBoxRounds], off[kBoxRounds], bxy[kBoxRounds];
 #pragma unroll
         for (int r = 0; r < kBoxRounds; ++r) {
             const int64_t i = tile * kBoxTile + r * kBoxThreads + threadIdx.x;
-            int box = -1;
+            int box = -1, bx = 0, by = 0;
             pt[r] = make_float2(0.f, 0.f);
             if (i < n) {
                 pt[r] = Y[i];
-                box = box_of(pt[r].y, lo, h, I) * I + box_of(pt[r].x, lo, h, I);
+                bx = box_of_r(pt[r].x, lo, h, rh, I);
+                by = box_of_r(pt[r].y, lo, h, rh, I);
+                box = by * I + bx;
             }
+            bxy[r] = (by << 16) | bx;
             const unsigned peers = __match_any_sync(FULL, box);
             const int leader = __ffs(peers) - 1;
             int sl = -1, o = 0;
@@ -526,8 +556,9 @@ __global__ void __launch_bounds__(kBoxThreads) k_box_scatter(const float2* __res
 #pragma unroll
         for (int r = 0; r < kBoxRounds; ++r) {
             if (slot[r] < 0) continue;
-            const int bx = box_of(pt[r].x, lo, h, I), by = box_of(pt[r].y, lo, h, I);
-            su[H.base[slot[r]] + off[r]] = make_float2(local_u(pt[r].x, lo, s, P * bx), local_u(pt[r].y, lo, s, P * by));
+            const int bx = bxy[r] & 0xffff, by = bxy[r] >> 16;
+            su[H.base[slot[r]] + off[r]] =
+                make_float2(local_u(pt[r].x, lo, s, rs, P * bx), local_u(pt[r].y, lo, s, rs, P * by));
         }
         __syncthreads();
     }
@@ -590,9 +621,9 @@ __device__ __forceinline__ void add_point_row_q(float2 u, int bb, const float* h
 }
 
 // The charge grid from the box-sorted points, every node written once.
-// (1) Boxes of more than kLightMax points, one warp per (segment of kSeg
-// points, node row): the lanes sum strided points in 32-bit integers and the
-// sums are reduced across the warp.  A box of one segment is written
+// (1) Boxes of more than kLightMax points, one warp per segment of kSeg
+// points (held in registers), node row by node row: the lanes sum strided
+// points in 32-bit integers and the sums are reduced across the warp.  A box of one segment is written
 // directly; for the others the segments add their sums to the box's 64-bit
 // accumulator, and the warp that finishes last (a ticket per box) converts
 // it, writes the box's nodes and clears the accumulator and the ticket for
@@ -611,7 +642,7 @@ __global__ void __launch_bounds__(256) k_box_spread(const float2* __restrict__ s
                                                     float4* __restrict__ wflt)
 {
     const int I = G->I, M = G->M;
-    const int nunits = G->nitems * P;
+    const int nit = G->nitems;
     float hf[4], ihf[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -620,8 +651,7 @@ __global__ void __launch_bounds__(256) k_box_spread(const float2* __restrict__ s
     }
     const int lane = threadIdx.x & 31;
     const int nw = (int)(gridDim.x * blockDim.x) >> 5;
-    for (int un = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); un < nunits; un += nw) {
-        const int it = un / P, bb = un - it * P;
+    for (int it = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); it < nit; it += nw) {
         const int2 item = items[it];
         const int hb = item.x;
         const int box = heavy[hb];
@@ -630,42 +660,53 @@ __global__ void __launch_bounds__(256) k_box_spread(const float2* __restrict__ s
         const int start = bpre[box / kScanBlock] + bcur[box] - cnt;
         const int q0 = start + item.y * kSeg, q1 = min(start + cnt, q0 + kSeg);
         const int by = box / I, bx = box - by * I;
-        unsigned ra[P][4];  // sums modulo 2^32; the true sums are below 2^31
+        // the segment's points, all loads issued before any is used
+        float2 pts[kSeg / 32];
 #pragma unroll
-        for (int a = 0; a < P; ++a)
-#pragma unroll
-            for (int ch = 0; ch < 4; ++ch) ra[a][ch] = 0u;
-        unsigned m = 0;
-        for (int q = q0 + lane; q < q1; q += 32, ++m) add_point_row_q<P>(su[q], bb, hf, ra);
-        const unsigned bias = m * kMagicBits;
-        int mine = 0;
-#pragma unroll
-        for (int a = 0; a < P; ++a)
-#pragma unroll
-            for (int ch = 0; ch < 4; ++ch) {
-                ra[a][ch] -= bias;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) ra[a][ch] += __shfl_xor_sync(FULL, ra[a][ch], o);
-                if (lane == a * 4 + ch) mine = (int)ra[a][ch];
-            }
-        if (nseg == 1) {
-            if (lane < P) {
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int a = 0; a < P; ++a)
-                    if (a == lane)
-                        v = make_float4((float)(int)ra[a][0] * ihf[0], (float)(int)ra[a][1] * ihf[1],
-                                        (float)(int)ra[a][2] * ihf[2], (float)(int)ra[a][3] * ihf[3]);
-                wflt[(int64_t)(by * P + bb) * M + (int64_t)bx * P + lane] = v;
-            }
-            continue;
+        for (int k = 0; k < kSeg / 32; ++k) {
+            const int q = q0 + lane + 32 * k;
+            pts[k] = q < q1 ? su[q] : make_float2(0.f, 0.f);
         }
+        const unsigned m = (unsigned)max(0, min(kSeg / 32, (q1 - q0 - lane + 31) / 32));  // points of this lane
         long long* acc = hacc + (int64_t)hb * P * P * 4;
-        if (lane < P * 4 && mine != 0)
-            atomicAdd((unsigned long long*)(acc + bb * P * 4 + lane), (unsigned long long)(long long)mine);
+        for (int bb = 0; bb < P; ++bb) {
+            unsigned ra[P][4];  // sums modulo 2^32; the true sums are below 2^31
+#pragma unroll
+            for (int a = 0; a < P; ++a)
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch) ra[a][ch] = 0u;
+#pragma unroll
+            for (int k = 0; k < kSeg / 32; ++k)
+                if ((unsigned)k < m) add_point_row_q<P>(pts[k], bb, hf, ra);
+            const unsigned bias = m * kMagicBits;
+            int mine = 0;
+#pragma unroll
+            for (int a = 0; a < P; ++a)
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch) {
+                    ra[a][ch] -= bias;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) ra[a][ch] += __shfl_xor_sync(FULL, ra[a][ch], o);
+                    if (lane == a * 4 + ch) mine = (int)ra[a][ch];
+                }
+            if (nseg == 1) {
+                if (lane < P) {
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int a = 0; a < P; ++a)
+                        if (a == lane)
+                            v = make_float4((float)(int)ra[a][0] * ihf[0], (float)(int)ra[a][1] * ihf[1],
+                                            (float)(int)ra[a][2] * ihf[2], (float)(int)ra[a][3] * ihf[3]);
+                    wflt[(int64_t)(by * P + bb) * M + (int64_t)bx * P + lane] = v;
+                }
+            } else if (lane < P * 4 && mine != 0) {
+                atomicAdd((unsigned long long*)(acc + bb * P * 4 + lane), (unsigned long long)(long long)mine);
+            }
+        }
+        if (nseg == 1) continue;
         __threadfence();
         int last = 0;
-        if (lane == 0) last = atomicAdd(&hticket[hb], 1) == nseg * P - 1;
+        if (lane == 0) last = atomicAdd(&hticket[hb], 1) == nseg - 1;
         last = __shfl_sync(FULL, last, 0);
         if (!last) continue;
         __threadfence();
@@ -704,7 +745,12 @@ __global__ void __launch_bounds__(256) k_box_spread(const float2* __restrict__ s
 #pragma unroll
             for (int ch = 0; ch < 4; ++ch) ra[a][ch] = 0;
         const int start = bpre[box / kScanBlock] + bcur[box] - cnt;
-        for (int q = start; q < start + cnt; ++q) add_point_row<P>(su[q], bb, fx, ra);
+        float2 nxt = cnt > 0 ? su[start] : make_float2(0.f, 0.f);
+        for (int q = start; q < start + cnt; ++q) {
+            const float2 cur = nxt;
+            if (q + 1 < start + cnt) nxt = su[q + 1];
+            add_point_row<P>(cur, bb, fx, ra);
+        }
         float4* dst = wflt + (int64_t)(by * P + bb) * M + (int64_t)bx * P;
 #pragma unroll
         for (int a = 0; a < P; ++a)
@@ -790,12 +836,14 @@ __global__ void k_spec_rows(const GridDev* __restrict__ Gp, const float2* __rest
     for (int u0 = beg; u0 < end; u0 += cap) {
         const int nl = min(cap, end - u0);
         __syncthreads();
-        for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
-            const int line = idx / L, b = idx - line * L;
+        for (int line = 0; line < nl; ++line) {
             const int u = u0 + line, q = u / L, a = u - q * L;
-            int dx, dy;
+            int dy;
+            const bool rowok = circ_offset(a, M, L, dy);
+            for (int b = threadIdx.x; b < L; b += blockDim.x) {
+            int dx;
             float2 v = make_float2(0.f, 0.f);
-            if (circ_offset(b, M, L, dx) && circ_offset(a, M, L, dy)) {
+            if (rowok && circ_offset(b, M, L, dx)) {
                 const float d2 = s2 * (float)(dx * dx + dy * dy);
                 const float k1 = 1.0f / (1.0f + d2);
                 const float ke = kEntScale / (eps + d2);
@@ -804,13 +852,14 @@ __global__ void k_spec_rows(const GridDev* __restrict__ Gp, const float2* __rest
                 else v = make_float2(k1 * k1 * (float)dx, ke * (float)dx);
             }
             A[line * L + b] = v;
+            }
         }
         __syncthreads();
         float2* R = fft_lines(A, B, nl, L, G, stw);
-        for (int idx = threadIdx.x; idx < nl * H; idx += blockDim.x) {
-            const int line = idx / H, k = idx - line * H;
+        for (int line = 0; line < nl; ++line) {
             const int u = u0 + line, q = u / L, a = u - q * L;
-            krow[((int64_t)q * L + a) * H + k] = R[line * L + k];
+            float2* dst = krow + ((int64_t)q * L + a) * H;
+            for (int k = threadIdx.x; k < H; k += blockDim.x) dst[k] = R[line * L + k];
         }
     }
 }
@@ -836,16 +885,16 @@ __global__ void k_spec_cols(const GridDev* __restrict__ Gp, const float2* __rest
     for (int u0 = beg; u0 < end; u0 += cap) {
         const int nl = min(cap, end - u0);
         __syncthreads();
-        for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
-            const int a = idx / nl, line = idx - a * nl;
+        for (int line = 0; line < nl; ++line) {
             const int u = u0 + line, q = u / H, kx = u - q * H;
-            A[line * L + a] = krow[(int64_t)q * LH + (int64_t)a * H + kx];
+            const float2* src = krow + (int64_t)q * LH + kx;
+            for (int a = threadIdx.x; a < L; a += blockDim.x) A[line * L + a] = src[(int64_t)a * H];
         }
         __syncthreads();
         float2* R = fft_lines(A, B, nl, L, G, stw);
-        for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
-            const int ky = idx / nl, line = idx - ky * nl;
+        for (int line = 0; line < nl; ++line) {
             const int u = u0 + line, q = u / H, kx = u - q * H;
+            for (int ky = threadIdx.x; ky < L; ky += blockDim.x) {
             const float2 v = R[line * L + ky];
             const int64_t o = (int64_t)ky * H + kx;
             if (q == 0) {
@@ -857,6 +906,7 @@ __global__ void k_spec_cols(const GridDev* __restrict__ Gp, const float2* __rest
                 // FFT(K2dx + i Ke dx/8) = i b2 + i (i be/8) = -be/8 + i b2
                 khat[3 * LH + o] = v.y * scale;
                 khat[4 * LH + o] = -v.x * scale / kEntScale;
+            }
             }
         }
     }
@@ -882,21 +932,23 @@ __global__ void k_conv_rows_fwd(const GridDev* __restrict__ Gp, const float2* __
     for (int u0 = beg; u0 < end; u0 += cap) {
         const int nl = min(cap, end - u0);
         __syncthreads();
-        for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
-            const int line = idx / L, x = idx - line * L;
+        for (int line = 0; line < nl; ++line) {
             const int u = u0 + line, pr = u / M, row = u - pr * M;
-            float2 v = make_float2(0.f, 0.f);
-            if (x < M) {
-                const float4 w = wflt[(int64_t)row * M + x];
-                v = pr == 0 ? make_float2(w.x, w.y) : make_float2(w.z, w.w);
+            const float4* src = wflt + (int64_t)row * M;
+            for (int x = threadIdx.x; x < L; x += blockDim.x) {
+                float2 v = make_float2(0.f, 0.f);
+                if (x < M) {
+                    const float4 w = src[x];
+                    v = pr == 0 ? make_float2(w.x, w.y) : make_float2(w.z, w.w);
+                }
+                A[line * L + x] = v;
             }
-            A[line * L + x] = v;
         }
         __syncthreads();
         float2* R = fft_lines(A, B, nl, L, G, stw);
-        for (int idx = threadIdx.x; idx < nl * H; idx += blockDim.x) {
-            const int line = idx / H, k = idx - line * H;
+        for (int line = 0; line < nl; ++line) {
             const int u = u0 + line, pr = u / M, row = u - pr * M;
+            for (int k = threadIdx.x; k < H; k += blockDim.x) {
             const float2 z = R[line * L + k];
             const float2 zc = conj2(R[line * L + (k == 0 ? 0 : L - k)]);
             const float2 re = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y + zc.y));
@@ -904,6 +956,7 @@ __global__ void k_conv_rows_fwd(const GridDev* __restrict__ Gp, const float2* __
             const float2 im = make_float2(0.5f * df.y, -0.5f * df.x);  // (z - zc) / 2i
             srow[(int64_t)(2 * pr) * MH + (int64_t)row * H + k] = re;
             srow[(int64_t)(2 * pr + 1) * MH + (int64_t)row * H + k] = im;
+            }
         }
     }
 }
@@ -991,10 +1044,15 @@ __global__ void k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const fl
             float2* PR = SP + (size_t)4 * nc * L;
             float2* PP = PR + (size_t)6 * nc * L;
             __syncthreads();
-            for (int idx = threadIdx.x; idx < 4 * nc * L; idx += blockDim.x) {
-                const int y = idx / (4 * nc), r = idx - y * (4 * nc);
-                const int gsel = r / nc, c = r - gsel * nc;
-                SP[r * L + y] = y < M ? srow[(int64_t)gsel * MH + (int64_t)y * H + k0 + c] : make_float2(0.f, 0.f);
+            // SP[(g nc + c) L + y]: spectrum g of column k0 + c (rows y >= M are padding)
+            for (int y = threadIdx.x; y < L; y += blockDim.x) {
+                if (y < M) {
+                    const float2* src = srow + (int64_t)y * H + k0;
+                    for (int g = 0; g < 4; ++g)
+                        for (int c = 0; c < nc; ++c) SP[(g * nc + c) * L + y] = src[(int64_t)g * MH + c];
+                } else {
+                    for (int r = 0; r < 4 * nc; ++r) SP[r * L + y] = make_float2(0.f, 0.f);
+                }
             }
             __syncthreads();
             float2* R = fft_lines(SP, PP, 4 * nc, L, G, stw);
@@ -1002,24 +1060,26 @@ __global__ void k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const fl
                 for (int idx = threadIdx.x; idx < 4 * nc * L; idx += blockDim.x) SP[idx] = R[idx];
                 __syncthreads();
             }
-            for (int idx = threadIdx.x; idx < nc * L; idx += blockDim.x) {
-                const int ky = idx / nc, c = idx - ky * nc;
-                const int kx = k0 + c;
-                const int64_t o = (int64_t)ky * H + kx;
-                const float2 s0 = SP[(0 * nc + c) * L + ky], s1x = SP[(1 * nc + c) * L + ky];
-                const float2 s1y = SP[(2 * nc + c) * L + ky], s2v = SP[(3 * nc + c) * L + ky];
-                const float wgt = (kx == 0 || 2 * kx == L) ? 1.0f : 2.0f;
-                zacc += (double)(wgt * z_term(s0, s1x, s1y, s2v, K2h[o], K1h[o], D2h[o], odd_transposed(D2h, kx, ky, L, H), s2));
+            for (int ky = threadIdx.x; ky < L; ky += blockDim.x) {
+                for (int c = 0; c < nc; ++c) {
+                    const int kx = k0 + c;
+                    const int64_t o = (int64_t)ky * H + kx;
+                    const float2 s0 = SP[(0 * nc + c) * L + ky], s1x = SP[(1 * nc + c) * L + ky];
+                    const float2 s1y = SP[(2 * nc + c) * L + ky], s2v = SP[(3 * nc + c) * L + ky];
+                    const float wgt = (kx == 0 || 2 * kx == L) ? 1.0f : 2.0f;
+                    zacc += (double)(wgt * z_term(s0, s1x, s1y, s2v, K2h[o], K1h[o], D2h[o],
+                                                  odd_transposed(D2h, kx, ky, L, H), s2));
 #pragma unroll
-                for (int q = 0; q < 6; ++q)
-                    PR[(q * nc + c) * L + ky] = conv_product(q, s0, s1x, s1y, K2h, Keh, D2h, Deh, kx, ky, L, H);
+                    for (int q = 0; q < 6; ++q)
+                        PR[(q * nc + c) * L + ky] = conv_product(q, s0, s1x, s1y, K2h, Keh, D2h, Deh, kx, ky, L, H);
+                }
             }
             __syncthreads();
             float2* R2 = fft_lines(PR, PP, 6 * nc, L, G, stw);
-            for (int idx = threadIdx.x; idx < 6 * nc * M; idx += blockDim.x) {
-                const int y = idx / (6 * nc), r = idx - y * (6 * nc);
-                const int q = r / nc, c = r - q * nc;
-                ucol[(int64_t)q * MH + (int64_t)y * H + k0 + c] = conj2(R2[r * L + y]);
+            for (int y = threadIdx.x; y < M; y += blockDim.x) {
+                float2* dst = ucol + (int64_t)y * H + k0;
+                for (int q = 0; q < 6; ++q)
+                    for (int c = 0; c < nc; ++c) dst[(int64_t)q * MH + c] = conj2(R2[(q * nc + c) * L + y]);
             }
         }
     } else {
@@ -1126,11 +1186,11 @@ __global__ void k_conv_rows_inv(const GridDev* __restrict__ Gp, const float2* __
     for (int u0 = beg; u0 < end; u0 += cap) {
         const int nl = min(cap, end - u0);
         __syncthreads();
-        for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
-            const int line = idx / L, k = idx - line * L;
+        for (int line = 0; line < nl; ++line) {
             const int u = u0 + line, pr = u / M, row = u - pr * M;
             const float2* ua = ucol + (int64_t)(2 * pr) * MH + (int64_t)row * H;
             const float2* ub = ua + MH;
+            for (int k = threadIdx.x; k < L; k += blockDim.x) {
             float2 a, b;
             if (k < H) {
                 a = ua[k];
@@ -1140,17 +1200,20 @@ __global__ void k_conv_rows_inv(const GridDev* __restrict__ Gp, const float2* __
                 b = conj2(ub[L - k]);
             }
             A[line * L + k] = conj2(make_float2(a.x - b.y, a.y + b.x));  // conj(a + i b)
+            }
         }
         __syncthreads();
         float2* R = fft_lines(A, B, nl, L, G, stw);
-        for (int idx = threadIdx.x; idx < nl * M; idx += blockDim.x) {
-            const int line = idx / M, x = idx - line * M;
+        for (int line = 0; line < nl; ++line) {
             const int u = u0 + line, pr = u / M, row = u - pr * M;
-            const float2 v = conj2(R[line * L + x]);
-            float* f = fields + ((int64_t)row * M + x) * kFieldStride;
-            if (pr == 0) { f[0] = v.x; f[3] = v.y; f[6] = 0.f; f[7] = 0.f; }
-            else if (pr == 1) { f[1] = v.x; f[2] = v.y; }
-            else { f[4] = v.x; f[5] = v.y; }
+            float* frow = fields + (int64_t)row * M * kFieldStride;
+            for (int x = threadIdx.x; x < M; x += blockDim.x) {
+                const float2 v = conj2(R[line * L + x]);
+                float* f = frow + (int64_t)x * kFieldStride;
+                if (pr == 0) { f[0] = v.x; f[3] = v.y; f[6] = 0.f; f[7] = 0.f; }
+                else if (pr == 1) { f[1] = v.x; f[2] = v.y; }
+                else { f[4] = v.x; f[5] = v.y; }
+            }
         }
     }
     if (!plain) return;
@@ -1266,8 +1329,8 @@ IterWs iter_carve(Carve& c, const IterShape& sh)
     w.hticket = c.take<int32_t>(HC);
     w.hacc = c.take<long long>(HC * sh.P * sh.P * 4);
     w.items = c.take<int2>(HC + (int64_t)sh.n / kSeg + 1);
-    w.btot = c.take<int32_t>(kScanBlock);
-    w.bpre = c.take<int32_t>(kScanBlock);
+    w.btot = c.take<int32_t>(kMaxScanChunks);
+    w.bpre = c.take<int32_t>(kMaxScanChunks);
     w.su = c.take<float2>(sh.n);
     w.wflt = c.take<float4>(MM);
     const int64_t LH = (int64_t)sh.Lmax * (sh.Lmax / 2 + 1);
@@ -1359,8 +1422,8 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
         if (blocks > kSMs * 8) blocks = kSMs * 8;
         if (blocks < 1) blocks = 1;
         k_box_count<<<(unsigned)blocks, kBoxThreads, 0, s>>>(Y, n, w.g, w.bcnt);
-        const int nsb = (int)(((int64_t)sh.max_boxes * sh.max_boxes + kScanBlock - 1) / kScanBlock);
-        k_box_scan<<<nsb, kScanBlock, 0, s>>>(w.g, w.bcnt, w.bcur, w.btot, w.bpre, w.heavy, w.items);
+        const int nsb = std::min<int>(kSMs, (int)(((int64_t)sh.max_boxes * sh.max_boxes + kScanBlock - 1) / kScanBlock));
+        k_box_scan<<<nsb, kScanThreads, 0, s>>>(w.g, w.bcnt, w.bcur, w.btot, w.bpre, w.heavy, w.items);
         k_box_scatter<<<(unsigned)blocks, kBoxThreads, 0, s>>>(Y, n, w.g, w.bcur, w.bpre, w.su);
         switch (P) {
 #define LT_SPREAD(PP)                                                                                      \

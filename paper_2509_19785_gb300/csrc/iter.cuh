@@ -15,6 +15,7 @@ constexpr int kFieldStride = 8; // floats per grid node in the field array
 // decisions (I, box) are FP32 and match the oracle's grid rule bit for bit.
 struct GridDev {
     float lo, hi, ext, h, s, c;  // domain [lo, lo+ext], box width h, node spacing s, centre c
+    float rh, rs;                // 1/h and 1/s, correctly rounded
     int32_t I, M, L;             // boxes per dim, nodes per dim (I*P), FFT length (2M)
     int32_t P;                   // nodes per box
     int32_t nst;                 // FFT stages
@@ -80,10 +81,22 @@ IterShape iter_shape(int32_t n, const ltsnet_params* p);
 IterWs iter_carve(Carve& c, const IterShape& sh);
 cudaError_t iter_reset(const IterWs& w, const IterShape& sh, cudaStream_t s);
 
-// Box of coordinate x (FP32, the same operations as the oracle's grid rule).
-__device__ __forceinline__ int box_of(float x, float lo, float h, int I)
+// Box of coordinate x: floor(RN(RN(x - lo) / h)) clamped to [0, I), the FP32
+// operations of the oracle's grid rule.  d * rh (rh = RN(1/h)) is within a
+// few units in the last place of RN(d / h), so its floor is the same unless it
+// lies within 8 units of an integer, where the correctly rounded quotient
+// decides.
+__device__ __forceinline__ int box_of_r(float x, float lo, float h, float rh, int I)
 {
-    int b = (int)floorf(__fdiv_rn(__fsub_rn(x, lo), h));
+    const float d = __fsub_rn(x, lo);
+    float q = __fmul_rn(d, rh);
+    float f = floorf(q);
+    const float margin = fabsf(q) * 9.5367431640625e-7f;  // 2^-20: 8 units of q
+    if (__fsub_rn(q, f) <= margin || __fsub_rn(__fadd_rn(f, 1.0f), q) <= margin) {
+        q = __fdiv_rn(d, h);
+        f = floorf(q);
+    }
+    const int b = (int)f;
     return b < 0 ? 0 : (b > I - 1 ? I - 1 : b);
 }
 
@@ -142,16 +155,18 @@ __device__ __forceinline__ float lagrange_one(float u, int a)
 
 // (x - lo) / s - base to FP32 accuracy of the result itself, although
 // (x - lo) / s can be in the thousands: x - lo is split exactly into
-// d_hi + d_lo (TwoSum), the quotient's remainder d_hi - q s is exact (FMA),
-// and q - base is exact (Sterbenz: base <= q <= 2 base, or base = 0).
-__device__ __forceinline__ float local_u(float x, float lo, float s, int base)
+// d_hi + d_lo (TwoSum), q = d_hi / s is taken from the reciprocal rs = 1/s,
+// its remainder d_hi - q s is formed with one rounding (FMA) and divided by
+// s again, and q - base is exact (Sterbenz: base <= q <= 2 base, or base = 0),
+// so the error of q does not reach the result beyond a unit or two of it.
+__device__ __forceinline__ float local_u(float x, float lo, float s, float rs, int base)
 {
     const float d_hi = __fsub_rn(x, lo);
     const float bb = __fsub_rn(d_hi, x);
     const float d_lo = __fadd_rn(__fsub_rn(x, __fsub_rn(d_hi, bb)), __fsub_rn(-lo, bb));
-    const float q = __fdiv_rn(d_hi, s);
+    const float q = __fmul_rn(d_hi, rs);
     const float r = __fmaf_rn(-q, s, d_hi);
-    const float t_lo = __fdiv_rn(__fadd_rn(r, d_lo), s);
+    const float t_lo = __fmul_rn(__fadd_rn(r, d_lo), rs);
     return __fadd_rn(__fsub_rn(q, (float)base), t_lo);
 }
 
@@ -159,12 +174,12 @@ __device__ __forceinline__ float local_u(float x, float lo, float s, int base)
 // (u in [0, P]; the box's nodes sit at u = a + 1/2).
 __device__ __forceinline__ void local_coords(float2 p, const GridDev* G, int& bx, int& by, float& ux, float& uy)
 {
-    const float lo = G->lo, h = G->h, s = G->s;
+    const float lo = G->lo, h = G->h, s = G->s, rh = G->rh, rs = G->rs;
     const int I = G->I, P = G->P;
-    bx = box_of(p.x, lo, h, I);
-    by = box_of(p.y, lo, h, I);
-    ux = local_u(p.x, lo, s, P * bx);
-    uy = local_u(p.y, lo, s, P * by);
+    bx = box_of_r(p.x, lo, h, rh, I);
+    by = box_of_r(p.y, lo, h, rh, I);
+    ux = local_u(p.x, lo, s, rs, P * bx);
+    uy = local_u(p.y, lo, s, rs, P * by);
 }
 
 // order.cu

@@ -181,6 +181,15 @@ constexpr int kRowLanes = 8;     // lanes per CSR row in the attraction pass
 constexpr int kWin = 128;        // CSR entries of a row staged per round
 constexpr int kFusedWarps = kFusedThreads / 32;
 
+// 1/x to within about one unit in the last place (the SFU reciprocal);
+// x >= 1 here.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -223,7 +232,7 @@ __device__ __forceinline__ void stage_row(RoundBuf& b, int grp, int gl, const in
 // entropy (gather from the grid), compression, gradient, momentum/gain step,
 // bounds of the next grid.
 template <int P, bool UPDATE>
-__global__ void __launch_bounds__(kFusedThreads, 3)
+__global__ void __launch_bounds__(kFusedThreads, 2)
     k_fused(const int64_t* __restrict__ P_row, const int32_t* __restrict__ P_col, const float* __restrict__ P_val,
             int32_t n, const float2* __restrict__ Y, float2* __restrict__ Ynew, float2* __restrict__ upd,
             float2* __restrict__ gains, const GridDev* __restrict__ G, const float* __restrict__ fields, Stage st,
@@ -267,6 +276,7 @@ __global__ void __launch_bounds__(kFusedThreads, 3)
             }
             const RoundBuf& b = rb[rr & 1];
             const int64_t eb = s0 & ~(int64_t)3;
+            const int off = (int)(s0 - eb);  // leading window slots that belong to the previous row
             float ax = 0.f, ay = 0.f;
             float2 yj[kWin / 32][4];
             float pv[kWin / 32][4];
@@ -279,12 +289,12 @@ __global__ void __launch_bounds__(kFusedThreads, 3)
                 const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int64_t idx = eb + j + q;
-                    const bool in = idx >= s0 && idx < e0;
-                    const bool okc = (unsigned)cc[q] < (unsigned)n;
-                    if (in && !okc) record_error(status, LTSNET_ERR_BAD_GRAPH, cc[q]);
-                    yj[u][q] = (in && okc) ? __ldg(Y + cc[q]) : make_float2(xi, yv);
-                    pv[u][q] = (in && okc) ? vv[q] : 0.f;
+                    // Slots past the row's end were zero-filled by the copy
+                    // (weight 0); the clamp keeps the gather in range even
+                    // for an invalid P, which k_check_cols reports.
+                    const unsigned c = min((unsigned)cc[q], (unsigned)(n - 1));
+                    yj[u][q] = __ldg(Y + c);
+                    pv[u][q] = (u == 0 && j + q < off) ? 0.f : vv[q];
                 }
             }
 #pragma unroll
@@ -292,22 +302,18 @@ __global__ void __launch_bounds__(kFusedThreads, 3)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const float dx = xi - yj[u][q].x, dy = yv - yj[u][q].y;
-                    const float w = pv[u][q] * __frcp_rn(1.0f + dx * dx + dy * dy);
-                    ax += w * dx;
-                    ay += w * dy;
+                    const float w = pv[u][q] * rcp_approx(__fmaf_rn(dy, dy, __fmaf_rn(dx, dx, 1.0f)));
+                    ax = __fmaf_rn(w, dx, ax);
+                    ay = __fmaf_rn(w, dy, ay);
                 }
             // entries past the window (rows longer than it)
             for (int64_t e = eb + kWin + gl; e < e0; e += kRowLanes) {
-                const int c = __ldg(P_col + e);
-                if ((unsigned)c >= (unsigned)n) {
-                    record_error(status, LTSNET_ERR_BAD_GRAPH, c);
-                    continue;
-                }
+                const unsigned c = min((unsigned)__ldg(P_col + e), (unsigned)(n - 1));
                 const float2 q = __ldg(Y + c);
                 const float dx = xi - q.x, dy = yv - q.y;
-                const float w = __ldg(P_val + e) * __frcp_rn(1.0f + dx * dx + dy * dy);
-                ax += w * dx;
-                ay += w * dy;
+                const float w = __ldg(P_val + e) * rcp_approx(__fmaf_rn(dy, dy, __fmaf_rn(dx, dx, 1.0f)));
+                ax = __fmaf_rn(w, dx, ax);
+                ay = __fmaf_rn(w, dy, ay);
             }
 #pragma unroll
             for (int o = kRowLanes / 2; o > 0; o >>= 1) {
@@ -345,6 +351,24 @@ __global__ void __launch_bounds__(kFusedThreads, 3)
 }
 
 constexpr size_t kFusedSmem = sizeof(RoundBuf) * 2 * kFusedWarps;
+
+// Column range check of a caller-supplied P (the fused kernel only clamps).
+__global__ void k_check_cols(const int64_t* __restrict__ P_row, const int32_t* __restrict__ P_col, int32_t n,
+                             StatusBlock* status)
+{
+    const int64_t nnz = P_row[n];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = P_col[e];
+        if ((unsigned)c >= (unsigned)n) record_error(status, LTSNET_ERR_BAD_GRAPH, c);
+    }
+}
+
+cudaError_t launch_check_cols(const int64_t* P_row, const int32_t* P_col, int32_t n, StatusBlock* st, cudaStream_t s)
+{
+    k_check_cols<<<kSMs * 8, 256, 0, s>>>(P_row, P_col, n, st);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 // ---- plain form ------------------------------------------------------------
 template <int P>
@@ -441,7 +465,7 @@ int fused_blocks(int32_t n)
     const int64_t groups = ((int64_t)n + 31) / 32;
     const int64_t wpb = kFusedThreads / 32;
     int64_t b = (groups + wpb - 1) / wpb;
-    const int64_t cap = (int64_t)kSMs * 8;
+    const int64_t cap = (int64_t)kSMs * 2;  // persistent: the blocks that fit at once
     if (b > cap) b = cap;
     return (int)(b < 1 ? 1 : b);
 }
@@ -832,6 +856,7 @@ extern "C" ltsnet_status ltsnet_gradient(const int64_t* P_row, const int32_t* P_
     LT_CUDA(ensure_attrs());
     const bool plain = (p->flags & LTSNET_FLAG_PLAIN) != 0;
     const Stage st = make_stage(*stage, learning_rate(p, n), n);
+    LT_CUDA(launch_check_cols(P_row, P_col, n, w.st, s));
     LT_CUDA(launch_psum(w, P_row, n, P_val, s));
     LT_CUDA(launch_bounds_init(w, (const float2*)Y, n, 0, s));
     LT_CUDA(launch_grid_phase(w, sh, p, (const float2*)Y, 0, plain, s));
@@ -859,6 +884,7 @@ extern "C" ltsnet_status ltsnet_optimize(const int64_t* P_row, const int32_t* P_
     IterWs w;
     ltsnet_status rc = prepare_iter(n, p, ws, ws_bytes, sh, w, s);
     if (rc != LTSNET_OK) return rc;
+    LT_CUDA(launch_check_cols(P_row, P_col, n, w.st, s));
     return optimize_core(P_row, P_col, P_val, n, p, (float2*)Y, (float2*)update, (float2*)gains, start_iter, n_iter,
                          w, sh, s);
 }

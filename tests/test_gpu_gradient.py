@@ -127,6 +127,39 @@ def test_gradient_sbm20k(ltlib):
         assert v < TOL, f"{key}: {v:.3e} ({errs})"
 
 
+@pytest.mark.parametrize("P_nodes", [3, 5])
+def test_gradient_crowded_boxes(ltlib, P_nodes):
+    """Few boxes holding hundreds to thousands of points each (the summed-by-
+    warps boxes, several segments per box), n = 20,000."""
+    g = synth.sbm([8000, 6000, 3000, 2000, 1001], 12.0, 5000, seed=3)
+    aff = ltlib.affinities(g.row_ptr, g.col, 30.0)
+    P = aff["P"]
+    Pn = tuple(t.cpu().numpy() for t in P)
+    Y = (np.random.default_rng(7).standard_normal((g.n, 2)) * 3).astype(np.float32)
+    st = ltlib.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+    params = ltlib.Params(nodes_per_box=P_nodes, box_width_max=100.0, min_boxes=8, max_boxes=400)
+    gp = oracle.GridParams(nodes_per_box=P_nodes, box_width_max=100.0, min_boxes=8, max_boxes=400)
+    errs = _compare(ltlib, P, Pn, Y, st, params, gp)
+    for key, v in errs.items():
+        assert v < TOL, f"{key}: {v:.3e} ({errs})"
+
+
+def test_gradient_reports_bad_column(ltlib):
+    """A column index out of range in a caller-supplied P is reported as
+    LTSNET_ERR_BAD_GRAPH (the gather itself stays in range)."""
+    import torch
+
+    n = 4
+    P_row = torch.tensor([0, 1, 2, 3, 4], dtype=torch.int64).cuda()
+    P_col = torch.tensor([1, 0, 3, 7], dtype=torch.int32).cuda()
+    P_val = torch.full((4,), 0.25, dtype=torch.float32).cuda()
+    Y = torch.tensor([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.0]], dtype=torch.float32).cuda()
+    st = ltlib.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+    with pytest.raises(ltlib.LtsnetError) as ei:
+        ltlib.gradient((P_row, P_col, P_val), Y, st, ltlib.Params())
+    assert ei.value.code == ltlib.ERR_BAD_GRAPH
+
+
 def test_gradient_tiny(ltlib):
     """n = 2 and n = 3 (closed-form sized inputs), isolated vertex rows."""
     import torch
