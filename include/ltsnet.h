@@ -227,6 +227,32 @@ ltsnet_status ltsnet_gradient(const int64_t* P_row, const int32_t* P_col, const 
                               void* ws, size_t ws_bytes, ltsnet_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * The cost of Eq. 1 at Y (entropy term in the reading whose gradient is the
+ * Sec. 3.3 kernel) and its derivative with respect to the stored P values:
+ *   C_KL  = lambda_KL [sum p ln p + sum p ln(1 + d^2) + S ln Z]   (Eq. 1, Eq. 4)
+ *   C_CMP = lambda_c / (2n) sum_i |X_i|^2                          (Eq. 1)
+ *   C_ENT = -lambda_r / (4 n^2) sum_{i != j} ln(eps + d_ij^2)      (Eq. 1, reading)
+ *   dC/dp_e = lambda_KL (ln p_e + 1 + ln(1 + d_e^2) + ln Z)        (each entry a leaf)
+ * The sparse sums are exact; Z and the entropy double sum come from the same
+ * grid as ltsnet_gradient (the entropy sum interpolates ln(eps + d^2) in both
+ * arguments: sum_t W0[t] (K_ln * W0)[t] - n ln eps, W0 the spread of charge
+ * 1).  The exaggeration factor does not enter.  Uses the gradient's workspace
+ * (ltsnet_gradient_workspace_size).
+ *   cost     f64[4] (device) or NULL: C_KL, C_CMP, C_ENT, total
+ *   dC_dPval f32[nnz] (device) or NULL (not both NULL)
+ * Column indices outside [0, n) are reported as LTSNET_ERR_BAD_GRAPH.
+ * ------------------------------------------------------------------------- */
+ltsnet_status ltsnet_cost(const int64_t* P_row, const int32_t* P_col, const float* P_val,
+                          int32_t n, const float* Y, const ltsnet_stage* stage,
+                          const ltsnet_params* p, double* cost, float* dC_dPval,
+                          void* ws, size_t ws_bytes, ltsnet_stream stream);
+/* ltsnet_cost with cost = NULL: dC/dp_e only. */
+ltsnet_status ltsnet_grad_pvals(const int64_t* P_row, const int32_t* P_col, const float* P_val,
+                                int32_t n, const float* Y, const ltsnet_stage* stage,
+                                const ltsnet_params* p, float* dC_dPval,
+                                void* ws, size_t ws_bytes, ltsnet_stream stream);
+
+/* ---------------------------------------------------------------------------
  * The descent loop (Alg. 3, "for iterations": gradient, then move every
  * vertex).  Runs iterations [start_iter, start_iter + n_iter) of the stage
  * schedule in `p`, updating Y, update (the previous step) and gains in place:

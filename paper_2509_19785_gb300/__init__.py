@@ -29,7 +29,8 @@ ABI_SYMBOLS = (
     "ltsnet_poll_status",
     "ltsnet_knn_bfs", "ltsnet_calibrate", "ltsnet_symmetrize_max_nnz", "ltsnet_symmetrize_workspace_size",
     "ltsnet_symmetrize", "ltsnet_symmetrize_static_max_entries", "ltsnet_symmetrize_static",
-    "ltsnet_bfs_order_workspace_size", "ltsnet_bfs_order", "ltsnet_gradient_workspace_size", "ltsnet_gradient", "ltsnet_optimize_workspace_size",
+    "ltsnet_bfs_order_workspace_size", "ltsnet_bfs_order", "ltsnet_gradient_workspace_size", "ltsnet_gradient",
+    "ltsnet_cost", "ltsnet_grad_pvals", "ltsnet_optimize_workspace_size",
     "ltsnet_optimize", "ltsnet_run_workspace_size", "ltsnet_run", "ltsnet_run_host", "ltsnet_launch_count",
     "ltsnet_profile_begin", "ltsnet_profile_end",
 )
@@ -90,6 +91,8 @@ def lib():
         L.ltsnet_gradient_workspace_size.argtypes = [i32, pp]
         L.ltsnet_gradient_workspace_size.restype = sz
         L.ltsnet_gradient.argtypes = [P, P, P, i32, P, ctypes.POINTER(CStage), pp, P, P, P, P, sz, P]
+        L.ltsnet_cost.argtypes = [P, P, P, i32, P, ctypes.POINTER(CStage), pp, P, P, P, sz, P]
+        L.ltsnet_grad_pvals.argtypes = [P, P, P, i32, P, ctypes.POINTER(CStage), pp, P, P, sz, P]
         L.ltsnet_optimize_workspace_size.argtypes = [i32, pp]
         L.ltsnet_optimize_workspace_size.restype = sz
         L.ltsnet_optimize.argtypes = [P, P, P, i32, pp, P, P, P, i32, i32, P, sz, P]
@@ -320,6 +323,68 @@ def gradient(P, Y, stage: Stage, params: Params | None = None, parts: bool = Fal
                                  _stream()), "ltsnet_gradient")
     _check(lib().ltsnet_poll_status(_ptr(ws), ws.numel(), _stream()), "ltsnet_gradient (device)")
     return grad, pt, terms
+
+
+def cost(P, Y, stage: Stage, params: Params | None = None, grad_pvals: bool = False, ws=None):
+    """The cost of Eq. 1 at Y: returns (cost f64[4] tensor = C_KL, C_CMP,
+    C_ENT, total; dC/dP_val f32[nnz] tensor or None)."""
+    torch = _torch()
+    params = params or Params()
+    P_row, P_col, P_val = P
+    Y = Y.contiguous()
+    n = Y.shape[0]
+    cp = params.to_c()
+    out = torch.empty((4,), dtype=torch.float64, device="cuda")
+    dP = torch.empty_like(P_val) if grad_pvals else None
+    need = lib().ltsnet_gradient_workspace_size(n, ctypes.byref(cp))
+    if need == 0:
+        raise LtsnetError(-1, "ltsnet_gradient_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need)
+    st = stage.to_c()
+    _check(lib().ltsnet_cost(_ptr(P_row), _ptr(P_col), _ptr(P_val), n, _ptr(Y), ctypes.byref(st), ctypes.byref(cp),
+                             _ptr(out), _ptr(dP), _ptr(ws), ws.numel(), _stream()), "ltsnet_cost")
+    _check(lib().ltsnet_poll_status(_ptr(ws), ws.numel(), _stream()), "ltsnet_cost (device)")
+    return out, dP
+
+
+def _cost_function():
+    torch = _torch()
+
+    class LTsNetCost(torch.autograd.Function):
+        """C(Y, P_val) of Eq. 1 as a differentiable scalar (f64, 0-dim):
+        forward by ltsnet_cost, backward by ltsnet_gradient (dC/dY, the
+        interpolated gradient of Eq. 6 and Eq. 8) and ltsnet_grad_pvals
+        (dC/dP_val).  P_row and P_col are structure, not differentiated."""
+
+        @staticmethod
+        def forward(ctx, Y, P_val, P_row, P_col, stage, params):
+            P = (P_row, P_col, P_val.detach().contiguous())
+            Yd = Y.detach().contiguous()
+            c, dP = cost(P, Yd, stage, params, grad_pvals=True)
+            g, _, _ = gradient(P, Yd, stage, params)
+            ctx.save_for_backward(g, dP)
+            return c[3].clone()
+
+        @staticmethod
+        def backward(ctx, go):
+            g, dP = ctx.saved_tensors
+            s = go.to(torch.float32)
+            return g * s, dP * s, None, None, None, None
+
+    return LTsNetCost
+
+
+_LTsNetCost = None
+
+
+def ltsnet_cost_fn():
+    """The torch.autograd.Function LTsNetCost: apply(Y, P_val, P_row, P_col,
+    stage, params) -> cost."""
+    global _LTsNetCost
+    if _LTsNetCost is None:
+        _LTsNetCost = _cost_function()
+    return _LTsNetCost
 
 
 def optimize(P, Y, update, gains, start_iter: int, n_iter: int, params: Params | None = None, ws=None,

@@ -813,10 +813,12 @@ __device__ __forceinline__ bool circ_offset(int a, int M, int L, int& d)
 }
 
 constexpr float kEntScale = 0.125f;  // Ke is packed scaled by 1/8 to match K2's magnitude
+constexpr float kLnScale = 1.0f / 1024.0f;  // ln(eps + d^2) packed beside K1, scaled to K1's magnitude
 
 // Kernel spectra, pass 1: rows a in [0, L) of the circulant embeddings of
 // three packed complex kernels over node offsets (dx, dy), d^2 = s^2 |.|^2:
-//   q = 0: K2 + i Ke/8      q = 1: K1      q = 2: K2 dx + i Ke dx / 8
+//   q = 0: K2 + i Ke/8      q = 1: K1 + i ln(eps + d^2)/1024
+//   q = 2: K2 dx + i Ke dx / 8
 // transformed along x; columns kx in [0, L/2] are kept (all five kernels are
 // even or odd in x, so the other half follows by symmetry).
 __global__ void k_spec_rows(const GridDev* __restrict__ Gp, const float2* __restrict__ tw, float eps,
@@ -848,7 +850,7 @@ __global__ void k_spec_rows(const GridDev* __restrict__ Gp, const float2* __rest
                 const float k1 = 1.0f / (1.0f + d2);
                 const float ke = kEntScale / (eps + d2);
                 if (q == 0) v = make_float2(k1 * k1, ke);
-                else if (q == 1) v = make_float2(k1, 0.f);
+                else if (q == 1) v = make_float2(k1, kLnScale * logf(eps + d2));
                 else v = make_float2(k1 * k1 * (float)dx, ke * (float)dx);
             }
             A[line * L + b] = v;
@@ -865,8 +867,9 @@ __global__ void k_spec_rows(const GridDev* __restrict__ Gp, const float2* __rest
 }
 
 // Kernel spectra, pass 2: columns kx in [0, L/2], scaled by 1/L^2 (the inverse
-// transforms are unnormalised).  khat[f][ky][kx], f = 0: K2^, 1: Ke^, 2: K1^
-// (real), 3: Im (K2 dx)^, 4: Im (Ke dx)^ (those two spectra are imaginary).
+// transforms are unnormalised).  khat[f][ky][kx], f = 0: K2^, 1: Ke^, 2: K1^,
+// 5: (ln(eps + d^2))^ (real), 3: Im (K2 dx)^, 4: Im (Ke dx)^ (those two
+// spectra are imaginary).
 __global__ void k_spec_cols(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
                             const float2* __restrict__ krow, float* __restrict__ khat, int sm_f2)
 {
@@ -902,6 +905,7 @@ __global__ void k_spec_cols(const GridDev* __restrict__ Gp, const float2* __rest
                 khat[1 * LH + o] = v.y * scale / kEntScale;
             } else if (q == 1) {
                 khat[2 * LH + o] = v.x * scale;
+                khat[5 * LH + o] = v.y * scale / kLnScale;
             } else {
                 // FFT(K2dx + i Ke dx/8) = i b2 + i (i be/8) = -be/8 + i b2
                 khat[3 * LH + o] = v.y * scale;
@@ -1014,6 +1018,21 @@ __device__ __forceinline__ float2 conv_product(int q, float2 s0, float2 s1x, flo
     return conj2(v);
 }
 
+// Sum of one double per thread over the block (tree in `red`, blockDim.x a
+// power of two <= 256); every thread gets the sum.
+__device__ __forceinline__ double block_sum_double(double v, double* red)
+{
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
 __global__ void k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const float2* __restrict__ srow,
                             const float* __restrict__ khat, float2* __restrict__ ucol, double* __restrict__ zblk,
                             int32_t n, int sm_f2)
@@ -1032,7 +1051,8 @@ __global__ void k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const fl
     const float* K1h = khat + 2 * LH;
     const float* D2h = khat + 3 * LH;
     const float* Deh = khat + 4 * LH;
-    double zacc = 0.0;
+    const float* Klh = khat + 5 * LH;
+    double zacc = 0.0, lacc = 0.0;  // Z + n; sum_t S0 (Kl * S0) (Parseval)
     int beg, end;
     block_range(H, beg, end);
     // Batched: 4 spectra + 6 products + 6 work lines per column, two FFT calls.
@@ -1069,6 +1089,7 @@ __global__ void k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const fl
                     const float wgt = (kx == 0 || 2 * kx == L) ? 1.0f : 2.0f;
                     zacc += (double)(wgt * z_term(s0, s1x, s1y, s2v, K2h[o], K1h[o], D2h[o],
                                                   odd_transposed(D2h, kx, ky, L, H), s2));
+                    lacc += (double)(wgt * Klh[o] * (s0.x * s0.x + s0.y * s0.y));
 #pragma unroll
                     for (int q = 0; q < 6; ++q)
                         PR[(q * nc + c) * L + ky] = conv_product(q, s0, s1x, s1y, K2h, Keh, D2h, Deh, kx, ky, L, H);
@@ -1116,6 +1137,8 @@ __global__ void k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const fl
                 zacc += (double)(wgt * z_term(spec[0][line * L + ky], spec[1][line * L + ky], spec[2][line * L + ky],
                                      spec[3][line * L + ky], K2h[o], K1h[o], D2h[o],
                                      odd_transposed(D2h, kx, ky, L, H), s2));
+                const float2 s0 = spec[0][line * L + ky];
+                lacc += (double)(wgt * Klh[o] * (s0.x * s0.x + s0.y * s0.y));
             }
             for (int q = 0; q < 6; ++q) {
                 __syncthreads();
@@ -1133,30 +1156,29 @@ __global__ void k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const fl
             }
         }
     }
-    red[threadIdx.x] = zacc;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
+    // block sums of both accumulators (one shared array, in turn), then the
+    // last block to finish adds the block sums in block order
+    const double zsum = block_sum_double(zacc, red);
+    const double lsum = block_sum_double(lacc, red);
     if (threadIdx.x == 0) {
-        zblk[blockIdx.x] = red[0];
+        zblk[blockIdx.x] = zsum;
+        zblk[512 + blockIdx.x] = lsum;
         __threadfence();
         last = atomicAdd(&Gp->ticket, 1) == (int)gridDim.x - 1;
     }
     __syncthreads();
     if (last) {
         __threadfence();
-        double v = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += ((volatile double*)zblk)[b];
-        red[threadIdx.x] = v;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-            __syncthreads();
+        double v = 0.0, v2 = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+            v += ((volatile double*)zblk)[b];
+            v2 += ((volatile double*)zblk)[512 + b];
         }
+        const double zt = block_sum_double(v, red);
+        const double lt2 = block_sum_double(v2, red);
         if (threadIdx.x == 0) {
-            const double Z = red[0] - (double)n;
+            Gp->Lsum = lt2;
+            const double Z = zt - (double)n;
             Gp->Z = Z;
             Gp->SoZ = (float)(Gp->S / Z);
         }
@@ -1336,7 +1358,7 @@ IterWs iter_carve(Carve& c, const IterShape& sh)
     const int64_t LH = (int64_t)sh.Lmax * (sh.Lmax / 2 + 1);
     const int64_t MH = (int64_t)sh.Mmax * (sh.Lmax / 2 + 1);
     w.krow = c.take<float2>(3 * LH);
-    w.khat = c.take<float>(5 * LH);
+    w.khat = c.take<float>(6 * LH);
     w.srow = c.take<float2>(4 * MH);
     w.ucol = c.take<float2>(6 * MH);
     w.fields = c.take<float>(MM * kFieldStride);

@@ -24,6 +24,7 @@ struct GridDev {
     float hf[4], ihf[4];         // 32-bit per-point quantisation of warp-summed boxes
     double Z;                    // sum_{i != j} 1/(1+d^2), from the grid
     double S;                    // sum of P values
+    double Lsum;                 // sum_{i,j} ln(eps + d^2) from the grid (self terms included)
     float SoZ;                   // S / Z rounded to FP32 (the repulsion scale)
     int32_t ticket;              // last-block counter for the Z reduction
     int32_t scan_ticket;         // last-block counter of the box scan

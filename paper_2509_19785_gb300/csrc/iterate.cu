@@ -178,7 +178,7 @@ __device__ __forceinline__ void block_bounds(float mn, float mx, int32_t* bounds
 
 constexpr int kFusedThreads = 256;
 constexpr int kRowLanes = 8;     // lanes per CSR row in the attraction pass
-constexpr int kWin = 128;        // CSR entries of a row staged per round
+constexpr int kWin = 128;        // CSR entries of a row taken per round (longer rows: the rest directly)
 constexpr int kFusedWarps = kFusedThreads / 32;
 
 // 1/x to within about one unit in the last place (the SFU reciprocal);
@@ -190,61 +190,103 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Per warp and round: the CSR windows of 4 rows (one per 8-lane group).
-struct RoundBuf {
-    int32_t col[4][kWin];
-    float val[4][kWin];
+// Per lane and round: 16 consecutive slots of its row's window (4 chunks of
+// 4 entries), columns as int32 indices or, for the library's own P, as int16
+// offsets from the row (col - row).
+// The raw words are kept until the round that uses them: decoding them at
+// load time would stall the warp on the load right away.
+struct Window {
+    int4 c[4];      // int32 columns, or int16 offsets in (x, y) of each chunk
+    float4 v[4];    // P values
 };
 
-// Stage the window [eb, eb + kWin) of a row (eb = s0 rounded down to a
-// multiple of 4, so every 16-byte copy is aligned); bytes past the row's end
-// are not read (the copy zero-fills them).
-__device__ __forceinline__ void stage_row(RoundBuf& b, int grp, int gl, const int32_t* __restrict__ P_col,
-                                          const float* __restrict__ P_val, int64_t eb, int64_t e0)
+template <bool D16>
+__device__ __forceinline__ void window_cols(const Window& w, int u, int rowi, int* cc)
+{
+    if (D16) {
+        const unsigned x = (unsigned)w.c[u].x, y = (unsigned)w.c[u].y;
+        cc[0] = rowi + (int)(int16_t)(x & 0xffffu);
+        cc[1] = rowi + (int)(int16_t)(x >> 16);
+        cc[2] = rowi + (int)(int16_t)(y & 0xffffu);
+        cc[3] = rowi + (int)(int16_t)(y >> 16);
+    } else {
+        cc[0] = w.c[u].x;
+        cc[1] = w.c[u].y;
+        cc[2] = w.c[u].z;
+        cc[3] = w.c[u].w;
+    }
+}
+
+// Window start: the row start rounded down so that every vector load is
+// aligned (4 int32 / float, or 8 int16 columns).
+template <bool D16>
+__device__ __forceinline__ int64_t window_start(int64_t s0)
+{
+    return D16 ? (s0 & ~(int64_t)7) : (s0 & ~(int64_t)3);
+}
+
+// Load the lane's slots j = 32 u + 4 gl + q (u, q < 4) of the window starting
+// at eb: vector loads that bypass L1 (the stream is read once), scalar
+// loads where a vector would pass the end of the arrays (nnz), nothing past
+// the row's end e0.
+template <bool D16>
+__device__ __forceinline__ void load_window(Window& w, const int32_t* __restrict__ P_col,
+                                            const int16_t* __restrict__ P_d16, const float* __restrict__ P_val,
+                                            int64_t nnz, int64_t eb, int64_t e0, int rowi, int gl)
 {
 #pragma unroll
-    for (int u = 0; u < kWin / 32; ++u) {
-        const int j = 32 * u + 4 * gl;
-        const int64_t e = eb + j;
-        const int64_t left = e0 - e;
-        const int bytes = left >= 4 ? 16 : (left > 0 ? (int)left * 4 : 0);
-        const int64_t src = bytes > 0 ? e : 0;
-        cp_async16(&b.col[grp][j], P_col + src, bytes);
-        cp_async16(&b.val[grp][j], P_val + src, bytes);
+    for (int u = 0; u < 4; ++u) {
+        const int64_t e = eb + 32 * u + 4 * gl;
+        if (e < e0 && e + 4 <= nnz) {
+            w.v[u] = __ldcs((const float4*)(P_val + e));
+            if (D16) {
+                const uint2 d = __ldcs((const uint2*)(P_d16 + e));
+                w.c[u] = make_int4((int)d.x, (int)d.y, 0, 0);
+            } else {
+                w.c[u] = __ldcs((const int4*)(P_col + e));
+            }
+        } else {
+            // near the end of the arrays or past the row: scalar loads (rare),
+            // missing entries as column offset 0 / the row itself, weight 0
+            float vv[4];
+            int cv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool ok = e + q < e0 && e + q < nnz;
+                vv[q] = ok ? P_val[e + q] : 0.f;
+                cv[q] = ok ? (D16 ? (int)(uint16_t)P_d16[e + q] : P_col[e + q]) : (D16 ? 0 : rowi);
+            }
+            w.v[u] = make_float4(vv[0], vv[1], vv[2], vv[3]);
+            w.c[u] = D16 ? make_int4((int)((unsigned)cv[0] | ((unsigned)cv[1] << 16)),
+                                     (int)((unsigned)cv[2] | ((unsigned)cv[3] << 16)), 0, 0)
+                         : make_int4(cv[0], cv[1], cv[2], cv[3]);
+        }
     }
 }
 
 // One warp per 32 consecutive vertices.  Attraction (Eq. 6, first term) in 8
-// rounds of 4 rows, one row per 8-lane group; the CSR windows of round r+1 are
-// copied into shared memory (cp.async) while round r gathers its neighbours'
-// coordinates and computes, so HBM streaming does not wait on the gathers.
-// Entries of rows longer than the window are read directly.  Row r's sum goes
-// to lane r, which then finishes its vertex: interpolated repulsion and
-// entropy (gather from the grid), compression, gradient, momentum/gain step,
-// bounds of the next grid.
-template <int P, bool UPDATE>
+// rounds of 4 rows, one row per 8-lane group, each lane taking 16 slots of
+// its row's 128-entry window; the next round's window is loaded into
+// registers before this round gathers its neighbours' coordinates, so the
+// HBM stream overlaps the gathers.  Entries past the window (rows longer
+// than it) are read directly.  Row r's sum goes to lane r, which then
+// finishes its vertex: interpolated repulsion and entropy (gather from the
+// grid), compression, gradient, momentum/gain step, bounds of the next grid.
+template <int P, bool UPDATE, bool D16>
 __global__ void __launch_bounds__(kFusedThreads, 2)
-    k_fused(const int64_t* __restrict__ P_row, const int32_t* __restrict__ P_col, const float* __restrict__ P_val,
+    k_fused(const int64_t* __restrict__ P_row, const int32_t* __restrict__ P_col, const int16_t* __restrict__ P_d16,
+            const float* __restrict__ P_val,
             int32_t n, const float2* __restrict__ Y, float2* __restrict__ Ynew, float2* __restrict__ upd,
             float2* __restrict__ gains, const GridDev* __restrict__ G, const float* __restrict__ fields, Stage st,
             int32_t* __restrict__ bounds_next, float2* __restrict__ grad_out, float* __restrict__ parts,
             StatusBlock* status)
 {
-    extern __shared__ __align__(16) unsigned char fsm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int grp = lane >> 3, gl = lane & 7;
     const unsigned gmask = 0xffu << (grp * 8);
-    RoundBuf* rb = (RoundBuf*)fsm + 2 * wib;
     const Coeffs k = coeffs(G, st);
+    const int64_t nnz = P_row[n];
     float mn = INFINITY, mx = -INFINITY;
     for (int64_t g0 = ((int64_t)blockIdx.x * kFusedWarps + wib) * 32; g0 < n;
          g0 += (int64_t)gridDim.x * kFusedWarps * 32) {
@@ -254,51 +296,47 @@ __global__ void __launch_bounds__(kFusedThreads, 2)
         const int64_t rs = has ? P_row[row] : 0;
         const int64_t re = has ? P_row[row + 1] : 0;
         float2 A = make_float2(0.f, 0.f);
+        Window nxt;
         {
-            const int src = grp;
-            const int64_t s0 = __shfl_sync(FULL, rs, src), e0 = __shfl_sync(FULL, re, src);
-            stage_row(rb[0], grp, gl, P_col, P_val, s0 & ~(int64_t)3, e0);
-            cp_async_commit();
+            const int64_t s0 = __shfl_sync(FULL, rs, grp), e0 = __shfl_sync(FULL, re, grp);
+            load_window<D16>(nxt, P_col, P_d16, P_val, nnz, window_start<D16>(s0), e0, (int)(g0 + grp), gl);
         }
 #pragma unroll 1
         for (int rr = 0; rr < 8; ++rr) {
+            const Window cur = nxt;
             const int src = rr * 4 + grp;
-            const int64_t s0 = __shfl_sync(FULL, rs, src), e0 = __shfl_sync(FULL, re, src);
-            const float xi = __shfl_sync(FULL, yi.x, src), yv = __shfl_sync(FULL, yi.y, src);
+            const int rowi = (int)(g0 + src);
             if (rr < 7) {
                 const int nsrc = src + 4;
                 const int64_t ns0 = __shfl_sync(FULL, rs, nsrc), ne0 = __shfl_sync(FULL, re, nsrc);
-                stage_row(rb[(rr + 1) & 1], grp, gl, P_col, P_val, ns0 & ~(int64_t)3, ne0);
-                cp_async_commit();
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
+                load_window<D16>(nxt, P_col, P_d16, P_val, nnz, window_start<D16>(ns0), ne0, rowi + 4, gl);
             }
-            const RoundBuf& b = rb[rr & 1];
-            const int64_t eb = s0 & ~(int64_t)3;
-            const int off = (int)(s0 - eb);  // leading window slots that belong to the previous row
+            const int64_t s0 = __shfl_sync(FULL, rs, src), e0 = __shfl_sync(FULL, re, src);
+            const float xi = __shfl_sync(FULL, yi.x, src), yv = __shfl_sync(FULL, yi.y, src);
+            const int64_t eb = window_start<D16>(s0);
+            const int off = (int)(s0 - eb);  // leading slots that belong to the previous row
+            const int64_t len = e0 - eb;     // slots from len on belong to the next rows
             float ax = 0.f, ay = 0.f;
-            float2 yj[kWin / 32][4];
-            float pv[kWin / 32][4];
+            float2 yj[4][4];
+            float pv[4][4];
 #pragma unroll
-            for (int u = 0; u < kWin / 32; ++u) {
+            for (int u = 0; u < 4; ++u) {
                 const int j = 32 * u + 4 * gl;
-                const int4 c4 = *(const int4*)&b.col[grp][j];
-                const float4 v4 = *(const float4*)&b.val[grp][j];
-                const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
-                const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+                const float vv[4] = {cur.v[u].x, cur.v[u].y, cur.v[u].z, cur.v[u].w};
+                int cc[4];
+                window_cols<D16>(cur, u, rowi, cc);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    // Slots past the row's end were zero-filled by the copy
-                    // (weight 0); the clamp keeps the gather in range even
-                    // for an invalid P, which k_check_cols reports.
+                    // Slots of other rows get weight 0; the clamp keeps
+                    // their gathers in range, and those of an invalid P
+                    // (which k_check_cols reports).
                     const unsigned c = min((unsigned)cc[q], (unsigned)(n - 1));
                     yj[u][q] = __ldg(Y + c);
-                    pv[u][q] = (u == 0 && j + q < off) ? 0.f : vv[q];
+                    pv[u][q] = (j + q >= off && j + q < len) ? vv[q] : 0.f;
                 }
             }
 #pragma unroll
-            for (int u = 0; u < kWin / 32; ++u)
+            for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const float dx = xi - yj[u][q].x, dy = yv - yj[u][q].y;
@@ -306,9 +344,9 @@ __global__ void __launch_bounds__(kFusedThreads, 2)
                     ax = __fmaf_rn(w, dx, ax);
                     ay = __fmaf_rn(w, dy, ay);
                 }
-            // entries past the window (rows longer than it)
             for (int64_t e = eb + kWin + gl; e < e0; e += kRowLanes) {
-                const unsigned c = min((unsigned)__ldg(P_col + e), (unsigned)(n - 1));
+                const int ce = D16 ? rowi + (int)__ldg(P_d16 + e) : __ldg(P_col + e);
+                const unsigned c = min((unsigned)ce, (unsigned)(n - 1));
                 const float2 q = __ldg(Y + c);
                 const float dx = xi - q.x, dy = yv - q.y;
                 const float w = __ldg(P_val + e) * rcp_approx(__fmaf_rn(dy, dy, __fmaf_rn(dx, dx, 1.0f)));
@@ -323,7 +361,6 @@ __global__ void __launch_bounds__(kFusedThreads, 2)
             const float sx = __shfl_sync(FULL, ax, (lane & 3) * 8);
             const float sy = __shfl_sync(FULL, ay, (lane & 3) * 8);
             if ((lane >> 2) == rr) A = make_float2(sx, sy);
-            __syncwarp();
         }
         if (has) {
             const Sums F = gather_sums<P>(yi, G, fields);
@@ -350,7 +387,94 @@ __global__ void __launch_bounds__(kFusedThreads, 2)
     if (UPDATE) block_bounds(mn, mx, bounds_next);
 }
 
-constexpr size_t kFusedSmem = sizeof(RoundBuf) * 2 * kFusedWarps;
+constexpr size_t kFusedSmem = 0;  // the windows live in registers
+
+// P's columns as int16 offsets from their row, one warp per row; `far` is set
+// if any offset does not fit (the int32 columns are used then).
+__global__ void k_pack_d16(const int64_t* __restrict__ P_row, const int32_t* __restrict__ P_col, int32_t n,
+                           int16_t* __restrict__ d16, int32_t* __restrict__ far)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += nw) {
+        const int64_t e1 = P_row[row + 1];
+        bool bad = false;
+        for (int64_t e = P_row[row] + lane; e < e1; e += 32) {
+            const int64_t d = (int64_t)P_col[e] - row;
+            bad |= d < -32767 || d > 32767;
+            d16[e] = (int16_t)d;
+        }
+        if (__any_sync(FULL, bad) && lane == 0) atomicExch(far, 1);
+    }
+}
+
+// The cost (Eq. 1 in the entropy reading) at Y: the sparse sums over P,
+//   sum p ln p, sum p ln(1 + d^2) (KL with q_ij = (1+d^2)^-1 / Z, Eq. 4),
+// the compression sum |X|^2, and optionally dC/dp_e = l_KL (ln p_e + 1 +
+// ln(1 + d_e^2) + ln Z) for every stored entry.  Z, S and the entropy grid sum
+// come from the grid phase.  One thread per row; FP64 sums per block, then
+// the last block to finish combines them in block order (deterministic).
+constexpr int kCostThreads = 256;
+constexpr int kCostBlocks = 304;
+
+__global__ void __launch_bounds__(kCostThreads) k_cost(const int64_t* __restrict__ P_row,
+                                                       const int32_t* __restrict__ P_col,
+                                                       const float* __restrict__ P_val, int32_t n,
+                                                       const float2* __restrict__ Y, GridDev* G, float lam_kl,
+                                                       float lam_c, float lam_r, float eps,
+                                                       float* __restrict__ dP, double* __restrict__ blk,
+                                                       double* __restrict__ cost)
+{
+    __shared__ double red[3][kCostThreads];
+    __shared__ bool last;
+    const float lnZ = (float)log(G->Z);
+    double plogp = 0.0, plogk = 0.0, sq = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 yi = Y[i];
+        sq += (double)yi.x * yi.x + (double)yi.y * yi.y;
+        const int64_t e1 = P_row[i + 1];
+        for (int64_t e = P_row[i]; e < e1; ++e) {
+            const float p = P_val[e];
+            const int c = P_col[e];
+            const unsigned cc = min((unsigned)c, (unsigned)(n - 1));
+            const float2 yj = Y[cc];
+            const float dx = yi.x - yj.x, dy = yi.y - yj.y;
+            const float lk = log1pf(__fmaf_rn(dy, dy, dx * dx));
+            if (p > 0.f) plogp += (double)p * (double)logf(p);
+            plogk += (double)p * (double)lk;
+            if (dP) dP[e] = lam_kl * (logf(p) + 1.0f + lk + lnZ);
+        }
+    }
+    red[0][threadIdx.x] = plogp;
+    red[1][threadIdx.x] = plogk;
+    red[2][threadIdx.x] = sq;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 3; ++k) blk[3 * blockIdx.x + k] = red[k][0];
+        __threadfence();
+        last = atomicAdd(&G->ticket, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double t[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < (int)gridDim.x; ++b)
+        for (int k = 0; k < 3; ++k) t[k] += ((volatile double*)blk)[3 * b + k];
+    G->ticket = 0;
+    if (!cost) return;
+    const double c_kl = (double)lam_kl * (t[0] + t[1] + G->S * log(G->Z));
+    const double c_cmp = (double)lam_c / (2.0 * n) * t[2];
+    const double c_ent = -(double)lam_r / (4.0 * (double)n * n) * (G->Lsum - (double)n * log((double)eps));
+    cost[0] = c_kl;
+    cost[1] = c_cmp;
+    cost[2] = c_ent;
+    cost[3] = c_kl + c_cmp + c_ent;
+}
 
 // Column range check of a caller-supplied P (the fused kernel only clamps).
 __global__ void k_check_cols(const int64_t* __restrict__ P_row, const int32_t* __restrict__ P_col, int32_t n,
@@ -479,8 +603,8 @@ int flat_blocks(int64_t n, int per_sm = 8)
 }
 
 template <bool UPDATE>
-cudaError_t launch_point_phase(const int64_t* P_row, const int32_t* P_col, const float* P_val, int32_t n,
-                               const float2* Y, float2* Ynew, float2* upd, float2* gains, const IterWs& w,
+cudaError_t launch_point_phase(const int64_t* P_row, const int32_t* P_col, const int16_t* P_d16, const float* P_val,
+                               int32_t n, const float2* Y, float2* Ynew, float2* upd, float2* gains, const IterWs& w,
                                const IterShape& sh, const Stage& st, int parity, float2* grad, float* parts,
                                bool plain, cudaStream_t s)
 {
@@ -489,9 +613,14 @@ cudaError_t launch_point_phase(const int64_t* P_row, const int32_t* P_col, const
     if (!plain) {
         const int nb = fused_blocks(n);
 #define LT_FUSED(PP)                                                                                          \
-    k_fused<PP, UPDATE><<<nb, kFusedThreads, kFusedSmem, s>>>(P_row, P_col, P_val, n, Y, Ynew, upd, gains, w.g,  \
-                                                              w.fields, \
-                                                     st, bn, grad, parts, w.st)
+    if (P_d16)                                                                                                \
+        k_fused<PP, UPDATE, true><<<nb, kFusedThreads, kFusedSmem, s>>>(P_row, P_col, P_d16, P_val, n, Y, Ynew,  \
+                                                                        upd, gains, w.g, w.fields, st, bn, grad, \
+                                                                        parts, w.st);                            \
+    else                                                                                                      \
+        k_fused<PP, UPDATE, false><<<nb, kFusedThreads, kFusedSmem, s>>>(P_row, P_col, P_d16, P_val, n, Y, Ynew, \
+                                                                         upd, gains, w.g, w.fields, st, bn, grad, \
+                                                                         parts, w.st)
         switch (sh.P) {
             case 2: LT_FUSED(2); break;
             case 3: LT_FUSED(3); break;
@@ -586,11 +715,13 @@ cudaError_t ensure_attrs()
     cudaError_t e = grid_set_smem_attrs();
     if (e != cudaSuccess) return e;
     const int fs = (int)kFusedSmem;
-#define LT_ATTR(PP, UU)                                                                                  \
-    if ((e = cudaFuncSetAttribute(k_fused<PP, UU>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs))) \
+#define LT_ATTR(PP, UU, DD)                                                                                  \
+    if ((e = cudaFuncSetAttribute(k_fused<PP, UU, DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs))) \
         return e;
-    LT_ATTR(2, true) LT_ATTR(3, true) LT_ATTR(4, true) LT_ATTR(5, true)
-    LT_ATTR(2, false) LT_ATTR(3, false) LT_ATTR(4, false) LT_ATTR(5, false)
+    LT_ATTR(2, true, false) LT_ATTR(3, true, false) LT_ATTR(4, true, false) LT_ATTR(5, true, false)
+    LT_ATTR(2, false, false) LT_ATTR(3, false, false) LT_ATTR(4, false, false) LT_ATTR(5, false, false)
+    LT_ATTR(2, true, true) LT_ATTR(3, true, true) LT_ATTR(4, true, true) LT_ATTR(5, true, true)
+    LT_ATTR(2, false, true) LT_ATTR(3, false, true) LT_ATTR(4, false, true) LT_ATTR(5, false, true)
 #undef LT_ATTR
     done = true;
     return cudaSuccess;
@@ -609,7 +740,8 @@ ltsnet_status read_status(StatusBlock* st, cudaStream_t s)
 // The loop over iterations [t0, t0 + niter) on a carved iteration workspace.
 // One iteration i (local index; parity i & 1 picks the layout buffer and
 // the bounds slot): grid phase, then the point phase.
-cudaError_t one_iteration(const int64_t* P_row, const int32_t* P_col, const float* P_val, int32_t n,
+cudaError_t one_iteration(const int64_t* P_row, const int32_t* P_col, const int16_t* P_d16, const float* P_val,
+                          int32_t n,
                           const ltsnet_params* p, float2* Y, float2* upd, float2* gains, const IterWs& w,
                           const IterShape& sh, const Stage& st, int parity, bool plain, cudaStream_t s)
 {
@@ -617,8 +749,8 @@ cudaError_t one_iteration(const int64_t* P_row, const int32_t* P_col, const floa
     float2* nxt = parity ? Y : w.yalt;
     cudaError_t e = launch_grid_phase(w, sh, p, cur, parity, plain, s);
     if (e != cudaSuccess) return e;
-    return launch_point_phase<true>(P_row, P_col, P_val, n, cur, nxt, upd, gains, w, sh, st, parity, nullptr, nullptr,
-                                    plain, s);
+    return launch_point_phase<true>(P_row, P_col, P_d16, P_val, n, cur, nxt, upd, gains, w, sh, st, parity, nullptr,
+                                    nullptr, plain, s);
 }
 
 bool same_stage(const ltsnet_stage& a, const ltsnet_stage& b)
@@ -633,7 +765,10 @@ bool same_stage(const ltsnet_stage& a, const ltsnet_stage& b)
 // graph's launches are counted as their kernels.  While kernels are being
 // timed one by one (ltsnet_profile_begin) every iteration is launched
 // directly.
-ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const float* P_val, int32_t n,
+// P_d16, when not null, holds P's columns as int16 offsets from their row
+// (the fused kernel then streams 6 bytes per entry instead of 8).
+ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const int16_t* P_d16, const float* P_val,
+                            int32_t n,
                             const ltsnet_params* p, float2* Y, float2* upd, float2* gains, int32_t t0, int32_t niter,
                             const IterWs& w, const IterShape& sh, cudaStream_t s)
 {
@@ -652,7 +787,7 @@ ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const fl
         const Stage st = make_stage(sg, lr, n);
         int32_t done = 0;
         if ((i & 1) && run > 0) {  // align to an even iteration
-            LT_CUDA(one_iteration(P_row, P_col, P_val, n, p, Y, upd, gains, w, sh, st, 1, plain, s));
+            LT_CUDA(one_iteration(P_row, P_col, P_d16, P_val, n, p, Y, upd, gains, w, sh, st, 1, plain, s));
             done = 1;
         }
         const int32_t pairs = graphs ? (run - done) / 2 : 0;
@@ -661,9 +796,9 @@ ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const fl
             cudaGraph_t graph = nullptr;
             cudaGraphExec_t exec = nullptr;
             LT_CUDA(cudaStreamBeginCapture(aux->capture, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = one_iteration(P_row, P_col, P_val, n, p, Y, upd, gains, w, sh, st, 0, plain, aux->capture);
+            cudaError_t e = one_iteration(P_row, P_col, P_d16, P_val, n, p, Y, upd, gains, w, sh, st, 0, plain, aux->capture);
             if (e == cudaSuccess)
-                e = one_iteration(P_row, P_col, P_val, n, p, Y, upd, gains, w, sh, st, 1, plain, aux->capture);
+                e = one_iteration(P_row, P_col, P_d16, P_val, n, p, Y, upd, gains, w, sh, st, 1, plain, aux->capture);
             cudaError_t e2 = cudaStreamEndCapture(aux->capture, &graph);
             if (e != cudaSuccess || e2 != cudaSuccess) {
                 if (graph) cudaGraphDestroy(graph);
@@ -683,7 +818,7 @@ ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const fl
             done += 2 * pairs;
         }
         for (; done < run; ++done)
-            LT_CUDA(one_iteration(P_row, P_col, P_val, n, p, Y, upd, gains, w, sh, st, (i + done) & 1, plain, s));
+            LT_CUDA(one_iteration(P_row, P_col, P_d16, P_val, n, p, Y, upd, gains, w, sh, st, (i + done) & 1, plain, s));
         i += run;
     }
     if (niter & 1) LT_CUDA(cudaMemcpyAsync(Y, w.yalt, sizeof(float2) * (size_t)n, cudaMemcpyDeviceToDevice, s));
@@ -697,6 +832,8 @@ struct RunWs {
     int32_t* cnt;
     double* beta;
     double* pcond;
+    int16_t* d16;      // P's columns as offsets from their row (aliases pcond, dead by then)
+    int32_t* far;      // set when some |col - row| exceeds the int16 range
     uint8_t* conv;
     int64_t* P_row;
     int32_t* P_col;
@@ -733,6 +870,8 @@ RunWs run_carve(Carve& c, int32_t n, int64_t m2, const ltsnet_params* p, bool ho
     r.cnt = c.take<int32_t>(n);
     r.beta = c.take<double>(n);
     r.pcond = c.take<double>(nk);
+    r.d16 = (int16_t*)r.pcond;  // 2 nnz <= 4 n k bytes <= 8 n k
+    r.far = c.take<int32_t>(1);
     r.conv = c.take<uint8_t>(n);
     r.P_row = c.take<int64_t>((int64_t)n + 1);
     r.P_col = c.take<int32_t>(2 * nk);
@@ -784,6 +923,18 @@ ltsnet_status run_core(const int64_t* row_ptr, const int32_t* col, int32_t n, co
                                r.sym, r.sym_bytes, s);
     }
     if (rc != LTSNET_OK) return rc;
+    // compact columns when every entry is within int16 range of its row
+    bool d16 = false;
+    if (!(p->flags & LTSNET_FLAG_PLAIN) && nnz > 0) {
+        LT_CUDA(cudaMemsetAsync(r.far, 0, sizeof(int32_t), s));
+        k_pack_d16<<<kSMs * 8, 256, 0, s>>>(r.P_row, r.P_col, n, r.d16, r.far);
+        count_launches(1);
+        LT_CHECK_LAUNCH();
+        int32_t far = 1;
+        LT_CUDA(cudaMemcpyAsync(&far, r.far, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LT_CUDA(cudaStreamSynchronize(s));
+        d16 = far == 0;
+    }
     k_init_state<<<flat_blocks(n), 256, 0, s>>>(r.upd, r.gains, n);
     count_launches(1);
     LT_CHECK_LAUNCH();
@@ -797,7 +948,8 @@ ltsnet_status run_core(const int64_t* row_ptr, const int32_t* col, int32_t n, co
         LT_CUDA(gather_rows2(Y, r.order, n, r.Y2, s));
         Yw = r.Y2;
     }
-    rc = optimize_core(r.P_row, r.P_col, r.P_val, n, p, Yw, r.upd, r.gains, 0, (int32_t)total, w, sh, s);
+    rc = optimize_core(r.P_row, r.P_col, d16 ? r.d16 : nullptr, r.P_val, n, p, Yw, r.upd, r.gains, 0, (int32_t)total,
+                       w, sh, s);
     if (rc != LTSNET_OK) return rc;
     if (reordered) LT_CUDA(gather_rows2(r.Y2, r.inv, n, Y, s));
     ltsnet_status a = read_status(w.st, s);
@@ -860,7 +1012,7 @@ extern "C" ltsnet_status ltsnet_gradient(const int64_t* P_row, const int32_t* P_
     LT_CUDA(launch_psum(w, P_row, n, P_val, s));
     LT_CUDA(launch_bounds_init(w, (const float2*)Y, n, 0, s));
     LT_CUDA(launch_grid_phase(w, sh, p, (const float2*)Y, 0, plain, s));
-    LT_CUDA(launch_point_phase<false>(P_row, P_col, P_val, n, (const float2*)Y, nullptr, nullptr, nullptr, w, sh, st,
+    LT_CUDA(launch_point_phase<false>(P_row, P_col, nullptr, P_val, n, (const float2*)Y, nullptr, nullptr, nullptr, w, sh, st,
                                       0, (float2*)grad, parts, plain, s));
     if (terms) {
         k_terms<<<1, 1, 0, s>>>(w.g, terms);
@@ -868,6 +1020,42 @@ extern "C" ltsnet_status ltsnet_gradient(const int64_t* P_row, const int32_t* P_
         LT_CHECK_LAUNCH();
     }
     return LTSNET_OK;
+}
+
+extern "C" ltsnet_status ltsnet_cost(const int64_t* P_row, const int32_t* P_col, const float* P_val, int32_t n,
+                                     const float* Y, const ltsnet_stage* stage, const ltsnet_params* p, double* cost,
+                                     float* dC_dPval, void* ws, size_t ws_bytes, ltsnet_stream stream)
+{
+    if (n < 1 || !P_row || !P_col || !P_val || !Y || !stage || (!cost && !dC_dPval) || !ws || !params_ok(p))
+        return LTSNET_ERR_INVALID_ARG;
+    if (!aligned16(P_col, P_val, Y) || ((uintptr_t)cost & 7) || ((uintptr_t)dC_dPval & 3))
+        return LTSNET_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    IterShape sh;
+    IterWs w;
+    ltsnet_status rc = prepare_iter(n, p, ws, ws_bytes, sh, w, s);
+    if (rc != LTSNET_OK) return rc;
+    LT_CUDA(ensure_attrs());
+    const bool plain = (p->flags & LTSNET_FLAG_PLAIN) != 0;
+    LT_CUDA(launch_check_cols(P_row, P_col, n, w.st, s));
+    LT_CUDA(launch_psum(w, P_row, n, P_val, s));
+    LT_CUDA(launch_bounds_init(w, (const float2*)Y, n, 0, s));
+    LT_CUDA(launch_grid_phase(w, sh, p, (const float2*)Y, 0, plain, s));
+    LT_CUDA(cudaMemsetAsync(&w.g->ticket, 0, sizeof(int32_t), s));
+    k_cost<<<kCostBlocks, kCostThreads, 0, s>>>(P_row, P_col, P_val, n, (const float2*)Y, w.g, stage->lambda_kl,
+                                                stage->lambda_c, stage->lambda_r, p->eps, dC_dPval, w.sblk, cost);
+    count_launches(1);
+    LT_CHECK_LAUNCH();
+    return LTSNET_OK;
+}
+
+extern "C" ltsnet_status ltsnet_grad_pvals(const int64_t* P_row, const int32_t* P_col, const float* P_val,
+                                           int32_t n, const float* Y, const ltsnet_stage* stage,
+                                           const ltsnet_params* p, float* dC_dPval, void* ws, size_t ws_bytes,
+                                           ltsnet_stream stream)
+{
+    if (!dC_dPval) return LTSNET_ERR_INVALID_ARG;
+    return ltsnet_cost(P_row, P_col, P_val, n, Y, stage, p, nullptr, dC_dPval, ws, ws_bytes, stream);
 }
 
 extern "C" ltsnet_status ltsnet_optimize(const int64_t* P_row, const int32_t* P_col, const float* P_val, int32_t n,
@@ -885,7 +1073,7 @@ extern "C" ltsnet_status ltsnet_optimize(const int64_t* P_row, const int32_t* P_
     ltsnet_status rc = prepare_iter(n, p, ws, ws_bytes, sh, w, s);
     if (rc != LTSNET_OK) return rc;
     LT_CUDA(launch_check_cols(P_row, P_col, n, w.st, s));
-    return optimize_core(P_row, P_col, P_val, n, p, (float2*)Y, (float2*)update, (float2*)gains, start_iter, n_iter,
+    return optimize_core(P_row, P_col, nullptr, P_val, n, p, (float2*)Y, (float2*)update, (float2*)gains, start_iter, n_iter,
                          w, sh, s);
 }
 

@@ -285,3 +285,94 @@ def test_run_with_and_without_reordering(ltlib, grid32):
     ca, _ = oracle.exact_cost(a.cpu().numpy().astype(np.float64), Pn[0], Pn[1], Pv, st)
     cb, _ = oracle.exact_cost(b.cpu().numpy().astype(np.float64), Pn[0], Pn[1], Pv, st)
     assert abs(ca - cb) / abs(cb) < 0.01, (ca, cb)
+
+
+def test_run_compact_columns_match_int32_columns(ltlib, grid32):
+    """ltsnet_run streams P's columns as int16 offsets from their row when they
+    fit; one iteration must then agree with ltsnet_optimize on the same P with
+    int32 columns up to FP32 summation order (the two formats align the CSR
+    windows differently, so the lanes sum the entries in different groups)."""
+    import torch
+
+    g, P, Pn = grid32
+    Y0 = synth.initial_layout(g.n, 9) * 1e4  # spread out: every term matters
+    params = ltlib.Params(stages=ltlib.default_stages(1), reorder=False)
+    a, _ = ltlib.run(g.row_ptr, g.col, torch.from_numpy(Y0), params)
+    Y = torch.from_numpy(Y0).cuda().clone()
+    upd = torch.zeros_like(Y)
+    gains = torch.ones_like(Y)
+    ltlib.optimize(P, Y, upd, gains, 0, 1, params)
+    step = (Y - torch.from_numpy(Y0).cuda()).abs().max().item()
+    assert step > 0
+    assert (a - Y).abs().max().item() <= 1e-5 * step + 1e-6 * Y.abs().max().item()
+
+
+@pytest.mark.parametrize("which", ["init", 300])
+def test_cost_terms_match_oracle(ltlib, grid32, snapshots, which):
+    """C_KL, C_CMP and C_ENT of ltsnet_cost against the oracle's cost with the
+    same interpolation (exact sparse sums, Z and the entropy double sum from
+    the grid)."""
+    import torch
+
+    g, P, Pn = grid32
+    Y = snapshots[0] if which == "init" else snapshots[300]
+    if which == "init":
+        Y = (np.random.default_rng(2).standard_normal((g.n, 2)) * 3).astype(np.float32)
+    st = ltlib.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+    c, dP = ltlib.cost(P, torch.from_numpy(Y).cuda(), st, ltlib.Params(), grad_pvals=True)
+    c = c.cpu().numpy()
+    ost = oracle.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+    ref = oracle.interp_cost(Y, Pn[0], Pn[1], Pn[2].astype(np.float64), ost, oracle.GridParams())
+    for k, key in enumerate(("kl", "cmp", "ent", "total")):
+        assert abs(c[k] - ref[key]) <= 1e-5 * abs(ref[key]) + 1e-9, (key, c[k], ref[key])
+    # dC/dp_e with the same Z
+    rows = np.repeat(np.arange(g.n), np.diff(Pn[0]))
+    d2 = np.sum((Y[rows].astype(np.float64) - Y[Pn[1]]) ** 2, axis=1)
+    want = 1.0 * (np.log(Pn[2].astype(np.float64)) + 1.0 + np.log1p(d2) + np.log(ref["Z"]))
+    got = dP.cpu().numpy()
+    assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want)), np.max(np.abs(got - want))
+
+
+def test_cost_autograd_matches_finite_differences(ltlib, grid32, snapshots):
+    """LTsNetCost: dC/dP_val from backward against central differences of the
+    forward (exact up to FP32 inputs), and dC/dY against central differences
+    of the cost.  The interpolated gradient approximates the derivative of the
+    interpolated cost only to interpolation accuracy (a fine grid here) and
+    the FP32 grid sums add noise to the differences, so dC/dY is held to 10%
+    of the largest gradient component: enough to catch a wrong sign, factor
+    or term."""
+    import torch
+
+    g, P, Pn = grid32
+    Y = torch.from_numpy(snapshots[60]).cuda()
+    st = ltlib.Stage(1, 1.0, 0.01, 0.0, 1.0, 0.8)
+    params = ltlib.Params(box_width_max=0.1, max_boxes=640)
+    F = ltlib.ltsnet_cost_fn()
+    Yv = Y.clone().requires_grad_(True)
+    Pv = P[2].clone().requires_grad_(True)
+    c = F.apply(Yv, Pv, P[0], P[1], st, params)
+    c.backward()
+    gY, gP = Yv.grad, Pv.grad
+    rng = np.random.default_rng(3)
+    for e in rng.choice(P[2].numel(), 5, replace=False):
+        h = float(P[2][e]) * 1e-2
+        Pp, Pm = P[2].clone(), P[2].clone()
+        Pp[e] += h
+        Pm[e] -= h
+        cp = F.apply(Y, Pp, P[0], P[1], st, params).item()
+        cm = F.apply(Y, Pm, P[0], P[1], st, params).item()
+        fd = (cp - cm) / (Pp[e] - Pm[e]).item()
+        assert abs(fd - gP[e].item()) <= 1e-3 * abs(gP[e].item()) + 1e-6, (e, fd, gP[e].item())
+    scale = float(gY.abs().max())
+    Yn = snapshots[60]
+    inner = np.where((Yn.min(1) > Yn.min() + 0.1) & (Yn.max(1) < Yn.max() - 0.1))[0]  # grid bounds unchanged
+    gmag = gY.abs().max(1).values.cpu().numpy()
+    for i in inner[np.argsort(-gmag[inner])[:4]]:  # the largest gradients: FD noise matters least
+        for d in range(2):
+            h = 2e-2
+            Yp, Ym = Y.clone(), Y.clone()
+            Yp[i, d] += h
+            Ym[i, d] -= h
+            fd = (F.apply(Yp, P[2], P[0], P[1], st, params).item()
+                  - F.apply(Ym, P[2], P[0], P[1], st, params).item()) / (2 * h)
+            assert abs(fd - gY[i, d].item()) <= 0.1 * scale, (i, d, fd, gY[i, d].item())

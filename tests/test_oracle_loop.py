@@ -206,3 +206,35 @@ def test_update_rule():
     np.testing.assert_allclose(g2, [[0.8, 0.01], [1.2, 1.2], [0.7, 0.4]])
     np.testing.assert_allclose(u2, 0.5 * upd - 10.0 * g2 * grad)
     np.testing.assert_allclose(Y2, u2)
+
+
+def test_log_kernel_sum_fft_equals_direct():
+    """The entropy double sum on the grid: FFT embedding equals the direct
+    sum over node pairs."""
+    rng = np.random.default_rng(11)
+    W0 = rng.random((9, 9))
+    W0[rng.random((9, 9)) < 0.3] = 0.0
+    a = oracle.log_kernel_sum(W0, 0.37, 0.05)
+    b = oracle.log_kernel_sum_direct(W0, 0.37, 0.05)
+    assert abs(a - b) <= 1e-11 * abs(b)
+
+
+def test_interp_entropy_sum_converges_to_exact():
+    """sum_{i,j} ln(eps + d^2) interpolated on finer and finer grids
+    approaches the exact double sum (self terms n ln eps included), with the
+    error falling as the boxes shrink."""
+    rng = np.random.default_rng(5)
+    n = 40
+    Y = (rng.standard_normal((n, 2)) * 1.5).astype(np.float32)
+    P_row = np.zeros(n + 1, np.int64)
+    P_col = np.zeros(0, np.int32)
+    P_val = np.zeros(0, np.float64)
+    _, parts = oracle.exact_cost(Y.astype(np.float64), P_row, P_col, P_val, oracle.Stage(1, 0, 0, 1, 1, 0))
+    exact = -parts["ent"] * 4 * n * n + n * np.log(oracle.EPS_DEFAULT)  # sum over all ordered pairs incl. i = j
+    errs = []
+    for bw in (1.0, 0.25, 0.0625):
+        gp = oracle.GridParams(box_width_max=bw, min_boxes=4, max_boxes=1350)
+        gi = oracle.grid_rule(Y, gp)
+        W, _ = oracle.spread(Y, gi, gp.nodes_per_box)
+        errs.append(abs(oracle.log_kernel_sum(W[0], gi.s, gp.eps) - exact) / abs(exact))
+    assert errs[2] < errs[0] and errs[2] < 1e-4, errs
