@@ -33,6 +33,8 @@ METRIC = "L-tsNET gradient iters/s at n=1M vs plain FP32 form; batched graphs/s"
 WORKLOAD = "rgg1m"
 PERPLEXITY = 30.0
 ITERS = 1000
+BATCH_ITERS = 750
+BATCH_WORKERS = 16
 FUSED_PROFILE = os.path.join(ROOT, "profiles", "fused_update_rgg1m.md")
 KERNEL_SOURCES = ("paper_2509_19785_gb300/csrc/iterate.cu", "paper_2509_19785_gb300/csrc/iter.cuh")
 
@@ -121,6 +123,25 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest of the ranks' values (timings: the job ends with the
+    slowest replica).  One rank: x itself."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, max_ms: float) -> float:
+    """Whole-job throughput of independent replicas: every rank's units over
+    the slowest rank's time."""
+    return world * units_per_rank / (max_ms / 1e3)
+
+
 def workload():
     import synth
 
@@ -179,15 +200,22 @@ def bench_ltsnet(args):
         ms = e0.elapsed_time(e1)
         launches = lt.launch_count() - l0
         prof = lt.profile_end(lt.KERNEL_FUSED_UPDATE) if profile else None
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, world)
         return ms, launches, prof, Y
 
     # C0 alone (reported, part of every step)
     aff = lt.affinities(g.row_ptr, g.col, PERPLEXITY)
     nnz = int(aff["P"][1].numel())
+    # Column format ltsnet_run streams: int16 offsets when, in the
+    # breadth-first numbering it applies, every column is within 32767 of
+    # its row (P has the same support as the graph's k-hop balls).
+    order, inv, reordered = lt.bfs_order(g.row_ptr, g.col)
+    col_bytes = 4
+    if reordered:
+        invn = inv.cpu().numpy().astype(np.int64)
+        rows = np.repeat(np.arange(n), np.diff(aff["P"][0].cpu().numpy()))
+        cols = aff["P"][1].cpu().numpy().astype(np.int64)
+        col_bytes = 2 if int(np.max(np.abs(invn[cols] - invn[rows]))) <= 32767 else 4
     torch.cuda.synchronize()
     c0 = []
     for _ in range(3):
@@ -209,12 +237,12 @@ def bench_ltsnet(args):
     Yn = Y.cpu().numpy()
     if not np.all(np.isfinite(Yn)):
         raise RuntimeError("non-finite layout")
-    value = world * args.steps * ITERS / (ms / 1e3)
+    value = job_rate(world, args.steps * ITERS, ms)
 
     # plain FP32 form, same workload
     plain = lt.Params(perplexity=PERPLEXITY, stages=lt.default_stages(ITERS), plain=True)
     ms_plain, _, _, _ = timed(plain, max(1, args.steps // 2), 1)
-    value_plain = world * max(1, args.steps // 2) * ITERS / (ms_plain / 1e3)
+    value_plain = job_rate(world, max(1, args.steps // 2) * ITERS, ms_plain)
 
     # end to end through the C ABI with host buffers (copies inside the region)
     Yh0 = synth.initial_layout(n, 1 + rank)
@@ -227,24 +255,44 @@ def bench_ltsnet(args):
         t1 = time.perf_counter()
         if i >= args.warmup:
             e2e_ms.append((t1 - t0) * 1e3)
-    e2e_total = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * args.steps * ITERS / (e2e_total / 1e3)
+    e2e_total = max_over_ranks(sum(e2e_ms), world)
+    e2e_value = job_rate(world, args.steps * ITERS, e2e_total)
 
     # roofline of the fused gather + attraction + compression + update kernel
     peaks = measured_peaks()
-    bytes_per_launch = 8 * nnz + 8 * (n + 1) + 48 * n
+    bytes_per_launch = 8 * nnz + 8 * (n + 1) + 48 * n  # the per-entry and per-vertex figures of the method
+    moved_per_launch = col_bytes * nnz + 4 * nnz + 8 * (n + 1) + 48 * n  # what this P format streams
     fused_ms, fused_launches = prof
     avg_s = fused_ms / 1e3 / max(1, fused_launches)
     achieved = bytes_per_launch / avg_s / 1e9
     roofline = {"kernel": "k_fused (gather + attraction + compression + update)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": ncu_traffic_per_launch(),
-                "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": round(avg_s * 1e6, 2),
+                "algorithmic_bytes_per_launch": bytes_per_launch, "moved_bytes_per_launch": moved_per_launch,
+                "column_format": "int16 offsets from the row" if col_bytes == 2 else "int32",
+                "avg_launch_us": round(avg_s * 1e6, 2),
                 "launches_timed": fused_launches, "peak_source": peaks["source"]}
+
+    # batched form: 512 independent graphs (grids, recursive trees, SBMs,
+    # n log-uniform in [200, 20000]), 750 iterations each, one call
+    batched = None
+    if not args.no_batched:
+        gs = synth.graph_batch(512)
+        y0s = [synth.initial_layout(gb.n, 100 + i) for i, gb in enumerate(gs)]
+        bparams = lt.Params(perplexity=PERPLEXITY, stages=lt.default_stages(BATCH_ITERS))
+        lt.run_batched(gs[:32], y0s[:32], bparams, workers=BATCH_WORKERS)  # warm-up
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        Yb, _ = lt.run_batched(gs, y0s, bparams, workers=BATCH_WORKERS)
+        torch.cuda.synchronize()
+        tb = max_over_ranks(time.perf_counter() - t0, world)
+        if not bool(torch.isfinite(Yb).all()):
+            raise RuntimeError("non-finite batched layout")
+        batched = {"value": round(job_rate(world, len(gs), tb * 1e3), 2), "unit": "graphs/s", "graphs": len(gs),
+                   "vertices": int(sum(gb.n for gb in gs)), "iters_per_graph": BATCH_ITERS, "seconds": round(tb, 3),
+                   "workers": BATCH_WORKERS, "form": "ltsnet_run_batched: host worker threads, one stream each"}
 
     if rank != 0:
         if world > 1:
@@ -269,7 +317,7 @@ def bench_ltsnet(args):
                                f"iterations, 3 nodes/box, min 50 boxes",
                    "n": n, "nnz_P": nnz, "iters_per_step": ITERS, "form": "optimised (fused, deterministic spread)",
                    "step": "C0 (BFS + calibration + symmetrisation) + all iterations",
-                   "l2": "inputs larger than L2: P is 8 bytes x nnz ~ 0.8 GB", "parallelism": f"replicas{world}"},
+                   "l2": "inputs larger than L2: P streams 6-8 bytes x nnz = 0.6-0.8 GB per iteration", "parallelism": f"replicas{world}"},
         "vertex_iters_per_s": round(value * n, 1),
         "c0_ms": round(statistics.median(c0), 3),
         "plain_fp32": {"value": round(value_plain, 2), "unit": "iters/s", "form": "unfused, atomic spread",
@@ -277,6 +325,7 @@ def bench_ltsnet(args):
         "roofline": roofline,
         "e2e": {"value": round(e2e_value, 2), "unit": "iters/s",
                 "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes + 8 * n), "d2h_bytes_per_step": 8 * n},
+        "batched": batched,
         "clocks": clocks,
         "gpu_launches": int(launches),
     }
@@ -367,6 +416,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ltsnet", choices=["ltsnet", "reference"])
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-graph batched measurement")
     args = ap.parse_args()
     line = bench_reference(args) if args.impl == "reference" else bench_ltsnet(args)
     if line is not None:

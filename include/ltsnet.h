@@ -286,6 +286,30 @@ ltsnet_status ltsnet_run_host(const int64_t* row_ptr_host, const int32_t* col_ho
                               ltsnet_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * Many independent graphs (the batched form of the method): ltsnet_run on
+ * each of n_graphs graphs, with the same parameters, concurrently.
+ *   vtx_off  int64[n_graphs+1] (HOST): graph g owns vertices
+ *            [vtx_off[g], vtx_off[g+1]) of Y (f32 [sum n][2], device, in: Y0,
+ *            out: final layouts); vtx_off[0] = 0, every graph non-empty
+ *   edge_off int64[n_graphs+1] (HOST): graph g's columns are
+ *            col[edge_off[g] .. edge_off[g+1]) (int32, device, local ids)
+ *   row_ptr  int64 (device): graph g's n_g+1 local row pointers (from 0) start
+ *            at row_ptr[vtx_off[g] + g]
+ * n_workers (1..64) host threads, each with its own stream and a workspace
+ * slice for the largest graph, take the graphs largest first.  Each graph's
+ * result equals ltsnet_run's for that graph alone.  Synchronous (waits for
+ * `stream` first); returns the first error, else LTSNET_WARN_NOT_CONVERGED if
+ * any graph had rows that missed the perplexity target, else LTSNET_OK.
+ * ------------------------------------------------------------------------- */
+size_t ltsnet_run_batched_workspace_size(int32_t n_graphs, const int64_t* vtx_off,
+                                         const int64_t* edge_off, const ltsnet_params* p,
+                                         int32_t n_workers);
+ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx_off, const int64_t* edge_off,
+                                 const int64_t* row_ptr, const int32_t* col, const ltsnet_params* p,
+                                 float* Y, void* ws, size_t ws_bytes, int32_t n_workers,
+                                 ltsnet_stream stream);
+
+/* ---------------------------------------------------------------------------
  * Instrumentation (host side, not part of the method).
  * ltsnet_launch_count: kernels this library has launched in this process.
  * ltsnet_profile_*: times every launch of one kernel with CUDA events on the

@@ -31,7 +31,8 @@ ABI_SYMBOLS = (
     "ltsnet_symmetrize", "ltsnet_symmetrize_static_max_entries", "ltsnet_symmetrize_static",
     "ltsnet_bfs_order_workspace_size", "ltsnet_bfs_order", "ltsnet_gradient_workspace_size", "ltsnet_gradient",
     "ltsnet_cost", "ltsnet_grad_pvals", "ltsnet_optimize_workspace_size",
-    "ltsnet_optimize", "ltsnet_run_workspace_size", "ltsnet_run", "ltsnet_run_host", "ltsnet_launch_count",
+    "ltsnet_optimize", "ltsnet_run_workspace_size", "ltsnet_run", "ltsnet_run_host",
+    "ltsnet_run_batched_workspace_size", "ltsnet_run_batched", "ltsnet_launch_count",
     "ltsnet_profile_begin", "ltsnet_profile_end",
 )
 
@@ -100,6 +101,9 @@ def lib():
         L.ltsnet_run_workspace_size.restype = sz
         L.ltsnet_run.argtypes = [P, P, i32, pp, P, P, sz, P]
         L.ltsnet_run_host.argtypes = [P, P, i32, pp, P, P, sz, P]
+        L.ltsnet_run_batched_workspace_size.argtypes = [i32, P, P, pp, i32]
+        L.ltsnet_run_batched_workspace_size.restype = sz
+        L.ltsnet_run_batched.argtypes = [i32, P, P, P, P, pp, P, P, sz, i32, P]
         L.ltsnet_launch_count.restype = i64
         L.ltsnet_profile_begin.argtypes = [i32, i32]
         L.ltsnet_profile_end.argtypes = [i32, ctypes.POINTER(f64), ctypes.POINTER(i32)]
@@ -431,6 +435,37 @@ def run(row_ptr, col, Y0, params: Params | None = None, ws=None):
     rc = lib().ltsnet_run(_ptr(row_ptr), _ptr(col), n, ctypes.byref(cp), _ptr(Y), _ptr(ws), ws.numel(), _stream())
     _check(rc, "ltsnet_run")
     return Y, rc
+
+
+def run_batched(graphs, Y0s, params: Params | None = None, workers: int = 16):
+    """The method on many independent graphs at once (ltsnet_run_batched).
+    graphs: objects with row_ptr (int64 [n+1]) and col (int32) numpy arrays;
+    Y0s: matching float32 [n,2] arrays.  Returns (Y, vtx_off): all final
+    layouts in one [sum n, 2] CUDA tensor, graph g in rows
+    vtx_off[g]:vtx_off[g+1]."""
+    import numpy as np
+    torch = _torch()
+    params = params or Params()
+    ns = [int(g.row_ptr.shape[0] - 1) for g in graphs]
+    ms = [int(g.col.shape[0]) for g in graphs]
+    vtx_off = np.zeros(len(graphs) + 1, np.int64)
+    edge_off = np.zeros(len(graphs) + 1, np.int64)
+    vtx_off[1:] = np.cumsum(ns)
+    edge_off[1:] = np.cumsum(ms)
+    rp = torch.from_numpy(np.concatenate([np.asarray(g.row_ptr, np.int64) for g in graphs])).cuda()
+    col = torch.from_numpy(np.concatenate([np.asarray(g.col, np.int32) for g in graphs])).cuda()
+    Y = torch.from_numpy(np.concatenate([np.asarray(y, np.float32) for y in Y0s])).cuda().contiguous()
+    cp = params.to_c()
+    workers = max(1, min(int(workers), 64, len(graphs)))
+    need = lib().ltsnet_run_batched_workspace_size(len(graphs), vtx_off.ctypes.data, edge_off.ctypes.data,
+                                                    ctypes.byref(cp), workers)
+    if need == 0:
+        raise LtsnetError(-1, "ltsnet_run_batched_workspace_size")
+    ws = _workspace(need)
+    rc = lib().ltsnet_run_batched(len(graphs), vtx_off.ctypes.data, edge_off.ctypes.data, _ptr(rp), _ptr(col),
+                                  ctypes.byref(cp), _ptr(Y), _ptr(ws), ws.numel(), workers, _stream())
+    _check(rc, "ltsnet_run_batched")
+    return Y, vtx_off
 
 
 def run_host(row_ptr, col, Y, params: Params | None = None, ws=None):

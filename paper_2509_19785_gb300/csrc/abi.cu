@@ -49,20 +49,34 @@ bool profiling_active()
 }
 
 namespace {
-std::mutex g_aux_mu;
-AuxStreams g_aux[64];
+// Per host thread and device: threads that drive different streams at once
+// (ltsnet_run_batched) each capture and fork on their own streams.
+struct AuxSet {
+    AuxStreams a[64];
+    ~AuxSet()
+    {
+        for (AuxStreams& x : a) {
+            if (!x.ready) continue;
+            cudaStreamDestroy(x.branch);
+            cudaStreamDestroy(x.capture);
+            cudaEventDestroy(x.fork);
+            cudaEventDestroy(x.join);
+        }
+    }
+};
+thread_local AuxSet t_aux;
 }  // namespace
 
-// Internal non-blocking streams and events of the current device, created on
-// first use (they carry the kernel-spectrum branch and graph capture).
+// Internal non-blocking streams and events of the calling thread on the
+// current device, created on first use (they carry the kernel-spectrum
+// branch and graph capture).
 cudaError_t aux_streams(AuxStreams** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_aux_mu);
-    AuxStreams& a = g_aux[dev];
+    AuxStreams& a = t_aux.a[dev];
     if (!a.ready) {
         if ((e = cudaStreamCreateWithFlags(&a.branch, cudaStreamNonBlocking)) != cudaSuccess) return e;
         if ((e = cudaStreamCreateWithFlags(&a.capture, cudaStreamNonBlocking)) != cudaSuccess) return e;

@@ -15,6 +15,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+#include <atomic>
+#include <thread>
 #include <vector>
 
 #include "iter.cuh"
@@ -1097,6 +1100,98 @@ extern "C" ltsnet_status ltsnet_run(const int64_t* row_ptr, const int32_t* col, 
     if (!c.ok()) return LTSNET_ERR_WORKSPACE;
     LT_CUDA(cudaMemsetAsync(r.st, 0, sizeof(StatusBlock), s));
     return run_core(row_ptr, col, n, p, (float2*)Y, r, s);
+}
+
+// ---- many independent graphs -------------------------------------------
+// Graph g occupies vertices [vtx_off[g], vtx_off[g+1]) of Y, its CSR row
+// pointers row_ptr[vtx_off[g] + g .. vtx_off[g+1] + g] (local, from 0) and its
+// columns col[edge_off[g] .. edge_off[g+1]) (local ids).  Host worker threads,
+// each with its own stream and workspace slice, take the graphs largest first
+// and run the whole method on each; graphs share nothing, so each result is
+// the one ltsnet_run gives for that graph alone.
+
+static bool batch_ok(int32_t n_graphs, const int64_t* vtx_off, const int64_t* edge_off, int64_t& max_n,
+                     int64_t& max_m)
+{
+    if (n_graphs < 1 || !vtx_off || !edge_off || vtx_off[0] != 0 || edge_off[0] != 0) return false;
+    max_n = 0;
+    max_m = 0;
+    for (int32_t g = 0; g < n_graphs; ++g) {
+        const int64_t ng = vtx_off[g + 1] - vtx_off[g], mg = edge_off[g + 1] - edge_off[g];
+        if (ng < 1 || ng > INT32_MAX || mg < 0) return false;
+        max_n = std::max(max_n, ng);
+        max_m = std::max(max_m, mg);
+    }
+    return true;
+}
+
+extern "C" size_t ltsnet_run_batched_workspace_size(int32_t n_graphs, const int64_t* vtx_off,
+                                                    const int64_t* edge_off, const ltsnet_params* p,
+                                                    int32_t n_workers)
+{
+    int64_t max_n, max_m;
+    if (!batch_ok(n_graphs, vtx_off, edge_off, max_n, max_m) || n_workers < 1 || n_workers > 64) return 0;
+    const size_t one = ltsnet_run_workspace_size((int32_t)max_n, max_m, p);
+    if (one == 0) return 0;
+    return align_up(one, 256) * (size_t)std::min(n_workers, n_graphs);
+}
+
+extern "C" ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx_off, const int64_t* edge_off,
+                                            const int64_t* row_ptr, const int32_t* col, const ltsnet_params* p,
+                                            float* Y, void* ws, size_t ws_bytes, int32_t n_workers,
+                                            ltsnet_stream stream)
+{
+    int64_t max_n, max_m;
+    if (!row_ptr || !col || !Y || !ws || !params_ok(p) || n_workers < 1 || n_workers > 64) return LTSNET_ERR_INVALID_ARG;
+    if (!batch_ok(n_graphs, vtx_off, edge_off, max_n, max_m)) return LTSNET_ERR_INVALID_ARG;
+    if (k_of(p) > LTSNET_MAX_K) return LTSNET_ERR_INVALID_ARG;
+    if ((uintptr_t)ws & 255) return LTSNET_ERR_WORKSPACE;
+    const int32_t workers = std::min(n_workers, n_graphs);
+    const size_t slice = align_up(ltsnet_run_workspace_size((int32_t)max_n, max_m, p), 256);
+    if (slice == 0 || ws_bytes < slice * (size_t)workers) return LTSNET_ERR_WORKSPACE;
+    int dev = 0;
+    LT_CUDA(cudaGetDevice(&dev));
+    // inputs written on the caller's stream are visible to the workers
+    LT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    std::vector<int32_t> order(n_graphs);
+    for (int32_t g = 0; g < n_graphs; ++g) order[g] = g;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return vtx_off[a + 1] - vtx_off[a] > vtx_off[b + 1] - vtx_off[b];
+    });
+    std::atomic<int32_t> next{0};
+    std::atomic<int> first_err{0};
+    // keeps the first error; a warning only while there is none
+    auto note = [&](int rc) {
+        int cur = first_err.load();
+        while ((rc < 0 && cur >= 0) || (rc > 0 && cur == 0))
+            if (first_err.compare_exchange_weak(cur, rc)) break;
+    };
+    auto work = [&](int32_t wi) {
+        cudaStream_t s = nullptr;
+        if (cudaSetDevice(dev) != cudaSuccess || cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            note((int)LTSNET_ERR_CUDA);
+            return;
+        }
+        void* mine = (char*)ws + slice * (size_t)wi;
+        for (int32_t t = next.fetch_add(1); t < n_graphs; t = next.fetch_add(1)) {
+            const int32_t g = order[t];
+            const int32_t ng = (int32_t)(vtx_off[g + 1] - vtx_off[g]);
+            Carve c(mine, slice);
+            RunWs r = run_carve(c, ng, 0, p, false);
+            ltsnet_status rc = LTSNET_OK;
+            if (!c.ok()) rc = LTSNET_ERR_WORKSPACE;
+            else if (cudaMemsetAsync(r.st, 0, sizeof(StatusBlock), s) != cudaSuccess) rc = LTSNET_ERR_CUDA;
+            else rc = run_core(row_ptr + vtx_off[g] + g, col + edge_off[g], ng, p, (float2*)Y + vtx_off[g], r, s);
+            note(rc);
+        }
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+    };
+    std::vector<std::thread> pool;
+    for (int32_t wi = 1; wi < workers; ++wi) pool.emplace_back(work, wi);
+    work(0);
+    for (std::thread& t : pool) t.join();
+    return (ltsnet_status)first_err.load();
 }
 
 extern "C" ltsnet_status ltsnet_run_host(const int64_t* row_ptr_host, const int32_t* col_host, int32_t n,

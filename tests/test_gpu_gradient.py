@@ -376,3 +376,19 @@ def test_cost_autograd_matches_finite_differences(ltlib, grid32, snapshots):
             fd = (F.apply(Yp, P[2], P[0], P[1], st, params).item()
                   - F.apply(Ym, P[2], P[0], P[1], st, params).item()) / (2 * h)
             assert abs(fd - gY[i, d].item()) <= 0.1 * scale, (i, d, fd, gY[i, d].item())
+
+
+def test_run_batched_equals_single_runs(ltlib):
+    """ltsnet_run_batched over graphs of several kinds and sizes, with fewer
+    workers than graphs, gives every graph exactly the layout ltsnet_run gives
+    it alone (deterministic kernels, nothing shared between graphs)."""
+    import torch
+
+    graphs = [synth.grid2d(20, 30), synth.random_recursive_tree(900, 5), synth.sbm([300, 250, 200], 9.5, 40, 7),
+              synth.grid2d(9, 7), synth.rgg(1500, seed=9, lcc=True), synth.random_recursive_tree(150, 2)]
+    Y0s = [synth.initial_layout(g.n, 11 + i) for i, g in enumerate(graphs)]
+    params = ltlib.Params(stages=ltlib.default_stages(120))
+    Y, off = ltlib.run_batched(graphs, Y0s, params, workers=3)
+    for i, (g, y0) in enumerate(zip(graphs, Y0s)):
+        a, _ = ltlib.run(g.row_ptr, g.col, torch.from_numpy(y0), params)
+        assert torch.equal(Y[off[i]:off[i + 1]], a), i
