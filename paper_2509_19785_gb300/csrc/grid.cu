@@ -15,8 +15,8 @@
 // layout's absolute coordinates, so the extent does not cost precision.
 //
 //  k_setup        grid rule from the layout bounds (FP32, same decisions as
-//                 the oracle), FFT plan and twiddles, fixed-point scales.
-//  k_box_count    points per box (per-block hash aggregation, then global
+//                 the oracle), FFT plan and twiddles, fixed-point scales, and
+//                 the points per box (per-block hash aggregation, then global
 //                 atomics).
 //  k_box_scan     box offsets, heavy boxes and their segments.
 //  k_box_scatter  local coordinates of the points, in box order.
@@ -251,68 +251,6 @@ __device__ void compute_grid(const int32_t* bounds, float bwm, int min_boxes, in
     }
 }
 
-__global__ void k_setup(const int32_t* __restrict__ bounds_cur, int32_t* __restrict__ bounds_next, GridDev* G,
-                        float2* __restrict__ tw, int32_t* __restrict__ bcnt, int32_t n, float bwm, int min_boxes,
-                        int max_boxes, int P)
-{
-    __shared__ GridDev g;
-    if (threadIdx.x == 0) compute_grid(bounds_cur, bwm, min_boxes, max_boxes, P, n, g);
-    __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        G->lo = g.lo; G->hi = g.hi; G->ext = g.ext; G->h = g.h; G->s = g.s; G->c = g.c;
-        G->rh = g.rh; G->rs = g.rs;
-        G->I = g.I; G->M = g.M; G->L = g.L; G->P = g.P;
-        G->nst = g.nst;
-        for (int i = 0; i < kMaxRadix; ++i) G->radix[i] = i < g.nst ? g.radix[i] : 0;
-        for (int c = 0; c < 4; ++c) {
-            G->fx[c] = g.fx[c];
-            G->ifx[c] = g.ifx[c];
-            G->hf[c] = g.hf[c];
-            G->ihf[c] = g.ihf[c];
-        }
-        G->ticket = 0;
-        bounds_next[0] = f2ord(INFINITY);
-        bounds_next[1] = f2ord(-INFINITY);
-    }
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = tid; t < g.L; t += nth) {
-        // e^{-2 pi i t/L} = (-i)^q e^{-(pi/2) i r/L} with 4t = q L + r, 0 <= r < L:
-        // the reduced argument r/L is in [0, 1) and correctly rounded.
-        const int q = (int)((4 * t) / g.L), r = (int)(4 * t - (int64_t)q * g.L);
-        float sn, cs;
-        sincospif(-0.5f * ((float)r / (float)g.L), &sn, &cs);
-        float2 v;
-        if (q == 0) v = make_float2(cs, sn);
-        else if (q == 1) v = make_float2(sn, -cs);
-        else if (q == 2) v = make_float2(-cs, -sn);
-        else v = make_float2(-sn, cs);
-        tw[t] = v;
-    }
-    for (int64_t t = tid; t < (int64_t)g.I * g.I; t += nth) bcnt[t] = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        G->nheavy = 0;
-        G->nitems = 0;
-        G->scan_ticket = 0;
-    }
-}
-
-// ---- deterministic spread: box sort, then integer sums per box ----
-// The Lagrange nodes a point feeds are those of its own box, so every node's
-// charges are sums over one box's points.  The points are counted per box,
-// the counts scanned, and the points scattered into box order with their
-// local coordinates.  Then every box is summed in integers -- a thread per
-// (box, node row) for boxes of at most kLightMax points, warps over segments
-// of kSeg points for the rest -- so the sums do not depend on the order of
-// the points within a box.  Every node's final FP32 charges are written once
-// per iteration, with no atomics on the grid and no clearing pass, and the
-// grid is bit-identical from run to run.
-
-constexpr int kScanBlock = 256;   // boxes per chunk of the box scan (one per thread)
-constexpr int kMaxScanChunks = 4096;  // max_boxes <= 1024
-constexpr int kLightMax = 8;      // boxes with more points are summed by warps
-constexpr int kSeg = 256;         // points per warp work item of a heavy box
-
 // Points are taken in tiles of kBoxTile consecutive indices per block.  The
 // boxes a tile touches are aggregated in a shared-memory hash table (at most
 // kBoxTile keys in 2 kBoxTile slots, linear probing), so a box that holds
@@ -350,13 +288,58 @@ __device__ __forceinline__ int box_hash_slot(BoxHash& H, int box)
     return -1;
 }
 
-__global__ void __launch_bounds__(kBoxThreads) k_box_count(const float2* __restrict__ Y, int32_t n,
-                                                           const GridDev* __restrict__ G,
-                                                           int32_t* __restrict__ bcnt)
+// Grid of this iteration (every block derives the same grid from the bounds;
+// block 0 publishes it), FFT twiddles, and -- unless the plain atomic spread
+// is in use -- the points per box, aggregated per tile of kBoxTile points in
+// a shared-memory hash table and added to bcnt, which the previous
+// iteration's last kernel (or the workspace reset) left zero.
+__global__ void __launch_bounds__(kBoxThreads) k_setup(const int32_t* __restrict__ bounds_cur,
+                                                       int32_t* __restrict__ bounds_next, GridDev* G,
+                                                       float2* __restrict__ tw, const float2* __restrict__ Y,
+                                                       int32_t* __restrict__ bcnt, int32_t n, float bwm, int min_boxes,
+                                                       int max_boxes, int P, int count)
 {
+    __shared__ GridDev g;
     __shared__ BoxHash H;
-    const float lo = G->lo, h = G->h, rh = G->rh;
-    const int I = G->I;
+    if (threadIdx.x == 0) compute_grid(bounds_cur, bwm, min_boxes, max_boxes, P, n, g);
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        G->lo = g.lo; G->hi = g.hi; G->ext = g.ext; G->h = g.h; G->s = g.s; G->c = g.c;
+        G->rh = g.rh; G->rs = g.rs;
+        G->I = g.I; G->M = g.M; G->L = g.L; G->P = g.P;
+        G->nst = g.nst;
+        for (int i = 0; i < kMaxRadix; ++i) G->radix[i] = i < g.nst ? g.radix[i] : 0;
+        for (int c = 0; c < 4; ++c) {
+            G->fx[c] = g.fx[c];
+            G->ifx[c] = g.ifx[c];
+            G->hf[c] = g.hf[c];
+            G->ihf[c] = g.ihf[c];
+        }
+        G->ticket = 0;
+        G->nheavy = 0;
+        G->nitems = 0;
+        G->scan_ticket = 0;
+        bounds_next[0] = f2ord(INFINITY);
+        bounds_next[1] = f2ord(-INFINITY);
+    }
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = tid; t < g.L; t += nth) {
+        // e^{-2 pi i t/L} = (-i)^q e^{-(pi/2) i r/L} with 4t = q L + r, 0 <= r < L:
+        // the reduced argument r/L is in [0, 1) and correctly rounded.
+        const int q = (int)((4 * t) / g.L), r = (int)(4 * t - (int64_t)q * g.L);
+        float sn, cs;
+        sincospif(-0.5f * ((float)r / (float)g.L), &sn, &cs);
+        float2 v;
+        if (q == 0) v = make_float2(cs, sn);
+        else if (q == 1) v = make_float2(sn, -cs);
+        else if (q == 2) v = make_float2(-cs, -sn);
+        else v = make_float2(-sn, cs);
+        tw[t] = v;
+    }
+    if (!count) return;
+    const float lo = g.lo, h = g.h, rh = g.rh;
+    const int I = g.I;
     const int lane = threadIdx.x & 31;
     const int64_t ntiles = ((int64_t)n + kBoxTile - 1) / kBoxTile;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -382,6 +365,22 @@ __global__ void __launch_bounds__(kBoxThreads) k_box_count(const float2* __restr
         __syncthreads();
     }
 }
+
+// ---- deterministic spread: box sort, then integer sums per box ----
+// The Lagrange nodes a point feeds are those of its own box, so every node's
+// charges are sums over one box's points.  The points are counted per box,
+// the counts scanned, and the points scattered into box order with their
+// local coordinates.  Then every box is summed in integers -- a thread per
+// (box, node row) for boxes of at most kLightMax points, warps over segments
+// of kSeg points for the rest -- so the sums do not depend on the order of
+// the points within a box.  Every node's final FP32 charges are written once
+// per iteration, with no atomics on the grid and no clearing pass, and the
+// grid is bit-identical from run to run.
+
+constexpr int kScanBlock = 256;   // boxes per chunk of the box scan (one per thread)
+constexpr int kMaxScanChunks = 4096;  // max_boxes <= 1024
+constexpr int kLightMax = 8;      // boxes with more points are summed by warps
+constexpr int kSeg = 256;         // points per warp work item of a heavy box
 
 // Box offsets, in chunks of kScanBlock boxes (one per thread): chunk-local
 // exclusive offsets into bcur (the scatter cursors), chunk totals into btot,
@@ -503,7 +502,7 @@ __global__ void __launch_bounds__(kScanThreads) k_box_scan(GridDev* __restrict__
     if (threadIdx.x == 0) G->scan_ticket = 0;
 }
 
-// Same tiles and hash table as k_box_count: each box a tile touches reserves
+// Same tiles and hash table as the counting in k_setup: each box a tile touches reserves
 // its range once (one global atomic), and the tile's points of that box take
 // consecutive places in it.
 __global__ void __launch_bounds__(kBoxThreads) k_box_scatter(const float2* __restrict__ Y, int32_t n,
@@ -1018,27 +1017,36 @@ __device__ __forceinline__ float2 conv_product(int q, float2 s0, float2 s1x, flo
     return conj2(v);
 }
 
-// Sum of one double per thread over the block (tree in `red`, blockDim.x a
-// power of two <= 256); every thread gets the sum.
+// Sum of one double per thread over the block (blockDim.x a multiple of 32,
+// at most 1024): warp sums by shuffles, then warp 0 adds the warp sums in
+// order (a fixed order, so the result is reproducible); every thread gets it.
 __device__ __forceinline__ double block_sum_double(double v, double* red)
 {
-    red[threadIdx.x] = v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[w] = v;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
+    if (w == 0) {
+        double t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+        if (lane == 0) red[32] = t;
     }
-    const double r = red[0];
+    __syncthreads();
+    const double r = red[32];
     __syncthreads();
     return r;
 }
 
-__global__ void k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const float2* __restrict__ srow,
+constexpr int kColThreads = 512;  // the column pass runs 4 and then 6 lines of a column at once
+
+__global__ void __launch_bounds__(kColThreads) k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const float2* __restrict__ srow,
                             const float* __restrict__ khat, float2* __restrict__ ucol, double* __restrict__ zblk,
                             int32_t n, int sm_f2)
 {
     extern __shared__ float2 smf[];
-    __shared__ double red[256];
+    __shared__ double red[33];
     __shared__ bool last;
     const GridDev& G = *Gp;
     const int L = G.L, M = G.M, H = L / 2 + 1;
@@ -1192,7 +1200,7 @@ __global__ void k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const fl
 // iteration; its readers have finished, so that is done here.
 __global__ void k_conv_rows_inv(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
                                 const float2* __restrict__ ucol, float* __restrict__ fields,
-                                float4* __restrict__ wflt, int plain, int sm_f2)
+                                float4* __restrict__ wflt, int32_t* __restrict__ bcnt, int plain, int sm_f2)
 {
     extern __shared__ float2 smf[];
     const GridDev& G = *Gp;
@@ -1238,6 +1246,10 @@ __global__ void k_conv_rows_inv(const GridDev* __restrict__ Gp, const float2* __
             }
         }
     }
+    // the box counts of this iteration are used up: cleared for the next
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)G.I * G.I;
+         t += (int64_t)gridDim.x * blockDim.x)
+        bcnt[t] = 0;
     if (!plain) return;
     for (int u = beg; u < end; ++u) {
         if (u >= M) break;  // units (0, row) cover every row once
@@ -1380,6 +1392,8 @@ cudaError_t iter_reset(const IterWs& w, const IterShape& sh, cudaStream_t s)
     if ((e = cudaMemsetAsync(w.st, 0, sizeof(StatusBlock), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.wflt, 0, sizeof(float4) * (size_t)sh.Mmax * sh.Mmax, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.hticket, 0, sizeof(int32_t) * (size_t)sh.hcap, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.bcnt, 0, sizeof(int32_t) * (size_t)sh.max_boxes * sh.max_boxes, s)) != cudaSuccess)
+        return e;
     return cudaMemsetAsync(w.hacc, 0, sizeof(long long) * (size_t)sh.hcap * sh.P * sh.P * 4, s);
 }
 
@@ -1409,8 +1423,12 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
 {
     const int32_t n = sh.n;
     const int P = sh.P;
-    k_setup<<<64, 256, 0, s>>>(w.bounds + 2 * parity, w.bounds + 2 * (parity ^ 1), w.g, w.tw, w.bcnt, n,
-                               p->box_width_max, p->min_boxes, p->max_boxes, P);
+    int64_t sblocks = ((int64_t)n + kBoxTile - 1) / kBoxTile;
+    if (sblocks > kSMs * 4) sblocks = kSMs * 4;
+    if (sblocks < 16) sblocks = 16;
+    k_setup<<<(unsigned)sblocks, kBoxThreads, 0, s>>>(w.bounds + 2 * parity, w.bounds + 2 * (parity ^ 1), w.g, w.tw,
+                                                      Y, w.bcnt, n, p->box_width_max, p->min_boxes, p->max_boxes, P,
+                                                      plain ? 0 : 1);
     count_launches(1);
     const size_t fsm = fft_smem_bytes(sh.Lmax);
     const int f2 = (int)(fsm / sizeof(float2));
@@ -1443,7 +1461,6 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
         int64_t blocks = ((int64_t)n + kBoxTile - 1) / kBoxTile;
         if (blocks > kSMs * 8) blocks = kSMs * 8;
         if (blocks < 1) blocks = 1;
-        k_box_count<<<(unsigned)blocks, kBoxThreads, 0, s>>>(Y, n, w.g, w.bcnt);
         const int nsb = std::min<int>(kSMs, (int)(((int64_t)sh.max_boxes * sh.max_boxes + kScanBlock - 1) / kScanBlock));
         k_box_scan<<<nsb, kScanThreads, 0, s>>>(w.g, w.bcnt, w.bcur, w.btot, w.bpre, w.heavy, w.items);
         k_box_scatter<<<(unsigned)blocks, kBoxThreads, 0, s>>>(Y, n, w.g, w.bcur, w.bpre, w.su);
@@ -1459,7 +1476,7 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
             default: LT_SPREAD(5)
 #undef LT_SPREAD
         }
-        count_launches(4);
+        count_launches(3);
     }
     profile_stop(LTSNET_KERNEL_SPREAD, s);
     cudaError_t e = cudaGetLastError();
@@ -1475,8 +1492,8 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
         cudaError_t e2 = cudaStreamWaitEvent(s, aux->join, 0);
         if (e2 != cudaSuccess) return e2;
     }
-    k_conv_cols<<<kSMs, kFftThreads, fsm, s>>>(w.g, w.tw, w.srow, w.khat, w.ucol, w.zblk, n, f2);
-    k_conv_rows_inv<<<kSMs, kFftThreads, fsm, s>>>(w.g, w.tw, w.ucol, w.fields, w.wflt, plain ? 1 : 0, f2);
+    k_conv_cols<<<kSMs, kColThreads, fsm, s>>>(w.g, w.tw, w.srow, w.khat, w.ucol, w.zblk, n, f2);
+    k_conv_rows_inv<<<kSMs, kFftThreads, fsm, s>>>(w.g, w.tw, w.ucol, w.fields, w.wflt, w.bcnt, plain ? 1 : 0, f2);
     count_launches(5);
     profile_stop(LTSNET_KERNEL_CONV, s);
     return cudaGetLastError();
