@@ -330,12 +330,13 @@ __global__ void __launch_bounds__(kFusedThreads, 2)
                 window_cols<D16>(cur, u, rowi, cc);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    // Slots of other rows get weight 0; the clamp keeps
-                    // their gathers in range, and those of an invalid P
-                    // (which k_check_cols reports).
+                    // Slots of other rows get weight 0 and no gather (the
+                    // point itself stands in); the clamp keeps the gathers
+                    // of an invalid P in range (k_check_cols reports it).
+                    const bool own = j + q >= off && j + q < len;
                     const unsigned c = min((unsigned)cc[q], (unsigned)(n - 1));
-                    yj[u][q] = __ldg(Y + c);
-                    pv[u][q] = (j + q >= off && j + q < len) ? vv[q] : 0.f;
+                    yj[u][q] = own ? __ldg(Y + c) : make_float2(xi, yv);
+                    pv[u][q] = own ? vv[q] : 0.f;
                 }
             }
 #pragma unroll
