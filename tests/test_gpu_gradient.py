@@ -392,3 +392,34 @@ def test_run_batched_equals_single_runs(ltlib):
     for i, (g, y0) in enumerate(zip(graphs, Y0s)):
         a, _ = ltlib.run(g.row_ptr, g.col, torch.from_numpy(y0), params)
         assert torch.equal(Y[off[i]:off[i + 1]], a), i
+
+
+def test_run_step_rgg1m_matches_oracle(ltlib):
+    """The benchmark's workload at full size (RGG, n = 999,019) through
+    ltsnet_run -- breadth-first renumbering, int16 columns, the kernels the
+    benchmark times -- for one iteration from a spread-out layout, against
+    the oracle's interpolated gradient and update rule on the same P (the
+    GPU's C0 in the original numbering, checked separately)."""
+    import torch
+
+    g = synth.config_graph("rgg1m")
+    aff = ltlib.affinities(g.row_ptr, g.col, 30.0)
+    Pn = tuple(t.cpu().numpy() for t in aff["P"])
+    Y0 = (np.random.default_rng(12).standard_normal((g.n, 2)) * 12).astype(np.float32)
+    params = ltlib.Params(perplexity=30.0, stages=[ltlib.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)])
+    Y1, _ = ltlib.run(g.row_ptr, g.col, torch.from_numpy(Y0), params)
+    step = Y1.cpu().numpy().astype(np.float64) - Y0
+    st = oracle.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+    gref, pr = oracle.interp_gradient(Y0, Pn[0], Pn[1], Pn[2].astype(np.float64), st, oracle.GridParams(max_boxes=640))
+    lr = oracle.auto_learning_rate(g.n)
+    Yr, _, _ = oracle.update(Y0.astype(np.float64), np.zeros_like(gref), np.ones_like(gref), gref, st.momentum, lr)
+    sref = Yr - Y0
+    n = g.n
+    scale = (np.linalg.norm(4 * st.lambda_kl * st.exaggeration * pr["A"])
+             + np.linalg.norm(4 * st.lambda_kl * pr["S"] / pr["Z"] * pr["R"])
+             + np.linalg.norm(st.lambda_c / n * Y0.astype(np.float64))
+             + np.linalg.norm(st.lambda_r / n ** 2 * pr["E"]))
+    # the first step is -lr * 1.2 * g (gains start at 1 and grow by 0.2;
+    # the previous update is 0)
+    err = float(np.linalg.norm(step - sref) / (lr * 1.2 * scale))
+    assert err < 1e-5, err
