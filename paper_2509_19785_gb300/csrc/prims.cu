@@ -125,17 +125,30 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const uint64_t* __
     for (int d = threadIdx.x; d < kDigits; d += kRadixThreads) hist[(int64_t)d * nblocks + blockIdx.x] = c[d];
 }
 
-__global__ void __launch_bounds__(kRadixThreads)
+// Stable scatter of one tile: per-warp digit counts, then every key's place
+// inside the tile (digit-major, input order within a digit) in shared
+// memory, then the tile is written out in that order, so each digit's run
+// goes to global memory as consecutive addresses.
+constexpr size_t kScatterSmem = (size_t)kRadixTile * (sizeof(uint64_t) + sizeof(double));
+
+__global__ void __launch_bounds__(kRadixThreads, 2)
     k_radix_scatter(const uint64_t* __restrict__ kin, const double* __restrict__ vin, uint64_t* __restrict__ kout,
                     double* __restrict__ vout, int64_t count, int shift, const uint32_t* __restrict__ offs,
                     int64_t nblocks)
 {
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    uint64_t* sk = (uint64_t*)rs_smem;
+    double* sv = (double*)(sk + kRadixTile);
     __shared__ uint32_t wh[kRadixWarps][kDigits];
+    __shared__ uint32_t dstart[kDigits];  // first tile-local place of each digit
+    __shared__ uint32_t gbase[kDigits];   // global place of each digit's first key of this tile
+    __shared__ uint32_t wt[33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned ltm = lanemask_lt();
     for (int d = lane; d < kDigits; d += 32) wh[w][d] = 0;
     __syncwarp();
-    const int64_t base = (int64_t)blockIdx.x * kRadixTile + (int64_t)w * (32 * kRadixItems);
+    const int64_t tile0 = (int64_t)blockIdx.x * kRadixTile;
+    const int64_t base = tile0 + (int64_t)w * (32 * kRadixItems);
     uint64_t kk[kRadixItems];
     double vv[kRadixItems];
 #pragma unroll
@@ -146,7 +159,7 @@ __global__ void __launch_bounds__(kRadixThreads)
             vv[i] = vin[e];
         }
     }
-    // Pass 1: per-warp digit counts over the warp's sub-tile.
+    // per-warp digit counts over the warp's sub-tile
 #pragma unroll
     for (int i = 0; i < kRadixItems; ++i) {
         const int64_t e = base + i * 32 + lane;
@@ -157,33 +170,48 @@ __global__ void __launch_bounds__(kRadixThreads)
         __syncwarp();
     }
     __syncthreads();
-    // Pass 2: warp offsets per digit = tile offset + counts of earlier warps.
-    for (int d = threadIdx.x; d < kDigits; d += kRadixThreads) {
-        uint32_t run = offs[(int64_t)d * nblocks + blockIdx.x];
-#pragma unroll
+    // tile totals per digit, their exclusive scan, and the warps' offsets
+    uint32_t tot = 0;
+    if (threadIdx.x < kDigits)
+        for (int ww = 0; ww < kRadixWarps; ++ww) tot += wh[ww][threadIdx.x];
+    uint32_t start = 0;
+    block_exclusive_scan(threadIdx.x < kDigits ? tot : 0u, wt, start);
+    if (threadIdx.x < kDigits) {
+        const int d = threadIdx.x;
+        dstart[d] = start;
+        gbase[d] = offs[(int64_t)d * nblocks + blockIdx.x];
+        uint32_t run = start;
         for (int ww = 0; ww < kRadixWarps; ++ww) {
-            uint32_t c = wh[ww][d];
+            const uint32_t c = wh[ww][d];
             wh[ww][d] = run;
             run += c;
         }
     }
     __syncthreads();
-    // Pass 3: stable scatter in input order.
+    // tile-local places, input order within a digit
 #pragma unroll
     for (int i = 0; i < kRadixItems; ++i) {
         const int64_t e = base + i * 32 + lane;
         const bool valid = e < count;
         const int d = valid ? (int)((kk[i] >> shift) & 0xffu) : -1;
         const unsigned peers = __match_any_sync(FULL, d);
-        uint32_t pos = 0;
-        if (valid) pos = wh[w][d] + __popc(peers & ltm);
-        __syncwarp();
         if (valid) {
-            kout[pos] = kk[i];
-            vout[pos] = vv[i];
-            if ((peers & ltm) == 0) wh[w][d] += __popc(peers);
+            const uint32_t lp = wh[w][d] + __popc(peers & ltm);
+            sk[lp] = kk[i];
+            sv[lp] = vv[i];
         }
         __syncwarp();
+        if (valid && (peers & ltm) == 0) wh[w][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    const int nt = (int)min((int64_t)kRadixTile, count - tile0);
+    for (int j = threadIdx.x; j < nt; j += kRadixThreads) {
+        const uint64_t key = sk[j];
+        const int d = (int)((key >> shift) & 0xffu);
+        const uint32_t gp = gbase[d] + ((uint32_t)j - dstart[d]);
+        kout[gp] = key;
+        vout[gp] = sv[j];
     }
 }
 
@@ -218,6 +246,13 @@ cudaError_t radix_sort_u64_f64(uint64_t* k0, double* v0, uint64_t* k1, double* v
     *in_alt = false;
     if (count <= 1) return cudaSuccess;
     const int64_t nb = (count + kRadixTile - 1) / kRadixTile;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kScatterSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
     uint64_t *ka = k0, *kb = k1;
     double *va = v0, *vb = v1;
     for (int shift = 0; shift < bits; shift += 8) {
@@ -225,7 +260,7 @@ cudaError_t radix_sort_u64_f64(uint64_t* k0, double* v0, uint64_t* k1, double* v
         count_launches(1);
         cudaError_t e = scan_u32_exclusive(hist, hist, nb * kDigits, tmp, s);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<(unsigned)nb, kRadixThreads, 0, s>>>(ka, va, kb, vb, count, shift, hist, nb);
+        k_radix_scatter<<<(unsigned)nb, kRadixThreads, kScatterSmem, s>>>(ka, va, kb, vb, count, shift, hist, nb);
         count_launches(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
