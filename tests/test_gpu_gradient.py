@@ -423,3 +423,84 @@ def test_run_step_rgg1m_matches_oracle(ltlib):
     # the previous update is 0)
     err = float(np.linalg.norm(step - sref) / (lr * 1.2 * scale))
     assert err < 1e-5, err
+
+
+def _bfs_ball(g, root: int, size: int):
+    """Induced subgraph on the first `size` vertices of a BFS from `root`,
+    relabelled in that order."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import breadth_first_order
+
+    A = csr_matrix((np.ones(g.col.shape[0]), g.col, g.row_ptr), shape=(g.n, g.n))
+    ball = breadth_first_order(A, root, directed=False, return_predecessors=False)[:size]
+    new = -np.ones(g.n, np.int64)
+    new[ball] = np.arange(ball.shape[0])
+    rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    keep = (new[rows] >= 0) & (new[g.col] >= 0)
+    return synth.csr_from_edges(ball.shape[0], new[rows[keep]], new[g.col[keep]])
+
+
+def test_ba4m_ball_pipeline_matches_oracle(ltlib):
+    """Barabasi-Albert graph (n = 4e6, 4 edges per new vertex), the induced
+    subgraph on a 50,000-vertex BFS ball from a seeded root, perplexity 50:
+    C0 and the gradient on both sides (GPU through the ABI, the oracle on its
+    own C0), hubs and all."""
+    import torch
+
+    g = synth.config_graph("ba4m")
+    root = int(np.random.default_rng(21).integers(g.n))
+    sub = _bfs_ball(g, root, 50_000)
+    aff = ltlib.affinities(sub.row_ptr, sub.col, 50.0)
+    ref = oracle.preprocess(sub.row_ptr, sub.col, 50.0)
+    P = aff["P"]
+    Pn = tuple(t.cpu().numpy() for t in P)
+    assert np.array_equal(Pn[0], ref.P_row) and np.array_equal(Pn[1], ref.P_col)
+    np.testing.assert_allclose(Pn[2], ref.P_val64, rtol=1e-6, atol=0)
+    Y = (np.random.default_rng(4).standard_normal((sub.n, 2)) * 10).astype(np.float32)
+    st = ltlib.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+    errs = _compare(ltlib, P, (ref.P_row, ref.P_col, ref.P_val64), Y, st, ltlib.Params(perplexity=50.0),
+                    oracle.GridParams())
+    for key, v in errs.items():
+        assert v < TOL, f"{key}: {v:.3e} ({errs})"
+
+
+def test_cost_autograd_sbm100k_64_coordinates(ltlib):
+    """The autograd wrapper on the 100,000-vertex SBM (perplexity 40): dC/dY
+    against central differences of the cost on 64 random coordinates and
+    dC/dP_val on 64 random entries."""
+    import torch
+
+    g = synth.config_graph("sbm100k")
+    aff = ltlib.affinities(g.row_ptr, g.col, 40.0)
+    P = aff["P"]
+    rng = np.random.default_rng(64)
+    Y = torch.from_numpy((rng.standard_normal((g.n, 2)) * 20).astype(np.float32)).cuda()
+    st = ltlib.Stage(1, 1.0, 0.01, 0.0, 1.0, 0.8)
+    params = ltlib.Params(perplexity=40.0, box_width_max=0.25)
+    F = ltlib.ltsnet_cost_fn()
+    Yv = Y.clone().requires_grad_(True)
+    Pv = P[2].clone().requires_grad_(True)
+    F.apply(Yv, Pv, P[0], P[1], st, params).backward()
+    gY, gP = Yv.grad, Pv.grad
+    scale = float(gY.abs().max())
+    Yn = Y.cpu().numpy()
+    inner = np.where((Yn.min(1) > Yn.min() + 1.0) & (Yn.max(1) < Yn.max() - 1.0))[0]
+    gmag = gY.abs().max(1).values.cpu().numpy()
+    picks = inner[np.argsort(-gmag[inner])[:32]]
+    for i in picks:
+        for d in range(2):
+            h = 5e-2
+            Yp, Ym = Y.clone(), Y.clone()
+            Yp[i, d] += h
+            Ym[i, d] -= h
+            fd = (F.apply(Yp, P[2], P[0], P[1], st, params).item()
+                  - F.apply(Ym, P[2], P[0], P[1], st, params).item()) / (2 * h)
+            assert abs(fd - gY[i, d].item()) <= 0.1 * scale, (i, d, fd, gY[i, d].item())
+    for e in rng.choice(P[2].numel(), 64, replace=False):
+        h = float(P[2][e]) * 1e-2
+        Pp, Pm = P[2].clone(), P[2].clone()
+        Pp[e] += h
+        Pm[e] -= h
+        fd = (F.apply(Y, Pp, P[0], P[1], st, params).item()
+              - F.apply(Y, Pm, P[0], P[1], st, params).item()) / (Pp[e] - Pm[e]).item()
+        assert abs(fd - gP[e].item()) <= 1e-3 * abs(gP[e].item()) + 1e-6, (e, fd, gP[e].item())
