@@ -183,6 +183,21 @@ constexpr int kFusedThreads = 256;
 constexpr int kRowLanes = 8;     // lanes per CSR row in the attraction pass
 constexpr int kWin = 128;        // CSR entries of a row taken per round (longer rows: the rest directly)
 constexpr int kFusedWarps = kFusedThreads / 32;
+constexpr int kHeavyRow = 2048;  // longer rows of P are summed in chunks by k_attr_chunks
+constexpr int kChunk = 2048;     // entries per chunk
+
+// Rows of P longer than kHeavyRow (hubs of scale-free graphs can sit in a
+// large part of all neighbour lists): their attraction sums are computed in
+// chunks of kChunk entries by whole warps, and the fused kernel adds a row's
+// chunk sums in chunk order (deterministic).  hbase[row] is the row's first
+// chunk; read only for rows longer than kHeavyRow.
+struct HeavyRows {
+    const int32_t* hbase = nullptr;
+    const int32_t* crow = nullptr;
+    const int64_t* cstart = nullptr;
+    float2* partial = nullptr;
+    int32_t nchunks = 0;
+};
 
 // 1/x to within about one unit in the last place (the SFU reciprocal);
 // x >= 1 here.
@@ -283,7 +298,7 @@ __global__ void __launch_bounds__(kFusedThreads, 2)
             int32_t n, const float2* __restrict__ Y, float2* __restrict__ Ynew, float2* __restrict__ upd,
             float2* __restrict__ gains, const GridDev* __restrict__ G, const float* __restrict__ fields, Stage st,
             int32_t* __restrict__ bounds_next, float2* __restrict__ grad_out, float* __restrict__ parts,
-            StatusBlock* status)
+            StatusBlock* status, const int32_t* __restrict__ hbase, const float2* __restrict__ hpartial)
 {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int grp = lane >> 3, gl = lane & 7;
@@ -314,8 +329,10 @@ __global__ void __launch_bounds__(kFusedThreads, 2)
                 const int64_t ns0 = __shfl_sync(FULL, rs, nsrc), ne0 = __shfl_sync(FULL, re, nsrc);
                 load_window<D16>(nxt, P_col, P_d16, P_val, nnz, window_start<D16>(ns0), ne0, rowi + 4, gl);
             }
-            const int64_t s0 = __shfl_sync(FULL, rs, src), e0 = __shfl_sync(FULL, re, src);
+            const int64_t s0 = __shfl_sync(FULL, rs, src), e0r = __shfl_sync(FULL, re, src);
             const float xi = __shfl_sync(FULL, yi.x, src), yv = __shfl_sync(FULL, yi.y, src);
+            const bool heavy = hbase != nullptr && e0r - s0 > kHeavyRow;  // summed in chunks already
+            const int64_t e0 = heavy ? s0 : e0r;
             const int64_t eb = window_start<D16>(s0);
             const int off = (int)(s0 - eb);  // leading slots that belong to the previous row
             const int64_t len = e0 - eb;     // slots from len on belong to the next rows
@@ -357,6 +374,15 @@ __global__ void __launch_bounds__(kFusedThreads, 2)
                 ax = __fmaf_rn(w, dx, ax);
                 ay = __fmaf_rn(w, dy, ay);
             }
+            if (heavy) {
+                const int b = hbase[rowi];
+                const int nc = (int)((e0r - s0 + kChunk - 1) / kChunk);
+                for (int c = gl; c < nc; c += kRowLanes) {
+                    const float2 q = hpartial[b + c];
+                    ax += q.x;
+                    ay += q.y;
+                }
+            }
 #pragma unroll
             for (int o = kRowLanes / 2; o > 0; o >>= 1) {
                 ax += __shfl_xor_sync(gmask, ax, o);
@@ -392,6 +418,61 @@ __global__ void __launch_bounds__(kFusedThreads, 2)
 }
 
 constexpr size_t kFusedSmem = 0;  // the windows live in registers
+
+// Attraction sums of the chunks of the long rows: one warp per chunk of
+// kChunk entries of one row, lanes striding over the entries.
+template <bool D16>
+__global__ void __launch_bounds__(256) k_attr_chunks(const int64_t* __restrict__ P_row,
+                                                     const int32_t* __restrict__ P_col,
+                                                     const int16_t* __restrict__ P_d16,
+                                                     const float* __restrict__ P_val, int32_t n,
+                                                     const float2* __restrict__ Y, const int32_t* __restrict__ crow,
+                                                     const int64_t* __restrict__ cstart, int32_t nchunks,
+                                                     float2* __restrict__ partial)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nw) {
+        const int32_t row = crow[c];
+        const int64_t a = cstart[c], b = min(a + kChunk, P_row[row + 1]);
+        const float2 yi = Y[row];
+        float ax = 0.f, ay = 0.f;
+        for (int64_t e = a + lane; e < b; e += 32) {
+            const int ce = D16 ? row + (int)P_d16[e] : P_col[e];
+            const float2 q = __ldg(Y + min((unsigned)ce, (unsigned)(n - 1)));
+            const float dx = yi.x - q.x, dy = yi.y - q.y;
+            const float w = __ldg(P_val + e) * rcp_approx(__fmaf_rn(dy, dy, __fmaf_rn(dx, dx, 1.0f)));
+            ax = __fmaf_rn(w, dx, ax);
+            ay = __fmaf_rn(w, dy, ay);
+        }
+        ax = warp_sum(ax);
+        ay = warp_sum(ay);
+        if (lane == 0) partial[c] = make_float2(ax, ay);
+    }
+}
+
+// Chunks per row (0 for rows of at most kHeavyRow entries).
+__global__ void k_heavy_count(const int64_t* __restrict__ P_row, int32_t n, uint32_t* __restrict__ nch)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t len = P_row[i + 1] - P_row[i];
+        nch[i] = len > kHeavyRow ? (uint32_t)((len + kChunk - 1) / kChunk) : 0u;
+    }
+}
+
+// The chunk list of the long rows, their first chunks at base[row].
+__global__ void k_heavy_emit(const int64_t* __restrict__ P_row, int32_t n, const uint32_t* __restrict__ nch,
+                             const uint32_t* __restrict__ base, int32_t* __restrict__ crow,
+                             int64_t* __restrict__ cstart)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t m = nch[i];
+        for (uint32_t c = 0; c < m; ++c) {
+            crow[base[i] + c] = (int32_t)i;
+            cstart[base[i] + c] = P_row[i] + (int64_t)c * kChunk;
+        }
+    }
+}
 
 // P's columns as int16 offsets from their row, one warp per row; `far` is set
 // if any offset does not fit (the int32 columns are used then).
@@ -608,11 +689,23 @@ int flat_blocks(int64_t n, int per_sm = 8)
 
 template <bool UPDATE>
 cudaError_t launch_point_phase(const int64_t* P_row, const int32_t* P_col, const int16_t* P_d16, const float* P_val,
-                               int32_t n, const float2* Y, float2* Ynew, float2* upd, float2* gains, const IterWs& w,
+                               const HeavyRows& hr, int32_t n, const float2* Y, float2* Ynew, float2* upd,
+                               float2* gains, const IterWs& w,
                                const IterShape& sh, const Stage& st, int parity, float2* grad, float* parts,
                                bool plain, cudaStream_t s)
 {
     int32_t* bn = w.bounds + 2 * (parity ^ 1);
+    if (!plain && hr.nchunks > 0) {
+        int64_t cb = ((int64_t)hr.nchunks * 32 + 255) / 256;
+        if (cb > kSMs * 8) cb = kSMs * 8;
+        if (P_d16)
+            k_attr_chunks<true><<<(unsigned)cb, 256, 0, s>>>(P_row, P_col, P_d16, P_val, n, Y, hr.crow, hr.cstart,
+                                                             hr.nchunks, hr.partial);
+        else
+            k_attr_chunks<false><<<(unsigned)cb, 256, 0, s>>>(P_row, P_col, P_d16, P_val, n, Y, hr.crow, hr.cstart,
+                                                              hr.nchunks, hr.partial);
+        count_launches(1);
+    }
     profile_start(LTSNET_KERNEL_FUSED_UPDATE, s);
     if (!plain) {
         const int nb = fused_blocks(n);
@@ -620,11 +713,11 @@ cudaError_t launch_point_phase(const int64_t* P_row, const int32_t* P_col, const
     if (P_d16)                                                                                                \
         k_fused<PP, UPDATE, true><<<nb, kFusedThreads, kFusedSmem, s>>>(P_row, P_col, P_d16, P_val, n, Y, Ynew,  \
                                                                         upd, gains, w.g, w.fields, st, bn, grad, \
-                                                                        parts, w.st);                            \
+                                                                        parts, w.st, hr.hbase, hr.partial);      \
     else                                                                                                      \
         k_fused<PP, UPDATE, false><<<nb, kFusedThreads, kFusedSmem, s>>>(P_row, P_col, P_d16, P_val, n, Y, Ynew, \
                                                                          upd, gains, w.g, w.fields, st, bn, grad, \
-                                                                         parts, w.st)
+                                                                         parts, w.st, hr.hbase, hr.partial)
         switch (sh.P) {
             case 2: LT_FUSED(2); break;
             case 3: LT_FUSED(3); break;
@@ -745,7 +838,7 @@ ltsnet_status read_status(StatusBlock* st, cudaStream_t s)
 // One iteration i (local index; parity i & 1 picks the layout buffer and
 // the bounds slot): grid phase, then the point phase.
 cudaError_t one_iteration(const int64_t* P_row, const int32_t* P_col, const int16_t* P_d16, const float* P_val,
-                          int32_t n,
+                          const HeavyRows& hr, int32_t n,
                           const ltsnet_params* p, float2* Y, float2* upd, float2* gains, const IterWs& w,
                           const IterShape& sh, const Stage& st, int parity, bool plain, cudaStream_t s)
 {
@@ -753,8 +846,8 @@ cudaError_t one_iteration(const int64_t* P_row, const int32_t* P_col, const int1
     float2* nxt = parity ? Y : w.yalt;
     cudaError_t e = launch_grid_phase(w, sh, p, cur, parity, plain, s);
     if (e != cudaSuccess) return e;
-    return launch_point_phase<true>(P_row, P_col, P_d16, P_val, n, cur, nxt, upd, gains, w, sh, st, parity, nullptr,
-                                    nullptr, plain, s);
+    return launch_point_phase<true>(P_row, P_col, P_d16, P_val, hr, n, cur, nxt, upd, gains, w, sh, st, parity,
+                                    nullptr, nullptr, plain, s);
 }
 
 bool same_stage(const ltsnet_stage& a, const ltsnet_stage& b)
@@ -772,7 +865,7 @@ bool same_stage(const ltsnet_stage& a, const ltsnet_stage& b)
 // P_d16, when not null, holds P's columns as int16 offsets from their row
 // (the fused kernel then streams 6 bytes per entry instead of 8).
 ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const int16_t* P_d16, const float* P_val,
-                            int32_t n,
+                            const HeavyRows& hr, int32_t n,
                             const ltsnet_params* p, float2* Y, float2* upd, float2* gains, int32_t t0, int32_t niter,
                             const IterWs& w, const IterShape& sh, cudaStream_t s)
 {
@@ -791,7 +884,7 @@ ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const in
         const Stage st = make_stage(sg, lr, n);
         int32_t done = 0;
         if ((i & 1) && run > 0) {  // align to an even iteration
-            LT_CUDA(one_iteration(P_row, P_col, P_d16, P_val, n, p, Y, upd, gains, w, sh, st, 1, plain, s));
+            LT_CUDA(one_iteration(P_row, P_col, P_d16, P_val, hr, n, p, Y, upd, gains, w, sh, st, 1, plain, s));
             done = 1;
         }
         const int32_t pairs = graphs ? (run - done) / 2 : 0;
@@ -800,9 +893,9 @@ ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const in
             cudaGraph_t graph = nullptr;
             cudaGraphExec_t exec = nullptr;
             LT_CUDA(cudaStreamBeginCapture(aux->capture, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = one_iteration(P_row, P_col, P_d16, P_val, n, p, Y, upd, gains, w, sh, st, 0, plain, aux->capture);
+            cudaError_t e = one_iteration(P_row, P_col, P_d16, P_val, hr, n, p, Y, upd, gains, w, sh, st, 0, plain, aux->capture);
             if (e == cudaSuccess)
-                e = one_iteration(P_row, P_col, P_d16, P_val, n, p, Y, upd, gains, w, sh, st, 1, plain, aux->capture);
+                e = one_iteration(P_row, P_col, P_d16, P_val, hr, n, p, Y, upd, gains, w, sh, st, 1, plain, aux->capture);
             cudaError_t e2 = cudaStreamEndCapture(aux->capture, &graph);
             if (e != cudaSuccess || e2 != cudaSuccess) {
                 if (graph) cudaGraphDestroy(graph);
@@ -822,7 +915,7 @@ ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const in
             done += 2 * pairs;
         }
         for (; done < run; ++done)
-            LT_CUDA(one_iteration(P_row, P_col, P_d16, P_val, n, p, Y, upd, gains, w, sh, st, (i + done) & 1, plain, s));
+            LT_CUDA(one_iteration(P_row, P_col, P_d16, P_val, hr, n, p, Y, upd, gains, w, sh, st, (i + done) & 1, plain, s));
         i += run;
     }
     if (niter & 1) LT_CUDA(cudaMemcpyAsync(Y, w.yalt, sizeof(float2) * (size_t)n, cudaMemcpyDeviceToDevice, s));
@@ -838,6 +931,13 @@ struct RunWs {
     double* pcond;
     int16_t* d16;      // P's columns as offsets from their row (aliases pcond, dead by then)
     int32_t* far;      // set when some |col - row| exceeds the int16 range
+    uint32_t* hnch;    // chunks per long row of P
+    uint32_t* hbase;   // first chunk of each long row
+    uint32_t* htmp;    // scan scratch
+    int32_t* hcrow;    // chunk -> row
+    int64_t* hcstart;  // chunk -> first entry
+    float2* hpartial;  // chunk sums
+    int64_t hmax;      // chunk capacity
     uint8_t* conv;
     int64_t* P_row;
     int32_t* P_col;
@@ -876,6 +976,15 @@ RunWs run_carve(Carve& c, int32_t n, int64_t m2, const ltsnet_params* p, bool ho
     r.pcond = c.take<double>(nk);
     r.d16 = (int16_t*)r.pcond;  // 2 nnz <= 4 n k bytes <= 8 n k
     r.far = c.take<int32_t>(1);
+    r.hnch = c.take<uint32_t>(n);
+    r.hbase = c.take<uint32_t>(n);
+    r.htmp = c.take<uint32_t>(scan_tmp_words(n));
+    // chunks: at most 2 nnz / kChunk (each long row has more than kChunk
+    // entries, and nnz <= 2 n k)
+    r.hmax = 2 * (2 * nk) / kChunk + 1;
+    r.hcrow = c.take<int32_t>(r.hmax);
+    r.hcstart = c.take<int64_t>(r.hmax);
+    r.hpartial = c.take<float2>(r.hmax);
     r.conv = c.take<uint8_t>(n);
     r.P_row = c.take<int64_t>((int64_t)n + 1);
     r.P_col = c.take<int32_t>(2 * nk);
@@ -939,6 +1048,30 @@ ltsnet_status run_core(const int64_t* row_ptr, const int32_t* col, int32_t n, co
         LT_CUDA(cudaStreamSynchronize(s));
         d16 = far == 0;
     }
+    // rows of P too long for one 8-lane group: chunk lists
+    HeavyRows hr;
+    if (!(p->flags & LTSNET_FLAG_PLAIN) && nnz > 0) {
+        k_heavy_count<<<flat_blocks(n), 256, 0, s>>>(r.P_row, n, r.hnch);
+        count_launches(1);
+        LT_CHECK_LAUNCH();
+        LT_CUDA(scan_u32_exclusive(r.hnch, r.hbase, n, r.htmp, s));
+        uint32_t last[2] = {0, 0};
+        LT_CUDA(cudaMemcpyAsync(&last[0], r.hbase + (n - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        LT_CUDA(cudaMemcpyAsync(&last[1], r.hnch + (n - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        LT_CUDA(cudaStreamSynchronize(s));
+        const int64_t nch = (int64_t)last[0] + last[1];
+        if (nch > r.hmax) return LTSNET_ERR_WORKSPACE;
+        if (nch > 0) {
+            k_heavy_emit<<<flat_blocks(n), 256, 0, s>>>(r.P_row, n, r.hnch, r.hbase, r.hcrow, r.hcstart);
+            count_launches(1);
+            LT_CHECK_LAUNCH();
+            hr.hbase = (const int32_t*)r.hbase;
+            hr.crow = r.hcrow;
+            hr.cstart = r.hcstart;
+            hr.partial = r.hpartial;
+            hr.nchunks = (int32_t)nch;
+        }
+    }
     k_init_state<<<flat_blocks(n), 256, 0, s>>>(r.upd, r.gains, n);
     count_launches(1);
     LT_CHECK_LAUNCH();
@@ -952,8 +1085,8 @@ ltsnet_status run_core(const int64_t* row_ptr, const int32_t* col, int32_t n, co
         LT_CUDA(gather_rows2(Y, r.order, n, r.Y2, s));
         Yw = r.Y2;
     }
-    rc = optimize_core(r.P_row, r.P_col, d16 ? r.d16 : nullptr, r.P_val, n, p, Yw, r.upd, r.gains, 0, (int32_t)total,
-                       w, sh, s);
+    rc = optimize_core(r.P_row, r.P_col, d16 ? r.d16 : nullptr, r.P_val, hr, n, p, Yw, r.upd, r.gains, 0,
+                       (int32_t)total, w, sh, s);
     if (rc != LTSNET_OK) return rc;
     if (reordered) LT_CUDA(gather_rows2(r.Y2, r.inv, n, Y, s));
     ltsnet_status a = read_status(w.st, s);
@@ -1016,7 +1149,7 @@ extern "C" ltsnet_status ltsnet_gradient(const int64_t* P_row, const int32_t* P_
     LT_CUDA(launch_psum(w, P_row, n, P_val, s));
     LT_CUDA(launch_bounds_init(w, (const float2*)Y, n, 0, s));
     LT_CUDA(launch_grid_phase(w, sh, p, (const float2*)Y, 0, plain, s));
-    LT_CUDA(launch_point_phase<false>(P_row, P_col, nullptr, P_val, n, (const float2*)Y, nullptr, nullptr, nullptr, w, sh, st,
+    LT_CUDA(launch_point_phase<false>(P_row, P_col, nullptr, P_val, HeavyRows{}, n, (const float2*)Y, nullptr, nullptr, nullptr, w, sh, st,
                                       0, (float2*)grad, parts, plain, s));
     if (terms) {
         k_terms<<<1, 1, 0, s>>>(w.g, terms);
@@ -1077,7 +1210,7 @@ extern "C" ltsnet_status ltsnet_optimize(const int64_t* P_row, const int32_t* P_
     ltsnet_status rc = prepare_iter(n, p, ws, ws_bytes, sh, w, s);
     if (rc != LTSNET_OK) return rc;
     LT_CUDA(launch_check_cols(P_row, P_col, n, w.st, s));
-    return optimize_core(P_row, P_col, nullptr, P_val, n, p, (float2*)Y, (float2*)update, (float2*)gains, start_iter, n_iter,
+    return optimize_core(P_row, P_col, nullptr, P_val, HeavyRows{}, n, p, (float2*)Y, (float2*)update, (float2*)gains, start_iter, n_iter,
                          w, sh, s);
 }
 

@@ -440,16 +440,22 @@ def _bfs_ball(g, root: int, size: int):
     return synth.csr_from_edges(ball.shape[0], new[rows[keep]], new[g.col[keep]])
 
 
-def test_ba4m_ball_pipeline_matches_oracle(ltlib):
-    """Barabasi-Albert graph (n = 4e6, 4 edges per new vertex), the induced
-    subgraph on a 50,000-vertex BFS ball from a seeded root, perplexity 50:
-    C0 and the gradient on both sides (GPU through the ABI, the oracle on its
-    own C0), hubs and all."""
-    import torch
-
+@pytest.fixture(scope="module")
+def ba_ball():
+    """The induced subgraph on a 50,000-vertex BFS ball, from a seeded root,
+    of the Barabasi-Albert graph (n = 4e6, 4 edges per new vertex)."""
     g = synth.config_graph("ba4m")
     root = int(np.random.default_rng(21).integers(g.n))
-    sub = _bfs_ball(g, root, 50_000)
+    return _bfs_ball(g, root, 50_000)
+
+
+def test_ba4m_ball_pipeline_matches_oracle(ltlib, ba_ball):
+    """The cfg-5 graph's 50,000-vertex BFS ball, perplexity 50: C0 and the
+    gradient on both sides (GPU through the ABI, the oracle on its own C0),
+    hubs and all."""
+    import torch
+
+    sub = ba_ball
     aff = ltlib.affinities(sub.row_ptr, sub.col, 50.0)
     ref = oracle.preprocess(sub.row_ptr, sub.col, 50.0)
     P = aff["P"]
@@ -504,3 +510,30 @@ def test_cost_autograd_sbm100k_64_coordinates(ltlib):
         fd = (F.apply(Y, Pp, P[0], P[1], st, params).item()
               - F.apply(Y, Pm, P[0], P[1], st, params).item()) / (Pp[e] - Pm[e]).item()
         assert abs(fd - gP[e].item()) <= 1e-3 * abs(gP[e].item()) + 1e-6, (e, fd, gP[e].item())
+
+
+def test_run_step_ba_ball_long_rows_match_oracle(ltlib, ba_ball):
+    """ltsnet_run on the cfg-5 ball for one iteration: the hubs' rows of P are
+    longer than one 8-lane group takes (they are summed in chunks by whole
+    warps); the step agrees with the oracle's gradient and update."""
+    import torch
+
+    sub = ba_ball
+    aff = ltlib.affinities(sub.row_ptr, sub.col, 50.0)
+    Pn = tuple(t.cpu().numpy() for t in aff["P"])
+    assert np.diff(Pn[0]).max() > 2048  # long rows present
+    Y0 = (np.random.default_rng(13).standard_normal((sub.n, 2)) * 8).astype(np.float32)
+    params = ltlib.Params(perplexity=50.0, stages=[ltlib.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)])
+    Y1, _ = ltlib.run(sub.row_ptr, sub.col, torch.from_numpy(Y0), params)
+    step = Y1.cpu().numpy().astype(np.float64) - Y0
+    st = oracle.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+    gref, pr = oracle.interp_gradient(Y0, Pn[0], Pn[1], Pn[2].astype(np.float64), st, oracle.GridParams(max_boxes=640))
+    lr = oracle.auto_learning_rate(sub.n)
+    Yr, _, _ = oracle.update(Y0.astype(np.float64), np.zeros_like(gref), np.ones_like(gref), gref, st.momentum, lr)
+    n = sub.n
+    scale = (np.linalg.norm(4 * st.lambda_kl * st.exaggeration * pr["A"])
+             + np.linalg.norm(4 * st.lambda_kl * pr["S"] / pr["Z"] * pr["R"])
+             + np.linalg.norm(st.lambda_c / n * Y0.astype(np.float64))
+             + np.linalg.norm(st.lambda_r / n ** 2 * pr["E"]))
+    err = float(np.linalg.norm(step - (Yr - Y0)) / (lr * 1.2 * scale))
+    assert err < 1e-5, err
