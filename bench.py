@@ -35,6 +35,7 @@ PERPLEXITY = 30.0
 ITERS = 1000
 BATCH_ITERS = 750
 BATCH_WORKERS = 16
+BATCH_MAX_BOXES = 128
 FUSED_PROFILE = os.path.join(ROOT, "profiles", "fused_update_rgg1m.md")
 KERNEL_SOURCES = ("paper_2509_19785_gb300/csrc/iterate.cu", "paper_2509_19785_gb300/csrc/iter.cuh")
 
@@ -282,7 +283,11 @@ def bench_ltsnet(args):
     if not args.no_batched:
         gs = synth.graph_batch(512)
         y0s = [synth.initial_layout(gb.n, 100 + i) for i, gb in enumerate(gs)]
-        bparams = lt.Params(perplexity=PERPLEXITY, stages=lt.default_stages(BATCH_ITERS))
+        # grid capped at 128 boxes per side: the cap binds only on layouts wider
+        # than 128 box widths (the 1M-vertex layout stays near 50), and with it
+        # the FFT kernels ask for 64 KB of shared memory instead of 215 KB, so
+        # the grid phases of several graphs can share an SM
+        bparams = lt.Params(perplexity=PERPLEXITY, stages=lt.default_stages(BATCH_ITERS), max_boxes=BATCH_MAX_BOXES)
         lt.run_batched(gs[:32], y0s[:32], bparams, workers=BATCH_WORKERS)  # warm-up
         torch.cuda.synchronize()
         if world > 1:
@@ -295,7 +300,33 @@ def bench_ltsnet(args):
             raise RuntimeError("non-finite batched layout")
         batched = {"value": round(job_rate(world, len(gs), tb * 1e3), 2), "unit": "graphs/s", "graphs": len(gs),
                    "vertices": int(sum(gb.n for gb in gs)), "iters_per_graph": BATCH_ITERS, "seconds": round(tb, 3),
-                   "workers": BATCH_WORKERS, "form": "ltsnet_run_batched: host worker threads, one stream each"}
+                   "workers": BATCH_WORKERS, "max_boxes": BATCH_MAX_BOXES,
+                   "form": "ltsnet_run_batched: host worker threads, one stream each"}
+
+    # scale-free workload: Barabasi-Albert, n = 4e6, 4 edges per new vertex,
+    # perplexity 50, 1000 iterations (whole run incl. C0, one step)
+    ba = None
+    if not args.no_batched:
+        gba = synth.config_graph("ba4m")
+        torch.cuda.synchronize()
+        base_mem = torch.cuda.memory_allocated()
+        torch.cuda.reset_peak_memory_stats()
+        rp_ba = torch.from_numpy(gba.row_ptr).cuda()
+        cl_ba = torch.from_numpy(gba.col).cuda()
+        y_ba = torch.from_numpy(synth.initial_layout(gba.n, 7 + rank)).cuda()
+        pba = lt.Params(perplexity=50.0, stages=lt.default_stages(ITERS))
+        ws_ba = lt.run_workspace(gba.n, gba.col.shape[0], pba)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        yb, rc = lt.run(rp_ba, cl_ba, y_ba, pba, ws=ws_ba)
+        torch.cuda.synchronize()
+        tba = max_over_ranks(time.perf_counter() - t0, world)
+        peak = torch.cuda.max_memory_allocated()
+        ba = {"value": round(job_rate(world, ITERS, tba * 1e3), 2), "unit": "iters/s", "n": gba.n, "m": gba.m,
+              "perplexity": 50, "iters": ITERS, "seconds_incl_C0": round(tba, 3),
+              "workspace_bytes": int(ws_ba.numel()), "peak_device_bytes": int(peak - base_mem),
+              "status": int(rc), "note": "status 1: rows whose perplexity target is unreachable (hubs) are flagged"}
+        del ws_ba, yb, rp_ba, cl_ba, y_ba
 
     if rank != 0:
         if world > 1:
@@ -329,6 +360,7 @@ def bench_ltsnet(args):
         "e2e": {"value": round(e2e_value, 2), "unit": "iters/s",
                 "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes + 8 * n), "d2h_bytes_per_step": 8 * n},
         "batched": batched,
+        "ba4m": ba,
         "clocks": clocks,
         "gpu_launches": int(launches),
     }
@@ -419,7 +451,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ltsnet", choices=["ltsnet", "reference"])
-    ap.add_argument("--no-batched", action="store_true", help="skip the 512-graph batched measurement")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 512-graph batched and the 4M-vertex Barabasi-Albert measurements")
     args = ap.parse_args()
     line = bench_reference(args) if args.impl == "reference" else bench_ltsnet(args)
     if line is not None:
