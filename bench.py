@@ -277,6 +277,25 @@ def bench_ltsnet(args):
                 "avg_launch_us": round(avg_s * 1e6, 2),
                 "launches_timed": fused_launches, "peak_source": peaks["source"]}
 
+    # Pivot MDS start (first step of Alg. 1-3) on the same graph, 100 pivots
+    pm = None
+    if not args.no_batched:
+        k_piv = 100
+        pws = lt.pivot_mds_workspace(n, k_piv)
+        lt.pivot_mds(row_ptr, col, k_piv, ws=pws)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Yp, piv, eig, dist_rows = lt.pivot_mds(row_ptr, col, k_piv, ws=pws, return_dist=True)
+        torch.cuda.synchronize()
+        tp = max_over_ranks(time.perf_counter() - t0, world)
+        finite = torch.where(dist_rows == 0xFFFF, 0, dist_rows.to(torch.int32))
+        levels = int((finite.max(dim=1).values + 1).sum())
+        pm = {"ms": round(tp * 1e3, 2), "pivots": k_piv, "n": n, "bfs_levels_total": levels,
+              "us_per_level": round(tp * 1e6 / levels, 3), "eigvals": [float(eig[0]), float(eig[1])],
+              "workspace_bytes": int(pws.numel()),
+              "note": "max-min pivots: 100 sequential BFS runs of about 1000 levels each, one launch per level"}
+        del pws, Yp, piv, dist_rows, finite
+
     # batched form: 512 independent graphs (grids, recursive trees, SBMs,
     # n log-uniform in [200, 20000]), 750 iterations each, one call
     batched = None
@@ -361,6 +380,7 @@ def bench_ltsnet(args):
                 "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes + 8 * n), "d2h_bytes_per_step": 8 * n},
         "batched": batched,
         "ba4m": ba,
+        "pivot_mds": pm,
         "clocks": clocks,
         "gpu_launches": int(launches),
     }

@@ -310,6 +310,44 @@ ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx_off, const
                                  ltsnet_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * Pivot MDS initial layout (Alg. 1-3, first step: every variant in the paper
+ * starts from a Pivot MDS layout, the method of Brandes and Pich, GD 2006;
+ * Sec. 2 names tsNET with this start tsNET*).  The paper fixes none of its
+ * parameters; this library takes:
+ *  - max-min pivots: pivots[0] = first_pivot; pivot t+1 maximises the BFS
+ *    distance to its nearest chosen pivot, the smallest vertex id on ties, a
+ *    vertex no chosen pivot reaches counting as infinitely far;
+ *  - D = BFS hop distances from the pivots; pairs in different components
+ *    take (largest finite distance + 1);
+ *  - C = -1/2 J_n (D o D) J_k (double centring, J_m = I - 11^T/m);
+ *    x_d = C v_d / sqrt(sigma_d) for the two leading unit eigenvectors v_d of
+ *    C^T C (eigenvalues sigma_1^2 >= sigma_2^2), each signed so that its
+ *    entry of largest magnitude is positive; an axis whose eigenvalue is at
+ *    most 1e-10 of the first is zero;
+ *  - one factor on both axes so that the RMS distance from the centroid is
+ *    sqrt(2) * init_std (init_std = 1e-4 gives the spread of the random
+ *    N(0, 1e-4^2) start); init_std = 0 keeps the MDS scale.
+ *   row_ptr, col  graph (device), as everywhere
+ *   n_pivots      k, 2 <= k <= min(n, 512); 0 <= first_pivot < n; n >= 2
+ *   Y             f32[n][2] (device, out)
+ *   pivots        int32[k] (device, out) in the order chosen
+ *   dist          uint16[k][n] (device, out, may be NULL): row t holds the
+ *                 distances from pivots[t], 0xFFFF where unreached
+ *   eigvals       f64[2] (HOST, out, may be NULL): sigma_1^2, sigma_2^2
+ * The distance sums behind C^T C are exact integers, so the result does not
+ * depend on the order of the GPU's additions.  A BFS distance above 65534
+ * returns LTSNET_ERR_INVALID_ARG; a column id outside [0, n) returns
+ * LTSNET_ERR_BAD_GRAPH.  Returns LTSNET_WARN_NOT_CONVERGED if the FP64
+ * eigen-solve (subspace iteration) stopped at its iteration cap.
+ * Synchronous.
+ * ------------------------------------------------------------------------- */
+size_t ltsnet_pivot_mds_workspace_size(int32_t n, int32_t n_pivots);
+ltsnet_status ltsnet_pivot_mds(const int64_t* row_ptr, const int32_t* col, int32_t n, int32_t n_pivots,
+                               int32_t first_pivot, double init_std, float* Y, int32_t* pivots,
+                               uint16_t* dist, double* eigvals, void* ws, size_t ws_bytes,
+                               ltsnet_stream stream);
+
+/* ---------------------------------------------------------------------------
  * Instrumentation (host side, not part of the method).
  * ltsnet_launch_count: kernels this library has launched in this process.
  * ltsnet_profile_*: times every launch of one kernel with CUDA events on the

@@ -33,7 +33,7 @@ ABI_SYMBOLS = (
     "ltsnet_cost", "ltsnet_grad_pvals", "ltsnet_optimize_workspace_size",
     "ltsnet_optimize", "ltsnet_run_workspace_size", "ltsnet_run", "ltsnet_run_host",
     "ltsnet_run_batched_workspace_size", "ltsnet_run_batched", "ltsnet_launch_count",
-    "ltsnet_profile_begin", "ltsnet_profile_end",
+    "ltsnet_profile_begin", "ltsnet_profile_end", "ltsnet_pivot_mds_workspace_size", "ltsnet_pivot_mds",
 )
 
 
@@ -104,6 +104,10 @@ def lib():
         L.ltsnet_run_batched_workspace_size.argtypes = [i32, P, P, pp, i32]
         L.ltsnet_run_batched_workspace_size.restype = sz
         L.ltsnet_run_batched.argtypes = [i32, P, P, P, P, pp, P, P, sz, i32, P]
+        L.ltsnet_pivot_mds_workspace_size.argtypes = [i32, i32]
+        L.ltsnet_pivot_mds_workspace_size.restype = sz
+        L.ltsnet_pivot_mds.argtypes = [P, P, i32, i32, i32, f64, P, P, P, ctypes.POINTER(f64), P, sz, P]
+        L.ltsnet_pivot_mds.restype = i32
         L.ltsnet_launch_count.restype = i64
         L.ltsnet_profile_begin.argtypes = [i32, i32]
         L.ltsnet_profile_end.argtypes = [i32, ctypes.POINTER(f64), ctypes.POINTER(i32)]
@@ -231,6 +235,37 @@ def knn_bfs(row_ptr, col, k: int):
                                 ws.numel(), _stream()), "ltsnet_knn_bfs")
     _check(lib().ltsnet_poll_status(_ptr(ws), ws.numel(), _stream()), "ltsnet_knn_bfs (device)")
     return nbr, hop, cnt
+
+
+def pivot_mds_workspace(n: int, n_pivots: int):
+    """Workspace for ltsnet_pivot_mds (device bytes)."""
+    nb = lib().ltsnet_pivot_mds_workspace_size(int(n), int(n_pivots))
+    if nb == 0:
+        raise LtsnetError(-1, "ltsnet_pivot_mds_workspace_size")
+    return _workspace(nb)
+
+
+def pivot_mds(row_ptr, col, n_pivots: int = 100, first: int = 0, init_std: float = 1e-4, ws=None,
+              return_dist: bool = False):
+    """Pivot MDS initial layout (the first step of Alg. 1-3).  Returns
+    (Y f32 [n,2], pivots int32 [k], eigvals (sigma_1^2, sigma_2^2)) on the GPU,
+    plus the distance rows uint16 [k,n] (0xFFFF = unreached) if
+    return_dist."""
+    torch = _torch()
+    row_ptr = _dev(row_ptr, torch.int64)
+    col = _dev(col, torch.int32)
+    n = row_ptr.numel() - 1
+    k = int(n_pivots)
+    if ws is None:
+        ws = pivot_mds_workspace(n, k)
+    Y = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+    piv = torch.empty((k,), dtype=torch.int32, device="cuda")
+    dist = torch.empty((k, n), dtype=torch.uint16, device="cuda") if return_dist else None
+    eig = (ctypes.c_double * 2)()
+    _check(lib().ltsnet_pivot_mds(_ptr(row_ptr), _ptr(col), n, k, int(first), float(init_std), _ptr(Y), _ptr(piv),
+                                  _ptr(dist), eig, _ptr(ws), ws.numel(), _stream()), "ltsnet_pivot_mds")
+    out = (Y, piv, (eig[0], eig[1]))
+    return out + (dist,) if return_dist else out
 
 
 def calibrate(hop, cnt, perplexity: float, tol: float = 1e-5, max_steps: int = 100):
