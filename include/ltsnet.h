@@ -322,8 +322,8 @@ ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx_off, const
  *  - C = -1/2 J_n (D o D) J_k (double centring, J_m = I - 11^T/m);
  *    x_d = C v_d / sqrt(sigma_d) for the two leading unit eigenvectors v_d of
  *    C^T C (eigenvalues sigma_1^2 >= sigma_2^2), each signed so that its
- *    entry of largest magnitude is positive; an axis whose eigenvalue is at
- *    most 1e-10 of the first is zero;
+ *    first entry whose magnitude is within a relative 1e-9 of the largest is
+ *    positive; an axis whose eigenvalue is at most 1e-10 of the first is zero;
  *  - one factor on both axes so that the RMS distance from the centroid is
  *    sqrt(2) * init_std (init_std = 1e-4 gives the spread of the random
  *    N(0, 1e-4^2) start); init_std = 0 keeps the MDS scale.

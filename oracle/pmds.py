@@ -31,8 +31,10 @@ Readings, because the paper leaves these open:
   axis 1 against axis 2 by sigma_1 / sigma_2.
 - An axis whose eigenvalue is at most 1e-10 of the first is set to zero
   (a path graph is one-dimensional).
-- Sign: each v_d is flipped so that its entry of largest magnitude is positive
-  (smallest index on equal magnitudes).
+- Sign: each v_d is flipped so that its first entry (smallest index) whose
+  magnitude is within a relative 1e-9 of the largest is positive.  The slack
+  keeps the choice stable under rounding where entries tie in magnitude (a
+  symmetric graph, or k = 2, where v = (1, -1)/sqrt(2)).
 - Final scale: both axes are multiplied by one factor so that the layout's
   RMS distance from its centroid is sqrt(2) * init_std, i.e. the same spread as
   the N(0, init_std^2) random start (init_std = 1e-4).  init_std = 0 keeps the
@@ -47,6 +49,7 @@ import numpy as np
 
 UNREACHED = -1
 AXIS_EPS = 1e-10
+SIGN_SLACK = 1e-9
 
 
 def bfs_distances(row_ptr: np.ndarray, col: np.ndarray, src: int) -> np.ndarray:
@@ -115,7 +118,8 @@ def pmds_coords(A: np.ndarray, init_std: float = 1e-4):
         if d >= k or lam[d] <= AXIS_EPS * lam[0]:
             continue
         v = V[:, d]
-        j = int(np.argmax(np.abs(v)))
+        a = np.abs(v)
+        j = int(np.flatnonzero(a >= (1.0 - SIGN_SLACK) * a.max())[0])
         if v[j] < 0:
             v = -v
         Y[:, d] = C @ v / np.sqrt(np.sqrt(lam[d]))

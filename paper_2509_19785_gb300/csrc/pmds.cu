@@ -22,9 +22,10 @@
 //     sqrt(2) init_std.
 //
 // The scale 1/sqrt(sigma_d) makes the method classical MDS when every
-// vertex is a pivot.  Each v_d is signed so that its entry of largest
-// magnitude is positive (smallest index on ties); an axis whose eigenvalue
-// is at most 1e-10 of the first is zero.
+// vertex is a pivot.  Each v_d is signed so that its first entry whose
+// magnitude is within a relative 1e-9 of the largest is positive (the slack
+// keeps the choice stable under rounding where entries tie in magnitude); an
+// axis whose eigenvalue is at most 1e-10 of the first is zero.
 #include <math.h>
 
 #include <algorithm>
@@ -46,6 +47,7 @@ constexpr int kRitz = 4;          // subspace dimension of the eigen-solve
 constexpr int kEigMaxIter = 20000;
 constexpr double kEigTol = 1e-13;
 constexpr double kAxisEps = 1e-10;
+constexpr double kSignSlack = 1e-9;
 constexpr int kFlatBlocks = kSMs * 4;
 
 struct PmdsCtl {
@@ -588,44 +590,36 @@ __global__ void __launch_bounds__(kThreads) k_pmds_eig(const unsigned long long*
     // coefficients of the two axes
     for (int d = 0; d < 2; ++d) {
         const bool axis = d < r && S.lam[0] > 0.0 && S.lam[d] > kAxisEps * S.lam[0];
-        // sign: entry of largest magnitude positive, smallest index on ties
-        double bestv = -1.0;
-        int bestj = 0x7fffffff;
-        double sgn = 1.0;
-        for (int j = threadIdx.x; j < k; j += kThreads) {
-            const double a = fabs(S.Q[j][d]);
-            if (a > bestv) {
-                bestv = a;
-                bestj = j;
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(FULL, bestv, o);
-            const int oj = __shfl_xor_sync(FULL, bestj, o);
-            if (ov > bestv || (ov == bestv && oj < bestj)) {
-                bestv = ov;
-                bestj = oj;
-            }
-        }
-        if (lane == 0) {
-            S.red[warp][0] = bestv;
-            S.red[warp][1] = (double)bestj;
-        }
+        // sign: the first entry (smallest index) whose magnitude is within a
+        // relative kSignSlack of the largest is made positive
+        double amax = 0.0;
+        for (int j = threadIdx.x; j < k; j += kThreads) amax = fmax(amax, fabs(S.Q[j][d]));
+        for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(FULL, amax, o));
+        if (lane == 0) S.red[warp][0] = amax;
         __syncthreads();
         if (threadIdx.x == 0) {
-            double bv = -1.0;
-            int bj = 0x7fffffff;
-            for (int q = 0; q < kThreads / 32; ++q) {
-                const int qj = (int)S.red[q][1];
-                if (S.red[q][0] > bv || (S.red[q][0] == bv && qj < bj)) {
-                    bv = S.red[q][0];
-                    bj = qj;
-                }
+            double m = 0.0;
+            for (int q = 0; q < kThreads / 32; ++q) m = fmax(m, S.red[q][0]);
+            S.scal[2] = m;
+        }
+        __syncthreads();
+        const double thr = (1.0 - kSignSlack) * S.scal[2];
+        int firstj = 0x7fffffff;
+        for (int j = threadIdx.x; j < k; j += kThreads)
+            if (fabs(S.Q[j][d]) >= thr) {
+                firstj = j;
+                break;
             }
+        for (int o = 16; o > 0; o >>= 1) firstj = min(firstj, __shfl_xor_sync(FULL, firstj, o));
+        if (lane == 0) S.red[warp][1] = (double)firstj;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int bj = 0x7fffffff;
+            for (int q = 0; q < kThreads / 32; ++q) bj = min(bj, (int)S.red[q][1]);
             S.scal[1] = (bj < k && S.Q[bj][d] < 0.0) ? -1.0 : 1.0;
         }
         __syncthreads();
-        sgn = S.scal[1];
+        const double sgn = S.scal[1];
         // J_k v: remove the mean over the pivots
         double mv[1] = {0.0};
         for (int j = threadIdx.x; j < k; j += kThreads) mv[0] += S.Q[j][d];
