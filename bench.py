@@ -277,6 +277,25 @@ def bench_ltsnet(args):
                 "avg_launch_us": round(avg_s * 1e6, 2),
                 "launches_timed": fused_launches, "peak_source": peaks["source"]}
 
+    # quality of the final layout (Sec. 4 metrics): NP over all vertices,
+    # stress over 64 sampled sources
+    qual = None
+    if not args.no_batched:
+        qws = lt.quality_workspace(n)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        npv, exc = lt.neighbourhood_preservation(row_ptr, col, Y, ws=qws)
+        torch.cuda.synchronize()
+        t_np = time.perf_counter() - t0
+        src = torch.from_numpy(np.random.default_rng(11).choice(n, 64, replace=False).astype(np.int32)).cuda()
+        t0 = time.perf_counter()
+        st, alpha, pairs, skipped = lt.stress(row_ptr, col, Y, sources=src, ws=qws)
+        t_st = time.perf_counter() - t0
+        qual = {"np_r2": round(npv, 5), "np_excluded": exc, "np_ms": round(t_np * 1e3, 2),
+                "stress": round(st, 5), "stress_sources": 64, "stress_pairs": pairs, "stress_ms": round(t_st * 1e3, 2),
+                "layout": "final layout of the timed run (1000 iterations from the random start)"}
+        del qws
+
     # Pivot MDS start (first step of Alg. 1-3) on the same graph, 100 pivots
     pm = None
     if not args.no_batched:
@@ -381,6 +400,7 @@ def bench_ltsnet(args):
         "batched": batched,
         "ba4m": ba,
         "pivot_mds": pm,
+        "quality": qual,
         "clocks": clocks,
         "gpu_launches": int(launches),
     }

@@ -348,6 +348,39 @@ ltsnet_status ltsnet_pivot_mds(const int64_t* row_ptr, const int32_t* col, int32
                                ltsnet_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * Layout quality metrics of Sec. 4 (the paper's NP and ST).  Synchronous.
+ * One workspace, ltsnet_quality_workspace_size(n) bytes, serves both calls.
+ *
+ * ltsnet_neighbourhood_preservation -- NP with r = 2: for every vertex v,
+ * b = |N_G(v,2)| (vertices within two hops, v excluded), N_D(v) the b
+ * vertices nearest to v in the drawing Y (f32[n][2], device), and
+ * c = |N_G(v,2) cap N_D(v)|; *np_out (host) = mean of c / (2b - c) over the
+ * vertices with b > 0 (the paper prints a sum but states NP lies in [0, 1]).
+ * "Nearest" orders (FP32 squared distance, vertex id), the squared distance
+ * formed as dx*dx + dy*dy with every operation rounded on its own; ties go to
+ * the smaller id.  A vertex whose 2-hop candidate count, deg(v) plus the sum
+ * of deg(w) over its adjacency entries w, exceeds 2048 is excluded: b = -1,
+ * and *excluded_out (host, may be NULL) counts them.
+ *   ball, common  int32[n] (device, out, may be NULL): b and c per vertex.
+ *
+ * ltsnet_stress -- ST: over the ordered pairs (s, j), j != s, for s in
+ * sources (int32[n_sources], device), of ((d_sj - alpha ||X_s - X_j||)/d_sj)^2,
+ * d the hop distance, at the scale alpha that minimises it (the drawing's
+ * scale is free); all vertices as sources give the paper's ST.  Pairs in
+ * different components are skipped.  out (host) f64[4]: ST, alpha, pairs
+ * counted, pairs skipped.  A BFS distance above 65534 returns
+ * LTSNET_ERR_INVALID_ARG; a source out of range too.
+ * ------------------------------------------------------------------------- */
+size_t ltsnet_quality_workspace_size(int32_t n);
+ltsnet_status ltsnet_neighbourhood_preservation(const int64_t* row_ptr, const int32_t* col, int32_t n,
+                                                const float* Y, int32_t* ball, int32_t* common,
+                                                double* np_out, int32_t* excluded_out, void* ws,
+                                                size_t ws_bytes, ltsnet_stream stream);
+ltsnet_status ltsnet_stress(const int64_t* row_ptr, const int32_t* col, int32_t n, const float* Y,
+                            const int32_t* sources, int32_t n_sources, double* out, void* ws,
+                            size_t ws_bytes, ltsnet_stream stream);
+
+/* ---------------------------------------------------------------------------
  * Instrumentation (host side, not part of the method).
  * ltsnet_launch_count: kernels this library has launched in this process.
  * ltsnet_profile_*: times every launch of one kernel with CUDA events on the

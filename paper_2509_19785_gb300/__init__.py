@@ -34,6 +34,7 @@ ABI_SYMBOLS = (
     "ltsnet_optimize", "ltsnet_run_workspace_size", "ltsnet_run", "ltsnet_run_host",
     "ltsnet_run_batched_workspace_size", "ltsnet_run_batched", "ltsnet_launch_count",
     "ltsnet_profile_begin", "ltsnet_profile_end", "ltsnet_pivot_mds_workspace_size", "ltsnet_pivot_mds",
+    "ltsnet_quality_workspace_size", "ltsnet_neighbourhood_preservation", "ltsnet_stress",
 )
 
 
@@ -108,6 +109,13 @@ def lib():
         L.ltsnet_pivot_mds_workspace_size.restype = sz
         L.ltsnet_pivot_mds.argtypes = [P, P, i32, i32, i32, f64, P, P, P, ctypes.POINTER(f64), P, sz, P]
         L.ltsnet_pivot_mds.restype = i32
+        L.ltsnet_quality_workspace_size.argtypes = [i32]
+        L.ltsnet_quality_workspace_size.restype = sz
+        L.ltsnet_neighbourhood_preservation.argtypes = [P, P, i32, P, P, P, ctypes.POINTER(f64),
+                                                        ctypes.POINTER(i32), P, sz, P]
+        L.ltsnet_neighbourhood_preservation.restype = i32
+        L.ltsnet_stress.argtypes = [P, P, i32, P, P, i32, ctypes.POINTER(f64), P, sz, P]
+        L.ltsnet_stress.restype = i32
         L.ltsnet_launch_count.restype = i64
         L.ltsnet_profile_begin.argtypes = [i32, i32]
         L.ltsnet_profile_end.argtypes = [i32, ctypes.POINTER(f64), ctypes.POINTER(i32)]
@@ -266,6 +274,49 @@ def pivot_mds(row_ptr, col, n_pivots: int = 100, first: int = 0, init_std: float
                                   _ptr(dist), eig, _ptr(ws), ws.numel(), _stream()), "ltsnet_pivot_mds")
     out = (Y, piv, (eig[0], eig[1]))
     return out + (dist,) if return_dist else out
+
+
+def quality_workspace(n: int):
+    """Workspace for the quality-metric calls (device bytes)."""
+    return _workspace(lib().ltsnet_quality_workspace_size(int(n)))
+
+
+def neighbourhood_preservation(row_ptr, col, Y, ws=None, return_counts: bool = False):
+    """NP with r = 2 (Sec. 4).  Returns (NP, excluded vertices), plus the
+    per-vertex ball sizes b and intersections c (int32 [n] on the GPU, b = -1
+    where excluded) if return_counts."""
+    torch = _torch()
+    row_ptr = _dev(row_ptr, torch.int64)
+    col = _dev(col, torch.int32)
+    Y = _dev(Y, torch.float32)
+    n = row_ptr.numel() - 1
+    if ws is None:
+        ws = quality_workspace(n)
+    b = torch.empty((n,), dtype=torch.int32, device="cuda") if return_counts else None
+    c = torch.empty((n,), dtype=torch.int32, device="cuda") if return_counts else None
+    npv, exc = ctypes.c_double(), ctypes.c_int32()
+    _check(lib().ltsnet_neighbourhood_preservation(_ptr(row_ptr), _ptr(col), n, _ptr(Y), _ptr(b), _ptr(c),
+                                                   ctypes.byref(npv), ctypes.byref(exc), _ptr(ws), ws.numel(),
+                                                   _stream()), "ltsnet_neighbourhood_preservation")
+    out = (npv.value, exc.value)
+    return out + (b, c) if return_counts else out
+
+
+def stress(row_ptr, col, Y, sources=None, ws=None):
+    """ST (Sec. 4) at its optimal scale over the pairs (s, j), s in sources
+    (all vertices if None).  Returns (ST, alpha, pairs, skipped pairs)."""
+    torch = _torch()
+    row_ptr = _dev(row_ptr, torch.int64)
+    col = _dev(col, torch.int32)
+    Y = _dev(Y, torch.float32)
+    n = row_ptr.numel() - 1
+    src = torch.arange(n, dtype=torch.int32, device="cuda") if sources is None else _dev(sources, torch.int32)
+    if ws is None:
+        ws = quality_workspace(n)
+    out = (ctypes.c_double * 4)()
+    _check(lib().ltsnet_stress(_ptr(row_ptr), _ptr(col), n, _ptr(Y), _ptr(src), src.numel(), out, _ptr(ws),
+                               ws.numel(), _stream()), "ltsnet_stress")
+    return out[0], out[1], int(out[2]), int(out[3])
 
 
 def calibrate(hop, cnt, perplexity: float, tol: float = 1e-5, max_steps: int = 100):

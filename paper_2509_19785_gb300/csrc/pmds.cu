@@ -6,9 +6,7 @@
 //     distance to its nearest chosen pivot is largest, the smallest index on
 //     ties, a vertex no pivot reaches counting as infinitely far.
 //  2. D: hop distances from every pivot, one uint16 row of n per pivot
-//     (0xFFFF = unreached), by level-synchronous BFS: one grid-wide launch
-//     per level, replayed from a CUDA graph in batches; no kernel waits on
-//     another.
+//     (0xFFFF = unreached), by the level-synchronous BFS of bfs_levels.cuh.
 //  3. A = D o D with unreached pairs at (largest finite distance + 1);
 //     C = -1/2 J_n A J_k.  Then C^T C = 1/4 J_k (G - s s^T / n) J_k with
 //     G = A^T A and s = A^T 1.  G and s are sums of integers, accumulated
@@ -30,16 +28,13 @@
 
 #include <algorithm>
 
-#include "common.cuh"
+#include "bfs_levels.cuh"
 
 namespace lt {
 namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxPivots = 512;
-constexpr uint16_t kUnreached = 0xFFFF;
-constexpr int kMaxDist = 65534;
-constexpr int kLevelBatch = 64;   // level launches per graph replay
 constexpr int kTile = 64;         // pivots per side of a Gram tile
 constexpr int kRows = 64;         // rows staged per step of the Gram kernel
 constexpr int kPad = 68;          // words per staged column: 16-byte aligned, spreads the banks
@@ -49,16 +44,6 @@ constexpr double kEigTol = 1e-13;
 constexpr double kAxisEps = 1e-10;
 constexpr double kSignSlack = 1e-9;
 constexpr int kFlatBlocks = kSMs * 4;
-
-struct PmdsCtl {
-    int32_t t;        // pivot whose BFS is running
-    int32_t cur;      // queue holding the current frontier
-    int32_t cnt[2];   // frontier sizes; cnt[cur ^ 1] is 0 between launches
-    int32_t levels;   // frontiers expanded in the current BFS
-    uint32_t ticket;  // blocks finished in the current launch
-    int32_t err;      // 1: a distance above kMaxDist, 2: a column id out of range
-    int32_t pad;
-};
 
 struct PmdsEig {
     double lam[2];   // sigma_d^2
@@ -79,102 +64,18 @@ __device__ __forceinline__ uint32_t sq_dist(uint16_t d, uint32_t fill)
 
 __global__ void k_pmds_pivot(int32_t t, int32_t first, int32_t n, const unsigned long long* __restrict__ best,
                              int32_t* __restrict__ pivots, uint16_t* __restrict__ D, int32_t* __restrict__ q0,
-                             PmdsCtl* ctl, StatusBlock* st)
+                             LevelCtl* ctl, StatusBlock* st)
 {
     int32_t p = first;
     if (t > 0) p = (int32_t)(0xFFFFFFFFu - (uint32_t)(best[t] & 0xFFFFFFFFull));
-    ctl->t = t;
-    ctl->cur = 0;
-    ctl->cnt[1] = 0;
-    ctl->levels = 0;
-    ctl->ticket = 0;
     if (p < 0 || p >= n) {  // cannot happen for 2 <= k <= n; kept as a guard
         record_error(st, LTSNET_ERR_INVALID_ARG, t);
-        ctl->cnt[0] = 0;
+        ctl->cnt[0] = ctl->cnt[1] = 0;
         ctl->err = 3;
         return;
     }
     pivots[t] = p;
-    D[(size_t)t * n + p] = 0;
-    q0[0] = p;
-    ctl->cnt[0] = 1;
-}
-
-// One BFS level: every frontier vertex claims its unreached neighbours
-// (16-bit compare-and-swap) and appends them to the other queue.  An 8-lane
-// group per frontier vertex; the last block to finish swaps the queues.
-__global__ void __launch_bounds__(kThreads) k_pmds_level(const int64_t* __restrict__ row_ptr,
-                                                         const int32_t* __restrict__ col, int32_t n,
-                                                         uint16_t* __restrict__ D, int32_t* __restrict__ q0,
-                                                         int32_t* __restrict__ q1, PmdsCtl* ctl, StatusBlock* st)
-{
-    const int cur = ctl->cur;
-    const int32_t count = ctl->cnt[cur];
-    if (count == 0) return;
-    uint16_t* d = D + (size_t)ctl->t * n;
-    const int32_t* qc = cur ? q1 : q0;
-    int32_t* qn = cur ? q0 : q1;
-    int32_t* ncnt = &ctl->cnt[cur ^ 1];
-    const int lane = threadIdx.x & 31, grp = lane >> 3, sub = lane & 7;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    bool overflow = false;
-    for (int64_t base = warp * 4; base < count; base += nwarps * 4) {
-        const int64_t idx = base + grp;
-        int64_t e0 = 0, e1 = 0;
-        uint32_t lev = 0;
-        if (idx < count) {
-            const int32_t u = qc[idx];
-            e0 = row_ptr[u];
-            e1 = row_ptr[u + 1];
-            lev = (uint32_t)d[u] + 1u;
-        }
-        int64_t trips = (e1 - e0 + 7) >> 3;
-        trips = max(trips, (int64_t)__shfl_xor_sync(FULL, (long long)trips, 8));
-        trips = max(trips, (int64_t)__shfl_xor_sync(FULL, (long long)trips, 16));
-        for (int64_t r = 0; r < trips; ++r) {
-            const int64_t e = e0 + r * 8 + sub;
-            bool push = false;
-            int32_t v = 0;
-            if (e < e1) {
-                v = col[e];
-                if ((uint32_t)v >= (uint32_t)n) {
-                    record_error(st, LTSNET_ERR_BAD_GRAPH, v);
-                    ctl->err = 2;
-                } else if (d[v] == kUnreached) {
-                    if (lev > (uint32_t)kMaxDist) {
-                        overflow = true;
-                    } else {
-                        push = atomicCAS(&d[v], kUnreached, (uint16_t)lev) == kUnreached;
-                    }
-                }
-            }
-            const unsigned b = __ballot_sync(FULL, push);
-            if (b) {
-                const int leader = __ffs(b) - 1;
-                int32_t pos = 0;
-                if (lane == leader) pos = atomicAdd(ncnt, __popc(b));
-                pos = __shfl_sync(FULL, pos, leader);
-                if (push) qn[pos + __popc(b & lanemask_lt())] = v;
-            }
-        }
-    }
-    if (overflow) {
-        record_error(st, LTSNET_ERR_INVALID_ARG, kMaxDist);
-        ctl->err = 1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const uint32_t done = atomicAdd(&ctl->ticket, 1u);
-        if (done == gridDim.x - 1) {
-            __threadfence();
-            ctl->cnt[cur] = 0;
-            ctl->cur = cur ^ 1;
-            ctl->levels += 1;
-            ctl->ticket = 0;
-        }
-    }
+    bfs_seed(ctl, D, n, t, p, q0);
 }
 
 __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
@@ -706,7 +607,7 @@ __global__ void __launch_bounds__(kThreads) k_pmds_scale(const double2* __restri
 
 struct PmdsWs {
     StatusBlock* st;
-    PmdsCtl* ctl;
+    LevelCtl* ctl;
     PmdsEig* eig;
     int32_t* dmax;
     uint16_t* D;
@@ -727,7 +628,7 @@ size_t pmds_carve(void* ws, int32_t n, int32_t k, PmdsWs* w)
     Carve c(ws, ~(size_t)0);
     PmdsWs t;
     t.st = c.take<StatusBlock>(1);
-    t.ctl = c.take<PmdsCtl>(1);
+    t.ctl = c.take<LevelCtl>(1);
     t.eig = c.take<PmdsEig>(1);
     t.dmax = c.take<int32_t>(1);
     t.D = c.take<uint16_t>((size_t)k * n);
@@ -771,7 +672,7 @@ extern "C" ltsnet_status ltsnet_pivot_mds(const int64_t* row_ptr, const int32_t*
     uint16_t* D = dist ? dist : w.D;
 
     LT_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StatusBlock), s));
-    LT_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(PmdsCtl), s));
+    LT_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(LevelCtl), s));
     LT_CUDA(cudaMemsetAsync(w.dmax, 0, sizeof(int32_t), s));
     LT_CUDA(cudaMemsetAsync(D, 0xFF, sizeof(uint16_t) * (size_t)k * n, s));
     LT_CUDA(cudaMemsetAsync(w.nearest, 0xFF, sizeof(uint32_t) * (size_t)n, s));
@@ -779,65 +680,15 @@ extern "C" ltsnet_status ltsnet_pivot_mds(const int64_t* row_ptr, const int32_t*
     LT_CUDA(cudaMemsetAsync(w.colsum, 0, sizeof(unsigned long long) * (size_t)k, s));
     LT_CUDA(cudaMemsetAsync(w.G, 0, sizeof(unsigned long long) * 2 * (size_t)k * k, s));
 
-    // a graph of kLevelBatch level launches (its arguments do not change:
-    // the pivot, the queues and the counts live in the control block)
-    const unsigned grid = kSMs * 2;
-    AuxStreams* aux = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    if (!profiling_active() && aux_streams(&aux) == cudaSuccess) {
-        cudaGraph_t graph = nullptr;
-        LT_CUDA(cudaStreamBeginCapture(aux->capture, cudaStreamCaptureModeThreadLocal));
-        for (int b = 0; b < kLevelBatch; ++b)
-            k_pmds_level<<<grid, kThreads, 0, aux->capture>>>(row_ptr, col, n, D, w.q0, w.q1, w.ctl, w.st);
-        cudaError_t e1 = cudaGetLastError();
-        cudaError_t e2 = cudaStreamEndCapture(aux->capture, &graph);
-        if (e1 != cudaSuccess || e2 != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            LT_CUDA(e1 != cudaSuccess ? e1 : e2);
-        }
-        cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        LT_CUDA(e3);
-    }
-    struct ExecGuard {
-        cudaGraphExec_t& x;
-        ~ExecGuard()
-        {
-            if (x) cudaGraphExecDestroy(x);
-        }
-    } guard{exec};
-
-    int32_t reps = 1;
+    LevelRunner lr{row_ptr, col, n, D, w.q0, w.q1, w.ctl, w.st};
+    if (ltsnet_status e = lr.prepare()) return e;
     for (int32_t t = 0; t < k; ++t) {
         k_pmds_pivot<<<1, 1, 0, s>>>(t, first_pivot, n, w.best, pivots, D, w.q0, w.ctl, w.st);
         count_launches(1);
         LT_CHECK_LAUNCH();
-        PmdsCtl h;
-        int64_t launched = 0;
-        for (;;) {
-            // a BFS that has not ended after kMaxDist + 2 levels would
-            // have set err; more launches than that mean a broken count
-            if (launched > kMaxDist + 2 * kLevelBatch) return LTSNET_ERR_DEVICE_TIMEOUT;
-            launched += (int64_t)reps * kLevelBatch;
-            for (int32_t q = 0; q < reps; ++q) {
-                if (exec) {
-                    LT_CUDA(cudaGraphLaunch(exec, s));
-                } else {
-                    for (int b = 0; b < kLevelBatch; ++b)
-                        k_pmds_level<<<grid, kThreads, 0, s>>>(row_ptr, col, n, D, w.q0, w.q1, w.ctl, w.st);
-                    LT_CHECK_LAUNCH();
-                }
-                count_launches(kLevelBatch);
-            }
-            LT_CUDA(cudaMemcpyAsync(&h, w.ctl, sizeof(PmdsCtl), cudaMemcpyDeviceToHost, s));
-            LT_CUDA(cudaStreamSynchronize(s));
-            if (h.err) break;
-            if (h.cnt[h.cur] == 0) break;
-            reps = std::min<int32_t>(reps * 2, 64);
-        }
+        LevelCtl h;
+        if (ltsnet_status e = lr.run(s, &h)) return e;
         if (h.err) break;
-        // the next pivot's BFS starts with enough batches for this one's depth
-        reps = std::max<int32_t>(1, (h.levels + kLevelBatch) / kLevelBatch);
         k_pmds_nearest<<<kFlatBlocks, kThreads, 0, s>>>(D, t, n, w.nearest, t + 1 < k ? w.best + t + 1 : nullptr,
                                                          w.dmax);
         count_launches(1);
