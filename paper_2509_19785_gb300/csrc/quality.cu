@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kNpWarps * 32) k_np(const int64_t* __restrict_
     for (int64_t v = (int64_t)blockIdx.x * kNpWarps + w; v < n; v += nw) {
         const int64_t a0 = row_ptr[v], a1 = row_ptr[v + 1];
         // (1) candidate count and the 2-hop ball
-        long long cand = a1 - a0;
+        long long cand = lane == 0 ? a1 - a0 : 0;  // deg(v) once, then the neighbours' degrees
         for (int64_t e = a0 + lane; e < a1; e += 32) {
             const int32_t x = col[e];
             if ((uint32_t)x < (uint32_t)n) cand += row_ptr[x + 1] - row_ptr[x];
