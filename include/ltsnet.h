@@ -348,6 +348,38 @@ ltsnet_status ltsnet_pivot_mds(const int64_t* row_ptr, const int32_t* col, int32
                                ltsnet_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * Quadtree (Barnes-Hut) gradient of BH-tsNET (Alg. 1) and FIt-tsNET (Alg. 2),
+ * the paper's other two algorithms, for comparison with L-tsNET.  Same
+ * gradient formula as ltsnet_gradient; the attraction A is the exact sparse
+ * sum in both variants.
+ *   LTSNET_VARIANT_BH:  Z, R and E from the quadtree (BH-SNE's repulsion for
+ *                       C1, Eq. 7 for C2).
+ *   LTSNET_VARIANT_FIT: A, R, Z and S from ltsnet_gradient's grid
+ *                       interpolation (C1), E from the quadtree (C2).
+ * The quadtree (the paper leaves its details open): the square at the
+ * drawing's minima with side e = the larger extent; depth 16; a point's cell
+ * column min(65535, floor((x - lo) * (65536 / e))) in FP32, Morton order;
+ * a node of one point is not split; centres of mass exact from fixed point
+ * (q = rint((x - lo) 2^36 / e), int64 sums, c = lo + (sum q / |N|) e 2^-36
+ * in FP64, rounded to FP32; a one-point node uses the point); a node is a
+ * summary for point i if it does not hold i and w^2 < theta^2 d^2 (w = e 2^-l
+ * its cell width, d from X_i to its centre, FP32); an opened depth-16 node
+ * contributes its points one by one.  theta = 0 gives the exact sums.
+ *   grad  f32[n][2] (device); parts f32[n][6] or NULL: (A, R, E) as used;
+ *   terms f64[2] (HOST) or NULL: Z, S.
+ * Synchronous.  theta >= 0; params as for ltsnet_gradient (only eps is used
+ * by the BH variant).
+ * ------------------------------------------------------------------------- */
+#define LTSNET_VARIANT_BH 1
+#define LTSNET_VARIANT_FIT 2
+size_t ltsnet_gradient_quadtree_workspace_size(int32_t n, const ltsnet_params* p, int32_t variant);
+ltsnet_status ltsnet_gradient_quadtree(const int64_t* P_row, const int32_t* P_col, const float* P_val,
+                                       int32_t n, const float* Y, const ltsnet_stage* stage,
+                                       const ltsnet_params* p, float theta, int32_t variant, float* grad,
+                                       float* parts, double* terms, void* ws, size_t ws_bytes,
+                                       ltsnet_stream stream);
+
+/* ---------------------------------------------------------------------------
  * Layout quality metrics of Sec. 4 (the paper's NP and ST).  Synchronous.
  * One workspace, ltsnet_quality_workspace_size(n) bytes, serves both calls.
  *

@@ -35,6 +35,7 @@ ABI_SYMBOLS = (
     "ltsnet_run_batched_workspace_size", "ltsnet_run_batched", "ltsnet_launch_count",
     "ltsnet_profile_begin", "ltsnet_profile_end", "ltsnet_pivot_mds_workspace_size", "ltsnet_pivot_mds",
     "ltsnet_quality_workspace_size", "ltsnet_neighbourhood_preservation", "ltsnet_stress",
+    "ltsnet_gradient_quadtree_workspace_size", "ltsnet_gradient_quadtree",
 )
 
 
@@ -116,6 +117,11 @@ def lib():
         L.ltsnet_neighbourhood_preservation.restype = i32
         L.ltsnet_stress.argtypes = [P, P, i32, P, P, i32, ctypes.POINTER(f64), P, sz, P]
         L.ltsnet_stress.restype = i32
+        L.ltsnet_gradient_quadtree_workspace_size.argtypes = [i32, pp, i32]
+        L.ltsnet_gradient_quadtree_workspace_size.restype = sz
+        L.ltsnet_gradient_quadtree.argtypes = [P, P, P, i32, P, ctypes.POINTER(CStage), pp, ctypes.c_float, i32, P, P,
+                                               ctypes.POINTER(f64), P, sz, P]
+        L.ltsnet_gradient_quadtree.restype = i32
         L.ltsnet_launch_count.restype = i64
         L.ltsnet_profile_begin.argtypes = [i32, i32]
         L.ltsnet_profile_end.argtypes = [i32, ctypes.POINTER(f64), ctypes.POINTER(i32)]
@@ -413,6 +419,36 @@ def gradient(P, Y, stage: Stage, params: Params | None = None, parts: bool = Fal
                                  _stream()), "ltsnet_gradient")
     _check(lib().ltsnet_poll_status(_ptr(ws), ws.numel(), _stream()), "ltsnet_gradient (device)")
     return grad, pt, terms
+
+
+VARIANTS = {"bh": 1, "fit": 2}
+
+
+def gradient_quadtree(P, Y, stage: Stage, params: Params | None = None, theta: float = 0.5, variant: str = "bh",
+                      parts: bool = False, ws=None):
+    """BH-tsNET ("bh", Alg. 1) or FIt-tsNET ("fit", Alg. 2) gradient at Y:
+    the repulsion and/or entropy from the quadtree with opening parameter
+    theta.  Returns (grad [n,2] f32, parts [n,6] f32 or None, (Z, S))."""
+    torch = _torch()
+    params = params or Params()
+    P_row, P_col, P_val = P
+    Y = Y.contiguous()
+    n = Y.shape[0]
+    cp = params.to_c()
+    v = VARIANTS[variant]
+    need = lib().ltsnet_gradient_quadtree_workspace_size(n, ctypes.byref(cp), v)
+    if need == 0:
+        raise LtsnetError(-1, "ltsnet_gradient_quadtree_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need)
+    grad = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+    pt = torch.empty((n, 6), dtype=torch.float32, device="cuda") if parts else None
+    terms = (ctypes.c_double * 2)()
+    st = stage.to_c()
+    _check(lib().ltsnet_gradient_quadtree(_ptr(P_row), _ptr(P_col), _ptr(P_val), n, _ptr(Y), ctypes.byref(st),
+                                          ctypes.byref(cp), float(theta), v, _ptr(grad), _ptr(pt), terms, _ptr(ws),
+                                          ws.numel(), _stream()), "ltsnet_gradient_quadtree")
+    return grad, pt, (terms[0], terms[1])
 
 
 def cost(P, Y, stage: Stage, params: Params | None = None, grad_pvals: bool = False, ws=None):
