@@ -296,6 +296,31 @@ def bench_ltsnet(args):
                 "layout": "final layout of the timed run (1000 iterations from the random start)"}
         del qws
 
+    # the paper's three algorithms' gradients at the final layout, same P:
+    # L-tsNET (grid for C1 and C2), FIt-tsNET (grid for C1, quadtree for C2),
+    # BH-tsNET (quadtree for both), theta = 0.5
+    variants = None
+    if not args.no_batched:
+        Pv = lt.affinities(row_ptr, col, PERPLEXITY)["P"]
+        stv = lt.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+        gws = None
+        times = {}
+        for name, fn in (("ltsnet", lambda: lt.gradient(Pv, Y, stv, params)),
+                         ("fit_tsnet", lambda: lt.gradient_quadtree(Pv, Y, stv, params, theta=0.5, variant="fit")),
+                         ("bh_tsnet", lambda: lt.gradient_quadtree(Pv, Y, stv, params, theta=0.5, variant="bh"))):
+            fn()
+            ts = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                fn()
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            times[name] = round(statistics.median(ts) * 1e3, 3)
+        variants = {"gradient_ms": times, "theta": 0.5, "n": n,
+                    "note": "one gradient call each (host-synchronous, workspace allocated per call), final layout"}
+        del Pv
+
     # Pivot MDS start (first step of Alg. 1-3) on the same graph, 100 pivots
     pm = None
     if not args.no_batched:
@@ -401,6 +426,7 @@ def bench_ltsnet(args):
         "ba4m": ba,
         "pivot_mds": pm,
         "quality": qual,
+        "variants": variants,
         "clocks": clocks,
         "gpu_launches": int(launches),
     }
