@@ -372,6 +372,15 @@ ltsnet_status ltsnet_pivot_mds(const int64_t* row_ptr, const int32_t* col, int32
  * ------------------------------------------------------------------------- */
 #define LTSNET_VARIANT_BH 1
 #define LTSNET_VARIANT_FIT 2
+/* The descent loop of Alg. 1 / Alg. 2 with these gradients: the same
+ * arguments, schedule, step rule and learning rate as ltsnet_optimize
+ * (Y, update, gains f32[n][2] device, in/out), the gradient of each
+ * iteration from ltsnet_gradient_quadtree.  Synchronous. */
+size_t ltsnet_optimize_quadtree_workspace_size(int32_t n, const ltsnet_params* p, int32_t variant);
+ltsnet_status ltsnet_optimize_quadtree(const int64_t* P_row, const int32_t* P_col, const float* P_val,
+                                       int32_t n, const ltsnet_params* p, float theta, int32_t variant,
+                                       float* Y, float* update, float* gains, int32_t start_iter,
+                                       int32_t n_iter, void* ws, size_t ws_bytes, ltsnet_stream stream);
 size_t ltsnet_gradient_quadtree_workspace_size(int32_t n, const ltsnet_params* p, int32_t variant);
 ltsnet_status ltsnet_gradient_quadtree(const int64_t* P_row, const int32_t* P_col, const float* P_val,
                                        int32_t n, const float* Y, const ltsnet_stage* stage,

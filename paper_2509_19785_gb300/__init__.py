@@ -36,6 +36,7 @@ ABI_SYMBOLS = (
     "ltsnet_profile_begin", "ltsnet_profile_end", "ltsnet_pivot_mds_workspace_size", "ltsnet_pivot_mds",
     "ltsnet_quality_workspace_size", "ltsnet_neighbourhood_preservation", "ltsnet_stress",
     "ltsnet_gradient_quadtree_workspace_size", "ltsnet_gradient_quadtree",
+    "ltsnet_optimize_quadtree_workspace_size", "ltsnet_optimize_quadtree",
 )
 
 
@@ -122,6 +123,10 @@ def lib():
         L.ltsnet_gradient_quadtree.argtypes = [P, P, P, i32, P, ctypes.POINTER(CStage), pp, ctypes.c_float, i32, P, P,
                                                ctypes.POINTER(f64), P, sz, P]
         L.ltsnet_gradient_quadtree.restype = i32
+        L.ltsnet_optimize_quadtree_workspace_size.argtypes = [i32, pp, i32]
+        L.ltsnet_optimize_quadtree_workspace_size.restype = sz
+        L.ltsnet_optimize_quadtree.argtypes = [P, P, P, i32, pp, ctypes.c_float, i32, P, P, P, i32, i32, P, sz, P]
+        L.ltsnet_optimize_quadtree.restype = i32
         L.ltsnet_launch_count.restype = i64
         L.ltsnet_profile_begin.argtypes = [i32, i32]
         L.ltsnet_profile_end.argtypes = [i32, ctypes.POINTER(f64), ctypes.POINTER(i32)]
@@ -449,6 +454,26 @@ def gradient_quadtree(P, Y, stage: Stage, params: Params | None = None, theta: f
                                           ctypes.byref(cp), float(theta), v, _ptr(grad), _ptr(pt), terms, _ptr(ws),
                                           ws.numel(), _stream()), "ltsnet_gradient_quadtree")
     return grad, pt, (terms[0], terms[1])
+
+
+def optimize_quadtree(P, Y, update, gains, start_iter: int, n_iter: int, params: Params | None = None,
+                      theta: float = 0.5, variant: str = "bh", ws=None):
+    """n_iter descent steps of BH-tsNET ("bh") or FIt-tsNET ("fit") from
+    global iteration start_iter; Y, update and gains are updated in place."""
+    params = params or Params()
+    P_row, P_col, P_val = P
+    n = Y.shape[0]
+    cp = params.to_c()
+    v = VARIANTS[variant]
+    need = lib().ltsnet_optimize_quadtree_workspace_size(n, ctypes.byref(cp), v)
+    if need == 0:
+        raise LtsnetError(-1, "ltsnet_optimize_quadtree_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need)
+    _check(lib().ltsnet_optimize_quadtree(_ptr(P_row), _ptr(P_col), _ptr(P_val), n, ctypes.byref(cp), float(theta),
+                                          v, _ptr(Y), _ptr(update), _ptr(gains), int(start_iter), int(n_iter),
+                                          _ptr(ws), ws.numel(), _stream()), "ltsnet_optimize_quadtree")
+    return Y
 
 
 def cost(P, Y, stage: Stage, params: Params | None = None, grad_pvals: bool = False, ws=None):

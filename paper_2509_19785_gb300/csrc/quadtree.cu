@@ -514,6 +514,33 @@ __global__ void k_qt_assemble(const float2* __restrict__ Y, int32_t n, const flo
     }
 }
 
+// The descent step of every variant (the same rule as ltsnet_optimize): a
+// gain grows by 0.2 where the gradient's sign differs from the previous
+// step's, else shrinks by x0.8, floored at 0.01; step = momentum step -
+// lr gain grad; Y += step.
+__device__ __forceinline__ float sign_of(float x) { return (float)((x > 0.0f) - (x < 0.0f)); }
+
+__global__ void k_qt_step(int32_t n, float2* __restrict__ Y, float2* __restrict__ upd, float2* __restrict__ gains,
+                          const float2* __restrict__ grad, float momentum, float lr, StatusBlock* st)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 g = grad[i];
+        float2 u = upd[i], gn = gains[i], y = Y[i];
+        gn.x = sign_of(g.x) != sign_of(u.x) ? gn.x + 0.2f : gn.x * 0.8f;
+        gn.y = sign_of(g.y) != sign_of(u.y) ? gn.y + 0.2f : gn.y * 0.8f;
+        gn.x = fmaxf(gn.x, 0.01f);
+        gn.y = fmaxf(gn.y, 0.01f);
+        u.x = momentum * u.x - lr * gn.x * g.x;
+        u.y = momentum * u.y - lr * gn.y * g.y;
+        y.x += u.x;
+        y.y += u.y;
+        if (!(isfinite(y.x) && isfinite(y.y))) record_error(st, LTSNET_ERR_NONFINITE, (int32_t)i);
+        upd[i] = u;
+        gains[i] = gn;
+        Y[i] = y;
+    }
+}
+
 struct QtWs {
     StatusBlock* st;
     QtScal* sc;
@@ -702,4 +729,56 @@ extern "C" ltsnet_status ltsnet_gradient_quadtree(const int64_t* P_row, const in
     }
     if (hs.code) return (ltsnet_status)hs.code;
     return LTSNET_OK;
+}
+
+extern "C" size_t ltsnet_optimize_quadtree_workspace_size(int32_t n, const ltsnet_params* p, int32_t variant)
+{
+    const size_t g = ltsnet_gradient_quadtree_workspace_size(n, p, variant);
+    if (g == 0) return 0;
+    return lt::align_up(sizeof(lt::StatusBlock) + sizeof(float) * 2 * (size_t)n, 256) + g;
+}
+
+extern "C" ltsnet_status ltsnet_optimize_quadtree(const int64_t* P_row, const int32_t* P_col, const float* P_val,
+                                                  int32_t n, const ltsnet_params* p, float theta, int32_t variant,
+                                                  float* Y, float* update, float* gains, int32_t start_iter,
+                                                  int32_t n_iter, void* ws, size_t ws_bytes, ltsnet_stream stream)
+{
+    using namespace lt;
+    if (!p || p->n_stages < 1 || !p->stages || !Y || !update || !gains || start_iter < 0 || n_iter < 0)
+        return LTSNET_ERR_INVALID_ARG;
+    const size_t need = ltsnet_optimize_quadtree_workspace_size(n, p, variant);
+    if (need == 0) return LTSNET_ERR_INVALID_ARG;
+    if (((uintptr_t)ws & 255) || ws_bytes < need) return LTSNET_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    Carve c(ws, ws_bytes);
+    StatusBlock* st = c.take<StatusBlock>(1);
+    float* grad = c.take<float>((size_t)2 * n);
+    const size_t gofs = align_up(c.off, 256);
+    void* gws = (char*)ws + gofs;
+    const size_t gbytes = ws_bytes - gofs;
+    LT_CUDA(cudaMemsetAsync(st, 0, sizeof(StatusBlock), s));
+    const float lr = p->learning_rate > 0.f ? p->learning_rate : std::max(200.0f, (float)n / 12.0f);
+    for (int64_t t = start_iter; t < (int64_t)start_iter + n_iter; ++t) {
+        // the stage of iteration t; past the schedule's end, the last stage
+        const ltsnet_stage* sg = &p->stages[p->n_stages - 1];
+        int64_t acc = 0;
+        for (int q = 0; q < p->n_stages; ++q) {
+            acc += p->stages[q].iters;
+            if (t < acc) {
+                sg = &p->stages[q];
+                break;
+            }
+        }
+        ltsnet_status e = ltsnet_gradient_quadtree(P_row, P_col, P_val, n, Y, sg, p, theta, variant, grad, nullptr,
+                                                   nullptr, gws, gbytes, stream);
+        if (e < 0) return e;
+        k_qt_step<<<kQtBlocks, kQtThreads, 0, s>>>(n, (float2*)Y, (float2*)update, (float2*)gains,
+                                                   (const float2*)grad, sg->momentum, lr, st);
+        count_launches(1);
+        LT_CHECK_LAUNCH();
+    }
+    StatusBlock hs;
+    LT_CUDA(cudaMemcpyAsync(&hs, st, sizeof(StatusBlock), cudaMemcpyDeviceToHost, s));
+    LT_CUDA(cudaStreamSynchronize(s));
+    return hs.code ? (ltsnet_status)hs.code : LTSNET_OK;
 }

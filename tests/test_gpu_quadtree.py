@@ -134,3 +134,36 @@ def test_bh_rgg1m_sampled_against_exact(ltlib):
         errs.append(np.linalg.norm(pt[i, 4:6] - e.sum(0)) / np.linalg.norm(e.sum(0)))
     assert np.median(errs) < 0.02 and np.max(errs) < 0.2
     assert np.isfinite(Z) and Z > 0
+
+
+@pytest.mark.parametrize("variant", ["bh", "fit"])
+def test_optimize_steps_match_oracle(ltlib, variant):
+    """Eight descent steps of BH-tsNET / FIt-tsNET from the same spread-out
+    start (entropy on): FP32 GPU against the FP64 oracle loop with the same
+    gradient and step rule."""
+    import torch
+
+    g = synth.grid2d(24, 20)
+    ref = oracle.preprocess(g.row_ptr, g.col, 10.0)
+    P = gpu_P(ltlib, ref)
+    pv = ref.P_val64.astype(np.float32).astype(np.float64)
+    Y0 = (np.random.default_rng(8).normal(size=(g.n, 2)) * 3).astype(np.float32)
+    params = ltlib.Params(perplexity=10.0, stages=[ltlib.Stage(8, 1.0, 0.01, 0.6, 1.0, 0.8)])
+    Yg = torch.from_numpy(Y0.copy()).cuda()
+    upd = torch.zeros_like(Yg)
+    gains = torch.ones_like(Yg)
+    ltlib.optimize_quadtree(P, Yg, upd, gains, 0, 8, params, theta=0.5, variant=variant)
+    Y = Y0.astype(np.float64)
+    u = np.zeros_like(Y)
+    gn = np.ones_like(Y)
+    lr = max(200.0, g.n / 12.0)
+    st = oracle.Stage(8, 1.0, 0.01, 0.6, 1.0, 0.8)
+    for _ in range(8):
+        Y32 = Y.astype(np.float32)
+        gp = None
+        if variant == "fit":
+            _, d = oracle.interp_gradient(Y32, ref.P_row, ref.P_col, pv, st, oracle.GridParams())
+            gp = (d["A"], d["R"], d["Z"])
+        grad, _ = quadtree.gradient(Y32, ref.P_row, ref.P_col, pv, st, 0.5, variant, grid_parts=gp)
+        Y, u, gn = oracle.update(Y, u, gn, grad, 0.8, lr)
+    assert rel(Yg.cpu().numpy(), Y) < 1e-4
