@@ -151,3 +151,14 @@ def test_rgg1m_hundred_pivots(ltlib):
     assert np.array_equal(dist.view(np.uint16), Do.astype(np.uint16))
     assert np.allclose(eig, lam, rtol=1e-9)
     check_layout(Y, Yo, lam)
+
+
+def test_two_vertices(ltlib):
+    g = synth.csr_from_edges(2, np.array([0]), np.array([1]))
+    Y, piv, eig = ltlib.pivot_mds(g.row_ptr, g.col, 2, first=1)
+    Y = Y.cpu().numpy().astype(np.float64)
+    assert list(piv.cpu().numpy()) == [1, 0]
+    # a path of two: x = +-c, and the RMS distance from the centroid is
+    # sqrt(2) init_std, so |x| = sqrt(2) 1e-4
+    assert np.all(Y[:, 1] == 0) and abs(Y[0, 0] + Y[1, 0]) < 1e-10
+    assert abs(abs(Y[0, 0]) - np.sqrt(2) * 1e-4) < 1e-10

@@ -167,3 +167,28 @@ def test_optimize_steps_match_oracle(ltlib, variant):
         grad, _ = quadtree.gradient(Y32, ref.P_row, ref.P_col, pv, st, 0.5, variant, grid_parts=gp)
         Y, u, gn = oracle.update(Y, u, gn, grad, 0.8, lr)
     assert rel(Yg.cpu().numpy(), Y) < 1e-4
+
+
+def test_degenerate_drawings(ltlib):
+    """All points at one position (zero extent: the domain side falls back
+    to 1, every point in one depth-16 cell, every pair exact: q = 1 and zero
+    forces), and two points."""
+    import torch
+
+    n = 50
+    Y = np.full((n, 2), 3.25, np.float32)
+    P = (torch.zeros(n + 1, dtype=torch.int64).cuda(), torch.zeros(1, dtype=torch.int32).cuda(),
+         torch.zeros(1, dtype=torch.float32).cuda())
+    _, parts, (Z, _) = ltlib.gradient_quadtree(P, torch.from_numpy(Y).cuda(), ltlib.Stage(*ST_ARGS), theta=0.5,
+                                               variant="bh", parts=True)
+    assert Z == n * (n - 1)
+    assert np.all(parts.cpu().numpy()[:, 2:] == 0)
+    Zp, R, E = quadtree.sums(Y, 0.5)
+    assert Zp.sum() == Z
+    Y2 = np.array([[0, 0], [1, 0]], np.float32)
+    P2 = (torch.zeros(3, dtype=torch.int64).cuda(), torch.zeros(1, dtype=torch.int32).cuda(),
+          torch.zeros(1, dtype=torch.float32).cuda())
+    _, parts, (Z, _) = ltlib.gradient_quadtree(P2, torch.from_numpy(Y2).cuda(), ltlib.Stage(*ST_ARGS), theta=10.0,
+                                               variant="bh", parts=True)
+    assert Z == pytest.approx(1.0, rel=1e-7)
+    assert np.allclose(parts.cpu().numpy()[:, 2:4], [[-0.25, 0], [0.25, 0]], rtol=1e-6)

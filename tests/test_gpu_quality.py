@@ -132,3 +132,23 @@ def test_quality_argument_errors(ltlib):
     with pytest.raises(ltlib.LtsnetError) as e:
         ltlib.neighbourhood_preservation(g.row_ptr, col, Y)
     assert e.value.code == -6
+
+
+def test_quality_degenerate_graphs(ltlib):
+    """Two vertices; isolated vertices (an empty ball is skipped by NP; their
+    pairs are skipped by stress); a single source."""
+    g = synth.csr_from_edges(2, np.array([0]), np.array([1]))
+    Y = np.array([[0, 0], [2, 1]], np.float32)
+    npv, exc, b, c = ltlib.neighbourhood_preservation(g.row_ptr, g.col, Y, return_counts=True)
+    assert npv == 1.0 and exc == 0 and list(b.cpu().numpy()) == [1, 1]
+    st, alpha, cnt, skipped = ltlib.stress(g.row_ptr, g.col, Y)
+    assert abs(st) < 1e-15 and cnt == 2 and skipped == 0
+    u = np.arange(5)
+    g = synth.csr_from_edges(9, u, u + 1)  # path 0..5, vertices 6, 7, 8 isolated
+    Y = np.random.default_rng(1).normal(size=(9, 2)).astype(np.float32)
+    npv, exc, b, c = ltlib.neighbourhood_preservation(g.row_ptr, g.col, Y, return_counts=True)
+    npo, bo, co = quality.neighbourhood_preservation(g.row_ptr, g.col, Y)
+    assert np.array_equal(b.cpu().numpy(), bo) and np.array_equal(c.cpu().numpy(), co)
+    assert list(bo[6:]) == [0, 0, 0] and npv == pytest.approx(npo, rel=1e-12)
+    got = ltlib.stress(g.row_ptr, g.col, Y, sources=np.array([7], np.int32))
+    assert got[2] == 0 and got[3] == 8 and got[0] == 0.0
