@@ -306,18 +306,8 @@ __global__ void __launch_bounds__(kFusedThreads, 2)
     const Coeffs k = coeffs(G, st);
     const int64_t nnz = P_row[n];
     float mn = INFINITY, mx = -INFINITY;
-    // Rows in 32-row chunks.  Block b sweeps one contiguous range of chunks,
-    // so the coordinates it gathers (graph neighbours have nearby indices
-    // after the breadth-first renumbering) stay in L1 from one chunk to the
-    // next; with the full persistent grid, the two blocks that share an SM
-    // (b and b + kSMs) take adjacent ranges.
-    const int64_t nchunk = ((int64_t)n + 31) / 32;
-    const int64_t per = (nchunk + gridDim.x - 1) / gridDim.x;
-    const int64_t rb = gridDim.x == 2 * kSMs ? (int64_t)(blockIdx.x % kSMs) * 2 + blockIdx.x / kSMs
-                                             : (int64_t)blockIdx.x;
-    const int64_t c1 = min(nchunk, (rb + 1) * per);
-    for (int64_t c = rb * per + wib; c < c1; c += kFusedWarps) {
-        const int64_t g0 = c * 32;
+    for (int64_t g0 = ((int64_t)blockIdx.x * kFusedWarps + wib) * 32; g0 < n;
+         g0 += (int64_t)gridDim.x * kFusedWarps * 32) {
         const int64_t row = g0 + lane;
         const bool has = row < n;
         const float2 yi = has ? Y[row] : make_float2(0.f, 0.f);
