@@ -1,6 +1,9 @@
-"""Run L-tsNET on a seeded synthetic graph and report time and final cost.
+"""Run L-tsNET (or BH-tsNET / FIt-tsNET) on a seeded synthetic graph and
+report the time, the layout's extent and, with --quality, its NP and stress.
 
   python -m paper_2509_19785_gb300.demo --graph rgg --n 200000 --iters 1000
+  python -m paper_2509_19785_gb300.demo --graph rgg --n 200000 --init pmds --quality
+  python -m paper_2509_19785_gb300.demo --graph rgg --n 300000 --variant bh --iters 20
 
 Graphs: grid (sqrt(n) x sqrt(n) mesh), rgg (random geometric graph, mean
 degree 8, largest component), sbm (power-law block sizes), ba
@@ -44,6 +47,12 @@ def main():
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--plain", action="store_true")
     ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--variant", choices=["ltsnet", "fit", "bh"], default="ltsnet",
+                    help="ltsnet: ltsnet_run (Alg. 3); fit / bh: C0, then ltsnet_optimize_quadtree (Alg. 2 / 1)")
+    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--init", choices=["random", "pmds"], default="random",
+                    help="random N(0, 1e-4^2) start, or Pivot MDS with 100 pivots (the paper's start)")
+    ap.add_argument("--quality", action="store_true", help="NP (r = 2) and stress over 64 sources of the result")
     args = ap.parse_args()
     import torch
 
@@ -52,21 +61,43 @@ def main():
 
     g = make_graph(args.graph, args.n, args.seed)
     params = lt.Params(perplexity=args.perplexity, stages=lt.default_stages(args.iters), plain=args.plain)
-    Y0 = torch.from_numpy(synth.initial_layout(g.n, 1)).cuda()
     row_ptr = torch.from_numpy(g.row_ptr).cuda()
     col = torch.from_numpy(g.col).cuda()
-    ws = lt.run_workspace(g.n, g.col.shape[0], params)
+    if args.init == "pmds":
+        Y0, _, _ = lt.pivot_mds(row_ptr, col, min(100, g.n))
+    else:
+        Y0 = torch.from_numpy(synth.initial_layout(g.n, 1)).cuda()
     times = []
-    for _ in range(args.repeat):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        Y, rc = lt.run(row_ptr, col, Y0, params, ws=ws)
-        torch.cuda.synchronize()
-        times.append(time.perf_counter() - t0)
+    rc = 0
+    if args.variant == "ltsnet":
+        ws = lt.run_workspace(g.n, g.col.shape[0], params)
+        for _ in range(args.repeat):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Y, rc = lt.run(row_ptr, col, Y0, params, ws=ws)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+    else:
+        P = lt.affinities(row_ptr, col, args.perplexity)["P"]
+        for _ in range(args.repeat):
+            Y = Y0.clone()
+            upd, gains = torch.zeros_like(Y), torch.ones_like(Y)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lt.optimize_quadtree(P, Y, upd, gains, 0, args.iters, params, theta=args.theta, variant=args.variant)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
     Yn = Y.cpu().numpy()
-    print(json.dumps({"graph": args.graph, "n": g.n, "m": g.m, "iters": args.iters, "status": int(rc),
-                      "seconds": [round(t, 4) for t in times], "iters_per_s": round(args.iters / min(times), 2),
-                      "extent": float(Yn.max() - Yn.min())}))
+    out = {"graph": args.graph, "n": g.n, "m": g.m, "variant": args.variant, "init": args.init,
+           "iters": args.iters, "status": int(rc), "seconds": [round(t, 4) for t in times],
+           "iters_per_s": round(args.iters / min(times), 2), "extent": float(Yn.max() - Yn.min())}
+    if args.quality:
+        import numpy as np
+
+        out["np_r2"], out["np_excluded"] = lt.neighbourhood_preservation(row_ptr, col, Y)
+        src = np.random.default_rng(11).choice(g.n, min(64, g.n), replace=False).astype(np.int32)
+        out["stress"] = lt.stress(row_ptr, col, Y, sources=src)[0]
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":
