@@ -76,3 +76,48 @@ def test_workspace_sizes_and_argument_checks(lib):
     assert L.ltsnet_calibrate(null, null, 10, 3, -1.0, 1e-5, 10, null, null, null, null) == -1
     assert L.ltsnet_gradient(null, null, null, 10, null, None, ctypes.byref(cp), null, null, null, null, 0,
                              null) == -1
+
+
+def test_calls_beside_the_path_check_arguments_on_the_host(lib):
+    """Pivot MDS, the quadtree variants and the quality metrics: workspace
+    sizes without a GPU, and argument errors returned before any CUDA call."""
+    L = lib.lib()
+    cp = lib.Params().to_c()
+    null = ctypes.c_void_p(0)
+    one = ctypes.c_void_p(256)  # never dereferenced: every call below fails its checks first
+    # Pivot MDS: 2 <= k <= min(n, 512); grows with n and k
+    assert L.ltsnet_pivot_mds_workspace_size(1000, 100) > L.ltsnet_pivot_mds_workspace_size(1000, 10) > 0
+    assert L.ltsnet_pivot_mds_workspace_size(2000, 10) > L.ltsnet_pivot_mds_workspace_size(1000, 10)
+    for n, k in ((1000, 1), (1000, 513), (10, 11), (1, 1)):
+        assert L.ltsnet_pivot_mds_workspace_size(n, k) == 0
+    eig = (ctypes.c_double * 2)()
+    for n, k, first in ((10, 1, 0), (10, 11, 0), (10, 4, -1), (10, 4, 10)):
+        assert L.ltsnet_pivot_mds(one, one, n, k, first, 1e-4, one, one, null, eig, one, 1 << 30, null) == -1
+    assert L.ltsnet_pivot_mds(one, one, 10, 4, 0, -1.0, one, one, null, eig, one, 1 << 30, null) == -1
+    # a workspace that is too small or misaligned
+    need = L.ltsnet_pivot_mds_workspace_size(10, 4)
+    assert L.ltsnet_pivot_mds(one, one, 10, 4, 0, 1e-4, one, one, null, eig, one, need - 1, null) == -2
+    assert L.ltsnet_pivot_mds(one, one, 10, 4, 0, 1e-4, one, one, null, eig, ctypes.c_void_p(257), need,
+                              null) == -2
+    # quadtree gradient and loop: variant 1 (BH) or 2 (FIt), theta >= 0
+    assert L.ltsnet_gradient_quadtree_workspace_size(1000, ctypes.byref(cp), 1) > 0
+    assert L.ltsnet_gradient_quadtree_workspace_size(1000, ctypes.byref(cp), 2) > \
+        L.ltsnet_gradient_quadtree_workspace_size(1000, ctypes.byref(cp), 1)
+    assert L.ltsnet_gradient_quadtree_workspace_size(1000, ctypes.byref(cp), 3) == 0
+    st = lib.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8).to_c()
+    terms = (ctypes.c_double * 2)()
+    for theta, variant in ((-0.5, 1), (0.5, 0), (float("nan"), 1)):
+        assert L.ltsnet_gradient_quadtree(one, one, one, 100, one, ctypes.byref(st), ctypes.byref(cp), theta,
+                                          variant, one, null, terms, one, 1 << 30, null) == -1
+    assert L.ltsnet_optimize_quadtree_workspace_size(1000, ctypes.byref(cp), 1) > \
+        L.ltsnet_gradient_quadtree_workspace_size(1000, ctypes.byref(cp), 1)
+    assert L.ltsnet_optimize_quadtree(one, one, one, 100, ctypes.byref(cp), 0.5, 1, one, one, one, -1, 5, one,
+                                      1 << 30, null) == -1
+    # quality metrics
+    assert L.ltsnet_quality_workspace_size(1000) > 0 and L.ltsnet_quality_workspace_size(0) == 0
+    npv, exc = ctypes.c_double(), ctypes.c_int32()
+    assert L.ltsnet_neighbourhood_preservation(one, one, 0, one, null, null, ctypes.byref(npv), ctypes.byref(exc),
+                                               one, 1 << 30, null) == -1
+    out = (ctypes.c_double * 4)()
+    assert L.ltsnet_stress(one, one, 10, one, one, 0, out, one, 1 << 30, null) == -1
+    assert L.ltsnet_stress(one, one, 10, one, one, 3, out, one, 16, null) == -2
