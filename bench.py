@@ -472,7 +472,7 @@ def oracle_iteration_time(g, aff, iters: int, lr: float):
         Y32 = Y.astype(np.float32)
         gr, _ = oracle.interp_gradient(Y32, aff.P_row, aff.P_col, aff.P_val64, st, oracle.GridParams())
         Y, upd, gains = oracle.update(Y32.astype(np.float64), upd, gains, gr, st.momentum, lr)
-    return (time.perf_counter() - t0) / iters
+    return (time.perf_counter() - t0) / max(1, iters)
 
 
 def cpu_baseline(g, n_sample: int = 100_000, iters: int = 3):
@@ -507,8 +507,9 @@ def bench_reference(args):
     aff = oracle_affinities(g)
     c0_s = time.perf_counter() - t0
     lr = oracle.auto_learning_rate(g.n)
-    oracle_iteration_time(g, aff, args.warmup, lr)
-    per_iter = oracle_iteration_time(g, aff, args.steps, lr)
+    if args.warmup > 0:
+        oracle_iteration_time(g, aff, args.warmup, lr)
+    per_iter = oracle_iteration_time(g, aff, max(1, args.steps), lr)
     run_s = c0_s + ITERS * per_iter
     value = ITERS / run_s
     cb = {"value": round(value, 5), "unit": "iters/s", "cores": 1, "kind": "oracle",

@@ -57,3 +57,15 @@ def test_single_rank_needs_no_process_group():
 
     assert bench.max_over_ranks(12.5, 1) == 12.5
     assert bench.job_rate(1, 1000, 500.0) == pytest.approx(2000.0)
+
+
+def test_oracle_iteration_time_accepts_zero_iterations():
+    """The reference arm's warm-up may be empty (--warmup 0)."""
+    import bench
+    import oracle
+    import synth
+
+    g = synth.grid2d(8, 8)
+    aff = oracle.preprocess(g.row_ptr, g.col, 5.0)
+    assert bench.oracle_iteration_time(g, aff, 0, 200.0) >= 0.0
+    assert bench.oracle_iteration_time(g, aff, 1, 200.0) > 0.0
