@@ -116,6 +116,28 @@ def test_beta_against_independent_root_finder():
     assert abs(beta[0] - root) <= 1e-5 / slope * 1.01
 
 
+def test_beta_above_one_against_root_finder():
+    """Three vertices one hop away and a hundred two hops away at u = 5: at
+    beta = 1 the mass sits mostly on the far shell (entropy about 3.3 > ln 5),
+    so the search must raise beta before it brackets the root; the result
+    agrees with brentq on the same equation."""
+    hop = np.concatenate([np.full(3, 1, np.int32), np.full(100, 2, np.int32)])[None, :]
+    u = 5.0
+    beta, pcond, conv = oracle.calibrate(hop, np.array([hop.shape[1]], np.int32), u)
+
+    def f(b):
+        d2 = hop[0].astype(np.longdouble) ** 2
+        w = np.exp(-np.longdouble(b) * (d2 - d2.min()))
+        return entropy_bits(w / w.sum()) * math.log(2) - math.log(u)
+
+    assert f(1.0) > 0
+    root = brentq(f, 1e-6, 50.0, xtol=1e-15)
+    assert root > 1.0 and conv[0] == 1
+    h = 1e-7
+    slope = abs(f(root + h) - f(root - h)) / (2 * h)
+    assert abs(beta[0] - root) <= 1e-5 / slope * 1.01
+
+
 @pytest.mark.parametrize("u", [5.0, 30.0, 40.0, 50.0])
 def test_calibrated_rows_sum_to_one_with_target_entropy(u):
     g = synth.sbm([300, 200, 150], 12.0, 100, seed=4)
