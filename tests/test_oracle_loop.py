@@ -143,6 +143,22 @@ def test_grid_rule():
         assert gi.M == gi.I * gp.nodes_per_box
 
 
+def test_grid_rule_by_hand():
+    """Hand-computed cases of the grid rule: extent 60.5 at box width 1 gives
+    ceil(60.5) = 61 boxes, rounded up to the next 5-smooth size 64 (not 63 =
+    7 * 9, not floor 60); h = 60.5 / 64, three nodes per box, the centre at
+    the midpoint 27.25.  A cap of 630 (= 2 * 3^2 * 5 * 7) falls back to the
+    largest 5-smooth size below it, 625."""
+    Y = np.array([[-3.0, 0.0], [57.5, 10.0]], np.float32)
+    gi = oracle.grid_rule(Y, oracle.GridParams(box_width_max=1.0, min_boxes=50, max_boxes=640, nodes_per_box=3))
+    assert (gi.lo, gi.hi, gi.ext, gi.I, gi.M) == (-3.0, 57.5, 60.5, 64, 192)
+    assert gi.h == float(np.float32(60.5) / np.float32(64)) and gi.centre == 27.25
+    assert gi.s == float(np.float32(gi.h) / np.float32(3))
+    Y = np.array([[0.0, 0.0], [900.0, 1.0]], np.float32)
+    gi = oracle.grid_rule(Y, oracle.GridParams(box_width_max=1.0, min_boxes=50, max_boxes=630, nodes_per_box=2))
+    assert gi.I == 625 and gi.M == 1250
+
+
 def test_direct_and_fft_convolution_agree():
     rng = np.random.default_rng(7)
     for M, s in ((9, 0.3), (24, 0.11), (30, 1.7)):
