@@ -254,3 +254,39 @@ def test_interp_entropy_sum_converges_to_exact():
         W, _ = oracle.spread(Y, gi, gp.nodes_per_box)
         errs.append(abs(oracle.log_kernel_sum(W[0], gi.s, gp.eps) - exact) / abs(exact))
     assert errs[2] < errs[0] and errs[2] < 1e-4, errs
+
+
+def test_exact_gradient_with_unnormalised_P():
+    """P scaled by 3 (S = 3): the repulsion carries S / Z, and the gradient
+    still matches central differences of the cost (whose KL term has
+    S ln Z)."""
+    g, aff, Y = small_problem()
+    st = oracle.Stage(1, 1.0, 0.05, 0.3, 1.0, 0.5)
+    pv = aff.P_val64 * 3.0
+    grad, parts = oracle.exact_gradient(Y, aff.P_row, aff.P_col, pv, st)
+    assert abs(parts["S"] - 3.0) < 1e-12
+    fd = np.zeros_like(Y)
+    for i in range(Y.shape[0]):
+        for d in range(2):
+            h = 1e-6 * max(1.0, abs(Y[i, d]))
+            Yp = Y.copy(); Yp[i, d] += h
+            Ym = Y.copy(); Ym[i, d] -= h
+            fd[i, d] = (oracle.exact_cost(Yp, aff.P_row, aff.P_col, pv, st)[0]
+                        - oracle.exact_cost(Ym, aff.P_row, aff.P_col, pv, st)[0]) / (2 * h)
+    assert rel(grad, fd) < 1e-6
+
+
+def test_interp_cost_entropy_converges_to_exact():
+    """The cost's entropy term from the grid (the double sum minus the n self
+    terms ln eps) approaches the exact term on a fine grid; keeping the self
+    terms would be off by lambda_r ln(eps) / (4n)."""
+    rng = np.random.default_rng(6)
+    n = 40
+    Y = (rng.standard_normal((n, 2)) * 1.5).astype(np.float32)
+    P = (np.zeros(n + 1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.float64))
+    st = oracle.Stage(1, 0.0, 0.0, 1.0, 1.0, 0.5)
+    _, parts = oracle.exact_cost(Y.astype(np.float64), *P, st)
+    gp = oracle.GridParams(box_width_max=0.0625, min_boxes=4, max_boxes=1350)
+    got = oracle.interp_cost(Y, *P, st, gp)["ent"]
+    self_terms = abs(np.log(oracle.EPS_DEFAULT) / (4 * n))
+    assert abs(got - parts["ent"]) < 0.05 * self_terms
