@@ -94,26 +94,33 @@ typedef struct {
 /* Largest supported k (partial BFS neighbours per vertex). */
 #define LTSNET_MAX_K 4096
 
-/* Defaults: perplexity 30, eps 1/20, P = 3, box_width_max 1, min_boxes 50,
- * max_boxes 640, automatic learning rate, beta search 100 steps / 1e-5, the
- * two-stage schedule of ltsnet_default_stages (1000 iterations). */
+/* Defaults: perplexity 30, eps 1/20 (Sec. 3.3), P = 3, box_width_max 1,
+ * min_boxes 50, max_boxes 640, automatic learning rate, beta search 100 steps
+ * / 1e-5, the two-stage schedule of ltsnet_default_stages (1000 iterations).
+ * Only eps comes from the paper; the rest are this library's readings
+ * (no counterpart in the paper). */
 ltsnet_params ltsnet_default_params(void);
 
 /* Writes the default schedule for `total_iters` iterations into `out` (host,
  * room for 2) and returns the number of stages: 250 iterations of
  * (lambda_KL, lambda_c, lambda_r) = (1, 1.2, 0) with momentum 0.5, then the
- * rest with (1, 0.01, 0.6) and momentum 0.8. */
+ * rest with (1, 0.01, 0.6) and momentum 0.8.  Sec. 2.1 says the multipliers
+ * change between stages but gives no values: these are a reading (no
+ * counterpart in the paper). */
 int32_t ltsnet_default_stages(int32_t total_iters, ltsnet_stage* out);
 
+/* Host: a static description of a status code (no counterpart in the paper;
+ * the status calls below are error plumbing). */
 const char* ltsnet_status_string(ltsnet_status s);
 
 /* Host: text of the last CUDA runtime failure seen by this library on the
  * calling thread (name, description and source location), "" if none.  The
- * string is owned by the library and valid until the thread's next failure. */
+ * string is owned by the library and valid until the thread's next failure.
+ * No counterpart in the paper. */
 const char* ltsnet_last_cuda_error(void);
 
 /* Synchronous: waits for `stream`, returns the status word recorded in `ws`
- * by earlier asynchronous calls and clears it. */
+ * by earlier asynchronous calls and clears it.  No counterpart in the paper. */
 ltsnet_status ltsnet_poll_status(void* ws, size_t ws_bytes, ltsnet_stream stream);
 
 /* ---------------------------------------------------------------------------
@@ -246,7 +253,8 @@ ltsnet_status ltsnet_cost(const int64_t* P_row, const int32_t* P_col, const floa
                           int32_t n, const float* Y, const ltsnet_stage* stage,
                           const ltsnet_params* p, double* cost, float* dC_dPval,
                           void* ws, size_t ws_bytes, ltsnet_stream stream);
-/* ltsnet_cost with cost = NULL: dC/dp_e only. */
+/* ltsnet_cost with cost = NULL: dC/dp_e only (the derivative of Eq. 1 with
+ * respect to each stored entry of P, as above). */
 ltsnet_status ltsnet_grad_pvals(const int64_t* P_row, const int32_t* P_col, const float* P_val,
                                 int32_t n, const float* Y, const ltsnet_stage* stage,
                                 const ltsnet_params* p, float* dC_dPval,
@@ -286,8 +294,9 @@ ltsnet_status ltsnet_run_host(const int64_t* row_ptr_host, const int32_t* col_ho
                               ltsnet_stream stream);
 
 /* ---------------------------------------------------------------------------
- * Many independent graphs (the batched form of the method): ltsnet_run on
- * each of n_graphs graphs, with the same parameters, concurrently.
+ * Many independent graphs (the batched form of the method): ltsnet_run
+ * (Alg. 3) on each of n_graphs graphs, with the same parameters,
+ * concurrently.  The batching has no counterpart in the paper.
  *   vtx_off  int64[n_graphs+1] (HOST): graph g owns vertices
  *            [vtx_off[g], vtx_off[g+1]) of Y (f32 [sum n][2], device, in: Y0,
  *            out: final layouts); vtx_off[0] = 0, every graph non-empty

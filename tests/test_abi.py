@@ -121,3 +121,20 @@ def test_calls_beside_the_path_check_arguments_on_the_host(lib):
     out = (ctypes.c_double * 4)()
     assert L.ltsnet_stress(one, one, 10, one, one, 0, out, one, 1 << 30, null) == -1
     assert L.ltsnet_stress(one, one, 10, one, one, 3, out, one, 16, null) == -2
+
+
+def test_every_entry_point_cites_the_paper_or_says_it_has_no_counterpart():
+    """Each declaration in include/ltsnet.h is governed by a block comment
+    (the closest one above it that is not a trailing comment of a #define)
+    that cites the passage defining the operation (Sec., Eq., Alg.) or says
+    that the call has no counterpart in the paper."""
+    text = open(os.path.join(ROOT, "include", "ltsnet.h")).read()
+    blocks = [(m.start(), m.end(), m.group(0)) for m in re.finditer(r"/\*.*?\*/", text, flags=re.S)
+              if not text[text.rfind("\n", 0, m.start()) + 1:m.start()].lstrip().startswith("#define")]
+    cite = re.compile(r"Sec\.|Eq\.|Alg\.|no counterpart|not part of the method", re.I)
+    for name in declared_functions():
+        pos = re.search(r"\b" + name + r"\s*\(", re.sub(r"/\*.*?\*/", lambda m: " " * len(m.group(0)), text,
+                                                        flags=re.S)).start()
+        above = [b for b in blocks if b[1] <= pos]
+        assert above, name
+        assert cite.search(above[-1][2]), name
