@@ -12,6 +12,11 @@ preprocessing amortised in), on a random geometric graph with n ~ 1e6.
 instead (bounded sample; see the cpu_baseline key).  Under torchrun each rank
 runs an independent replica (the single-graph path does not shard without an
 exchange step); value = iterations of all ranks / max time over ranks.
+
+Beside the headline (unless --no-batched): the 512-graph batched form
+(graphs/s), the 4M-vertex Barabasi-Albert run, the quality of the final
+layout (NP with r = 2, stress), the gradients and descent loops of
+FIt-tsNET and BH-tsNET on the same P, and the Pivot MDS start (100 pivots).
 """
 from __future__ import annotations
 
