@@ -291,8 +291,11 @@ __global__ void __launch_bounds__(kNpWarps * 32) k_np(const int64_t* __restrict_
             // (2) the smallest square of cells around v with b other points
             const float2 yv = Y[v];
             const int cx = cell_of(yv.x, lx, ih, G), cy = cell_of(yv.y, ly, ih, G);
+            // at R = G - 1 the square is the whole grid (n >= b + 1 points), so
+            // the cap never binds; it keeps the loop bounded by construction
             int R = 0;
-            while (sat_box(sat, G, max(cx - R, 0), min(cx + R, G - 1), max(cy - R, 0), min(cy + R, G - 1)) < b + 1)
+            while (R < G - 1 &&
+                   sat_box(sat, G, max(cx - R, 0), min(cx + R, G - 1), max(cy - R, 0), min(cy + R, G - 1)) < b + 1)
                 ++R;
             // every point of that square lies within sqrt(2) (R + 1) cell
             // widths of v, or (R + 2) where rounding put a point or v one cell
