@@ -94,11 +94,16 @@ typedef struct {
 /* Largest supported k (partial BFS neighbours per vertex). */
 #define LTSNET_MAX_K 4096
 
-/* Defaults: perplexity 30, eps 1/20 (Sec. 3.3), P = 3, box_width_max 1,
+/* Defaults: perplexity 30, eps 1/20 (Sec. 3.3), P = 3, box_width_max 0.25,
  * min_boxes 50, max_boxes 640, automatic learning rate, beta search 100 steps
  * / 1e-5, the two-stage schedule of ltsnet_default_stages (1000 iterations).
  * Only eps comes from the paper; the rest are this library's readings
- * (no counterpart in the paper). */
+ * (no counterpart in the paper).  The grid defaults hold the interpolated
+ * repulsion and entropy sums and Z within 5e-3 relative L2 of the exact
+ * O(n^2) sums on the layouts of whole runs (the entropy kernel
+ * 1/(eps + d^2) is only sqrt(eps) = 0.22 wide: boxes of width 0.5 leave its
+ * sums 1.7e-2 off on clustered layouts), as long as max_boxes does not bind
+ * (layout extent <= 160). */
 ltsnet_params ltsnet_default_params(void);
 
 /* Writes the default schedule for `total_iters` iterations into `out` (host,
@@ -178,8 +183,9 @@ ltsnet_status ltsnet_symmetrize(const int32_t* nbr, const int32_t* cnt, const do
 /* ---------------------------------------------------------------------------
  * ltsnet_symmetrize without a workspace argument (no counterpart in the
  * paper; an interface for callers that cannot allocate device memory where
- * they need this step, e.g. while capturing a stream into a CUDA graph, or in
- * a host that forbids device allocation).  The scratch is a device array
+ * they need this step: plug-ins and embedded hosts handed a fixed
+ * device-memory budget that forbid allocation, and loops that must not pay
+ * for cudaMalloc's implicit synchronisation).  The scratch is a device array
  * built into the library (about 10.6 MB on every GPU that loads it, held until
  * the process exits); nothing is allocated by the call.  Limit:
  * 2 * n * k <= ltsnet_symmetrize_static_max_entries() (2^18); larger inputs
@@ -221,8 +227,13 @@ ltsnet_status ltsnet_bfs_order(const int64_t* row_ptr, const int32_t* col, int32
  *   S   = sum of P_val (1 for a normalised P), alpha = stage exaggeration.
  * The interpolation: lo/hi = min/max over all coordinates, I boxes per
  * dimension by the grid rule of ltsnet_params, nodes_per_box Lagrange nodes
- * per box, charges (1, x, y, x^2+y^2) in coordinates centred on the domain,
- * kernels (1+d^2)^-2 and 1/(eps+d^2) convolved on the node grid by FFT.
+ * per box.  The paper's sums carry the charges (1, x, y, x^2+y^2); this
+ * library computes the same sums rearranged exactly: every point spreads its
+ * node-local moments S0 = L, S1 = L e, S2 = L |e|^2 (L its Lagrange weight at
+ * a node, e its offset from that node in node spacings), which are convolved
+ * on the node grid with the kernels (1+d^2)^-2 and 1/(eps+d^2) and with
+ * those kernels times the node offset (zero-padded FFT), and gathered back;
+ * no FP32 value carries the layout's absolute coordinates.
  *   grad  f32[n][2]       (device)
  *   parts f32[n][6] or NULL: (A_i, R_i, E_i) unscaled, for per-term checks
  *   terms f64[8] or NULL: Z, S, I, h, lo, centre, M, 0

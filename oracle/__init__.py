@@ -44,8 +44,14 @@ def build(force: bool = False) -> str:
     """Compile the C oracle (gcc, FP64, no FMA contraction)."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        # OpenMP splits only loops over independent rows (each row summed by
+        # one thread in a fixed order): results do not depend on the threads.
+        # Without an OpenMP runtime the same source builds serial.
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp]
+        try:
+            subprocess.check_call(base + ["-fopenmp", _SRC, "-lm"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base + [_SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -68,6 +74,9 @@ def lib():
         L.or_conv_direct.argtypes = [i32, f64, f64, P, P]
         L.or_gather.argtypes = [i32, P, P, P, i32, P, P]
         L.or_attractive.argtypes = [i32, P, P, P, P, P]
+        L.or_exact_rows.argtypes = [i32, P, P, P, P, f64, i32, P, P, P, P]
+        L.or_exact_z.argtypes = [i32, P, P]
+        L.or_exact_cost_step.argtypes = [i32, P, P, P, P, f64, i32, i32, f64, P]
         _lib = L
     return _lib
 
@@ -195,7 +204,7 @@ class GridParams:
     """Interpolation grid rule (Sec. 2.3: I intervals, P nodes per interval;
     constants not in the paper)."""
     nodes_per_box: int = 3
-    box_width_max: float = 1.0
+    box_width_max: float = 0.25
     min_boxes: int = 50
     max_boxes: int = 1350
     eps: float = EPS_DEFAULT
@@ -213,6 +222,47 @@ def exact_sums(Y, P_row, P_col, P_val, eps: float = EPS_DEFAULT):
     A = np.empty((n, 2)); R = np.empty((n, 2)); E = np.empty((n, 2)); Z = np.zeros(1)
     lib().or_exact_sums(n, _p(Y), _p(P_row), _p(P_col), _p(P_val), float(eps), _p(A), _p(R), _p(E), _p(Z))
     return A, R, E, float(Z[0])
+
+
+def exact_rows(Y, P_row, P_col, P_val, rows, eps: float = EPS_DEFAULT):
+    """The O(n^2) sums A, R, E of exact_sums for the target rows ``rows``
+    only (each over every source); Z is not included (exact_z)."""
+    Y = _c(Y, np.float64)
+    P_row, P_col, P_val = as_csr64(P_row, P_col, P_val)
+    rows = _c(rows, np.int32)
+    m = rows.shape[0]
+    A = np.empty((m, 2)); R = np.empty((m, 2)); E = np.empty((m, 2))
+    if lib().or_exact_rows(Y.shape[0], _p(Y), _p(P_row), _p(P_col), _p(P_val), float(eps), m, _p(rows),
+                           _p(A), _p(R), _p(E)) != 0:
+        raise ValueError("or_exact_rows: row out of range")
+    return A, R, E
+
+
+def exact_z(Y) -> float:
+    """Z = sum_{i != j} 1/(1 + d_ij^2) over all ordered pairs."""
+    Y = _c(Y, np.float64)
+    z = np.zeros(1)
+    if lib().or_exact_z(Y.shape[0], _p(Y), _p(z)) != 0:
+        raise MemoryError("or_exact_z")
+    return float(z[0])
+
+
+def exact_cost_central_difference(Y, P_row, P_col, P_val, st: Stage, i: int, d: int, h: float, Z: float,
+                                  eps: float = EPS_DEFAULT) -> float:
+    """(C(Y + h e_id) - C(Y - h e_id)) / 2h for the exact cost of exact_cost
+    (Eq. 1, entropy reading), from only the terms that involve vertex i;
+    Z = exact_z(Y) and S = sum of P_val are the unperturbed values."""
+    Y = _c(Y, np.float64)
+    P_row, P_col, P_val = as_csr64(P_row, P_col, P_val)
+    n = Y.shape[0]
+    o = np.zeros(5)
+    if lib().or_exact_cost_step(n, _p(Y), _p(P_row), _p(P_col), _p(P_val), float(eps), int(i), int(d), float(h),
+                                _p(o)) != 0:
+        raise ValueError("or_exact_cost_step: bad coordinate")
+    S = float(np.sum(P_val))
+    dc = (st.lambda_kl * (o[0] + S * (math.log(Z + o[1]) - math.log(Z + o[2])))
+          + st.lambda_c / (2.0 * n) * o[4] - st.lambda_r / (4.0 * n * n) * o[3])
+    return dc / (2.0 * h)
 
 
 def assemble(Y, A, R, E, Z: float, S: float, st: Stage, n: int):
@@ -460,6 +510,21 @@ def interp_gradient(Y32, P_row, P_col, P_val, st: Stage, gp: GridParams, conv: s
     S = float(np.sum(np.asarray(P_val, np.float64)))
     g = assemble(Y32, A, R, E, Z, S, st, n)
     return g, dict(A=A, R=R, E=E, Z=Z, S=S, grid=gi, Phi=Phi, W=W, fields=fld)
+
+
+def interp_grad_pvals(Y32, P_row, P_col, P_val, st: Stage, gp: GridParams):
+    """dC/dp_e of interp_cost, each stored entry an independent leaf:
+    l_KL (ln p_e + 1 + ln(1 + d_e^2) + ln Z) with Z from the grid (Z does not
+    depend on P, so this is grad_pvals with the interpolated Z)."""
+    Y32 = _c(Y32, np.float32)
+    P_row, P_col, P_val = as_csr64(P_row, P_col, P_val)
+    n = Y32.shape[0]
+    Phi, _, _, gi = interp_fields(Y32, gp)
+    Z = z_from_points(Y32, Phi, gi.centre)
+    Y = Y32.astype(np.float64)
+    rows = np.repeat(np.arange(n), np.diff(P_row))
+    d2 = np.sum((Y[rows] - Y[P_col]) ** 2, axis=1)
+    return st.lambda_kl * (np.log(P_val) + 1.0 + np.log1p(d2) + math.log(Z))
 
 
 def update(Y, upd, gains, grad, momentum: float, lr: float):

@@ -457,3 +457,116 @@ int or_attractive(int32_t n, const float* Y, const int64_t* P_row, const int32_t
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* EXACT sums of or_exact_sums for selected target rows only (A_i, R_i, E_i   */
+/* over every source j != i, Eq. 6 and the Sec. 3.3 kernel), for sampled     */
+/* checks of layouts too large for the O(n^2) pass over all rows.  Output    */
+/* row r belongs to vertex rows[r].  Each row is summed by one thread in     */
+/* source order (OpenMP over the listed rows when built with -fopenmp), so    */
+/* the result does not depend on the thread count.                            */
+/* ------------------------------------------------------------------------ */
+int or_exact_rows(int32_t n, const double* Y, const int64_t* P_row, const int32_t* P_col,
+                  const double* P_val, double eps, int32_t nrows, const int32_t* rows,
+                  double* A, double* R, double* E)
+{
+    for (int32_t r = 0; r < nrows; ++r)
+        if (rows[r] < 0 || rows[r] >= n) return -1;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int32_t r = 0; r < nrows; ++r) {
+        int32_t i = rows[r];
+        double xi = Y[2 * i], yi = Y[2 * i + 1];
+        double rx = 0, ry = 0, ex = 0, ey = 0, ax = 0, ay = 0;
+        for (int32_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx = xi - Y[2 * j], dy = yi - Y[2 * j + 1];
+            double d2 = dx * dx + dy * dy;
+            double k1 = 1.0 / (1.0 + d2);
+            double ke = 1.0 / (eps + d2);
+            rx += k1 * k1 * dx; ry += k1 * k1 * dy;
+            ex += ke * dx; ey += ke * dy;
+        }
+        for (int64_t e = P_row[i]; e < P_row[i + 1]; ++e) {
+            int32_t j = P_col[e];
+            double dx = xi - Y[2 * j], dy = yi - Y[2 * j + 1];
+            double k1 = 1.0 / (1.0 + dx * dx + dy * dy);
+            ax += P_val[e] * k1 * dx; ay += P_val[e] * k1 * dy;
+        }
+        A[2 * r] = ax; A[2 * r + 1] = ay;
+        R[2 * r] = rx; R[2 * r + 1] = ry;
+        E[2 * r] = ex; E[2 * r + 1] = ey;
+    }
+    return 0;
+}
+
+/* Z = sum_{i != j} 1/(1 + |X_i - X_j|^2) (the normalisation of q_ij, Sec.   */
+/* 2.1 and Eq. 6): row sums in source order (OpenMP over rows), then the row  */
+/* sums added in row order.                                                   */
+int or_exact_z(int32_t n, const double* Y, double* Z_out)
+{
+    double* rs = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!rs) return -2;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int32_t i = 0; i < n; ++i) {
+        double xi = Y[2 * i], yi = Y[2 * i + 1], z = 0.0;
+        for (int32_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx = xi - Y[2 * j], dy = yi - Y[2 * j + 1];
+            z += 1.0 / (1.0 + dx * dx + dy * dy);
+        }
+        rs[i] = z;
+    }
+    double Z = 0.0;
+    for (int32_t i = 0; i < n; ++i) Z += rs[i];
+    free(rs);
+    *Z_out = Z;
+    return 0;
+}
+
+/* Change of the EXACT cost's pieces (or_exact_cost_parts) when coordinate d  */
+/* (0 = x, 1 = y) of vertex i moves by +h and by -h, from only the terms that */
+/* involve i, so that central differences of the cost need O(n + nnz) work:   */
+/*   out[0] = sum over entries e touching i (row i and column i) of           */
+/*            p_e [ln(1 + d_e+^2) - ln(1 + d_e-^2)]                           */
+/*   out[1] = Z(+h) - Z,  out[2] = Z(-h) - Z  (ordered pairs, i on either side) */
+/*   out[3] = sum_{i != j} ln(eps + d^2) at +h minus at -h (both orders)       */
+/*   out[4] = |X|^2 at +h minus at -h                                          */
+/* The cost at +h minus the cost at -h is then                                 */
+/*   l_KL [out0 + S (ln(Z + out1) - ln(Z + out2))] + l_c/(2n) out4             */
+/*   - l_r/(4n^2) out3.                                                        */
+int or_exact_cost_step(int32_t n, const double* Y, const int64_t* P_row, const int32_t* P_col,
+                       const double* P_val, double eps, int32_t i, int32_t d, double h, double* out)
+{
+    if (i < 0 || i >= n || d < 0 || d > 1) return -1;
+    double xp[2] = {Y[2 * i], Y[2 * i + 1]}, xm[2] = {Y[2 * i], Y[2 * i + 1]}, x0[2] = {Y[2 * i], Y[2 * i + 1]};
+    xp[d] += h;
+    xm[d] -= h;
+    double kl = 0.0, zp = 0.0, zm = 0.0, le = 0.0;
+    for (int32_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        double yj0 = Y[2 * j], yj1 = Y[2 * j + 1];
+        double ap = xp[0] - yj0, bp = xp[1] - yj1, am = xm[0] - yj0, bm = xm[1] - yj1;
+        double a0 = x0[0] - yj0, b0 = x0[1] - yj1;
+        double d2p = ap * ap + bp * bp, d2m = am * am + bm * bm, d20 = a0 * a0 + b0 * b0;
+        double k0 = 1.0 / (1.0 + d20);
+        zp += 2.0 * (1.0 / (1.0 + d2p) - k0);
+        zm += 2.0 * (1.0 / (1.0 + d2m) - k0);
+        le += 2.0 * (log(eps + d2p) - log(eps + d2m));
+    }
+    for (int32_t r = 0; r < n; ++r)
+        for (int64_t e = P_row[r]; e < P_row[r + 1]; ++e) {
+            int32_t c = P_col[e];
+            if (r != i && c != i) continue;
+            if (r == i && c == i) continue; /* a self entry has d = 0 either way */
+            int32_t j = r == i ? c : r;
+            double ap = xp[0] - Y[2 * j], bp = xp[1] - Y[2 * j + 1];
+            double am = xm[0] - Y[2 * j], bm = xm[1] - Y[2 * j + 1];
+            kl += P_val[e] * (log(1.0 + ap * ap + bp * bp) - log(1.0 + am * am + bm * bm));
+        }
+    out[0] = kl;
+    out[1] = zp;
+    out[2] = zm;
+    out[3] = le;
+    out[4] = xp[d] * xp[d] - xm[d] * xm[d];
+    return 0;
+}

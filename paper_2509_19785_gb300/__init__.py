@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libltsnet.so")
 OK = 0
 WARN_NOT_CONVERGED = 1
 ERR_BAD_GRAPH = -6
+ERR_NONFINITE = -5
 FLAG_PLAIN = 1
 FLAG_NO_REORDER = 2
 MAX_K = 4096
@@ -178,7 +179,7 @@ class Params:
     perplexity: float = 30.0
     eps: float = 1.0 / 20.0
     nodes_per_box: int = 3
-    box_width_max: float = 1.0
+    box_width_max: float = 0.25
     min_boxes: int = 50
     max_boxes: int = 640
     learning_rate: float = 0.0
@@ -499,6 +500,27 @@ def cost(P, Y, stage: Stage, params: Params | None = None, grad_pvals: bool = Fa
     return out, dP
 
 
+def grad_pvals(P, Y, stage: Stage, params: Params | None = None, ws=None):
+    """dC/dP_val (f32 [nnz] tensor) at Y by ltsnet_grad_pvals."""
+    torch = _torch()
+    params = params or Params()
+    P_row, P_col, P_val = P
+    Y = Y.contiguous()
+    n = Y.shape[0]
+    cp = params.to_c()
+    dP = torch.empty_like(P_val)
+    need = lib().ltsnet_gradient_workspace_size(n, ctypes.byref(cp))
+    if need == 0:
+        raise LtsnetError(-1, "ltsnet_gradient_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need)
+    st = stage.to_c()
+    _check(lib().ltsnet_grad_pvals(_ptr(P_row), _ptr(P_col), _ptr(P_val), n, _ptr(Y), ctypes.byref(st),
+                                   ctypes.byref(cp), _ptr(dP), _ptr(ws), ws.numel(), _stream()), "ltsnet_grad_pvals")
+    _check(lib().ltsnet_poll_status(_ptr(ws), ws.numel(), _stream()), "ltsnet_grad_pvals (device)")
+    return dP
+
+
 def _cost_function():
     torch = _torch()
 
@@ -506,22 +528,48 @@ def _cost_function():
         """C(Y, P_val) of Eq. 1 as a differentiable scalar (f64, 0-dim):
         forward by ltsnet_cost, backward by ltsnet_gradient (dC/dY, the
         interpolated gradient of Eq. 6 and Eq. 8) and ltsnet_grad_pvals
-        (dC/dP_val).  P_row and P_col are structure, not differentiated."""
+        (dC/dP_val).  P_row and P_col are structure, not differentiated.
+
+        The cost of Eq. 1 has no exaggeration factor (early exaggeration
+        scales P in the optimiser's gradient only), so a stage with
+        exaggeration != 1 is rejected rather than given a backward that is not
+        the derivative of the forward.
+
+        recompute=False keeps dC/dY (8n bytes) and dC/dP_val (4 nnz bytes)
+        from the forward pass until backward; recompute=True keeps only
+        references to the inputs and recomputes the grid fields, the gradient
+        and dC/dP_val (only if P_val needs a gradient) in backward, so that
+        nothing of size nnz is held between the two passes."""
 
         @staticmethod
-        def forward(ctx, Y, P_val, P_row, P_col, stage, params):
+        def forward(ctx, Y, P_val, P_row, P_col, stage, params, recompute=False):
+            if stage.exaggeration != 1.0:
+                raise ValueError("LTsNetCost: the cost of Eq. 1 has no exaggeration; use a stage with "
+                                 "exaggeration = 1")
             P = (P_row, P_col, P_val.detach().contiguous())
             Yd = Y.detach().contiguous()
-            c, dP = cost(P, Yd, stage, params, grad_pvals=True)
-            g, _, _ = gradient(P, Yd, stage, params)
-            ctx.save_for_backward(g, dP)
+            ctx.stage, ctx.params, ctx.recompute = stage, params, bool(recompute)
+            if recompute:
+                c, _ = cost(P, Yd, stage, params, grad_pvals=False)
+                ctx.save_for_backward(Yd, P[2], P_row, P_col)
+            else:
+                c, dP = cost(P, Yd, stage, params, grad_pvals=True)
+                g, _, _ = gradient(P, Yd, stage, params)
+                ctx.save_for_backward(g, dP)
             return c[3].clone()
 
         @staticmethod
         def backward(ctx, go):
-            g, dP = ctx.saved_tensors
+            if ctx.recompute:
+                Yd, Pv, P_row, P_col = ctx.saved_tensors
+                P = (P_row, P_col, Pv)
+                g = gradient(P, Yd, ctx.stage, ctx.params)[0] if ctx.needs_input_grad[0] else None
+                dP = grad_pvals(P, Yd, ctx.stage, ctx.params) if ctx.needs_input_grad[1] else None
+            else:
+                g, dP = ctx.saved_tensors
             s = go.to(torch.float32)
-            return g * s, dP * s, None, None, None, None
+            return (g * s if g is not None else None, dP * s if dP is not None else None,
+                    None, None, None, None, None)
 
     return LTsNetCost
 
@@ -531,7 +579,7 @@ _LTsNetCost = None
 
 def ltsnet_cost_fn():
     """The torch.autograd.Function LTsNetCost: apply(Y, P_val, P_row, P_col,
-    stage, params) -> cost."""
+    stage, params, recompute=False) -> cost."""
     global _LTsNetCost
     if _LTsNetCost is None:
         _LTsNetCost = _cost_function()

@@ -32,6 +32,39 @@ const ltsnet_stage kDefaultStages[2] = {
 void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 namespace {
+constexpr int kMaxDev = 64;
+std::mutex g_dev_mu;
+int g_sms[kMaxDev] = {};
+bool g_once[kOnceSlots][kMaxDev] = {};
+}  // namespace
+
+int num_sms()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return kSplitBlocks;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (g_sms[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return kSplitBlocks;
+        g_sms[dev] = v;
+    }
+    return g_sms[dev];
+}
+
+cudaError_t once_per_device(int slot, cudaError_t (*f)())
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDev || slot < 0 || slot >= kOnceSlots) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (g_once[slot][dev]) return cudaSuccess;
+    e = f();
+    if (e == cudaSuccess) g_once[slot][dev] = true;
+    return e;
+}
+
+namespace {
 thread_local char g_err[256] = "";
 }
 
@@ -115,7 +148,7 @@ extern "C" ltsnet_params ltsnet_default_params(void)
     p.perplexity = 30.0f;
     p.eps = 1.0f / 20.0f;
     p.nodes_per_box = 3;
-    p.box_width_max = 1.0f;
+    p.box_width_max = 0.25f;
     p.min_boxes = 50;
     p.max_boxes = 640;
     p.learning_rate = 0.0f;

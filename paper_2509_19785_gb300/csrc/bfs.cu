@@ -195,7 +195,7 @@ extern "C" ltsnet_status ltsnet_knn_bfs(const int64_t* row_ptr, const int32_t* c
     LT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_partial_bfs, wpb * 32, smem));
     if (per_sm < 1) per_sm = 1;
     int64_t want = ((int64_t)n + wpb - 1) / wpb;
-    int64_t grid = (int64_t)kSMs * per_sm;
+    int64_t grid = (int64_t)num_sms() * per_sm;
     if (grid > want) grid = want;
     k_partial_bfs<<<(unsigned)grid, wpb * 32, smem, s>>>(row_ptr, col, n, k, hlog2, (int32_t)wb, nbr, hop, cnt,
                                                           (StatusBlock*)ws);

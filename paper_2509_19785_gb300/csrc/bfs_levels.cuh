@@ -132,7 +132,7 @@ struct LevelRunner {
     StatusBlock* st;
     cudaGraphExec_t exec = nullptr;
     int32_t reps = 1;  // graph replays before the first check of the next BFS
-    static constexpr unsigned kGrid = kSMs * 2;
+    unsigned grid = 2u * (unsigned)num_sms();  // two waves of blocks per SM
 
     ~LevelRunner()
     {
@@ -149,7 +149,7 @@ struct LevelRunner {
         cudaGraph_t graph = nullptr;
         LT_CUDA(cudaStreamBeginCapture(aux->capture, cudaStreamCaptureModeThreadLocal));
         for (int b = 0; b < kLevelBatch; ++b)
-            k_bfs_level<<<kGrid, kBfsThreads, 0, aux->capture>>>(row_ptr, col, n, D, q0, q1, ctl, st);
+            k_bfs_level<<<grid, kBfsThreads, 0, aux->capture>>>(row_ptr, col, n, D, q0, q1, ctl, st);
         cudaError_t e1 = cudaGetLastError();
         cudaError_t e2 = cudaStreamEndCapture(aux->capture, &graph);
         if (e1 != cudaSuccess || e2 != cudaSuccess) {
@@ -178,7 +178,7 @@ struct LevelRunner {
                     LT_CUDA(cudaGraphLaunch(exec, s));
                 } else {
                     for (int b = 0; b < kLevelBatch; ++b)
-                        k_bfs_level<<<kGrid, kBfsThreads, 0, s>>>(row_ptr, col, n, D, q0, q1, ctl, st);
+                        k_bfs_level<<<grid, kBfsThreads, 0, s>>>(row_ptr, col, n, D, q0, q1, ctl, st);
                     LT_CHECK_LAUNCH();
                 }
                 count_launches(kLevelBatch);

@@ -327,20 +327,18 @@ extern "C" ltsnet_status ltsnet_calibrate(const uint16_t* hop, const int32_t* cn
     if (!hop || !cnt || !beta || !pcond || !converged) return LTSNET_ERR_INVALID_ARG;
     if (k <= kTileK) {
         const size_t smem = (size_t)kCalThreads * k * sizeof(uint16_t);
-        static bool attr = false;
-        if (!attr) {
-            LT_CUDA(cudaFuncSetAttribute(k_calibrate_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((size_t)kCalThreads * kTileK * sizeof(uint16_t))));
-            attr = true;
-        }
+        LT_CUDA(once_per_device(kOnceCalib, [] {
+            return cudaFuncSetAttribute(k_calibrate_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)((size_t)kCalThreads * kTileK * sizeof(uint16_t)));
+        }));
         int64_t blocks = ((int64_t)n + kCalThreads - 1) / kCalThreads;
-        const int64_t cap = (int64_t)kSMs * 16;
+        const int64_t cap = (int64_t)num_sms() * 16;
         if (blocks > cap) blocks = cap;
         k_calibrate_rows<<<(unsigned)blocks, kCalThreads, smem, (cudaStream_t)stream>>>(
             hop, cnt, n, k, log(perplexity), tol, max_steps, beta, pcond, converged);
     } else {
         int64_t blocks = ((int64_t)n + kRowsPerBlock - 1) / kRowsPerBlock;
-        const int64_t cap = (int64_t)kSMs * 16;
+        const int64_t cap = (int64_t)num_sms() * 16;
         if (blocks > cap) blocks = cap;
         k_calibrate<<<(unsigned)blocks, kGroup * kRowsPerBlock, 0, (cudaStream_t)stream>>>(
             hop, cnt, n, k, log(perplexity), tol, max_steps, beta, pcond, converged);

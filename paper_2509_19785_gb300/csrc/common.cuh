@@ -9,7 +9,10 @@
 namespace lt {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kSMs = 152;  // GB300: 2 dies x 76 SMs
+// Fixed block count of the kernels whose per-block partial sums live in the
+// workspace or on the host stack: a constant, so that workspace sizes and the
+// order of those sums do not depend on the device (152 = GB300's SM count).
+constexpr int kSplitBlocks = 152;
 
 // Status block at the start of every workspace (256 bytes).
 struct StatusBlock {
@@ -49,6 +52,15 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
+// Host: SM count of the current device (queried once per device); launch
+// sizes that should fill the GPU in waves take multiples of it.
+int num_sms();
+// Host: runs `f` once per (slot, device) and remembers success, so that a
+// kernel's function attribute (which the runtime keeps per device) is raised
+// on every device that launches it; thread-safe.  A failure is returned and
+// retried on the next call.
+enum OnceSlot { kOnceGridAttrs = 0, kOnceFusedAttrs, kOnceRadix, kOnceCalib, kOnceDft, kOnceSlots };
+cudaError_t once_per_device(int slot, cudaError_t (*f)());
 // Host: kernels launched by this library (instrumentation).
 void count_launches(int64_t k);
 // Host: remember the last failing CUDA call of this thread (ltsnet_last_cuda_error).

@@ -1402,7 +1402,7 @@ cudaError_t launch_bounds_init(const IterWs& w, const float2* Y, int32_t n, int 
     int32_t* b = w.bounds + 2 * parity;
     k_bounds_init<<<1, 1, 0, s>>>(b);
     int64_t blocks = ((int64_t)n + 255) / 256;
-    if (blocks > kSMs * 4) blocks = kSMs * 4;
+    if (blocks > num_sms() * 4) blocks = num_sms() * 4;
     if (blocks < 1) blocks = 1;
     k_bounds<<<(unsigned)blocks, 256, 0, s>>>(Y, n, b);
     count_launches(2);
@@ -1424,7 +1424,7 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
     const int32_t n = sh.n;
     const int P = sh.P;
     int64_t sblocks = ((int64_t)n + kBoxTile - 1) / kBoxTile;
-    if (sblocks > kSMs * 4) sblocks = kSMs * 4;
+    if (sblocks > num_sms() * 4) sblocks = num_sms() * 4;
     if (sblocks < 16) sblocks = 16;
     k_setup<<<(unsigned)sblocks, kBoxThreads, 0, s>>>(w.bounds + 2 * parity, w.bounds + 2 * (parity ^ 1), w.g, w.tw,
                                                       Y, w.bcnt, n, p->box_width_max, p->min_boxes, p->max_boxes, P,
@@ -1432,6 +1432,7 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
     count_launches(1);
     const size_t fsm = fft_smem_bytes(sh.Lmax);
     const int f2 = (int)(fsm / sizeof(float2));
+    const int fb = std::min(num_sms(), 512);  // FFT blocks: one per SM; zblk holds 512 partials
     // The kernel spectra need only the grid parameters: unless kernels are
     // being timed one by one, they run on a side stream next to the spread
     // and join before the column pass.
@@ -1441,14 +1442,14 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
         cudaError_t e2;
         if ((e2 = cudaEventRecord(aux->fork, s)) != cudaSuccess) return e2;
         if ((e2 = cudaStreamWaitEvent(aux->branch, aux->fork, 0)) != cudaSuccess) return e2;
-        k_spec_rows<<<kSMs, kFftThreads, fsm, aux->branch>>>(w.g, w.tw, p->eps, w.krow, f2);
-        k_spec_cols<<<kSMs, kFftThreads, fsm, aux->branch>>>(w.g, w.tw, w.krow, w.khat, f2);
+        k_spec_rows<<<fb, kFftThreads, fsm, aux->branch>>>(w.g, w.tw, p->eps, w.krow, f2);
+        k_spec_cols<<<fb, kFftThreads, fsm, aux->branch>>>(w.g, w.tw, w.krow, w.khat, f2);
         if ((e2 = cudaEventRecord(aux->join, aux->branch)) != cudaSuccess) return e2;
     }
     profile_start(LTSNET_KERNEL_SPREAD, s);
     if (plain) {
         int64_t blocks = ((int64_t)n + kBoxTile - 1) / kBoxTile;
-        if (blocks > kSMs * 8) blocks = kSMs * 8;
+        if (blocks > num_sms() * 8) blocks = num_sms() * 8;
         if (blocks < 1) blocks = 1;
         switch (P) {
             case 2: k_spread_atomic<2><<<(unsigned)blocks, 256, 0, s>>>(Y, n, w.g, w.wflt); break;
@@ -1459,15 +1460,15 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
         count_launches(1);
     } else {
         int64_t blocks = ((int64_t)n + kBoxTile - 1) / kBoxTile;
-        if (blocks > kSMs * 8) blocks = kSMs * 8;
+        if (blocks > num_sms() * 8) blocks = num_sms() * 8;
         if (blocks < 1) blocks = 1;
-        const int nsb = std::min<int>(kSMs, (int)(((int64_t)sh.max_boxes * sh.max_boxes + kScanBlock - 1) / kScanBlock));
+        const int nsb = std::min<int>(num_sms(), (int)(((int64_t)sh.max_boxes * sh.max_boxes + kScanBlock - 1) / kScanBlock));
         k_box_scan<<<nsb, kScanThreads, 0, s>>>(w.g, w.bcnt, w.bcur, w.btot, w.bpre, w.heavy, w.items);
         k_box_scatter<<<(unsigned)blocks, kBoxThreads, 0, s>>>(Y, n, w.g, w.bcur, w.bpre, w.su);
         switch (P) {
 #define LT_SPREAD(PP)                                                                                      \
     case PP:                                                                                               \
-        k_box_spread<PP><<<kSMs * 4, 256, 0, s>>>(w.su, w.bcnt, w.bcur, w.bpre, w.heavy, w.items, w.hacc, \
+        k_box_spread<PP><<<num_sms() * 4, 256, 0, s>>>(w.su, w.bcnt, w.bcur, w.bpre, w.heavy, w.items, w.hacc, \
                                                    w.hticket, w.g, w.wflt);                               \
         break;
             LT_SPREAD(2)
@@ -1484,16 +1485,16 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
 
     profile_start(LTSNET_KERNEL_CONV, s);
     if (!fork) {
-        k_spec_rows<<<kSMs, kFftThreads, fsm, s>>>(w.g, w.tw, p->eps, w.krow, f2);
-        k_spec_cols<<<kSMs, kFftThreads, fsm, s>>>(w.g, w.tw, w.krow, w.khat, f2);
+        k_spec_rows<<<fb, kFftThreads, fsm, s>>>(w.g, w.tw, p->eps, w.krow, f2);
+        k_spec_cols<<<fb, kFftThreads, fsm, s>>>(w.g, w.tw, w.krow, w.khat, f2);
     }
-    k_conv_rows_fwd<<<kSMs, kFftThreads, fsm, s>>>(w.g, w.tw, w.wflt, w.srow, f2);
+    k_conv_rows_fwd<<<fb, kFftThreads, fsm, s>>>(w.g, w.tw, w.wflt, w.srow, f2);
     if (fork) {
         cudaError_t e2 = cudaStreamWaitEvent(s, aux->join, 0);
         if (e2 != cudaSuccess) return e2;
     }
-    k_conv_cols<<<kSMs, kColThreads, fsm, s>>>(w.g, w.tw, w.srow, w.khat, w.ucol, w.zblk, n, f2);
-    k_conv_rows_inv<<<kSMs, kFftThreads, fsm, s>>>(w.g, w.tw, w.ucol, w.fields, w.wflt, w.bcnt, plain ? 1 : 0, f2);
+    k_conv_cols<<<fb, kColThreads, fsm, s>>>(w.g, w.tw, w.srow, w.khat, w.ucol, w.zblk, n, f2);
+    k_conv_rows_inv<<<fb, kFftThreads, fsm, s>>>(w.g, w.tw, w.ucol, w.fields, w.wflt, w.bcnt, plain ? 1 : 0, f2);
     count_launches(5);
     profile_stop(LTSNET_KERNEL_CONV, s);
     return cudaGetLastError();

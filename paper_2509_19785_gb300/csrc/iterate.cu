@@ -574,7 +574,7 @@ __global__ void k_check_cols(const int64_t* __restrict__ P_row, const int32_t* _
 
 cudaError_t launch_check_cols(const int64_t* P_row, const int32_t* P_col, int32_t n, StatusBlock* st, cudaStream_t s)
 {
-    k_check_cols<<<kSMs * 8, 256, 0, s>>>(P_row, P_col, n, st);
+    k_check_cols<<<num_sms() * 8, 256, 0, s>>>(P_row, P_col, n, st);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -674,7 +674,7 @@ int fused_blocks(int32_t n)
     const int64_t groups = ((int64_t)n + 31) / 32;
     const int64_t wpb = kFusedThreads / 32;
     int64_t b = (groups + wpb - 1) / wpb;
-    const int64_t cap = (int64_t)kSMs * 2;  // persistent: the blocks that fit at once
+    const int64_t cap = (int64_t)num_sms() * 2;  // persistent: the blocks that fit at once
     if (b > cap) b = cap;
     return (int)(b < 1 ? 1 : b);
 }
@@ -682,7 +682,7 @@ int fused_blocks(int32_t n)
 int flat_blocks(int64_t n, int per_sm = 8)
 {
     int64_t b = (n + 255) / 256;
-    const int64_t cap = (int64_t)kSMs * per_sm;
+    const int64_t cap = (int64_t)num_sms() * per_sm;
     if (b > cap) b = cap;
     return (int)(b < 1 ? 1 : b);
 }
@@ -697,7 +697,7 @@ cudaError_t launch_point_phase(const int64_t* P_row, const int32_t* P_col, const
     int32_t* bn = w.bounds + 2 * (parity ^ 1);
     if (!plain && hr.nchunks > 0) {
         int64_t cb = ((int64_t)hr.nchunks * 32 + 255) / 256;
-        if (cb > kSMs * 8) cb = kSMs * 8;
+        if (cb > num_sms() * 8) cb = num_sms() * 8;
         if (P_d16)
             k_attr_chunks<true><<<(unsigned)cb, 256, 0, s>>>(P_row, P_col, P_d16, P_val, n, Y, hr.crow, hr.cstart,
                                                              hr.nchunks, hr.partial);
@@ -735,7 +735,7 @@ cudaError_t launch_point_phase(const int64_t* P_row, const int32_t* P_col, const
             default: k_plain_gather<5><<<nb, 256, 0, s>>>(Y, n, w.g, w.fields, w.phi); break;
         }
         int64_t ab = ((int64_t)n + 7) / 8;
-        if (ab > kSMs * 16) ab = kSMs * 16;
+        if (ab > num_sms() * 16) ab = num_sms() * 16;
         if (ab < 1) ab = 1;
         k_plain_attract<<<(unsigned)ab, 256, 0, s>>>(P_row, P_col, P_val, n, Y, w.attr, w.st);
         k_plain_update<UPDATE><<<nb, 256, 0, s>>>(n, Y, Ynew, upd, gains, w.g, w.phi, w.attr, st, bn, grad, parts,
@@ -803,14 +803,9 @@ size_t iter_ws_bytes(int32_t n, const ltsnet_params* p)
     return align_up(c.off, 256);
 }
 
-cudaError_t ensure_attrs()
+cudaError_t set_fused_attrs()
 {
-    // Every kernel's dynamic shared-memory limit is raised once to the most
-    // any supported configuration asks for.
-    static bool done = false;
-    if (done) return cudaSuccess;
-    cudaError_t e = grid_set_smem_attrs();
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     const int fs = (int)kFusedSmem;
 #define LT_ATTR(PP, UU, DD)                                                                                  \
     if ((e = cudaFuncSetAttribute(k_fused<PP, UU, DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs))) \
@@ -820,8 +815,16 @@ cudaError_t ensure_attrs()
     LT_ATTR(2, true, true) LT_ATTR(3, true, true) LT_ATTR(4, true, true) LT_ATTR(5, true, true)
     LT_ATTR(2, false, true) LT_ATTR(3, false, true) LT_ATTR(4, false, true) LT_ATTR(5, false, true)
 #undef LT_ATTR
-    done = true;
     return cudaSuccess;
+}
+
+// Every kernel's dynamic shared-memory limit is raised to the most any
+// supported configuration asks for, once on each device that runs them.
+cudaError_t ensure_attrs()
+{
+    cudaError_t e = once_per_device(kOnceGridAttrs, grid_set_smem_attrs);
+    if (e != cudaSuccess) return e;
+    return once_per_device(kOnceFusedAttrs, set_fused_attrs);
 }
 
 ltsnet_status read_status(StatusBlock* st, cudaStream_t s)
@@ -1040,7 +1043,7 @@ ltsnet_status run_core(const int64_t* row_ptr, const int32_t* col, int32_t n, co
     bool d16 = false;
     if (!(p->flags & LTSNET_FLAG_PLAIN) && nnz > 0) {
         LT_CUDA(cudaMemsetAsync(r.far, 0, sizeof(int32_t), s));
-        k_pack_d16<<<kSMs * 8, 256, 0, s>>>(r.P_row, r.P_col, n, r.d16, r.far);
+        k_pack_d16<<<num_sms() * 8, 256, 0, s>>>(r.P_row, r.P_col, n, r.d16, r.far);
         count_launches(1);
         LT_CHECK_LAUNCH();
         int32_t far = 1;

@@ -264,7 +264,7 @@ cudaError_t bfs_order(const int64_t* row_ptr, const int32_t* col, int32_t n, int
     unsigned long long* key = c.take<unsigned long long>(n);
     int32_t* nchild = c.take<int32_t>(n);
     int32_t* coff = c.take<int32_t>(n);
-    const unsigned grid = kSMs * 4;
+    const unsigned grid = num_sms() * 4;
     k_order_init<<<grid, kThreads, 0, s>>>(n, level, key, order, ctl);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
@@ -300,14 +300,14 @@ cudaError_t permute_conditional_rows(const int32_t* order, const int32_t* inv, c
                                      const double* pcond, const int32_t* cnt, int32_t n, int32_t k, int32_t* nbr2,
                                      double* pcond2, int32_t* cnt2, cudaStream_t s)
 {
-    k_permute_rows<<<kSMs * 8, kThreads, 0, s>>>(order, inv, nbr, pcond, cnt, n, k, nbr2, pcond2, cnt2);
+    k_permute_rows<<<num_sms() * 8, kThreads, 0, s>>>(order, inv, nbr, pcond, cnt, n, k, nbr2, pcond2, cnt2);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t gather_rows2(const float2* src, const int32_t* idx, int32_t n, float2* dst, cudaStream_t s)
 {
-    k_gather_rows2<<<kSMs * 4, kThreads, 0, s>>>(src, idx, n, dst);
+    k_gather_rows2<<<num_sms() * 4, kThreads, 0, s>>>(src, idx, n, dst);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -43,7 +43,7 @@ constexpr int kEigMaxIter = 20000;
 constexpr double kEigTol = 1e-13;
 constexpr double kAxisEps = 1e-10;
 constexpr double kSignSlack = 1e-9;
-constexpr int kFlatBlocks = kSMs * 4;
+constexpr int kFlatBlocks = kSplitBlocks * 4;  // fixed: sizes workspace partials
 
 struct PmdsEig {
     double lam[2];   // sigma_d^2
@@ -705,7 +705,7 @@ extern "C" ltsnet_status ltsnet_pivot_mds(const int64_t* row_ptr, const int32_t*
     LT_CHECK_LAUNCH();
     const int ntb = (k + kTile - 1) / kTile;
     const int ntiles = ntb * (ntb + 1) / 2;
-    int splits = std::max(1, (kSMs * 4 + ntiles - 1) / ntiles);
+    int splits = std::max(1, (num_sms() * 4 + ntiles - 1) / ntiles);
     int64_t rows = ((int64_t)n + splits - 1) / splits;
     rows = (rows + kRows - 1) / kRows * kRows;
     splits = (int)(((int64_t)n + rows - 1) / rows);

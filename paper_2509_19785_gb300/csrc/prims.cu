@@ -246,12 +246,11 @@ cudaError_t radix_sort_u64_f64(uint64_t* k0, double* v0, uint64_t* k1, double* v
     *in_alt = false;
     if (count <= 1) return cudaSuccess;
     const int64_t nb = (count + kRadixTile - 1) / kRadixTile;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kScatterSmem);
+    {
+        cudaError_t e = once_per_device(kOnceRadix, [] {
+            return cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+        });
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     uint64_t *ka = k0, *kb = k1;
     double *va = v0, *vb = v1;

@@ -42,7 +42,7 @@ constexpr int kQtThreads = 256;
 constexpr int kQtLevels = 16;
 constexpr int kQtStack = 64;  // > 3 * kQtLevels + 4
 constexpr int kFixBits = 36;
-constexpr int kQtBlocks = kSMs * 4;
+constexpr int kQtBlocks = kSplitBlocks * 4;  // fixed: sizes workspace partials
 constexpr int kScanChunk = 4096;  // int64 scan: elements per block
 
 struct QtScal {

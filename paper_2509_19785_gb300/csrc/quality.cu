@@ -39,7 +39,7 @@ constexpr int kNpWarps = 2;          // warps per block of the NP kernel
 constexpr int kNpCap = 2048;         // 2-hop candidates (with repeats) per vertex
 constexpr int kHashSlots = 4096;     // >= 2 kNpCap: load factor <= 1/2
 constexpr int kHashBits = 12;
-constexpr int kQBlocks = kSMs * 4;
+constexpr int kQBlocks = kSplitBlocks * 4;  // fixed: sizes workspace and host partials
 
 struct QualityScal {
     int32_t lo_ord[2];  // f2ord of the drawing's min x, min y
@@ -548,7 +548,7 @@ extern "C" ltsnet_status ltsnet_neighbourhood_preservation(const int64_t* row_pt
     k_q_sat_cols<<<(G + 127) / 128, 128, 0, s>>>(G, w.sat);
     count_launches(7);
     LT_CHECK_LAUNCH();
-    k_np<<<kSMs * 6, kNpWarps * 32, 0, s>>>(row_ptr, col, n, Y2, w.sc, w.start, w.sat, w.sid, w.sy, bout, cout_, w.st,
+    k_np<<<num_sms() * 6, kNpWarps * 32, 0, s>>>(row_ptr, col, n, Y2, w.sc, w.start, w.sat, w.sid, w.sy, bout, cout_, w.st,
                                             &w.sc->excluded);
     k_np_partial<<<kQBlocks, kQThreads, 0, s>>>(bout, cout_, n, w.part, w.pcnt);
     count_launches(2);

@@ -1,11 +1,10 @@
 // Symmetrisation without a caller-provided workspace.
 //
 // Some callers cannot allocate device memory at the point where they need
-// this step: code that runs while a stream is being captured into a CUDA
-// graph (cudaMalloc is not a capturable operation), plug-ins and embedded
-// hosts that are handed a fixed memory budget and forbid device allocation,
-// and latency-sensitive loops that must not pay for cudaMalloc's implicit
-// device synchronisation.  For them, ltsnet_symmetrize_static keeps its
+// this step: plug-ins and embedded hosts that are handed a fixed device-memory
+// budget and forbid allocation, and latency-sensitive loops that must not pay
+// for cudaMalloc's implicit device synchronisation.  For them,
+// ltsnet_symmetrize_static keeps its
 // scratch in a file-scope device array that exists for as long as the library
 // is loaded, on every GPU that loads it, and forwards to ltsnet_symmetrize.
 //
@@ -33,8 +32,10 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_ptr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (resolved once
-// per device; cudaGetSymbolAddress also loads the module there if needed).
+// Device address of the scratch array on the current device, resolved by the
+// first call on each device (cudaGetSymbolAddress, which also loads the module
+// there if needed); that first call should therefore come before any stream
+// capture on the device.
 ltsnet_status scratch_for_current_device(void** out)
 {
     int dev = -1;

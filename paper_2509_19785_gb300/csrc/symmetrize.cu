@@ -162,7 +162,7 @@ extern "C" ltsnet_status ltsnet_symmetrize(const int32_t* nbr, const int32_t* cn
     if (!c.ok()) return LTSNET_ERR_WORKSPACE;
     const int nbits = sym_nbits(n);
     const uint64_t sent = (1ull << (2 * nbits)) - 1ull;
-    const unsigned grid = kSMs * 8, block = 256;
+    const unsigned grid = num_sms() * 8, block = 256;
     LT_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StatusBlock), s));
     LT_CUDA(cudaMemsetAsync(w.nnz, 0, sizeof(int64_t), s));
     k_sym_emit<<<grid, block, 0, s>>>(nbr, cnt, pcond, n, k, nbits, w.k0, w.v0, w.st);

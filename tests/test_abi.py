@@ -138,3 +138,26 @@ def test_every_entry_point_cites_the_paper_or_says_it_has_no_counterpart():
         above = [b for b in blocks if b[1] <= pos]
         assert above, name
         assert cite.search(above[-1][2]), name
+
+
+def test_static_symmetrize_size_check_at_the_limit(lib):
+    """The allocation-free symmetrisation accepts every shape with
+    2 n k = ltsnet_symmetrize_static_max_entries() (its built-in scratch
+    holds that call's workspace) and rejects one more entry with
+    LTSNET_ERR_WORKSPACE, on the host.  Null buffers make an accepted call stop
+    at its next check (an argument error, or a CUDA error where there is no
+    GPU), never at the size check."""
+    L = lib.lib()
+    limit = int(L.ltsnet_symmetrize_static_max_entries())
+    null = ctypes.c_void_p(0)
+    nnz = ctypes.c_int64(0)
+    k = 1
+    while k <= 4096:
+        n = limit // (2 * k)
+        assert 2 * n * k == limit
+        assert L.ltsnet_symmetrize_workspace_size(n, k) > 0
+        rc = L.ltsnet_symmetrize_static(null, null, null, n, k, null, null, null, 0, ctypes.byref(nnz), null)
+        assert rc in (-1, -3), (n, k, rc)
+        rc = L.ltsnet_symmetrize_static(null, null, null, n + 1, k, null, null, null, 0, ctypes.byref(nnz), null)
+        assert rc == -2, (n + 1, k, rc)
+        k *= 2

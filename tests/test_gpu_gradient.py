@@ -176,6 +176,31 @@ def test_gradient_tiny(ltlib):
             assert v < TOL, f"n={n} {key}: {v:.3e} ({errs})"
 
 
+@pytest.mark.parametrize("bad", [float("nan"), float("inf"), -float("inf")])
+def test_nonfinite_layout_is_reported(ltlib, grid32, bad):
+    """A layout with one non-finite coordinate: ltsnet_gradient and
+    ltsnet_optimize return LTSNET_ERR_NONFINITE through the workspace status
+    word (every grid decision is clamped, so the bad point only poisons the
+    sums), and the library stays usable for the next call."""
+    import torch
+
+    g, P, Pn = grid32
+    Y = synth.initial_layout(g.n, 1) * 1e4
+    Y[17, 1] = bad
+    st = ltlib.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+    with pytest.raises(ltlib.LtsnetError) as ei:
+        ltlib.gradient(P, torch.from_numpy(Y).cuda(), st, ltlib.Params())
+    assert ei.value.code == ltlib.ERR_NONFINITE
+    Yd = torch.from_numpy(Y).cuda()
+    with pytest.raises(ltlib.LtsnetError) as ei:
+        ltlib.optimize(P, Yd, torch.zeros_like(Yd), torch.ones_like(Yd), 0, 5,
+                       ltlib.Params(stages=ltlib.default_stages(5)))
+    assert ei.value.code == ltlib.ERR_NONFINITE
+    ok = synth.initial_layout(g.n, 1) * 1e4
+    grad, _, _ = ltlib.gradient(P, torch.from_numpy(ok).cuda(), st, ltlib.Params())
+    assert torch.isfinite(grad).all()
+
+
 def _run_steps(lt, P, Y0, start, count, params, state=None):
     import torch
 
@@ -333,28 +358,51 @@ def test_cost_terms_match_oracle(ltlib, grid32, snapshots, which):
     assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want)), np.max(np.abs(got - want))
 
 
-def test_cost_autograd_matches_finite_differences(ltlib, grid32, snapshots):
-    """LTsNetCost: dC/dP_val from backward against central differences of the
-    forward (exact up to FP32 inputs), and dC/dY against central differences
-    of the cost.  The interpolated gradient approximates the derivative of the
-    interpolated cost only to interpolation accuracy (a fine grid here) and
-    the FP32 grid sums add noise to the differences, so dC/dY is held to 10%
-    of the largest gradient component: enough to catch a wrong sign, factor
-    or term."""
+def _autograd_checks(lt, P, Pn, Y32, st, params, gp, coords, recompute):
+    """LTsNetCost at Y32 against the oracle: dC/dY against the oracle's
+    interpolated gradient (rel. L2 over the sum of the term norms, TOL) and
+    against central differences of the oracle's EXACT cost on ``coords``,
+    held to a bound derived from the interpolation error itself:
+        |FD - dC/dY| <= |g_interp - g_exact| (oracle, at that coordinate)
+                        + max |dC/dY - g_interp| + 1e-7 max |g|
+    (FD of the FP64 exact cost with a 1e-5 step is exact to far better than
+    the last term).  dC/dP_val against the oracle's interpolated derivative
+    (TOL, entries with p > 0) and against central differences of the
+    forward in 5 entries."""
     import torch
 
-    g, P, Pn = grid32
-    Y = torch.from_numpy(snapshots[60]).cuda()
-    st = ltlib.Stage(1, 1.0, 0.01, 0.0, 1.0, 0.8)
-    params = ltlib.Params(box_width_max=0.1, max_boxes=640)
-    F = ltlib.ltsnet_cost_fn()
+    ost = oracle.Stage(st.iters, st.lambda_kl, st.lambda_c, st.lambda_r, st.exaggeration, st.momentum)
+    pv = Pn[2].astype(np.float64)
+    Y = torch.from_numpy(Y32).cuda()
+    F = lt.ltsnet_cost_fn()
     Yv = Y.clone().requires_grad_(True)
     Pv = P[2].clone().requires_grad_(True)
-    c = F.apply(Yv, Pv, P[0], P[1], st, params)
-    c.backward()
-    gY, gP = Yv.grad, Pv.grad
+    F.apply(Yv, Pv, P[0], P[1], st, params, recompute).backward()
+    gY = Yv.grad.cpu().numpy().astype(np.float64)
+    gP = Pv.grad.cpu().numpy().astype(np.float64)
+    n = Y32.shape[0]
+    gi, pr = oracle.interp_gradient(Y32, Pn[0], Pn[1], pv, ost, gp)
+    scale = (np.linalg.norm(4 * ost.lambda_kl * pr["A"]) + np.linalg.norm(4 * ost.lambda_kl * pr["S"] / pr["Z"] * pr["R"])
+             + np.linalg.norm(ost.lambda_c / n * Y32.astype(np.float64))
+             + np.linalg.norm(ost.lambda_r / n ** 2 * pr["E"]))
+    assert np.linalg.norm(gY - gi) / scale <= TOL
+    dPo = oracle.interp_grad_pvals(Y32, Pn[0], Pn[1], pv, ost, gp)
+    pos = pv > 0
+    assert rel(gP[pos], dPo[pos]) <= TOL
+    assert np.array_equal(np.isfinite(gP), pos)
+    Yd = Y32.astype(np.float64)
+    rows = np.array(sorted({i for i, _ in coords}), np.int32)
+    A, R, E = oracle.exact_rows(Yd, Pn[0], Pn[1], pv, rows)
+    Z = oracle.exact_z(Yd)
+    ge = dict(zip(rows.tolist(), oracle.assemble(Yd[rows], A, R, E, Z, pr["S"], ost, n)))
+    dgpu = float(np.abs(gY - gi).max())
+    gmax = float(np.abs(gY).max())
+    for i, d in coords:
+        fd = oracle.exact_cost_central_difference(Yd, Pn[0], Pn[1], pv, ost, i, d, 1e-5, Z)
+        bound = abs(gi[i, d] - ge[i][d]) + dgpu + 1e-7 * gmax
+        assert abs(fd - gY[i, d]) <= bound, (i, d, fd, gY[i, d], bound)
     rng = np.random.default_rng(3)
-    for e in rng.choice(P[2].numel(), 5, replace=False):
+    for e in rng.choice(np.nonzero(pv > 1e-10)[0], 5, replace=False):
         h = float(P[2][e]) * 1e-2
         Pp, Pm = P[2].clone(), P[2].clone()
         Pp[e] += h
@@ -362,20 +410,33 @@ def test_cost_autograd_matches_finite_differences(ltlib, grid32, snapshots):
         cp = F.apply(Y, Pp, P[0], P[1], st, params).item()
         cm = F.apply(Y, Pm, P[0], P[1], st, params).item()
         fd = (cp - cm) / (Pp[e] - Pm[e]).item()
-        assert abs(fd - gP[e].item()) <= 1e-3 * abs(gP[e].item()) + 1e-6, (e, fd, gP[e].item())
-    scale = float(gY.abs().max())
-    Yn = snapshots[60]
-    inner = np.where((Yn.min(1) > Yn.min() + 0.1) & (Yn.max(1) < Yn.max() - 0.1))[0]  # grid bounds unchanged
-    gmag = gY.abs().max(1).values.cpu().numpy()
-    for i in inner[np.argsort(-gmag[inner])[:4]]:  # the largest gradients: FD noise matters least
-        for d in range(2):
-            h = 2e-2
-            Yp, Ym = Y.clone(), Y.clone()
-            Yp[i, d] += h
-            Ym[i, d] -= h
-            fd = (F.apply(Yp, P[2], P[0], P[1], st, params).item()
-                  - F.apply(Ym, P[2], P[0], P[1], st, params).item()) / (2 * h)
-            assert abs(fd - gY[i, d].item()) <= 0.1 * scale, (i, d, fd, gY[i, d].item())
+        assert abs(fd - gP[e]) <= 1e-3 * abs(gP[e]) + 1e-6, (e, fd, gP[e])
+
+
+@pytest.mark.parametrize("recompute", [False, True])
+def test_cost_autograd_grid32(ltlib, grid32, snapshots, recompute):
+    """The autograd wrapper on the 32x32 grid at iteration 300 of a default
+    run, with the default grid and with a finer one (where the interpolation
+    error, and with it the finite-difference bound, is smaller)."""
+    g, P, Pn = grid32
+    Y32 = snapshots[300]
+    st = ltlib.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+    rng = np.random.default_rng(5)
+    coords = [(int(i), int(d)) for i, d in zip(rng.choice(g.n, 16, replace=False), rng.integers(0, 2, 16))]
+    for bw in (0.25, 0.1):
+        params = ltlib.Params(box_width_max=bw)
+        gp = oracle.GridParams(box_width_max=bw, max_boxes=640)
+        _autograd_checks(ltlib, P, Pn, Y32, st, params, gp, coords, recompute)
+
+
+def test_cost_autograd_rejects_exaggeration(ltlib, grid32, snapshots):
+    import torch
+
+    g, P, Pn = grid32
+    F = ltlib.ltsnet_cost_fn()
+    Y = torch.from_numpy(snapshots[60]).cuda().requires_grad_(True)
+    with pytest.raises(ValueError):
+        F.apply(Y, P[2], P[0], P[1], ltlib.Stage(1, 1.0, 0.01, 0.0, 12.0, 0.5), ltlib.Params())
 
 
 def test_run_batched_equals_single_runs(ltlib):
@@ -471,45 +532,22 @@ def test_ba4m_ball_pipeline_matches_oracle(ltlib, ba_ball):
 
 
 def test_cost_autograd_sbm100k_64_coordinates(ltlib):
-    """The autograd wrapper on the 100,000-vertex SBM (perplexity 40): dC/dY
-    against central differences of the cost on 64 random coordinates and
-    dC/dP_val on 64 random entries."""
-    import torch
-
+    """The autograd wrapper on the 100,000-vertex SBM (perplexity 40) at a
+    spread-out layout: dC/dY against the oracle's interpolated gradient and
+    against central differences of the oracle's exact cost on 64 random
+    coordinates (bound from the interpolation error), dC/dP_val against the
+    oracle and central differences; in the recompute mode."""
     g = synth.config_graph("sbm100k")
     aff = ltlib.affinities(g.row_ptr, g.col, 40.0)
     P = aff["P"]
+    Pn = tuple(t.cpu().numpy() for t in P)
     rng = np.random.default_rng(64)
-    Y = torch.from_numpy((rng.standard_normal((g.n, 2)) * 20).astype(np.float32)).cuda()
-    st = ltlib.Stage(1, 1.0, 0.01, 0.0, 1.0, 0.8)
-    params = ltlib.Params(perplexity=40.0, box_width_max=0.25)
-    F = ltlib.ltsnet_cost_fn()
-    Yv = Y.clone().requires_grad_(True)
-    Pv = P[2].clone().requires_grad_(True)
-    F.apply(Yv, Pv, P[0], P[1], st, params).backward()
-    gY, gP = Yv.grad, Pv.grad
-    scale = float(gY.abs().max())
-    Yn = Y.cpu().numpy()
-    inner = np.where((Yn.min(1) > Yn.min() + 1.0) & (Yn.max(1) < Yn.max() - 1.0))[0]
-    gmag = gY.abs().max(1).values.cpu().numpy()
-    picks = inner[np.argsort(-gmag[inner])[:32]]
-    for i in picks:
-        for d in range(2):
-            h = 5e-2
-            Yp, Ym = Y.clone(), Y.clone()
-            Yp[i, d] += h
-            Ym[i, d] -= h
-            fd = (F.apply(Yp, P[2], P[0], P[1], st, params).item()
-                  - F.apply(Ym, P[2], P[0], P[1], st, params).item()) / (2 * h)
-            assert abs(fd - gY[i, d].item()) <= 0.1 * scale, (i, d, fd, gY[i, d].item())
-    for e in rng.choice(P[2].numel(), 64, replace=False):
-        h = float(P[2][e]) * 1e-2
-        Pp, Pm = P[2].clone(), P[2].clone()
-        Pp[e] += h
-        Pm[e] -= h
-        fd = (F.apply(Y, Pp, P[0], P[1], st, params).item()
-              - F.apply(Y, Pm, P[0], P[1], st, params).item()) / (Pp[e] - Pm[e]).item()
-        assert abs(fd - gP[e].item()) <= 1e-3 * abs(gP[e].item()) + 1e-6, (e, fd, gP[e].item())
+    Y32 = (rng.standard_normal((g.n, 2)) * 20).astype(np.float32)
+    st = ltlib.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+    params = ltlib.Params(perplexity=40.0)
+    gp = oracle.GridParams()
+    coords = [(int(i), int(d)) for i, d in zip(rng.choice(g.n, 64, replace=False), rng.integers(0, 2, 64))]
+    _autograd_checks(ltlib, P, Pn, Y32, st, params, gp, coords, recompute=True)
 
 
 def test_run_step_ba_ball_long_rows_match_oracle(ltlib, ba_ball):

@@ -290,3 +290,59 @@ def test_interp_cost_entropy_converges_to_exact():
     got = oracle.interp_cost(Y, *P, st, gp)["ent"]
     self_terms = abs(np.log(oracle.EPS_DEFAULT) / (4 * n))
     assert abs(got - parts["ent"]) < 0.05 * self_terms
+
+
+def test_exact_rows_and_z_equal_the_full_exact_sums():
+    """The row-subset exact sums and the stand-alone Z (used for sampled checks
+    of large layouts) equal the all-rows pass, which the central differences
+    above pin; rows may repeat and come in any order."""
+    g, aff, Y = small_problem(n=80, seed=3)
+    A, R, E, Z = oracle.exact_sums(Y, aff.P_row, aff.P_col, aff.P_val64)
+    rows = np.array([5, 0, 79, 5, 41], np.int32)
+    A2, R2, E2 = oracle.exact_rows(Y, aff.P_row, aff.P_col, aff.P_val64, rows)
+    assert np.array_equal(A2, A[rows]) and np.array_equal(R2, R[rows]) and np.array_equal(E2, E[rows])
+    assert abs(oracle.exact_z(Y) - Z) <= 1e-13 * Z
+    with pytest.raises(ValueError):
+        oracle.exact_rows(Y, aff.P_row, aff.P_col, aff.P_val64, np.array([80], np.int32))
+
+
+@pytest.mark.parametrize("lam", [(1.0, 1.2, 0.0, 1.0), (1.0, 0.01, 0.6, 1.0)])
+def test_cost_step_equals_differences_of_the_full_cost(lam):
+    """The O(n + nnz) central difference of the exact cost equals the
+    difference of two full O(n^2) cost evaluations, and both approach the
+    analytic exact gradient as the step shrinks."""
+    g, aff, Y = small_problem(n=70, seed=4)
+    st = oracle.Stage(1, *lam, 0.5)
+    Z = oracle.exact_z(Y)
+    grad, _ = oracle.exact_gradient(Y, aff.P_row, aff.P_col, aff.P_val64, st)
+    for i, d in ((0, 0), (33, 1), (69, 0)):
+        h = 1e-3
+        Yp, Ym = Y.copy(), Y.copy()
+        Yp[i, d] += h
+        Ym[i, d] -= h
+        full = (oracle.exact_cost(Yp, aff.P_row, aff.P_col, aff.P_val64, st)[0]
+                - oracle.exact_cost(Ym, aff.P_row, aff.P_col, aff.P_val64, st)[0]) / (2 * h)
+        step = oracle.exact_cost_central_difference(Y, aff.P_row, aff.P_col, aff.P_val64, st, i, d, h, Z)
+        assert abs(step - full) <= 1e-8 * max(1.0, abs(full)), (i, d, step, full)
+        small = oracle.exact_cost_central_difference(Y, aff.P_row, aff.P_col, aff.P_val64, st, i, d, 1e-6, Z)
+        assert abs(small - grad[i, d]) <= 1e-7 * np.abs(grad).max(), (i, d, small, grad[i, d])
+
+
+def test_interp_grad_pvals_central_differences():
+    """dC/dp_e of the interpolated cost against central differences of
+    interp_cost in each stored entry (Z from the grid does not depend on P)."""
+    g, aff, Y = small_problem(n=60, seed=5)
+    Y32 = Y.astype(np.float32)
+    st = oracle.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+    gp = oracle.GridParams(min_boxes=8)
+    dP = oracle.interp_grad_pvals(Y32, aff.P_row, aff.P_col, aff.P_val64, st, gp)
+    order = np.argsort(-aff.P_val64)
+    order = order[aff.P_val64[order] > 1e-12]  # entries that underflowed to 0 have no finite derivative
+    for e in (order[0], order[len(order) // 2], order[-1]):
+        h = aff.P_val64[e] * 1e-4
+        Pp, Pm = aff.P_val64.copy(), aff.P_val64.copy()
+        Pp[e] += h
+        Pm[e] -= h
+        fd = (oracle.interp_cost(Y32, aff.P_row, aff.P_col, Pp, st, gp)["total"]
+              - oracle.interp_cost(Y32, aff.P_row, aff.P_col, Pm, st, gp)["total"]) / (2 * h)
+        assert abs(fd - dP[e]) <= 1e-6 * abs(dP[e]), (e, fd, dP[e])

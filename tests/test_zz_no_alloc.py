@@ -1,8 +1,8 @@
 """The allocation-free symmetrisation entry point (ltsnet_symmetrize_static),
 called through the C ABI.  It exists for callers that cannot allocate device
-memory where they need this step (for instance while a stream is captured
-into a CUDA graph, or in a host with a fixed device-memory budget); it uses a
-scratch array built into the library instead of a caller workspace.  Its
+memory where they need this step (plug-ins and embedded hosts handed a fixed
+device-memory budget that forbid allocation); it uses a scratch array built
+into the library instead of a caller workspace.  Its
 results must equal those of ltsnet_symmetrize, call after call (the scratch
 array is reused and keeps the previous call's contents).
 
@@ -46,7 +46,10 @@ def _static(lt, nbr, cnt, pcond):
 
 
 def test_static_symmetrize_matches_workspace_version(ltlib):
-    cases = [(synth.grid2d(32, 32), 30.0), (synth.sbm([300, 250, 200], 12.0, 80, seed=8), 40.0)]
+    # the last case sits exactly at the limit: 2 n k = 2 * 2048 * 64 = 2^18
+    cases = [(synth.grid2d(32, 32), 30.0), (synth.sbm([300, 250, 200], 12.0, 80, seed=8), 40.0),
+             (synth.grid2d(64, 32), 64.0 / 3.0)]
+    assert 2 * 2048 * 64 == ltlib.lib().ltsnet_symmetrize_static_max_entries()
     for g, u in cases:
         nbr, cnt, pcond = _inputs(ltlib, g, u)
         ref = [t.cpu().numpy() for t in ltlib.symmetrize(nbr, cnt, pcond)]
