@@ -16,10 +16,8 @@ number of vertices nearest to v in the drawing; v scores the Jaccard index
   same decisions in the same precision.
 - Both sets have b = |N_G| members, so the union has 2b - c members where c
   is the size of the intersection.
-- Limit: a vertex whose 2-hop candidate count deg(v) + sum over neighbours w
-  of deg(w) (adjacency entries, with repeats) exceeds ``cap`` = 2048 is
-  excluded and counted; hubs of scale-free graphs and their neighbours are
-  the ones this drops.
+- Every vertex counts, hubs of scale-free graphs and their neighbours
+  included (the paper averages over all vertices).
 
 Stress (the paper's ST): the mean over ordered pairs i != j of
 ((d_ij - ||X_i - X_j||) / d_ij)^2 with d_ij the hop distance.  Readings:
@@ -36,9 +34,6 @@ from __future__ import annotations
 import numpy as np
 
 from . import pmds
-
-NP_CAP = 2048
-
 
 def two_hop_ball(row_ptr, col, v: int) -> np.ndarray:
     """Vertices u != v with hop distance at most 2 from v (sorted ids)."""
@@ -72,16 +67,14 @@ def nearest_in_drawing(Y32, v: int, b: int) -> np.ndarray:
     return idx[keep][order[:b]]
 
 
-def neighbourhood_preservation(row_ptr, col, Y32, cap: int = NP_CAP):
-    """Returns (NP, b int64[n], c int64[n]) with b = |N_G(v, 2)| (-1 where
-    excluded by the cap) and c = |N_G cap N_D| (0 where excluded)."""
+def neighbourhood_preservation(row_ptr, col, Y32):
+    """Returns (NP, b int64[n], c int64[n]) with b = |N_G(v, 2)| and
+    c = |N_G cap N_D|, over every vertex."""
     n = row_ptr.shape[0] - 1
-    b = np.full(n, -1, dtype=np.int64)
+    b = np.zeros(n, dtype=np.int64)
     c = np.zeros(n, dtype=np.int64)
     scores = []
     for v in range(n):
-        if candidate_count(row_ptr, col, v) > cap:
-            continue
         ball = two_hop_ball(row_ptr, col, v)
         b[v] = ball.shape[0]
         if b[v] == 0:

@@ -77,15 +77,39 @@ def test_np_against_scipy(seed):
     assert npv == pytest.approx(np.mean(scores), rel=1e-15)
 
 
-def test_np_cap_excludes_hubs():
+def test_np_counts_hubs():
+    """A star with 3000 leaves: every vertex reaches all others within two
+    hops (the hub has 6000 two-hop candidates, each leaf 3001), so N_D is all
+    other vertices whatever the drawing and NP = 1 -- hubs included."""
     g = star(3000)
-    npv, b, c = quality.neighbourhood_preservation(g.row_ptr, g.col, np.zeros((3001, 2), np.float32))
-    assert np.all(b == -1)  # the hub has 3000 + 3000 candidates, each leaf 1 + 3000
-    g = star(100)
-    Y = np.random.default_rng(1).normal(size=(101, 2)).astype(np.float32)
+    for Y in (np.zeros((3001, 2), np.float32), np.random.default_rng(1).normal(size=(3001, 2)).astype(np.float32)):
+        npv, b, c = quality.neighbourhood_preservation(g.row_ptr, g.col, Y)
+        assert np.all(b == 3000) and np.all(c == 3000) and npv == 1.0
+        assert quality.candidate_count(g.row_ptr, g.col, 0) == 6000
+
+
+def test_np_against_scipy_with_hubs():
+    """A Barabasi-Albert graph (hubs of more than 2048 two-hop candidates)
+    against scipy's shortest paths and KD-tree neighbours."""
+    g = synth.barabasi_albert(3000, 4, seed=3)
+    n = g.n
+    assert max(quality.candidate_count(g.row_ptr, g.col, v) for v in range(n)) > 2048
+    Y = np.random.default_rng(2).normal(size=(n, 2)).astype(np.float32)
     npv, b, c = quality.neighbourhood_preservation(g.row_ptr, g.col, Y)
-    assert np.all(b == 100)  # every vertex reaches all others within two hops
-    assert npv == 1.0
+    A = csr_matrix((np.ones(g.col.shape[0]), g.col, g.row_ptr), shape=(n, n))
+    D = dijkstra(A, unweighted=True, limit=2.5)
+    tree = cKDTree(Y.astype(np.float64))
+    scores = []
+    for v in range(n):
+        ball = set(np.flatnonzero(np.isfinite(D[v])).tolist()) - {v}
+        assert b[v] == len(ball)
+        _, nn = tree.query(Y[v].astype(np.float64), k=len(ball) + 1)
+        near = set(np.atleast_1d(nn).tolist()) - {v}
+        near = set(list(near)[:len(ball)]) if len(near) > len(ball) else near
+        inter = len(ball & near)
+        assert c[v] == inter
+        scores.append(inter / (2 * len(ball) - inter))
+    assert npv == pytest.approx(np.mean(scores), rel=1e-15)
 
 
 def test_np_ties_go_to_the_smaller_id():
