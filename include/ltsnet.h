@@ -76,7 +76,20 @@ typedef struct {
     int32_t n_stages;      /* stage schedule; stages is a HOST pointer */
     const ltsnet_stage* stages;
     int32_t flags;         /* LTSNET_FLAG_* */
+    int32_t conv_mode;     /* grid convolution (Sec. 2.3): LTSNET_CONV_* */
 } ltsnet_params;
+
+/* conv_mode: how the kernels are convolved with the charge grids (the
+ * interpolation of Sec. 2.3 and Sec. 3.3; the paper uses FFTs).
+ * LTSNET_CONV_FFT: FP32 FFTs of the zero-padded grids (default).
+ * LTSNET_CONV_DFT_GEMM: the same sums as real DFT matrix products on the
+ * tensor cores (tcgen05), every FP32 operand split into three BF16 terms
+ * (v = v0 + v1 + v2) and each product taken as the six term products
+ * a_i b_j with i + j <= 2, accumulated in FP32; not with LTSNET_FLAG_PLAIN.
+ * Its workspace adds about 400 (nodes_per_box max_boxes)^2 bytes (1.45 GB at
+ * P = 3 and 640 boxes). */
+#define LTSNET_CONV_FFT 0
+#define LTSNET_CONV_DFT_GEMM 1
 
 /* flags: LTSNET_FLAG_PLAIN selects the unfused FP32 baseline form of the loop
  * (atomic spread in input order, separate gather/attraction/update kernels)
@@ -410,18 +423,22 @@ ltsnet_status ltsnet_gradient_quadtree(const int64_t* P_row, const int32_t* P_co
 
 /* ---------------------------------------------------------------------------
  * Layout quality metrics of Sec. 4 (the paper's NP and ST).  Synchronous.
- * One workspace, ltsnet_quality_workspace_size(n) bytes, serves both calls.
+ * One workspace, ltsnet_quality_workspace_size(n, nnz_graph) bytes (nnz_graph
+ * = row_ptr[n], the adjacency entries), serves both calls; the stress call
+ * needs only its first part.
  *
  * ltsnet_neighbourhood_preservation -- NP with r = 2: for every vertex v,
  * b = |N_G(v,2)| (vertices within two hops, v excluded), N_D(v) the b
  * vertices nearest to v in the drawing Y (f32[n][2], device), and
  * c = |N_G(v,2) cap N_D(v)|; *np_out (host) = mean of c / (2b - c) over the
- * vertices with b > 0 (the paper prints a sum but states NP lies in [0, 1]).
+ * vertices with b > 0 (the paper prints a sum but states NP lies in [0, 1]),
+ * every vertex counted, hubs included.
  * "Nearest" orders (FP32 squared distance, vertex id), the squared distance
  * formed as dx*dx + dy*dy with every operation rounded on its own; ties go to
- * the smaller id.  A vertex whose 2-hop candidate count, deg(v) plus the sum
- * of deg(w) over its adjacency entries w, exceeds 2048 is excluded: b = -1,
- * and *excluded_out (host, may be NULL) counts them.
+ * the smaller id.  Balls with more than 2048 two-hop candidates (deg(v) plus
+ * the sum of deg(w) over its adjacency entries w) are held in hash tables in
+ * the workspace, processed in batches that fit it; LTSNET_ERR_WORKSPACE if one
+ * vertex's table does not.
  *   ball, common  int32[n] (device, out, may be NULL): b and c per vertex.
  *
  * ltsnet_stress -- ST: over the ordered pairs (s, j), j != s, for s in
@@ -432,11 +449,11 @@ ltsnet_status ltsnet_gradient_quadtree(const int64_t* P_row, const int32_t* P_co
  * counted, pairs skipped.  A BFS distance above 65534 returns
  * LTSNET_ERR_INVALID_ARG; a source out of range too.
  * ------------------------------------------------------------------------- */
-size_t ltsnet_quality_workspace_size(int32_t n);
+size_t ltsnet_quality_workspace_size(int32_t n, int64_t nnz_graph);
 ltsnet_status ltsnet_neighbourhood_preservation(const int64_t* row_ptr, const int32_t* col, int32_t n,
                                                 const float* Y, int32_t* ball, int32_t* common,
-                                                double* np_out, int32_t* excluded_out, void* ws,
-                                                size_t ws_bytes, ltsnet_stream stream);
+                                                double* np_out, void* ws, size_t ws_bytes,
+                                                ltsnet_stream stream);
 ltsnet_status ltsnet_stress(const int64_t* row_ptr, const int32_t* col, int32_t n, const float* Y,
                             const int32_t* sources, int32_t n_sources, double* out, void* ws,
                             size_t ws_bytes, ltsnet_stream stream);

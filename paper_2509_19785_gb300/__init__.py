@@ -21,6 +21,8 @@ ERR_BAD_GRAPH = -6
 ERR_NONFINITE = -5
 FLAG_PLAIN = 1
 FLAG_NO_REORDER = 2
+CONV_FFT = 0
+CONV_DFT_GEMM = 1
 MAX_K = 4096
 KERNEL_FUSED_UPDATE, KERNEL_SPREAD, KERNEL_CONV = 1, 2, 3
 
@@ -59,7 +61,8 @@ class CParams(ctypes.Structure):
     _fields_ = [("perplexity", ctypes.c_float), ("eps", ctypes.c_float), ("nodes_per_box", ctypes.c_int32),
                 ("box_width_max", ctypes.c_float), ("min_boxes", ctypes.c_int32), ("max_boxes", ctypes.c_int32),
                 ("learning_rate", ctypes.c_float), ("beta_max_steps", ctypes.c_int32), ("beta_tol", ctypes.c_double),
-                ("n_stages", ctypes.c_int32), ("stages", ctypes.POINTER(CStage)), ("flags", ctypes.c_int32)]
+                ("n_stages", ctypes.c_int32), ("stages", ctypes.POINTER(CStage)), ("flags", ctypes.c_int32),
+                ("conv_mode", ctypes.c_int32)]
 
 
 _lib = None
@@ -112,10 +115,9 @@ def lib():
         L.ltsnet_pivot_mds_workspace_size.restype = sz
         L.ltsnet_pivot_mds.argtypes = [P, P, i32, i32, i32, f64, P, P, P, ctypes.POINTER(f64), P, sz, P]
         L.ltsnet_pivot_mds.restype = i32
-        L.ltsnet_quality_workspace_size.argtypes = [i32]
+        L.ltsnet_quality_workspace_size.argtypes = [i32, i64]
         L.ltsnet_quality_workspace_size.restype = sz
-        L.ltsnet_neighbourhood_preservation.argtypes = [P, P, i32, P, P, P, ctypes.POINTER(f64),
-                                                        ctypes.POINTER(i32), P, sz, P]
+        L.ltsnet_neighbourhood_preservation.argtypes = [P, P, i32, P, P, P, ctypes.POINTER(f64), P, sz, P]
         L.ltsnet_neighbourhood_preservation.restype = i32
         L.ltsnet_stress.argtypes = [P, P, i32, P, P, i32, ctypes.POINTER(f64), P, sz, P]
         L.ltsnet_stress.restype = i32
@@ -188,6 +190,7 @@ class Params:
     stages: list = field(default_factory=lambda: None)
     plain: bool = False
     reorder: bool = True
+    conv_mode: int = 0  # 0: FP32 FFT; 1: split-BF16 DFT matrix products on the tensor cores
 
     @property
     def k(self) -> int:
@@ -202,7 +205,8 @@ class Params:
         p = CParams(self.perplexity, self.eps, self.nodes_per_box, self.box_width_max, self.min_boxes,
                     self.max_boxes, self.learning_rate, self.beta_max_steps, self.beta_tol, len(st),
                     ctypes.cast(arr, ctypes.POINTER(CStage)),
-                    (FLAG_PLAIN if self.plain else 0) | (0 if self.reorder else FLAG_NO_REORDER))
+                    (FLAG_PLAIN if self.plain else 0) | (0 if self.reorder else FLAG_NO_REORDER),
+                    int(self.conv_mode))
         p._keep = arr  # keep the stage array alive with the struct
         return p
 
@@ -288,30 +292,29 @@ def pivot_mds(row_ptr, col, n_pivots: int = 100, first: int = 0, init_std: float
     return out + (dist,) if return_dist else out
 
 
-def quality_workspace(n: int):
+def quality_workspace(n: int, nnz_graph: int):
     """Workspace for the quality-metric calls (device bytes)."""
-    return _workspace(lib().ltsnet_quality_workspace_size(int(n)))
+    return _workspace(lib().ltsnet_quality_workspace_size(int(n), int(nnz_graph)))
 
 
 def neighbourhood_preservation(row_ptr, col, Y, ws=None, return_counts: bool = False):
-    """NP with r = 2 (Sec. 4).  Returns (NP, excluded vertices), plus the
-    per-vertex ball sizes b and intersections c (int32 [n] on the GPU, b = -1
-    where excluded) if return_counts."""
+    """NP with r = 2 (Sec. 4) over every vertex.  Returns NP, or (NP, b, c)
+    with the per-vertex ball sizes b and intersections c (int32 [n] on the
+    GPU) if return_counts."""
     torch = _torch()
     row_ptr = _dev(row_ptr, torch.int64)
     col = _dev(col, torch.int32)
     Y = _dev(Y, torch.float32)
     n = row_ptr.numel() - 1
     if ws is None:
-        ws = quality_workspace(n)
+        ws = quality_workspace(n, col.numel())
     b = torch.empty((n,), dtype=torch.int32, device="cuda") if return_counts else None
     c = torch.empty((n,), dtype=torch.int32, device="cuda") if return_counts else None
-    npv, exc = ctypes.c_double(), ctypes.c_int32()
+    npv = ctypes.c_double()
     _check(lib().ltsnet_neighbourhood_preservation(_ptr(row_ptr), _ptr(col), n, _ptr(Y), _ptr(b), _ptr(c),
-                                                   ctypes.byref(npv), ctypes.byref(exc), _ptr(ws), ws.numel(),
-                                                   _stream()), "ltsnet_neighbourhood_preservation")
-    out = (npv.value, exc.value)
-    return out + (b, c) if return_counts else out
+                                                   ctypes.byref(npv), _ptr(ws), ws.numel(), _stream()),
+           "ltsnet_neighbourhood_preservation")
+    return (npv.value, b, c) if return_counts else npv.value
 
 
 def stress(row_ptr, col, Y, sources=None, ws=None):
@@ -324,7 +327,7 @@ def stress(row_ptr, col, Y, sources=None, ws=None):
     n = row_ptr.numel() - 1
     src = torch.arange(n, dtype=torch.int32, device="cuda") if sources is None else _dev(sources, torch.int32)
     if ws is None:
-        ws = quality_workspace(n)
+        ws = quality_workspace(n, col.numel())
     out = (ctypes.c_double * 4)()
     _check(lib().ltsnet_stress(_ptr(row_ptr), _ptr(col), n, _ptr(Y), _ptr(src), src.numel(), out, _ptr(ws),
                                ws.numel(), _stream()), "ltsnet_stress")

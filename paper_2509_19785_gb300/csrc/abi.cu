@@ -157,6 +157,7 @@ extern "C" ltsnet_params ltsnet_default_params(void)
     p.n_stages = 2;
     p.stages = lt::kDefaultStages;
     p.flags = 0;
+    p.conv_mode = LTSNET_CONV_FFT;
     return p;
 }
 

@@ -1342,6 +1342,7 @@ IterShape iter_shape(int32_t n, const ltsnet_params* p)
     sh.Lmax = 2 * sh.Mmax;
     // boxes of more than kLightMax points: at most n / (kLightMax + 1)
     sh.hcap = std::min<int64_t>((int64_t)sh.max_boxes * sh.max_boxes, (int64_t)n / (kLightMax + 1) + 1);
+    sh.conv_mode = p->conv_mode;
     return sh;
 }
 
@@ -1379,6 +1380,8 @@ IterWs iter_carve(Carve& c, const IterShape& sh)
     w.yalt = c.take<float2>(sh.n);
     w.phi = c.take<float>((int64_t)sh.n * 8);
     w.attr = c.take<float2>(sh.n);
+    w.dft = DftWs{};
+    if (sh.conv_mode == LTSNET_CONV_DFT_GEMM) dft_carve(c, sh, w.dft);
     return w;
 }
 
@@ -1394,6 +1397,7 @@ cudaError_t iter_reset(const IterWs& w, const IterShape& sh, cudaStream_t s)
     if ((e = cudaMemsetAsync(w.hticket, 0, sizeof(int32_t) * (size_t)sh.hcap, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.bcnt, 0, sizeof(int32_t) * (size_t)sh.max_boxes * sh.max_boxes, s)) != cudaSuccess)
         return e;
+    if (sh.conv_mode == LTSNET_CONV_DFT_GEMM && (e = dft_reset(w.dft, s)) != cudaSuccess) return e;
     return cudaMemsetAsync(w.hacc, 0, sizeof(long long) * (size_t)sh.hcap * sh.P * sh.P * 4, s);
 }
 
@@ -1444,6 +1448,7 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
         if ((e2 = cudaStreamWaitEvent(aux->branch, aux->fork, 0)) != cudaSuccess) return e2;
         k_spec_rows<<<fb, kFftThreads, fsm, aux->branch>>>(w.g, w.tw, p->eps, w.krow, f2);
         k_spec_cols<<<fb, kFftThreads, fsm, aux->branch>>>(w.g, w.tw, w.krow, w.khat, f2);
+        count_launches(2);
         if ((e2 = cudaEventRecord(aux->join, aux->branch)) != cudaSuccess) return e2;
     }
     profile_start(LTSNET_KERNEL_SPREAD, s);
@@ -1487,6 +1492,15 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
     if (!fork) {
         k_spec_rows<<<fb, kFftThreads, fsm, s>>>(w.g, w.tw, p->eps, w.krow, f2);
         k_spec_cols<<<fb, kFftThreads, fsm, s>>>(w.g, w.tw, w.krow, w.khat, f2);
+        count_launches(2);
+    }
+    if (sh.conv_mode == LTSNET_CONV_DFT_GEMM) {
+        // DFT matrix products on the tensor cores (dftgemm.cu)
+        if ((e = launch_dft_prep(w, s)) != cudaSuccess) return e;
+        if (fork && (e = cudaStreamWaitEvent(s, aux->join, 0)) != cudaSuccess) return e;
+        if ((e = launch_dft_products(w, n, s)) != cudaSuccess) return e;
+        profile_stop(LTSNET_KERNEL_CONV, s);
+        return cudaGetLastError();
     }
     k_conv_rows_fwd<<<fb, kFftThreads, fsm, s>>>(w.g, w.tw, w.wflt, w.srow, f2);
     if (fork) {
@@ -1495,7 +1509,7 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
     }
     k_conv_cols<<<fb, kColThreads, fsm, s>>>(w.g, w.tw, w.srow, w.khat, w.ucol, w.zblk, n, f2);
     k_conv_rows_inv<<<fb, kFftThreads, fsm, s>>>(w.g, w.tw, w.ucol, w.fields, w.wflt, w.bcnt, plain ? 1 : 0, f2);
-    count_launches(5);
+    count_launches(3);
     profile_stop(LTSNET_KERNEL_CONV, s);
     return cudaGetLastError();
 }

@@ -42,6 +42,18 @@ struct Stage {
     float momentum, lr;
 };
 
+// Split-BF16 operand matrices of the DFT-as-GEMM convolution (dftgemm.cu):
+// the DFT tables F and G, the charges W, the x-transforms X, the kernel
+// products Q and the inverse y-transforms R; each holds its BF16 split terms
+// as consecutive planes of the stated number of elements.
+struct DftWs {
+    uint16_t *F, *G, *W, *X, *Q, *R;
+    int64_t pF, pG, pW, pX, pQ, pR;  // elements per plane
+    float* kpack;                    // kernel spectra packed for k_dft_products
+    float* T;                        // FP32 spectra of the charges (S2 output)
+    int32_t* tabM;                   // grid size the tables hold (-1: none)
+};
+
 // Device buffers of one gradient/optimize call, carved from the workspace.
 struct IterWs {
     StatusBlock* st;
@@ -68,6 +80,7 @@ struct IterWs {
     float2* yalt;        // n, ping-pong layout
     float* phi;          // n * 8 (plain form gather output)
     float2* attr;        // n (plain form attraction output)
+    DftWs dft;           // conv_mode 1 only (null pointers otherwise)
 };
 
 struct IterShape {
@@ -76,6 +89,7 @@ struct IterShape {
     int32_t max_boxes;
     int32_t Mmax, Lmax;
     int64_t hcap;  // capacity of the heavy-box lists
+    int conv_mode;
 };
 
 IterShape iter_shape(int32_t n, const ltsnet_params* p);
@@ -196,6 +210,12 @@ cudaError_t gather_rows2(const float2* src, const int32_t* idx, int32_t n, float
 cudaError_t launch_bounds_init(const IterWs& w, const float2* Y, int32_t n, int parity, cudaStream_t s);
 cudaError_t launch_psum(const IterWs& w, const int64_t* P_row, int32_t n, const float* P_val, cudaStream_t s);
 cudaError_t grid_set_smem_attrs();
+// dftgemm.cu
+void dft_carve(Carve& c, const IterShape& sh, DftWs& w);
+cudaError_t dft_reset(const DftWs& w, cudaStream_t s);
+cudaError_t dft_set_attrs();
+cudaError_t launch_dft_prep(const IterWs& w, cudaStream_t s);
+cudaError_t launch_dft_products(const IterWs& w, int32_t n, cudaStream_t s);
 cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet_params* p, const float2* Y,
                               int parity, bool plain, cudaStream_t s);
 

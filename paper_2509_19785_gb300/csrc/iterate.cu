@@ -754,6 +754,8 @@ bool params_ok(const ltsnet_params* p)
     if (p->min_boxes < 1 || p->max_boxes < p->min_boxes) return false;
     if ((int64_t)2 * p->nodes_per_box * p->max_boxes > kLMax) return false;
     if (p->n_stages < 1 || !p->stages) return false;
+    if (p->conv_mode != LTSNET_CONV_FFT && p->conv_mode != LTSNET_CONV_DFT_GEMM) return false;
+    if (p->conv_mode == LTSNET_CONV_DFT_GEMM && (p->flags & LTSNET_FLAG_PLAIN)) return false;
     for (int i = 0; i < p->n_stages; ++i)
         if (p->stages[i].iters < 0) return false;
     return true;
@@ -824,6 +826,7 @@ cudaError_t ensure_attrs()
 {
     cudaError_t e = once_per_device(kOnceGridAttrs, grid_set_smem_attrs);
     if (e != cudaSuccess) return e;
+    if ((e = once_per_device(kOnceDft, dft_set_attrs)) != cudaSuccess) return e;
     return once_per_device(kOnceFusedAttrs, set_fused_attrs);
 }
 

@@ -94,7 +94,7 @@ def main():
     if args.quality:
         import numpy as np
 
-        out["np_r2"], out["np_excluded"] = lt.neighbourhood_preservation(row_ptr, col, Y)
+        out["np_r2"] = lt.neighbourhood_preservation(row_ptr, col, Y)
         src = np.random.default_rng(11).choice(g.n, min(64, g.n), replace=False).astype(np.int32)
         out["stress"] = lt.stress(row_ptr, col, Y, sources=src)[0]
     print(json.dumps(out))

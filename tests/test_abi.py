@@ -114,10 +114,11 @@ def test_calls_beside_the_path_check_arguments_on_the_host(lib):
     assert L.ltsnet_optimize_quadtree(one, one, one, 100, ctypes.byref(cp), 0.5, 1, one, one, one, -1, 5, one,
                                       1 << 30, null) == -1
     # quality metrics
-    assert L.ltsnet_quality_workspace_size(1000) > 0 and L.ltsnet_quality_workspace_size(0) == 0
-    npv, exc = ctypes.c_double(), ctypes.c_int32()
-    assert L.ltsnet_neighbourhood_preservation(one, one, 0, one, null, null, ctypes.byref(npv), ctypes.byref(exc),
-                                               one, 1 << 30, null) == -1
+    assert L.ltsnet_quality_workspace_size(1000, 4000) > 0 and L.ltsnet_quality_workspace_size(0, 0) == 0
+    assert L.ltsnet_quality_workspace_size(1000, 400000) > L.ltsnet_quality_workspace_size(1000, 4000)
+    npv = ctypes.c_double()
+    assert L.ltsnet_neighbourhood_preservation(one, one, 0, one, null, null, ctypes.byref(npv), one, 1 << 30,
+                                               null) == -1
     out = (ctypes.c_double * 4)()
     assert L.ltsnet_stress(one, one, 10, one, one, 0, out, one, 1 << 30, null) == -1
     assert L.ltsnet_stress(one, one, 10, one, one, 3, out, one, 16, null) == -2
