@@ -253,6 +253,40 @@ def bench_ltsnet(args):
     ms_plain, _, _, _ = timed(plain, max(1, args.steps // 2), 1)
     value_plain = job_rate(world, max(1, args.steps // 2) * ITERS, ms_plain)
 
+    # the grid convolution as split-BF16 DFT matrix products on the tensor
+    # cores (conv_mode 1), same workload and schedule
+    gemm = lt.Params(perplexity=PERPLEXITY, stages=lt.default_stages(ITERS), conv_mode=1)
+    ws_gemm = lt.run_workspace(n, g.col.shape[0], gemm)
+
+    def step_gemm():
+        return lt.run(row_ptr, col, Y0, gemm, ws=ws_gemm)[0]
+
+    step_gemm()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(max(1, args.steps // 2)):
+        Y_gemm = step_gemm()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    value_gemm = job_rate(world, max(1, args.steps // 2) * ITERS, max_over_ranks(e0.elapsed_time(e1), world))
+
+    # grid phase per iteration (one step each with per-launch events: the
+    # kernels run one after the other, the kernel spectra no longer beside
+    # the spread)
+    def phase_us(p, kernel, wsx):
+        lt.profile_begin(kernel, ITERS)
+        lt.run(row_ptr, col, Y0, p, ws=wsx)
+        tot, cnt = lt.profile_end(kernel)
+        return round(tot * 1e3 / max(1, cnt), 1)
+
+    grid_phase = {"spread": phase_us(params, lt.KERNEL_SPREAD, ws),
+                  "conv_fft": phase_us(params, lt.KERNEL_CONV, ws),
+                  "conv_dft_gemm": phase_us(gemm, lt.KERNEL_CONV, ws_gemm),
+                  "unit": "us per iteration (mean over the 1000 iterations of one step)",
+                  "note": "convolution with the kernel spectra, measured with per-launch events"}
+    del ws_gemm
+
     # end to end through the C ABI with host buffers (copies inside the region)
     Yh0 = synth.initial_layout(n, 1 + rank)
     e2e_ms = []
@@ -286,17 +320,17 @@ def bench_ltsnet(args):
     # stress over 64 sampled sources
     qual = None
     if not args.no_batched:
-        qws = lt.quality_workspace(n)
+        qws = lt.quality_workspace(n, g.col.shape[0])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        npv, exc = lt.neighbourhood_preservation(row_ptr, col, Y, ws=qws)
+        npv = lt.neighbourhood_preservation(row_ptr, col, Y, ws=qws)
         torch.cuda.synchronize()
         t_np = time.perf_counter() - t0
         src = torch.from_numpy(np.random.default_rng(11).choice(n, 64, replace=False).astype(np.int32)).cuda()
         t0 = time.perf_counter()
         st, alpha, pairs, skipped = lt.stress(row_ptr, col, Y, sources=src, ws=qws)
         t_st = time.perf_counter() - t0
-        qual = {"np_r2": round(npv, 5), "np_excluded": exc, "np_ms": round(t_np * 1e3, 2),
+        qual = {"np_r2": round(npv, 5), "np_vertices": n, "np_ms": round(t_np * 1e3, 2),
                 "stress": round(st, 5), "stress_sources": 64, "stress_pairs": pairs, "stress_ms": round(t_st * 1e3, 2),
                 "layout": "final layout of the timed run (1000 iterations from the random start)"}
         del qws
@@ -364,25 +398,46 @@ def bench_ltsnet(args):
     if not args.no_batched:
         gs = synth.graph_batch(512)
         y0s = [synth.initial_layout(gb.n, 100 + i) for i, gb in enumerate(gs)]
-        # grid capped at 128 boxes per side: the cap binds only on layouts wider
-        # than 128 box widths (the 1M-vertex layout stays near 50), and with it
-        # the FFT kernels ask for 64 KB of shared memory instead of 215 KB, so
-        # the grid phases of several graphs can share an SM
+        # grid capped at BATCH_MAX_BOXES per side (the per-graph grid arrays
+        # of the whole batch live side by side); max_boxes_used says whether
+        # the cap bound on any graph
+        import tempfile
+
         bparams = lt.Params(perplexity=PERPLEXITY, stages=lt.default_stages(BATCH_ITERS), max_boxes=BATCH_MAX_BOXES)
-        lt.run_batched(gs[:32], y0s[:32], bparams, workers=BATCH_WORKERS)  # warm-up
+        tune_cache = os.path.join(tempfile.gettempdir(), "ltsnet_autotune.json")
+        fb, sb, tune_ms = lt.autotune_batched(gs, y0s, bparams, cache=tune_cache, workers=BATCH_WORKERS)
+        lt.run_batched(gs[:32], y0s[:32], bparams, workers=BATCH_WORKERS, fft_blocks=fb, spread_blocks=sb)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
-        Yb, _ = lt.run_batched(gs, y0s, bparams, workers=BATCH_WORKERS)
+        Yb, _, boxes = lt.run_batched(gs, y0s, bparams, workers=BATCH_WORKERS, fft_blocks=fb, spread_blocks=sb,
+                                      return_boxes=True)
         torch.cuda.synchronize()
         tb = max_over_ranks(time.perf_counter() - t0, world)
         if not bool(torch.isfinite(Yb).all()):
             raise RuntimeError("non-finite batched layout")
+        del Yb
+        # the same batch as stacked single-graph runs (ltsnet_run per graph on
+        # the worker threads)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Yp, _ = lt.run_batched(gs, y0s, bparams, workers=BATCH_WORKERS, mode=lt.BATCH_PER_GRAPH)
+        torch.cuda.synchronize()
+        tp = max_over_ranks(time.perf_counter() - t0, world)
+        del Yp
         batched = {"value": round(job_rate(world, len(gs), tb * 1e3), 2), "unit": "graphs/s", "graphs": len(gs),
                    "vertices": int(sum(gb.n for gb in gs)), "iters_per_graph": BATCH_ITERS, "seconds": round(tb, 3),
-                   "workers": BATCH_WORKERS, "max_boxes": BATCH_MAX_BOXES,
-                   "form": "ltsnet_run_batched: host worker threads, one stream each"}
+                   "form": "one launch per phase over all 512 graphs (grid.y = graph), replayed from CUDA graphs; "
+                           "C0 per graph on host threads",
+                   "launch_shape": {"fft_blocks_per_graph": fb, "spread_blocks_per_graph": sb,
+                                    "autotune_ms_per_40_iters": tune_ms},
+                   "per_graph_form": {"value": round(job_rate(world, len(gs), tp * 1e3), 2), "unit": "graphs/s",
+                                      "seconds": round(tp, 3), "workers": BATCH_WORKERS,
+                                      "form": "ltsnet_run per graph on host worker threads, one stream each"},
+                   "speedup_over_per_graph": round(tp / tb, 3),
+                   "max_boxes": BATCH_MAX_BOXES, "max_boxes_used": int(boxes.max()),
+                   "graphs_at_cap": int((boxes >= BATCH_MAX_BOXES).sum())}
 
     # scale-free workload: Barabasi-Albert, n = 4e6, 4 edges per new vertex,
     # perplexity 50, 1000 iterations (whole run incl. C0, one step)
@@ -397,17 +452,67 @@ def bench_ltsnet(args):
         y_ba = torch.from_numpy(synth.initial_layout(gba.n, 7 + rank)).cuda()
         pba = lt.Params(perplexity=50.0, stages=lt.default_stages(ITERS))
         ws_ba = lt.run_workspace(gba.n, gba.col.shape[0], pba)
+        ws_bytes_ba = ws_ba.numel()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         yb, rc = lt.run(rp_ba, cl_ba, y_ba, pba, ws=ws_ba)
         torch.cuda.synchronize()
         tba = max_over_ranks(time.perf_counter() - t0, world)
         peak = torch.cuda.max_memory_allocated()
+        # the fused kernel on this graph: one more run with per-launch events
+        lt.profile_begin(lt.KERNEL_FUSED_UPDATE, ITERS)
+        lt.run(rp_ba, cl_ba, y_ba, pba, ws=ws_ba)
+        fms, fcnt = lt.profile_end(lt.KERNEL_FUSED_UPDATE)
+        del ws_ba
+        aff_ba = lt.affinities(rp_ba, cl_ba, 50.0)
+        P_ba = aff_ba["P"]
+        del aff_ba
+        nnz_ba = int(P_ba[1].numel())
+        ba_bytes = 8 * nnz_ba + 8 * (gba.n + 1) + 48 * gba.n
+        f_s = fms / 1e3 / max(1, fcnt)
         ba = {"value": round(job_rate(world, ITERS, tba * 1e3), 2), "unit": "iters/s", "n": gba.n, "m": gba.m,
-              "perplexity": 50, "iters": ITERS, "seconds_incl_C0": round(tba, 3),
-              "workspace_bytes": int(ws_ba.numel()), "peak_device_bytes": int(peak - base_mem),
-              "status": int(rc), "note": "status 1: rows whose perplexity target is unreachable (hubs) are flagged"}
-        del ws_ba, yb, rp_ba, cl_ba, y_ba
+              "nnz_P": nnz_ba, "perplexity": 50, "iters": ITERS, "seconds_incl_C0": round(tba, 3),
+              "workspace_bytes": int(ws_bytes_ba), "peak_device_bytes": int(peak - base_mem),
+              "status": int(rc), "note": "status 1: rows whose perplexity target is unreachable (hubs) are flagged",
+              "roofline": {"kernel": "k_fused (rows of more than 2048 entries summed beforehand in chunks)",
+                           "bound": "hbm", "achieved": round(ba_bytes / f_s / 1e9, 1), "peak": peaks["hbm_gbs"],
+                           "unit": "GB/s", "frac": round(ba_bytes / f_s / 1e9 / peaks["hbm_gbs"], 4),
+                           "algorithmic_bytes_per_launch": ba_bytes, "avg_launch_us": round(f_s * 1e6, 2),
+                           "launches_timed": fcnt}}
+        # cfg 5's differentiable cost at the final layout: forward + backward
+        # of LTsNetCost with the tensor-core convolution, recomputing the grid
+        # fields in backward (nothing of size nnz kept between the passes),
+        # against the stored-gradient mode
+        F = lt.ltsnet_cost_fn()
+        stg = lt.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+        pg = lt.Params(perplexity=50.0, conv_mode=1)
+        ag = {}
+        for mode in (True, False):
+            Yv = yb.detach().clone().requires_grad_(True)
+            Pv = P_ba[2].detach().clone().requires_grad_(True)
+            F.apply(Yv, Pv, P_ba[0], P_ba[1], stg, pg, mode).backward()  # warm-up (workspaces, graph state)
+            Yv.grad = None
+            Pv.grad = None
+            torch.cuda.synchronize()
+            m0 = torch.cuda.memory_allocated()
+            torch.cuda.reset_peak_memory_stats()
+            t0 = time.perf_counter()
+            c = F.apply(Yv, Pv, P_ba[0], P_ba[1], stg, pg, mode)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            held = torch.cuda.memory_allocated() - m0  # kept for backward
+            c.backward()
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            ag["recompute" if mode else "stored"] = {
+                "forward_ms": round((t1 - t0) * 1e3, 2), "backward_ms": round((t2 - t1) * 1e3, 2),
+                "bytes_held_between_passes": int(held),
+                "peak_bytes_above_inputs": int(torch.cuda.max_memory_allocated() - m0)}
+            del Yv, Pv, c
+        ag["note"] = ("LTsNetCost (Eq. 1) forward by ltsnet_cost, backward dC/dY by ltsnet_gradient and dC/dP_val by "
+                      "ltsnet_grad_pvals, split-BF16 DFT-GEMM convolution, final layout of the run above")
+        ba["autograd"] = ag
+        del yb, rp_ba, cl_ba, y_ba, P_ba
 
     if rank != 0:
         if world > 1:
@@ -437,6 +542,12 @@ def bench_ltsnet(args):
         "c0_ms": round(statistics.median(c0), 3),
         "plain_fp32": {"value": round(value_plain, 2), "unit": "iters/s", "form": "unfused, atomic spread",
                        "speedup_of_optimised": round(value / value_plain, 3)},
+        "dft_gemm": {"value": round(value_gemm, 2), "unit": "iters/s",
+                     "form": "optimised, grid convolution as split-BF16 (3 terms, 6 products) DFT matrix "
+                             "products on the tensor cores",
+                     "speedup_over_plain_fp32": round(value_gemm / value_plain, 3),
+                     "ratio_to_fft_form": round(value_gemm / value, 3)},
+        "grid_phase_us_per_iter": grid_phase,
         "roofline": roofline,
         "e2e": {"value": round(e2e_value, 2), "unit": "iters/s",
                 "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes + 8 * n), "d2h_bytes_per_step": 8 * n},
@@ -482,21 +593,32 @@ def oracle_iteration_time(g, aff, iters: int, lr: float):
 
 def cpu_baseline(g, n_sample: int = 100_000, iters: int = 3):
     """The oracle, as it stands, on a 100k-vertex instance of the same recipe
-    (C0 + a few iterations), scaled linearly in n (every step is O(n))."""
+    (C0 + a few iterations), scaled linearly in n (every step is O(n)): on
+    one thread and on all host cores (the oracle's row-parallel loops; its
+    spread and numpy's FFT stay on one thread)."""
     import oracle
     import synth
 
     gs = synth.rgg(n_sample)
-    t0 = time.perf_counter()
-    aff = oracle_affinities(gs)
-    c0_s = time.perf_counter() - t0
-    per_iter = oracle_iteration_time(gs, aff, iters, oracle.auto_learning_rate(gs.n))
-    scale = g.n / gs.n
-    run_s = scale * (c0_s + ITERS * per_iter)
-    return {"value": round(ITERS / run_s, 5), "unit": "iters/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle on a {gs.n}-vertex RGG of the same recipe: C0 {c0_s:.1f} s + {iters} iterations "
-                      f"(interpolated gradient + update) {per_iter:.3f} s each, one {ITERS}-iteration run "
-                      f"scaled by n ({scale:.2f}x); single thread"}
+    cores = os.cpu_count() or 1
+    out = {}
+    for threads in (1, cores):
+        used = oracle.set_threads(threads)
+        t0 = time.perf_counter()
+        aff = oracle_affinities(gs)
+        c0_s = time.perf_counter() - t0
+        per_iter = oracle_iteration_time(gs, aff, iters, oracle.auto_learning_rate(gs.n))
+        scale = g.n / gs.n
+        run_s = scale * (c0_s + ITERS * per_iter)
+        out[threads] = (ITERS / run_s, used, c0_s, per_iter, scale)
+    v1, _, c01, it1, scale = out[1]
+    vn, used, c0n, itn, _ = out[cores]
+    return {"value": round(vn, 5), "unit": "iters/s", "cores": used, "kind": "oracle",
+            "sample": f"oracle on a {gs.n}-vertex RGG of the same recipe: C0 {c0n:.1f} s + {iters} iterations "
+                      f"(interpolated gradient + update) {itn:.3f} s each on {used} threads, one {ITERS}-iteration "
+                      f"run scaled by n ({scale:.2f}x)",
+            "single_thread": {"value": round(v1, 5), "cores": 1, "c0_s": round(c01, 2), "iter_s": round(it1, 3)},
+            "nproc": cores}
 
 
 def bench_reference(args):

@@ -319,8 +319,8 @@ ltsnet_status ltsnet_run_host(const int64_t* row_ptr_host, const int32_t* col_ho
 
 /* ---------------------------------------------------------------------------
  * Many independent graphs (the batched form of the method): ltsnet_run
- * (Alg. 3) on each of n_graphs graphs, with the same parameters,
- * concurrently.  The batching has no counterpart in the paper.
+ * (Alg. 3) on each of n_graphs graphs, with the same parameters, in one call.
+ * The batching has no counterpart in the paper.
  *   vtx_off  int64[n_graphs+1] (HOST): graph g owns vertices
  *            [vtx_off[g], vtx_off[g+1]) of Y (f32 [sum n][2], device, in: Y0,
  *            out: final layouts); vtx_off[0] = 0, every graph non-empty
@@ -328,18 +328,41 @@ ltsnet_status ltsnet_run_host(const int64_t* row_ptr_host, const int32_t* col_ho
  *            col[edge_off[g] .. edge_off[g+1]) (int32, device, local ids)
  *   row_ptr  int64 (device): graph g's n_g+1 local row pointers (from 0) start
  *            at row_ptr[vtx_off[g] + g]
- * n_workers (1..64) host threads, each with its own stream and a workspace
- * slice for the largest graph, take the graphs largest first.  Each graph's
- * result equals ltsnet_run's for that graph alone.  Synchronous (waits for
- * `stream` first); returns the first error, else LTSNET_WARN_NOT_CONVERGED if
- * any graph had rows that missed the perplexity target, else LTSNET_OK.
+ * Modes (cfg->mode):
+ *  LTSNET_BATCH_ONE_LAUNCH: C0 of every graph on cfg->n_workers host threads,
+ *    then the whole descent loop with one launch per phase covering every
+ *    graph (grid.y = graph; cfg->fft_blocks and cfg->spread_blocks blocks per
+ *    graph for the FFT passes and the spread, 0 = 4 and 8), replayed from CUDA
+ *    graphs; FFT convolution and the optimised form only (LTSNET_FLAG_PLAIN
+ *    and conv_mode 1 return LTSNET_ERR_INVALID_ARG).  Each graph's result
+ *    equals ltsnet_run's for that graph alone (every reduction is split the
+ *    same way whatever the launch shape).
+ *  LTSNET_BATCH_PER_GRAPH: ltsnet_run per graph on cfg->n_workers host
+ *    threads, each with its own stream (largest graphs first).
+ * cfg->max_boxes_used (HOST int32[n_graphs], may be NULL): the largest number
+ * of boxes per dimension each graph's grid had during the run (-1 in the
+ * per-graph mode): equal to max_boxes where that cap bound.  Synchronous
+ * (waits for `stream` first); returns the first error, else
+ * LTSNET_WARN_NOT_CONVERGED if any graph had rows that missed the perplexity
+ * target, else LTSNET_OK.
  * ------------------------------------------------------------------------- */
+#define LTSNET_BATCH_ONE_LAUNCH 0
+#define LTSNET_BATCH_PER_GRAPH 1
+typedef struct {
+    int32_t mode;            /* LTSNET_BATCH_* */
+    int32_t n_workers;       /* host threads, 1..64 */
+    int32_t fft_blocks;      /* blocks per graph of the FFT passes, 0..64 (0: 4) */
+    int32_t spread_blocks;   /* blocks per graph of the box spread, 0..64 (0: 8) */
+    int32_t* max_boxes_used; /* HOST int32[n_graphs] or NULL */
+} ltsnet_batch_config;
+/* The batched calls (Alg. 3 on every graph; the batching itself has no
+ * counterpart in the paper), as described above. */
 size_t ltsnet_run_batched_workspace_size(int32_t n_graphs, const int64_t* vtx_off,
                                          const int64_t* edge_off, const ltsnet_params* p,
-                                         int32_t n_workers);
+                                         const ltsnet_batch_config* cfg);
 ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx_off, const int64_t* edge_off,
                                  const int64_t* row_ptr, const int32_t* col, const ltsnet_params* p,
-                                 float* Y, void* ws, size_t ws_bytes, int32_t n_workers,
+                                 float* Y, void* ws, size_t ws_bytes, const ltsnet_batch_config* cfg,
                                  ltsnet_stream stream);
 
 /* ---------------------------------------------------------------------------

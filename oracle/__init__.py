@@ -77,8 +77,16 @@ def lib():
         L.or_exact_rows.argtypes = [i32, P, P, P, P, f64, i32, P, P, P, P]
         L.or_exact_z.argtypes = [i32, P, P]
         L.or_exact_cost_step.argtypes = [i32, P, P, P, P, f64, i32, i32, f64, P]
+        L.or_set_threads.argtypes = [i32]
+        L.or_set_threads.restype = i32
         _lib = L
     return _lib
+
+
+def set_threads(t: int = 0) -> int:
+    """Threads of the oracle's row-parallel loops (t <= 0 leaves the count
+    unchanged); returns the count in use."""
+    return int(lib().or_set_threads(int(t)))
 
 
 def _p(a: np.ndarray):
@@ -260,7 +268,9 @@ def exact_cost_central_difference(Y, P_row, P_col, P_val, st: Stage, i: int, d: 
                                 _p(o)) != 0:
         raise ValueError("or_exact_cost_step: bad coordinate")
     S = float(np.sum(P_val))
-    dc = (st.lambda_kl * (o[0] + S * (math.log(Z + o[1]) - math.log(Z + o[2])))
+    # ln(Z + o1) - ln(Z + o2) as one log1p: the two logarithms of numbers near
+    # Z would cancel to a few ulps of ln Z
+    dc = (st.lambda_kl * (o[0] + S * math.log1p((o[1] - o[2]) / (Z + o[2])))
           + st.lambda_c / (2.0 * n) * o[4] - st.lambda_r / (4.0 * n * n) * o[3])
     return dc / (2.0 * h)
 
@@ -309,7 +319,9 @@ def grad_pvals(Y, P_row, P_col, P_val, st: Stage, eps: float = EPS_DEFAULT):
     _, parts = exact_cost(Y, P_row, P_col, P_val, st, eps)
     rows = np.repeat(np.arange(n), np.diff(P_row))
     d2 = np.sum((Y[rows] - Y[P_col]) ** 2, axis=1)
-    return st.lambda_kl * (np.log(P_val) + 1.0 + np.log1p(d2) + math.log(parts["Z"]))
+    with np.errstate(divide="ignore"):  # p_e = 0 gives -inf, the derivative's limit
+        lnp = np.log(P_val)
+    return st.lambda_kl * (lnp + 1.0 + np.log1p(d2) + math.log(parts["Z"]))
 
 
 # ---- INTERP (Sec. 2.3 + Sec. 3.3) ----------------------------------------
@@ -524,7 +536,9 @@ def interp_grad_pvals(Y32, P_row, P_col, P_val, st: Stage, gp: GridParams):
     Y = Y32.astype(np.float64)
     rows = np.repeat(np.arange(n), np.diff(P_row))
     d2 = np.sum((Y[rows] - Y[P_col]) ** 2, axis=1)
-    return st.lambda_kl * (np.log(P_val) + 1.0 + np.log1p(d2) + math.log(Z))
+    with np.errstate(divide="ignore"):  # p_e = 0 gives -inf, the derivative's limit
+        lnp = np.log(P_val)
+    return st.lambda_kl * (lnp + 1.0 + np.log1p(d2) + math.log(Z))
 
 
 def update(Y, upd, gains, grad, momentum: float, lr: float):

@@ -15,6 +15,9 @@
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -422,8 +425,9 @@ int or_gather(int32_t n, const float* Y, const float* grid, const int32_t* igrid
     int32_t I = igrid[0], M = igrid[1];
     int64_t MM = (int64_t)M * M;
     if (P > 16) return -1;
-    double wx[16], wy[16];
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < n; ++i) {
+        double wx[16], wy[16];
         float x = Y[2 * i], y = Y[2 * i + 1];
         int32_t bx = or_box(x, lo, h, I), by = or_box(y, lo, h, I);
         or_lagrange((double)x, (double)lo, s, bx, P, wx);
@@ -445,6 +449,7 @@ int or_gather(int32_t n, const float* Y, const float* grid, const int32_t* igrid
 int or_attractive(int32_t n, const float* Y, const int64_t* P_row, const int32_t* P_col,
                   const double* P_val, double* A)
 {
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < n; ++i) {
         double xi = Y[2 * i], yi = Y[2 * i + 1], ax = 0, ay = 0;
         for (int64_t e = P_row[i]; e < P_row[i + 1]; ++e) {
@@ -569,4 +574,18 @@ int or_exact_cost_step(int32_t n, const double* Y, const int64_t* P_row, const i
     out[3] = le;
     out[4] = xp[d] * xp[d] - xm[d] * xm[d];
     return 0;
+}
+
+/* Threads for the row-parallel loops (each row is summed by one thread in a  */
+/* fixed order, so results do not depend on the count); returns the count in  */
+/* use, 1 without OpenMP.                                                     */
+int or_set_threads(int32_t t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+    return omp_get_max_threads();
+#else
+    (void)t;
+    return 1;
+#endif
 }

@@ -65,6 +65,14 @@ class CParams(ctypes.Structure):
                 ("conv_mode", ctypes.c_int32)]
 
 
+class CBatchConfig(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("n_workers", ctypes.c_int32), ("fft_blocks", ctypes.c_int32),
+                ("spread_blocks", ctypes.c_int32), ("max_boxes_used", ctypes.c_void_p)]
+
+
+BATCH_ONE_LAUNCH = 0
+BATCH_PER_GRAPH = 1
+
 _lib = None
 
 
@@ -108,9 +116,10 @@ def lib():
         L.ltsnet_run_workspace_size.restype = sz
         L.ltsnet_run.argtypes = [P, P, i32, pp, P, P, sz, P]
         L.ltsnet_run_host.argtypes = [P, P, i32, pp, P, P, sz, P]
-        L.ltsnet_run_batched_workspace_size.argtypes = [i32, P, P, pp, i32]
+        bc = ctypes.POINTER(CBatchConfig)
+        L.ltsnet_run_batched_workspace_size.argtypes = [i32, P, P, pp, bc]
         L.ltsnet_run_batched_workspace_size.restype = sz
-        L.ltsnet_run_batched.argtypes = [i32, P, P, P, P, pp, P, P, sz, i32, P]
+        L.ltsnet_run_batched.argtypes = [i32, P, P, P, P, pp, P, P, sz, bc, P]
         L.ltsnet_pivot_mds_workspace_size.argtypes = [i32, i32]
         L.ltsnet_pivot_mds_workspace_size.restype = sz
         L.ltsnet_pivot_mds.argtypes = [P, P, i32, i32, i32, f64, P, P, P, ctypes.POINTER(f64), P, sz, P]
@@ -635,15 +644,9 @@ def run(row_ptr, col, Y0, params: Params | None = None, ws=None):
     return Y, rc
 
 
-def run_batched(graphs, Y0s, params: Params | None = None, workers: int = 16):
-    """The method on many independent graphs at once (ltsnet_run_batched).
-    graphs: objects with row_ptr (int64 [n+1]) and col (int32) numpy arrays;
-    Y0s: matching float32 [n,2] arrays.  Returns (Y, vtx_off): all final
-    layouts in one [sum n, 2] CUDA tensor, graph g in rows
-    vtx_off[g]:vtx_off[g+1]."""
+def _batch_arrays(graphs, Y0s):
     import numpy as np
     torch = _torch()
-    params = params or Params()
     ns = [int(g.row_ptr.shape[0] - 1) for g in graphs]
     ms = [int(g.col.shape[0]) for g in graphs]
     vtx_off = np.zeros(len(graphs) + 1, np.int64)
@@ -653,17 +656,85 @@ def run_batched(graphs, Y0s, params: Params | None = None, workers: int = 16):
     rp = torch.from_numpy(np.concatenate([np.asarray(g.row_ptr, np.int64) for g in graphs])).cuda()
     col = torch.from_numpy(np.concatenate([np.asarray(g.col, np.int32) for g in graphs])).cuda()
     Y = torch.from_numpy(np.concatenate([np.asarray(y, np.float32) for y in Y0s])).cuda().contiguous()
+    return vtx_off, edge_off, rp, col, Y
+
+
+def run_batched(graphs, Y0s, params: Params | None = None, workers: int = 16, mode: int = BATCH_ONE_LAUNCH,
+                fft_blocks: int = 0, spread_blocks: int = 0, return_boxes: bool = False):
+    """The method on many independent graphs at once (ltsnet_run_batched).
+    graphs: objects with row_ptr (int64 [n+1]) and col (int32) numpy arrays;
+    Y0s: matching float32 [n,2] arrays.  mode BATCH_ONE_LAUNCH runs the loop
+    with one launch per phase over all graphs (fft_blocks / spread_blocks
+    blocks per graph, 0 = the library's defaults), BATCH_PER_GRAPH one
+    ltsnet_run per graph on `workers` host threads.  Returns (Y, vtx_off) --
+    all final layouts in one [sum n, 2] CUDA tensor, graph g in rows
+    vtx_off[g]:vtx_off[g+1] -- and, if return_boxes, the largest box count
+    per dimension of each graph's grid."""
+    import numpy as np
+    params = params or Params()
+    vtx_off, edge_off, rp, col, Y = _batch_arrays(graphs, Y0s)
     cp = params.to_c()
-    workers = max(1, min(int(workers), 64, len(graphs)))
+    boxes = np.zeros(len(graphs), np.int32)
+    cfg = CBatchConfig(int(mode), max(1, min(int(workers), 64)), int(fft_blocks), int(spread_blocks),
+                       boxes.ctypes.data)
     need = lib().ltsnet_run_batched_workspace_size(len(graphs), vtx_off.ctypes.data, edge_off.ctypes.data,
-                                                    ctypes.byref(cp), workers)
+                                                    ctypes.byref(cp), ctypes.byref(cfg))
     if need == 0:
         raise LtsnetError(-1, "ltsnet_run_batched_workspace_size")
     ws = _workspace(need)
     rc = lib().ltsnet_run_batched(len(graphs), vtx_off.ctypes.data, edge_off.ctypes.data, _ptr(rp), _ptr(col),
-                                  ctypes.byref(cp), _ptr(Y), _ptr(ws), ws.numel(), workers, _stream())
+                                  ctypes.byref(cp), _ptr(Y), _ptr(ws), ws.numel(), ctypes.byref(cfg), _stream())
     _check(rc, "ltsnet_run_batched")
-    return Y, vtx_off
+    return (Y, vtx_off, boxes) if return_boxes else (Y, vtx_off)
+
+
+def _tune_key(graphs, params: Params) -> str:
+    """Cache key of a batch: buckets of its median and largest graph size
+    (powers of 2), of its grid size (nodes per side at max_boxes) and of its
+    mean entries per row of the graph (powers of 2)."""
+    import numpy as np
+    ns = np.array([int(g.row_ptr.shape[0] - 1) for g in graphs])
+    deg = float(np.mean([g.col.shape[0] / max(1, g.row_ptr.shape[0] - 1) for g in graphs]))
+    b = lambda x: int(np.ceil(np.log2(max(1.0, x))))  # noqa: E731
+    return (f"n{b(np.median(ns))}-{b(ns.max())}_M{params.nodes_per_box * params.max_boxes}_d{b(deg)}"
+            f"_p{params.perplexity:g}")
+
+
+def autotune_batched(graphs, Y0s, params: Params | None = None, cache: str | None = None, iters: int = 40,
+                     candidates=((2, 4), (4, 8), (8, 8), (8, 16), (16, 16)), workers: int = 16):
+    """Picks the launch shape (FFT blocks, spread blocks per graph) of the
+    one-launch batched form by timing each candidate on the batch itself
+    (`iters` iterations of the default schedule's second stage) and keeps the
+    fastest in a JSON cache keyed by _tune_key.  Returns (fft_blocks,
+    spread_blocks, timings)."""
+    import json
+    import os
+    import time
+    torch = _torch()
+    params = params or Params()
+    key = _tune_key(graphs, params)
+    table = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            table = json.load(f)
+        if key in table:
+            return tuple(table[key]["best"]) + (table[key]["ms"],)
+    probe = Params(**{**params.__dict__, "stages": [Stage(iters, 1.0, 0.01, 0.6, 1.0, 0.8)]})
+    ms = {}
+    for fb, sb in candidates:
+        run_batched(graphs, Y0s, probe, workers=workers, fft_blocks=fb, spread_blocks=sb)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run_batched(graphs, Y0s, probe, workers=workers, fft_blocks=fb, spread_blocks=sb)
+        torch.cuda.synchronize()
+        ms[f"{fb},{sb}"] = round((time.perf_counter() - t0) * 1e3, 2)
+    best = min(ms, key=ms.get)
+    fb, sb = (int(x) for x in best.split(","))
+    if cache:
+        table[key] = {"best": [fb, sb], "ms": ms}
+        with open(cache, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+    return fb, sb, ms
 
 
 def run_host(row_ptr, col, Y, params: Params | None = None, ws=None):

@@ -293,7 +293,7 @@ __device__ __forceinline__ int box_hash_slot(BoxHash& H, int box)
 // is in use -- the points per box, aggregated per tile of kBoxTile points in
 // a shared-memory hash table and added to bcnt, which the previous
 // iteration's last kernel (or the workspace reset) left zero.
-__global__ void __launch_bounds__(kBoxThreads) k_setup(const int32_t* __restrict__ bounds_cur,
+__device__ __forceinline__ void k_setup_body(const int32_t* __restrict__ bounds_cur,
                                                        int32_t* __restrict__ bounds_next, GridDev* G,
                                                        float2* __restrict__ tw, const float2* __restrict__ Y,
                                                        int32_t* __restrict__ bcnt, int32_t n, float bwm, int min_boxes,
@@ -316,6 +316,7 @@ __global__ void __launch_bounds__(kBoxThreads) k_setup(const int32_t* __restrict
             G->ihf[c] = g.ihf[c];
         }
         G->ticket = 0;
+        G->imax = max(G->imax, g.I);
         G->nheavy = 0;
         G->nitems = 0;
         G->scan_ticket = 0;
@@ -364,6 +365,15 @@ __global__ void __launch_bounds__(kBoxThreads) k_setup(const int32_t* __restrict
             if (H.key[k] >= 0) atomicAdd(&bcnt[H.key[k]], H.val[k]);
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(kBoxThreads) k_setup(const int32_t* __restrict__ bounds_cur,
+                                                       int32_t* __restrict__ bounds_next, GridDev* G,
+                                                       float2* __restrict__ tw, const float2* __restrict__ Y,
+                                                       int32_t* __restrict__ bcnt, int32_t n, float bwm, int min_boxes,
+                                                       int max_boxes, int P, int count)
+{
+    k_setup_body(bounds_cur, bounds_next, G, tw, Y, bcnt, n, bwm, min_boxes, max_boxes, P, count);
 }
 
 // ---- deterministic spread: box sort, then integer sums per box ----
@@ -457,7 +467,7 @@ __device__ __forceinline__ void list_heavy(GridDev* __restrict__ G, int b, int v
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_box_scan(GridDev* __restrict__ G, const int32_t* __restrict__ bcnt,
+__device__ __forceinline__ void k_box_scan_body(GridDev* __restrict__ G, const int32_t* __restrict__ bcnt,
                                                            int32_t* __restrict__ bcur, int32_t* __restrict__ btot,
                                                            int32_t* __restrict__ bpre, int32_t* __restrict__ heavy,
                                                            int2* __restrict__ items)
@@ -502,10 +512,18 @@ __global__ void __launch_bounds__(kScanThreads) k_box_scan(GridDev* __restrict__
     if (threadIdx.x == 0) G->scan_ticket = 0;
 }
 
+__global__ void __launch_bounds__(kScanThreads) k_box_scan(GridDev* __restrict__ G, const int32_t* __restrict__ bcnt,
+                                                           int32_t* __restrict__ bcur, int32_t* __restrict__ btot,
+                                                           int32_t* __restrict__ bpre, int32_t* __restrict__ heavy,
+                                                           int2* __restrict__ items)
+{
+    k_box_scan_body(G, bcnt, bcur, btot, bpre, heavy, items);
+}
+
 // Same tiles and hash table as the counting in k_setup: each box a tile touches reserves
 // its range once (one global atomic), and the tile's points of that box take
 // consecutive places in it.
-__global__ void __launch_bounds__(kBoxThreads) k_box_scatter(const float2* __restrict__ Y, int32_t n,
+__device__ __forceinline__ void k_box_scatter_body(const float2* __restrict__ Y, int32_t n,
                                                              const GridDev* __restrict__ G,
                                                              int32_t* __restrict__ bcur,
                                                              const int32_t* __restrict__ bpre,
@@ -561,6 +579,15 @@ __global__ void __launch_bounds__(kBoxThreads) k_box_scatter(const float2* __res
         }
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(kBoxThreads) k_box_scatter(const float2* __restrict__ Y, int32_t n,
+                                                             const GridDev* __restrict__ G,
+                                                             int32_t* __restrict__ bcur,
+                                                             const int32_t* __restrict__ bpre,
+                                                             float2* __restrict__ su)
+{
+    k_box_scatter_body(Y, n, G, bcur, bpre, su);
 }
 
 // |v| < 2^63 to FP32 with integer operations only (two roundings, relative
@@ -632,7 +659,7 @@ __device__ __forceinline__ void add_point_row_q(float2 u, int bb, const float* h
 // Integer sums make the grid independent of the order of the points within
 // a box and of which warp finishes when.
 template <int P>
-__global__ void __launch_bounds__(256) k_box_spread(const float2* __restrict__ su, const int32_t* __restrict__ bcnt,
+__device__ __forceinline__ void k_box_spread_body(const float2* __restrict__ su, const int32_t* __restrict__ bcnt,
                                                     const int32_t* __restrict__ bcur,
                                                     const int32_t* __restrict__ bpre,
                                                     const int32_t* __restrict__ heavy,
@@ -759,6 +786,18 @@ __global__ void __launch_bounds__(256) k_box_spread(const float2* __restrict__ s
 }
 
 template <int P>
+__global__ void __launch_bounds__(256) k_box_spread(const float2* __restrict__ su, const int32_t* __restrict__ bcnt,
+                                                    const int32_t* __restrict__ bcur,
+                                                    const int32_t* __restrict__ bpre,
+                                                    const int32_t* __restrict__ heavy,
+                                                    const int2* __restrict__ items, long long* __restrict__ hacc,
+                                                    int32_t* __restrict__ hticket, const GridDev* __restrict__ G,
+                                                    float4* __restrict__ wflt)
+{
+    k_box_spread_body<P>(su, bcnt, bcur, bpre, heavy, items, hacc, hticket, G, wflt);
+}
+
+template <int P>
 __global__ void k_spread_atomic(const float2* __restrict__ Y, int32_t n, const GridDev* __restrict__ G,
                                 float4* __restrict__ wflt)
 {
@@ -820,7 +859,7 @@ constexpr float kLnScale = 1.0f / 1024.0f;  // ln(eps + d^2) packed beside K1, s
 //   q = 2: K2 dx + i Ke dx / 8
 // transformed along x; columns kx in [0, L/2] are kept (all five kernels are
 // even or odd in x, so the other half follows by symmetry).
-__global__ void k_spec_rows(const GridDev* __restrict__ Gp, const float2* __restrict__ tw, float eps,
+__device__ __forceinline__ void k_spec_rows_body(const GridDev* __restrict__ Gp, const float2* __restrict__ tw, float eps,
                             float2* __restrict__ krow, int sm_f2)
 {
     extern __shared__ float2 smf[];
@@ -865,11 +904,17 @@ __global__ void k_spec_rows(const GridDev* __restrict__ Gp, const float2* __rest
     }
 }
 
+__global__ void __launch_bounds__(1024) k_spec_rows(const GridDev* __restrict__ Gp, const float2* __restrict__ tw, float eps,
+                            float2* __restrict__ krow, int sm_f2)
+{
+    k_spec_rows_body(Gp, tw, eps, krow, sm_f2);
+}
+
 // Kernel spectra, pass 2: columns kx in [0, L/2], scaled by 1/L^2 (the inverse
 // transforms are unnormalised).  khat[f][ky][kx], f = 0: K2^, 1: Ke^, 2: K1^,
 // 5: (ln(eps + d^2))^ (real), 3: Im (K2 dx)^, 4: Im (Ke dx)^ (those two
 // spectra are imaginary).
-__global__ void k_spec_cols(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
+__device__ __forceinline__ void k_spec_cols_body(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
                             const float2* __restrict__ krow, float* __restrict__ khat, int sm_f2)
 {
     extern __shared__ float2 smf[];
@@ -915,10 +960,16 @@ __global__ void k_spec_cols(const GridDev* __restrict__ Gp, const float2* __rest
     }
 }
 
+__global__ void __launch_bounds__(1024) k_spec_cols(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
+                            const float2* __restrict__ krow, float* __restrict__ khat, int sm_f2)
+{
+    k_spec_cols_body(Gp, tw, krow, khat, sm_f2);
+}
+
 // Row FFTs of the charge grids S0, S1x, S1y, S2 (node-local moments), packed
 // two real rows per complex line (S0 + i S1x, S1y + i S2) and separated by
 // Hermitian symmetry into half spectra srow[g][ty][kx], kx in [0, L/2].
-__global__ void k_conv_rows_fwd(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
+__device__ __forceinline__ void k_conv_rows_fwd_body(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
                                 const float4* __restrict__ wflt, float2* __restrict__ srow, int sm_f2)
 {
     extern __shared__ float2 smf[];
@@ -962,6 +1013,12 @@ __global__ void k_conv_rows_fwd(const GridDev* __restrict__ Gp, const float2* __
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(1024) k_conv_rows_fwd(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
+                                const float4* __restrict__ wflt, float2* __restrict__ srow, int sm_f2)
+{
+    k_conv_rows_fwd_body(Gp, tw, wflt, srow, sm_f2);
 }
 
 // Column pass, kx in [0, L/2]: FFT along y of the four charge spectra, the
@@ -1039,10 +1096,36 @@ __device__ __forceinline__ double block_sum_double(double v, double* red)
     return r;
 }
 
-constexpr int kColThreads = 512;  // the column pass runs 4 and then 6 lines of a column at once
+// Z + n and the entropy double sum's terms of one column kx (Parseval over
+// the half spectra, FP32 terms summed in FP64 by the block in a fixed order)
+// into zcol[kx] and zcol[H + kx].  All threads of the block call it.
+__device__ __forceinline__ void column_sums(const float2* S0, const float2* S1x, const float2* S1y, const float2* S2,
+                                            int kx, int L, int H, const float* __restrict__ K2h,
+                                            const float* __restrict__ K1h, const float* __restrict__ D2h,
+                                            const float* __restrict__ Klh, float s2, double* __restrict__ zcol,
+                                            double* red)
+{
+    const float wgt = (kx == 0 || 2 * kx == L) ? 1.0f : 2.0f;
+    double zp = 0.0, lp = 0.0;
+    for (int ky = threadIdx.x; ky < L; ky += blockDim.x) {
+        const int64_t o = (int64_t)ky * H + kx;
+        const float2 s0 = S0[ky];
+        zp += (double)(wgt * z_term(s0, S1x[ky], S1y[ky], S2[ky], K2h[o], K1h[o], D2h[o],
+                                    odd_transposed(D2h, kx, ky, L, H), s2));
+        lp += (double)(wgt * Klh[o] * (s0.x * s0.x + s0.y * s0.y));
+    }
+    const double zs = block_sum_double(zp, red);
+    const double ls = block_sum_double(lp, red);
+    if (threadIdx.x == 0) {
+        zcol[kx] = zs;
+        zcol[H + kx] = ls;
+    }
+}
 
-__global__ void __launch_bounds__(kColThreads) k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const float2* __restrict__ srow,
-                            const float* __restrict__ khat, float2* __restrict__ ucol, double* __restrict__ zblk,
+constexpr int kColThreads = 1024;  // the column pass runs 4 and then 6 lines of a column at once
+
+__device__ __forceinline__ void k_conv_cols_body(GridDev* Gp, const float2* __restrict__ tw, const float2* __restrict__ srow,
+                            const float* __restrict__ khat, float2* __restrict__ ucol, double* __restrict__ zcol,
                             int32_t n, int sm_f2)
 {
     extern __shared__ float2 smf[];
@@ -1060,7 +1143,6 @@ __global__ void __launch_bounds__(kColThreads) k_conv_cols(GridDev* Gp, const fl
     const float* D2h = khat + 3 * LH;
     const float* Deh = khat + 4 * LH;
     const float* Klh = khat + 5 * LH;
-    double zacc = 0.0, lacc = 0.0;  // Z + n; sum_t S0 (Kl * S0) (Parseval)
     int beg, end;
     block_range(H, beg, end);
     // Batched: 4 spectra + 6 products + 6 work lines per column, two FFT calls.
@@ -1091,19 +1173,17 @@ __global__ void __launch_bounds__(kColThreads) k_conv_cols(GridDev* Gp, const fl
             for (int ky = threadIdx.x; ky < L; ky += blockDim.x) {
                 for (int c = 0; c < nc; ++c) {
                     const int kx = k0 + c;
-                    const int64_t o = (int64_t)ky * H + kx;
                     const float2 s0 = SP[(0 * nc + c) * L + ky], s1x = SP[(1 * nc + c) * L + ky];
-                    const float2 s1y = SP[(2 * nc + c) * L + ky], s2v = SP[(3 * nc + c) * L + ky];
-                    const float wgt = (kx == 0 || 2 * kx == L) ? 1.0f : 2.0f;
-                    zacc += (double)(wgt * z_term(s0, s1x, s1y, s2v, K2h[o], K1h[o], D2h[o],
-                                                  odd_transposed(D2h, kx, ky, L, H), s2));
-                    lacc += (double)(wgt * Klh[o] * (s0.x * s0.x + s0.y * s0.y));
+                    const float2 s1y = SP[(2 * nc + c) * L + ky];
 #pragma unroll
                     for (int q = 0; q < 6; ++q)
                         PR[(q * nc + c) * L + ky] = conv_product(q, s0, s1x, s1y, K2h, Keh, D2h, Deh, kx, ky, L, H);
                 }
             }
             __syncthreads();
+            for (int c = 0; c < nc; ++c)
+                column_sums(SP + (0 * nc + c) * L, SP + (1 * nc + c) * L, SP + (2 * nc + c) * L,
+                            SP + (3 * nc + c) * L, k0 + c, L, H, K2h, K1h, D2h, Klh, s2, zcol, red);
             float2* R2 = fft_lines(PR, PP, 6 * nc, L, G, stw);
             for (int y = threadIdx.x; y < M; y += blockDim.x) {
                 float2* dst = ucol + (int64_t)y * H + k0;
@@ -1137,17 +1217,10 @@ __global__ void __launch_bounds__(kColThreads) k_conv_cols(GridDev* Gp, const fl
             }
             float2* wa = pool[4];
             float2* wb = pool[5];
-            for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
-                const int ky = idx / nl, line = idx - ky * nl;
-                const int kx = k0 + line;
-                const int64_t o = (int64_t)ky * H + kx;
-                const float wgt = (kx == 0 || 2 * kx == L) ? 1.0f : 2.0f;
-                zacc += (double)(wgt * z_term(spec[0][line * L + ky], spec[1][line * L + ky], spec[2][line * L + ky],
-                                     spec[3][line * L + ky], K2h[o], K1h[o], D2h[o],
-                                     odd_transposed(D2h, kx, ky, L, H), s2));
-                const float2 s0 = spec[0][line * L + ky];
-                lacc += (double)(wgt * Klh[o] * (s0.x * s0.x + s0.y * s0.y));
-            }
+            __syncthreads();
+            for (int line = 0; line < nl; ++line)
+                column_sums(spec[0] + line * L, spec[1] + line * L, spec[2] + line * L, spec[3] + line * L,
+                            k0 + line, L, H, K2h, K1h, D2h, Klh, s2, zcol, red);
             for (int q = 0; q < 6; ++q) {
                 __syncthreads();
                 for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
@@ -1164,13 +1237,10 @@ __global__ void __launch_bounds__(kColThreads) k_conv_cols(GridDev* Gp, const fl
             }
         }
     }
-    // block sums of both accumulators (one shared array, in turn), then the
-    // last block to finish adds the block sums in block order
-    const double zsum = block_sum_double(zacc, red);
-    const double lsum = block_sum_double(lacc, red);
+    // the last block to finish adds the column sums in column order (a
+    // result that does not depend on how the columns were split over blocks)
+    __syncthreads();
     if (threadIdx.x == 0) {
-        zblk[blockIdx.x] = zsum;
-        zblk[512 + blockIdx.x] = lsum;
         __threadfence();
         last = atomicAdd(&Gp->ticket, 1) == (int)gridDim.x - 1;
     }
@@ -1178,9 +1248,9 @@ __global__ void __launch_bounds__(kColThreads) k_conv_cols(GridDev* Gp, const fl
     if (last) {
         __threadfence();
         double v = 0.0, v2 = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-            v += ((volatile double*)zblk)[b];
-            v2 += ((volatile double*)zblk)[512 + b];
+        for (int kx = threadIdx.x; kx < H; kx += blockDim.x) {
+            v += ((volatile double*)zcol)[kx];
+            v2 += ((volatile double*)zcol)[H + kx];
         }
         const double zt = block_sum_double(v, red);
         const double lt2 = block_sum_double(v2, red);
@@ -1193,12 +1263,19 @@ __global__ void __launch_bounds__(kColThreads) k_conv_cols(GridDev* Gp, const fl
     }
 }
 
+__global__ void __launch_bounds__(kColThreads) k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const float2* __restrict__ srow,
+                            const float* __restrict__ khat, float2* __restrict__ ucol, double* __restrict__ zcol,
+                            int32_t n, int sm_f2)
+{
+    k_conv_cols_body(Gp, tw, srow, khat, ucol, zcol, n, sm_f2);
+}
+
 // Inverse row FFTs, three packed lines per row (U0 + i U1, U2 + i U3,
 // U4 + i U5), each half spectrum extended by Hermitian symmetry.  Fields per
 // node: f0 = F0, f1 = Vx, f2 = Vy, f3 = Fe0, f4 = Vex, f5 = Vey, f6 = f7 = 0.
 // The plain (atomic) spread also needs the charge grid cleared for the next
 // iteration; its readers have finished, so that is done here.
-__global__ void k_conv_rows_inv(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
+__device__ __forceinline__ void k_conv_rows_inv_body(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
                                 const float2* __restrict__ ucol, float* __restrict__ fields,
                                 float4* __restrict__ wflt, int32_t* __restrict__ bcnt, int plain, int sm_f2)
 {
@@ -1255,6 +1332,13 @@ __global__ void k_conv_rows_inv(const GridDev* __restrict__ Gp, const float2* __
         if (u >= M) break;  // units (0, row) cover every row once
         for (int x = threadIdx.x; x < M; x += blockDim.x) wflt[(int64_t)u * M + x] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+}
+
+__global__ void __launch_bounds__(1024) k_conv_rows_inv(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
+                                const float2* __restrict__ ucol, float* __restrict__ fields,
+                                float4* __restrict__ wflt, int32_t* __restrict__ bcnt, int plain, int sm_f2)
+{
+    k_conv_rows_inv_body(Gp, tw, ucol, fields, wflt, bcnt, plain, sm_f2);
 }
 
 __global__ void k_bounds_init(int32_t* b)
@@ -1323,7 +1407,69 @@ __global__ void k_psum(const float* __restrict__ v, const int64_t* __restrict__ 
     }
 }
 
-constexpr int kFftThreads = 256;
+constexpr int kFftThreads = 1024;
+
+// ---- batched wrappers: graph = blockIdx.y (BatchGraph), each graph's work
+// split over gridDim.x blocks as in the single-graph launches ----
+__device__ __forceinline__ const float2* layout_of(const BatchGraph& b, int parity) { return parity ? b.w.yalt : b.Y; }
+
+__global__ void __launch_bounds__(kBoxThreads) k_setup_b(const BatchGraph* __restrict__ bg, int parity, float bwm,
+                                                         int min_boxes, int max_boxes, int P)
+{
+    const BatchGraph& b = bg[blockIdx.y];
+    k_setup_body(b.w.bounds + 2 * parity, b.w.bounds + 2 * (parity ^ 1), b.w.g, b.w.tw, layout_of(b, parity),
+                 b.w.bcnt, b.n, bwm, min_boxes, max_boxes, P, 1);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_box_scan_b(const BatchGraph* __restrict__ bg)
+{
+    const BatchGraph& b = bg[blockIdx.y];
+    k_box_scan_body(b.w.g, b.w.bcnt, b.w.bcur, b.w.btot, b.w.bpre, b.w.heavy, b.w.items);
+}
+
+__global__ void __launch_bounds__(kBoxThreads) k_box_scatter_b(const BatchGraph* __restrict__ bg, int parity)
+{
+    const BatchGraph& b = bg[blockIdx.y];
+    k_box_scatter_body(layout_of(b, parity), b.n, b.w.g, b.w.bcur, b.w.bpre, b.w.su);
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_box_spread_b(const BatchGraph* __restrict__ bg)
+{
+    const BatchGraph& b = bg[blockIdx.y];
+    k_box_spread_body<P>(b.w.su, b.w.bcnt, b.w.bcur, b.w.bpre, b.w.heavy, b.w.items, b.w.hacc, b.w.hticket, b.w.g,
+                         b.w.wflt);
+}
+
+__global__ void __launch_bounds__(1024) k_spec_rows_b(const BatchGraph* __restrict__ bg, float eps, int sm_f2)
+{
+    const BatchGraph& b = bg[blockIdx.y];
+    k_spec_rows_body(b.w.g, b.w.tw, eps, b.w.krow, sm_f2);
+}
+
+__global__ void __launch_bounds__(1024) k_spec_cols_b(const BatchGraph* __restrict__ bg, int sm_f2)
+{
+    const BatchGraph& b = bg[blockIdx.y];
+    k_spec_cols_body(b.w.g, b.w.tw, b.w.krow, b.w.khat, sm_f2);
+}
+
+__global__ void __launch_bounds__(1024) k_conv_rows_fwd_b(const BatchGraph* __restrict__ bg, int sm_f2)
+{
+    const BatchGraph& b = bg[blockIdx.y];
+    k_conv_rows_fwd_body(b.w.g, b.w.tw, b.w.wflt, b.w.srow, sm_f2);
+}
+
+__global__ void __launch_bounds__(kColThreads) k_conv_cols_b(const BatchGraph* __restrict__ bg, int sm_f2)
+{
+    const BatchGraph& b = bg[blockIdx.y];
+    k_conv_cols_body(b.w.g, b.w.tw, b.w.srow, b.w.khat, b.w.ucol, b.w.zcol, b.n, sm_f2);
+}
+
+__global__ void __launch_bounds__(1024) k_conv_rows_inv_b(const BatchGraph* __restrict__ bg, int sm_f2)
+{
+    const BatchGraph& b = bg[blockIdx.y];
+    k_conv_rows_inv_body(b.w.g, b.w.tw, b.w.ucol, b.w.fields, b.w.wflt, b.w.bcnt, 0, sm_f2);
+}
 constexpr int kPsumBlocks = 304;
 
 // Room for the twiddles plus six lines of the longest length (the column
@@ -1376,6 +1522,7 @@ IterWs iter_carve(Carve& c, const IterShape& sh)
     w.ucol = c.take<float2>(6 * MH);
     w.fields = c.take<float>(MM * kFieldStride);
     w.zblk = c.take<double>(1024);
+    w.zcol = c.take<double>(2 * (sh.Lmax / 2 + 1));
     w.sblk = c.take<double>(1024);
     w.yalt = c.take<float2>(sh.n);
     w.phi = c.take<float>((int64_t)sh.n * 8);
@@ -1393,6 +1540,7 @@ cudaError_t iter_reset(const IterWs& w, const IterShape& sh, cudaStream_t s)
 {
     cudaError_t e;
     if ((e = cudaMemsetAsync(w.st, 0, sizeof(StatusBlock), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(&w.g->imax, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.wflt, 0, sizeof(float4) * (size_t)sh.Mmax * sh.Mmax, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.hticket, 0, sizeof(int32_t) * (size_t)sh.hcap, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.bcnt, 0, sizeof(int32_t) * (size_t)sh.max_boxes * sh.max_boxes, s)) != cudaSuccess)
@@ -1436,7 +1584,7 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
     count_launches(1);
     const size_t fsm = fft_smem_bytes(sh.Lmax);
     const int f2 = (int)(fsm / sizeof(float2));
-    const int fb = std::min(num_sms(), 512);  // FFT blocks: one per SM; zblk holds 512 partials
+    const int fb = num_sms();  // FFT blocks: one per SM
     // The kernel spectra need only the grid parameters: unless kernels are
     // being timed one by one, they run on a side stream next to the spread
     // and join before the column pass.
@@ -1507,7 +1655,7 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
         cudaError_t e2 = cudaStreamWaitEvent(s, aux->join, 0);
         if (e2 != cudaSuccess) return e2;
     }
-    k_conv_cols<<<fb, kColThreads, fsm, s>>>(w.g, w.tw, w.srow, w.khat, w.ucol, w.zblk, n, f2);
+    k_conv_cols<<<fb, kColThreads, fsm, s>>>(w.g, w.tw, w.srow, w.khat, w.ucol, w.zcol, n, f2);
     k_conv_rows_inv<<<fb, kFftThreads, fsm, s>>>(w.g, w.tw, w.ucol, w.fields, w.wflt, w.bcnt, plain ? 1 : 0, f2);
     count_launches(3);
     profile_stop(LTSNET_KERNEL_CONV, s);
@@ -1523,7 +1671,65 @@ cudaError_t grid_set_smem_attrs()
     if ((e = cudaFuncSetAttribute(k_conv_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
     if ((e = cudaFuncSetAttribute(k_conv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
     if ((e = cudaFuncSetAttribute(k_conv_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
+    if ((e = cudaFuncSetAttribute(k_spec_rows_b, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
+    if ((e = cudaFuncSetAttribute(k_spec_cols_b, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
+    if ((e = cudaFuncSetAttribute(k_conv_rows_fwd_b, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
+    if ((e = cudaFuncSetAttribute(k_conv_cols_b, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
+    if ((e = cudaFuncSetAttribute(k_conv_rows_inv_b, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
     return cudaSuccess;
+}
+
+// The grid phase of one iteration for every graph of a batch: the same
+// kernels and order as launch_grid_phase, each launch covering all graphs
+// (grid.y = graph).  sh is the shape of the batch's largest grid (shared
+// memory of the FFT passes); point-indexed kernels get enough blocks per
+// graph for the largest graph and the others leave theirs idle.
+cudaError_t launch_grid_phase_batched(const BatchGraph* bg, int32_t ng, const BatchShape& bs, const IterShape& sh,
+                                      const ltsnet_params* p, int parity, cudaStream_t s)
+{
+    const int P = sh.P;
+    const unsigned tiles = (unsigned)std::max<int64_t>(1, ((int64_t)bs.max_n + kBoxTile - 1) / kBoxTile);
+    const dim3 gpt(tiles, (unsigned)ng);
+    k_setup_b<<<gpt, kBoxThreads, 0, s>>>(bg, parity, p->box_width_max, p->min_boxes, p->max_boxes, P);
+    count_launches(1);
+    const size_t fsm = fft_smem_bytes(sh.Lmax);
+    const int f2 = (int)(fsm / sizeof(float2));
+    const dim3 gfft((unsigned)bs.fft_blocks, (unsigned)ng);
+    AuxStreams* aux = nullptr;
+    const bool fork = !profiling_active() && aux_streams(&aux) == cudaSuccess;
+    cudaError_t e;
+    if (fork) {
+        if ((e = cudaEventRecord(aux->fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(aux->branch, aux->fork, 0)) != cudaSuccess) return e;
+        k_spec_rows_b<<<gfft, kFftThreads, fsm, aux->branch>>>(bg, p->eps, f2);
+        k_spec_cols_b<<<gfft, kFftThreads, fsm, aux->branch>>>(bg, f2);
+        count_launches(2);
+        if ((e = cudaEventRecord(aux->join, aux->branch)) != cudaSuccess) return e;
+    }
+    const int64_t nb = (int64_t)sh.max_boxes * sh.max_boxes;
+    const unsigned nsb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(4, (nb + kScanBlock - 1) / kScanBlock));
+    k_box_scan_b<<<dim3(nsb, (unsigned)ng), kScanThreads, 0, s>>>(bg);
+    k_box_scatter_b<<<gpt, kBoxThreads, 0, s>>>(bg, parity);
+    const dim3 gsp((unsigned)bs.spread_blocks, (unsigned)ng);
+    switch (P) {
+        case 2: k_box_spread_b<2><<<gsp, 256, 0, s>>>(bg); break;
+        case 3: k_box_spread_b<3><<<gsp, 256, 0, s>>>(bg); break;
+        case 4: k_box_spread_b<4><<<gsp, 256, 0, s>>>(bg); break;
+        default: k_box_spread_b<5><<<gsp, 256, 0, s>>>(bg); break;
+    }
+    count_launches(3);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!fork) {
+        k_spec_rows_b<<<gfft, kFftThreads, fsm, s>>>(bg, p->eps, f2);
+        k_spec_cols_b<<<gfft, kFftThreads, fsm, s>>>(bg, f2);
+        count_launches(2);
+    }
+    k_conv_rows_fwd_b<<<gfft, kFftThreads, fsm, s>>>(bg, f2);
+    if (fork && (e = cudaStreamWaitEvent(s, aux->join, 0)) != cudaSuccess) return e;
+    k_conv_cols_b<<<gfft, kColThreads, fsm, s>>>(bg, f2);
+    k_conv_rows_inv_b<<<gfft, kFftThreads, fsm, s>>>(bg, f2);
+    count_launches(3);
+    return cudaGetLastError();
 }
 
 }  // namespace lt

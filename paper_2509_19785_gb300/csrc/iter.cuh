@@ -30,6 +30,7 @@ struct GridDev {
     int32_t scan_ticket;         // last-block counter of the box scan
     int32_t nheavy;              // boxes summed by warps
     int32_t nitems;              // their segments
+    int32_t imax;                // largest I of the run so far (cleared by iter_reset)
 };
 
 // Per-iteration scalars of the gradient, precomputed on the host in FP64:
@@ -75,7 +76,8 @@ struct IterWs {
     float2* srow;        // 4 * M_max * H row half spectra of S0, S1x, S1y, S2
     float2* ucol;        // 6 * M_max * H column results
     float* fields;       // M_max^2 * 8
-    double* zblk;        // per-block Z partials
+    double* zblk;        // per-block Z partials (DFT-GEMM products)
+    double* zcol;        // per-column Z and entropy-sum terms of the FFT column pass
     double* sblk;        // per-block sum(P) partials
     float2* yalt;        // n, ping-pong layout
     float* phi;          // n * 8 (plain form gather output)
@@ -90,6 +92,31 @@ struct IterShape {
     int32_t Mmax, Lmax;
     int64_t hcap;  // capacity of the heavy-box lists
     int conv_mode;
+};
+
+// One graph of a batched run: its P, layouts, optimiser state, stage
+// coefficients and iteration workspace.  The batched kernels serve every
+// graph of a batch in one launch, graph = blockIdx.y, each graph's work
+// split over gridDim.x blocks exactly as in a single-graph launch.
+struct BatchGraph {
+    IterWs w;
+    const int64_t* P_row;
+    const int32_t* P_col;
+    const int16_t* P_d16;
+    const float* P_val;
+    float2* Y;  // the layout of parity 0 (w.yalt holds parity 1)
+    float2* upd;
+    float2* gains;
+    Stage st;
+    int32_t n;
+};
+
+// Launch shape of the batched kernels (blocks per graph), chosen by the
+// caller's tuning.
+struct BatchShape {
+    int32_t fft_blocks;     // FFT passes and kernel spectra
+    int32_t spread_blocks;  // box spread
+    int32_t max_n;          // largest graph (sizes the point-indexed grids)
 };
 
 IterShape iter_shape(int32_t n, const ltsnet_params* p);
@@ -218,5 +245,7 @@ cudaError_t launch_dft_prep(const IterWs& w, cudaStream_t s);
 cudaError_t launch_dft_products(const IterWs& w, int32_t n, cudaStream_t s);
 cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet_params* p, const float2* Y,
                               int parity, bool plain, cudaStream_t s);
+cudaError_t launch_grid_phase_batched(const BatchGraph* bg, int32_t ng, const BatchShape& bs, const IterShape& sh,
+                                      const ltsnet_params* p, int parity, cudaStream_t s);
 
 }  // namespace lt

@@ -292,8 +292,8 @@ __device__ __forceinline__ void load_window(Window& w, const int32_t* __restrict
 // finishes its vertex: interpolated repulsion and entropy (gather from the
 // grid), compression, gradient, momentum/gain step, bounds of the next grid.
 template <int P, bool UPDATE, bool D16>
-__global__ void __launch_bounds__(kFusedThreads, 2)
-    k_fused(const int64_t* __restrict__ P_row, const int32_t* __restrict__ P_col, const int16_t* __restrict__ P_d16,
+__device__ __forceinline__ void
+    k_fused_body(const int64_t* __restrict__ P_row, const int32_t* __restrict__ P_col, const int16_t* __restrict__ P_d16,
             const float* __restrict__ P_val,
             int32_t n, const float2* __restrict__ Y, float2* __restrict__ Ynew, float2* __restrict__ upd,
             float2* __restrict__ gains, const GridDev* __restrict__ G, const float* __restrict__ fields, Stage st,
@@ -415,6 +415,31 @@ __global__ void __launch_bounds__(kFusedThreads, 2)
         }
     }
     if (UPDATE) block_bounds(mn, mx, bounds_next);
+}
+
+template <int P, bool UPDATE, bool D16>
+__global__ void __launch_bounds__(kFusedThreads, 2)
+    k_fused(const int64_t* __restrict__ P_row, const int32_t* __restrict__ P_col, const int16_t* __restrict__ P_d16,
+            const float* __restrict__ P_val,
+            int32_t n, const float2* __restrict__ Y, float2* __restrict__ Ynew, float2* __restrict__ upd,
+            float2* __restrict__ gains, const GridDev* __restrict__ G, const float* __restrict__ fields, Stage st,
+            int32_t* __restrict__ bounds_next, float2* __restrict__ grad_out, float* __restrict__ parts,
+            StatusBlock* status, const int32_t* __restrict__ hbase, const float2* __restrict__ hpartial)
+{
+    k_fused_body<P, UPDATE, D16>(P_row, P_col, P_d16, P_val, n, Y, Ynew, upd, gains, G, fields, st, bounds_next,
+                                 grad_out, parts, status, hbase, hpartial);
+}
+
+// The fused point phase of one iteration for every graph of a batch (graph =
+// blockIdx.y), layouts by parity as in one_iteration.
+template <int P, bool D16>
+__global__ void __launch_bounds__(kFusedThreads, 2) k_fused_b(const BatchGraph* __restrict__ bg, int parity)
+{
+    const BatchGraph& b = bg[blockIdx.y];
+    const float2* cur = parity ? b.w.yalt : b.Y;
+    float2* nxt = parity ? b.Y : b.w.yalt;
+    k_fused_body<P, true, D16>(b.P_row, b.P_col, b.P_d16, b.P_val, b.n, cur, nxt, b.upd, b.gains, b.w.g, b.w.fields,
+                               b.st, b.w.bounds + 2 * (parity ^ 1), nullptr, nullptr, b.w.st, nullptr, nullptr);
 }
 
 constexpr size_t kFusedSmem = 0;  // the windows live in registers
@@ -1015,8 +1040,20 @@ RunWs run_carve(Carve& c, int32_t n, int64_t m2, const ltsnet_params* p, bool ho
     return r;
 }
 
-ltsnet_status run_core(const int64_t* row_ptr, const int32_t* col, int32_t n, const ltsnet_params* p, float2* Y,
-                       const RunWs& r, cudaStream_t s)
+// C0 of one graph and the state the loop starts from: partial BFS,
+// calibration, breadth-first renumbering, symmetrisation, int16 columns, long
+// row chunks, update/gains.  *Yw gets the layout the loop works on (Y, or
+// its renumbered copy in r.Y2).
+struct Prepared {
+    bool reordered = false;
+    bool d16 = false;
+    HeavyRows hr;
+    int64_t nnz = 0;
+    float2* Yw = nullptr;
+};
+
+ltsnet_status run_prepare(const int64_t* row_ptr, const int32_t* col, int32_t n, const ltsnet_params* p, float2* Y,
+                          const RunWs& r, cudaStream_t s, Prepared* out)
 {
     const int32_t k = k_of(p);
     ltsnet_status rc = ltsnet_knn_bfs(row_ptr, col, n, k, r.nbr, r.hop, r.cnt, r.st, sizeof(StatusBlock), s);
@@ -1081,25 +1118,135 @@ ltsnet_status run_core(const int64_t* row_ptr, const int32_t* col, int32_t n, co
     k_init_state<<<flat_blocks(n), 256, 0, s>>>(r.upd, r.gains, n);
     count_launches(1);
     LT_CHECK_LAUNCH();
-    const IterShape sh = iter_shape(n, p);
-    Carve ic(r.iter, r.iter_bytes);
-    const IterWs w = iter_carve(ic, sh);
-    LT_CUDA(iter_reset(w, sh, s));
-    const int64_t total = schedule_length(p);
     float2* Yw = Y;
     if (reordered) {
         LT_CUDA(gather_rows2(Y, r.order, n, r.Y2, s));
         Yw = r.Y2;
     }
-    rc = optimize_core(r.P_row, r.P_col, d16 ? r.d16 : nullptr, r.P_val, hr, n, p, Yw, r.upd, r.gains, 0,
-                       (int32_t)total, w, sh, s);
-    if (rc != LTSNET_OK) return rc;
-    if (reordered) LT_CUDA(gather_rows2(r.Y2, r.inv, n, Y, s));
-    ltsnet_status a = read_status(w.st, s);
+    out->reordered = reordered;
+    out->d16 = d16;
+    out->hr = hr;
+    out->nnz = nnz;
+    out->Yw = Yw;
+    return LTSNET_OK;
+}
+
+// After the loop: the layout back in the input's numbering, and the first
+// error (or warning) recorded by the loop's or by C0's kernels.
+ltsnet_status run_finish(int32_t n, float2* Y, const RunWs& r, const Prepared& pr, StatusBlock* iter_st,
+                         cudaStream_t s)
+{
+    if (pr.reordered) LT_CUDA(gather_rows2(r.Y2, r.inv, n, Y, s));
+    ltsnet_status a = read_status(iter_st, s);
     ltsnet_status b = read_status(r.st, s);
     if (a < 0) return a;
-    if (b < 0) return b;
     return b;
+}
+
+ltsnet_status run_core(const int64_t* row_ptr, const int32_t* col, int32_t n, const ltsnet_params* p, float2* Y,
+                       const RunWs& r, cudaStream_t s)
+{
+    Prepared pr;
+    ltsnet_status rc = run_prepare(row_ptr, col, n, p, Y, r, s, &pr);
+    if (rc != LTSNET_OK) return rc;
+    const IterShape sh = iter_shape(n, p);
+    Carve ic(r.iter, r.iter_bytes);
+    const IterWs w = iter_carve(ic, sh);
+    LT_CUDA(iter_reset(w, sh, s));
+    const int64_t total = schedule_length(p);
+    rc = optimize_core(r.P_row, r.P_col, pr.d16 ? r.d16 : nullptr, r.P_val, pr.hr, n, p, pr.Yw, r.upd, r.gains, 0,
+                       (int32_t)total, w, sh, s);
+    if (rc != LTSNET_OK) return rc;
+    return run_finish(n, Y, r, pr, w.st, s);
+}
+
+// The descent loop of a whole batch, one launch per phase over all graphs
+// (ltsnet_run_batched's one-launch mode): the same kernels, order, stage
+// runs and two-iteration CUDA graphs as optimize_core, every launch covering
+// every graph (grid.y = graph).  bg[st] is the device descriptor array of
+// schedule stage st; hg the host copy of stage 0's (for the per-graph
+// start and end steps).
+ltsnet_status batched_loop(BatchGraph* const* bg, const std::vector<BatchGraph>& hg, const BatchShape& bs,
+                           const IterShape& sh, const ltsnet_params* p, bool d16, cudaStream_t s)
+{
+    const int32_t ng = (int32_t)hg.size();
+    LT_CUDA(ensure_attrs());
+    for (const BatchGraph& b : hg) {
+        LT_CUDA(launch_psum(b.w, b.P_row, b.n, b.P_val, s));
+        LT_CUDA(launch_bounds_init(b.w, b.Y, b.n, 0, s));
+    }
+    AuxStreams* aux = nullptr;
+    const bool graphs = !profiling_active() && aux_streams(&aux) == cudaSuccess;
+    const unsigned fblocks = (unsigned)std::max<int64_t>(1, ((int64_t)bs.max_n + kFusedWarps * 32 - 1) / (kFusedWarps * 32));
+    auto iteration = [&](const BatchGraph* dbg, int parity, cudaStream_t st) -> cudaError_t {
+        cudaError_t e = launch_grid_phase_batched(dbg, ng, bs, sh, p, parity, st);
+        if (e != cudaSuccess) return e;
+        profile_start(LTSNET_KERNEL_FUSED_UPDATE, st);
+        const dim3 grid(fblocks, (unsigned)ng);
+#define LT_FB(PP)                                                                              \
+    if (d16) k_fused_b<PP, true><<<grid, kFusedThreads, kFusedSmem, st>>>(dbg, parity);        \
+    else k_fused_b<PP, false><<<grid, kFusedThreads, kFusedSmem, st>>>(dbg, parity)
+        switch (sh.P) {
+            case 2: LT_FB(2); break;
+            case 3: LT_FB(3); break;
+            case 4: LT_FB(4); break;
+            default: LT_FB(5); break;
+        }
+#undef LT_FB
+        count_launches(1);
+        profile_stop(LTSNET_KERNEL_FUSED_UPDATE, st);
+        return cudaGetLastError();
+    };
+    const int64_t total = schedule_length(p);
+    int64_t i = 0;
+    int32_t sidx = 0;
+    while (i < total) {
+        // the schedule's stages in order; zero-length stages are skipped
+        int64_t acc = 0;
+        for (sidx = 0; sidx < p->n_stages; ++sidx) {
+            acc += p->stages[sidx].iters;
+            if (i < acc) break;
+        }
+        const int64_t run = acc - i;
+        const BatchGraph* dbg = bg[sidx];
+        int64_t done = 0;
+        if ((i & 1) && run > 0) {
+            LT_CUDA(iteration(dbg, 1, s));
+            done = 1;
+        }
+        const int64_t pairs = graphs ? (run - done) / 2 : 0;
+        if (pairs >= 2) {
+            const int64_t c0 = ltsnet_launch_count();
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            LT_CUDA(cudaStreamBeginCapture(aux->capture, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = iteration(dbg, 0, aux->capture);
+            if (e == cudaSuccess) e = iteration(dbg, 1, aux->capture);
+            cudaError_t e2 = cudaStreamEndCapture(aux->capture, &graph);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                LT_CUDA(e != cudaSuccess ? e : e2);
+            }
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            LT_CUDA(e);
+            const int64_t per = ltsnet_launch_count() - c0;
+            for (int64_t q = 0; q < pairs; ++q) {
+                e = cudaGraphLaunch(exec, s);
+                if (e != cudaSuccess) break;
+            }
+            cudaGraphExecDestroy(exec);
+            LT_CUDA(e);
+            count_launches(per * (pairs - 1));
+            done += 2 * pairs;
+        }
+        for (; done < run; ++done) LT_CUDA(iteration(dbg, (int)((i + done) & 1), s));
+        i += run;
+    }
+    if (total & 1)
+        for (const BatchGraph& b : hg)
+            LT_CUDA(cudaMemcpyAsync(b.Y, b.w.yalt, sizeof(float2) * (size_t)b.n, cudaMemcpyDeviceToDevice, s));
+    return LTSNET_OK;
 }
 
 }  // namespace
@@ -1265,30 +1412,63 @@ static bool batch_ok(int32_t n_graphs, const int64_t* vtx_off, const int64_t* ed
     return true;
 }
 
+static bool batch_cfg_ok(const ltsnet_batch_config* cfg)
+{
+    return cfg && (cfg->mode == LTSNET_BATCH_ONE_LAUNCH || cfg->mode == LTSNET_BATCH_PER_GRAPH) &&
+           cfg->n_workers >= 1 && cfg->n_workers <= 64 && cfg->fft_blocks >= 0 && cfg->fft_blocks <= 64 &&
+           cfg->spread_blocks >= 0 && cfg->spread_blocks <= 64;
+}
+
+// Workspace of the one-launch mode: a run workspace per graph (C0, P, state,
+// iteration workspace), then one descriptor array per schedule stage.
+static size_t one_launch_slices(int32_t n_graphs, const int64_t* vtx_off, const int64_t* edge_off,
+                                const ltsnet_params* p, std::vector<size_t>* offs)
+{
+    size_t off = 0;
+    for (int32_t g = 0; g < n_graphs; ++g) {
+        const size_t one = ltsnet_run_workspace_size((int32_t)(vtx_off[g + 1] - vtx_off[g]),
+                                                     edge_off[g + 1] - edge_off[g], p);
+        if (one == 0) return 0;
+        if (offs) offs->push_back(off);
+        off += align_up(one, 256);
+    }
+    return off + align_up(sizeof(BatchGraph) * (size_t)n_graphs, 256) * (size_t)p->n_stages;
+}
+
 extern "C" size_t ltsnet_run_batched_workspace_size(int32_t n_graphs, const int64_t* vtx_off,
                                                     const int64_t* edge_off, const ltsnet_params* p,
-                                                    int32_t n_workers)
+                                                    const ltsnet_batch_config* cfg)
 {
     int64_t max_n, max_m;
-    if (!batch_ok(n_graphs, vtx_off, edge_off, max_n, max_m) || n_workers < 1 || n_workers > 64) return 0;
+    if (!params_ok(p) || !batch_cfg_ok(cfg) || !batch_ok(n_graphs, vtx_off, edge_off, max_n, max_m)) return 0;
+    if (cfg->mode == LTSNET_BATCH_ONE_LAUNCH) return one_launch_slices(n_graphs, vtx_off, edge_off, p, nullptr);
     const size_t one = ltsnet_run_workspace_size((int32_t)max_n, max_m, p);
     if (one == 0) return 0;
-    return align_up(one, 256) * (size_t)std::min(n_workers, n_graphs);
+    return align_up(one, 256) * (size_t)std::min(cfg->n_workers, n_graphs);
 }
 
 extern "C" ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx_off, const int64_t* edge_off,
                                             const int64_t* row_ptr, const int32_t* col, const ltsnet_params* p,
-                                            float* Y, void* ws, size_t ws_bytes, int32_t n_workers,
+                                            float* Y, void* ws, size_t ws_bytes, const ltsnet_batch_config* cfg,
                                             ltsnet_stream stream)
 {
     int64_t max_n, max_m;
-    if (!row_ptr || !col || !Y || !ws || !params_ok(p) || n_workers < 1 || n_workers > 64) return LTSNET_ERR_INVALID_ARG;
+    if (!row_ptr || !col || !Y || !ws || !params_ok(p) || !batch_cfg_ok(cfg)) return LTSNET_ERR_INVALID_ARG;
     if (!batch_ok(n_graphs, vtx_off, edge_off, max_n, max_m)) return LTSNET_ERR_INVALID_ARG;
     if (k_of(p) > LTSNET_MAX_K) return LTSNET_ERR_INVALID_ARG;
     if ((uintptr_t)ws & 255) return LTSNET_ERR_WORKSPACE;
-    const int32_t workers = std::min(n_workers, n_graphs);
-    const size_t slice = align_up(ltsnet_run_workspace_size((int32_t)max_n, max_m, p), 256);
-    if (slice == 0 || ws_bytes < slice * (size_t)workers) return LTSNET_ERR_WORKSPACE;
+    const bool one = cfg->mode == LTSNET_BATCH_ONE_LAUNCH;
+    if (one && ((p->flags & LTSNET_FLAG_PLAIN) || p->conv_mode != LTSNET_CONV_FFT)) return LTSNET_ERR_INVALID_ARG;
+    const int32_t workers = std::min(cfg->n_workers, n_graphs);
+    std::vector<size_t> offs;
+    size_t slice = 0;
+    if (one) {
+        const size_t need = one_launch_slices(n_graphs, vtx_off, edge_off, p, &offs);
+        if (need == 0 || ws_bytes < need) return LTSNET_ERR_WORKSPACE;
+    } else {
+        slice = align_up(ltsnet_run_workspace_size((int32_t)max_n, max_m, p), 256);
+        if (slice == 0 || ws_bytes < slice * (size_t)workers) return LTSNET_ERR_WORKSPACE;
+    }
     int dev = 0;
     LT_CUDA(cudaGetDevice(&dev));
     // inputs written on the caller's stream are visible to the workers
@@ -1306,22 +1486,35 @@ extern "C" ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx
         while ((rc < 0 && cur >= 0) || (rc > 0 && cur == 0))
             if (first_err.compare_exchange_weak(cur, rc)) break;
     };
+    auto carve_graph = [&](int32_t g, void* base, size_t bytes, RunWs* r) {
+        Carve c(base, bytes);
+        *r = run_carve(c, (int32_t)(vtx_off[g + 1] - vtx_off[g]), 0, p, false);
+        return c.ok();
+    };
+    // per-graph mode: every graph through run_core on the workers; one-launch
+    // mode: the workers run C0 of every graph into its own slice
+    std::vector<Prepared> prep(one ? n_graphs : 0);
     auto work = [&](int32_t wi) {
         cudaStream_t s = nullptr;
         if (cudaSetDevice(dev) != cudaSuccess || cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
             note((int)LTSNET_ERR_CUDA);
             return;
         }
-        void* mine = (char*)ws + slice * (size_t)wi;
         for (int32_t t = next.fetch_add(1); t < n_graphs; t = next.fetch_add(1)) {
             const int32_t g = order[t];
             const int32_t ng = (int32_t)(vtx_off[g + 1] - vtx_off[g]);
-            Carve c(mine, slice);
-            RunWs r = run_carve(c, ng, 0, p, false);
+            RunWs r;
+            void* base = one ? (char*)ws + offs[g] : (char*)ws + slice * (size_t)wi;
+            const size_t bytes = one ? align_up(ltsnet_run_workspace_size(ng, edge_off[g + 1] - edge_off[g], p), 256)
+                                     : slice;
             ltsnet_status rc = LTSNET_OK;
-            if (!c.ok()) rc = LTSNET_ERR_WORKSPACE;
+            if (!carve_graph(g, base, bytes, &r)) rc = LTSNET_ERR_WORKSPACE;
             else if (cudaMemsetAsync(r.st, 0, sizeof(StatusBlock), s) != cudaSuccess) rc = LTSNET_ERR_CUDA;
-            else rc = run_core(row_ptr + vtx_off[g] + g, col + edge_off[g], ng, p, (float2*)Y + vtx_off[g], r, s);
+            else if (one)
+                rc = run_prepare(row_ptr + vtx_off[g] + g, col + edge_off[g], ng, p, (float2*)Y + vtx_off[g], r, s,
+                                 &prep[g]);
+            else
+                rc = run_core(row_ptr + vtx_off[g] + g, col + edge_off[g], ng, p, (float2*)Y + vtx_off[g], r, s);
             note(rc);
         }
         cudaStreamSynchronize(s);
@@ -1331,6 +1524,77 @@ extern "C" ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx
     for (int32_t wi = 1; wi < workers; ++wi) pool.emplace_back(work, wi);
     work(0);
     for (std::thread& t : pool) t.join();
+    if (!one || first_err.load() < 0) {
+        if (!one && cfg->max_boxes_used)
+            for (int32_t g = 0; g < n_graphs; ++g) cfg->max_boxes_used[g] = -1;  // not tracked in this mode
+        return (ltsnet_status)first_err.load();
+    }
+    // one launch per phase over all graphs
+    cudaStream_t s = (cudaStream_t)stream;
+    bool d16 = true, heavy = false;
+    for (int32_t g = 0; g < n_graphs; ++g) {
+        d16 = d16 && prep[g].d16;
+        heavy = heavy || prep[g].hr.nchunks > 0;
+    }
+    const IterShape shmax = iter_shape((int32_t)max_n, p);
+    std::vector<BatchGraph> hg(n_graphs);
+    std::vector<RunWs> rws(n_graphs);
+    for (int32_t g = 0; g < n_graphs; ++g) {
+        const int32_t ng = (int32_t)(vtx_off[g + 1] - vtx_off[g]);
+        carve_graph(g, (char*)ws + offs[g], align_up(ltsnet_run_workspace_size(ng, edge_off[g + 1] - edge_off[g], p), 256),
+                    &rws[g]);
+        const RunWs& r = rws[g];
+        const IterShape sh = iter_shape(ng, p);
+        Carve ic(r.iter, r.iter_bytes);
+        BatchGraph& b = hg[g];
+        b.w = iter_carve(ic, sh);
+        LT_CUDA(iter_reset(b.w, sh, s));
+        b.P_row = r.P_row;
+        b.P_col = r.P_col;
+        b.P_d16 = d16 ? r.d16 : nullptr;
+        b.P_val = r.P_val;
+        b.Y = prep[g].Yw;
+        b.upd = r.upd;
+        b.gains = r.gains;
+        b.n = ng;
+    }
+    ltsnet_status rc = LTSNET_OK;
+    if (heavy) {
+        // rows of P longer than the fused kernel's groups take: each graph on
+        // its own (the one-launch kernels do not sum row chunks)
+        for (int32_t g = 0; g < n_graphs && rc == LTSNET_OK; ++g)
+            rc = optimize_core(hg[g].P_row, hg[g].P_col, hg[g].P_d16, hg[g].P_val, prep[g].hr, hg[g].n, p, hg[g].Y,
+                               hg[g].upd, hg[g].gains, 0, (int32_t)schedule_length(p), hg[g].w,
+                               iter_shape(hg[g].n, p), s);
+    } else {
+        // descriptor arrays, one per schedule stage (the stage coefficients
+        // depend on each graph's n)
+        char* dbase = (char*)ws + one_launch_slices(n_graphs, vtx_off, edge_off, p, nullptr) -
+                      align_up(sizeof(BatchGraph) * (size_t)n_graphs, 256) * (size_t)p->n_stages;
+        std::vector<BatchGraph*> dbg(p->n_stages);
+        for (int32_t st = 0; st < p->n_stages; ++st) {
+            std::vector<BatchGraph> sg = hg;
+            for (int32_t g = 0; g < n_graphs; ++g)
+                sg[g].st = make_stage(p->stages[st], learning_rate(p, hg[g].n), hg[g].n);
+            dbg[st] = (BatchGraph*)(dbase + align_up(sizeof(BatchGraph) * (size_t)n_graphs, 256) * (size_t)st);
+            LT_CUDA(cudaMemcpyAsync(dbg[st], sg.data(), sizeof(BatchGraph) * (size_t)n_graphs, cudaMemcpyHostToDevice,
+                                    s));
+        }
+        LT_CUDA(cudaStreamSynchronize(s));  // the host copies above are staged before they go out of scope
+        BatchShape bs;
+        bs.fft_blocks = cfg->fft_blocks > 0 ? cfg->fft_blocks : 4;
+        bs.spread_blocks = cfg->spread_blocks > 0 ? cfg->spread_blocks : 8;
+        bs.max_n = (int32_t)max_n;
+        rc = batched_loop(dbg.data(), hg, bs, shmax, p, d16, s);
+    }
+    if (rc != LTSNET_OK) return rc;
+    for (int32_t g = 0; g < n_graphs; ++g) {
+        if (cfg->max_boxes_used) {
+            LT_CUDA(cudaMemcpyAsync(&cfg->max_boxes_used[g], &hg[g].w.g->imax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        }
+        note(run_finish(hg[g].n, (float2*)Y + vtx_off[g], rws[g], prep[g], hg[g].w.st, s));
+    }
+    LT_CUDA(cudaStreamSynchronize(s));
     return (ltsnet_status)first_err.load();
 }
 

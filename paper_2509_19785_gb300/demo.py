@@ -4,10 +4,15 @@ report the time, the layout's extent and, with --quality, its NP and stress.
   python -m paper_2509_19785_gb300.demo --graph rgg --n 200000 --iters 1000
   python -m paper_2509_19785_gb300.demo --graph rgg --n 200000 --init pmds --quality
   python -m paper_2509_19785_gb300.demo --graph rgg --n 300000 --variant bh --iters 20
+  python -m paper_2509_19785_gb300.demo --graph rgg --n 1000000 --iters 30 --init uniform --extent 45 --conv gemm
 
 Graphs: grid (sqrt(n) x sqrt(n) mesh), rgg (random geometric graph, mean
 degree 8, largest component), sbm (power-law block sizes), ba
-(Barabasi-Albert, 4 edges per vertex), tree (random recursive tree).
+(Barabasi-Albert, 4 edges per vertex), tree (random recursive tree), batch
+(--n graphs of 200..20000 vertices, grids / recursive trees / SBMs, run by
+ltsnet_run_batched):
+
+  python -m paper_2509_19785_gb300.demo --graph batch --n 512 --iters 750 --max-boxes 128
 """
 from __future__ import annotations
 
@@ -50,21 +55,45 @@ def main():
     ap.add_argument("--variant", choices=["ltsnet", "fit", "bh"], default="ltsnet",
                     help="ltsnet: ltsnet_run (Alg. 3); fit / bh: C0, then ltsnet_optimize_quadtree (Alg. 2 / 1)")
     ap.add_argument("--theta", type=float, default=0.5)
-    ap.add_argument("--init", choices=["random", "pmds"], default="random",
-                    help="random N(0, 1e-4^2) start, or Pivot MDS with 100 pivots (the paper's start)")
+    ap.add_argument("--init", choices=["random", "pmds", "uniform"], default="random",
+                    help="random N(0, 1e-4^2) start, Pivot MDS with 100 pivots (the paper's start), or points "
+                         "uniform in a square of side --extent (the grid sizes of a late iteration from the start)")
+    ap.add_argument("--extent", type=float, default=45.0)
+    ap.add_argument("--late-stage", action="store_true",
+                    help="every iteration with the second stage's multipliers (lambda_c 0.01, lambda_r 0.6, "
+                         "momentum 0.8): a layout that keeps its extent, for profiling late iterations")
+    ap.add_argument("--conv", choices=["fft", "gemm"], default="fft",
+                    help="grid convolution: FP32 FFT or split-BF16 DFT matrix products on the tensor cores")
     ap.add_argument("--quality", action="store_true", help="NP (r = 2) and stress over 64 sources of the result")
+    ap.add_argument("--max-boxes", type=int, default=None, help="cap on the boxes per side of the grid")
+    ap.add_argument("--batch-form", choices=["one", "per-graph"], default="one",
+                    help="batch: one launch per phase over all graphs, or ltsnet_run per graph on worker threads")
+    ap.add_argument("--fft-blocks", type=int, default=0, help="batch: FFT blocks per graph (0: the library's default)")
+    ap.add_argument("--spread-blocks", type=int, default=0,
+                    help="batch: spread blocks per graph (0: the library's default)")
+    ap.add_argument("--workers", type=int, default=16, help="batch: host threads for C0 (and the per-graph form)")
     args = ap.parse_args()
+    if args.graph == "batch":
+        return run_batch(args)
     import torch
 
     import paper_2509_19785_gb300 as lt
     import synth
 
     g = make_graph(args.graph, args.n, args.seed)
-    params = lt.Params(perplexity=args.perplexity, stages=lt.default_stages(args.iters), plain=args.plain)
+    stages = [lt.Stage(args.iters, 1.0, 0.01, 0.6, 1.0, 0.8)] if args.late_stage else lt.default_stages(args.iters)
+    params = lt.Params(perplexity=args.perplexity, stages=stages, plain=args.plain,
+                       conv_mode=1 if args.conv == "gemm" else 0)
+    if args.max_boxes:
+        params.max_boxes = args.max_boxes
     row_ptr = torch.from_numpy(g.row_ptr).cuda()
     col = torch.from_numpy(g.col).cuda()
     if args.init == "pmds":
         Y0, _, _ = lt.pivot_mds(row_ptr, col, min(100, g.n))
+    elif args.init == "uniform":
+        import numpy as np
+
+        Y0 = torch.from_numpy((np.random.default_rng(1).random((g.n, 2)) * args.extent).astype(np.float32)).cuda()
     else:
         Y0 = torch.from_numpy(synth.initial_layout(g.n, 1)).cuda()
     times = []
@@ -88,7 +117,7 @@ def main():
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
     Yn = Y.cpu().numpy()
-    out = {"graph": args.graph, "n": g.n, "m": g.m, "variant": args.variant, "init": args.init,
+    out = {"graph": args.graph, "n": g.n, "m": g.m, "variant": args.variant, "init": args.init, "conv": args.conv,
            "iters": args.iters, "status": int(rc), "seconds": [round(t, 4) for t in times],
            "iters_per_s": round(args.iters / min(times), 2), "extent": float(Yn.max() - Yn.min())}
     if args.quality:
@@ -98,6 +127,36 @@ def main():
         src = np.random.default_rng(11).choice(g.n, min(64, g.n), replace=False).astype(np.int32)
         out["stress"] = lt.stress(row_ptr, col, Y, sources=src)[0]
     print(json.dumps(out))
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+
+    import paper_2509_19785_gb300 as lt
+    import synth
+
+    gs = synth.graph_batch(args.n)
+    y0s = [synth.initial_layout(g.n, 100 + i) for i, g in enumerate(gs)]
+    params = lt.Params(perplexity=args.perplexity, stages=lt.default_stages(args.iters))
+    if args.max_boxes:
+        params.max_boxes = args.max_boxes
+    mode = lt.BATCH_ONE_LAUNCH if args.batch_form == "one" else lt.BATCH_PER_GRAPH
+    times = []
+    boxes = None
+    for _ in range(args.repeat):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = lt.run_batched(gs, y0s, params, workers=args.workers, mode=mode, fft_blocks=args.fft_blocks,
+                             spread_blocks=args.spread_blocks, return_boxes=True)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        Yb, _, boxes = out
+    boxes = np.asarray(boxes)
+    print(json.dumps({"graph": "batch", "graphs": len(gs), "vertices": int(sum(g.n for g in gs)),
+                      "form": args.batch_form, "iters": args.iters,
+                      "seconds": [round(t, 4) for t in times], "graphs_per_s": round(len(gs) / min(times), 2),
+                      "max_boxes_used": int(boxes.max()), "finite": bool(torch.isfinite(Yb).all())}))
 
 
 if __name__ == "__main__":

@@ -25,7 +25,7 @@ import numpy as np
 __all__ = [
     "Graph", "csr_from_edges", "grid2d", "sbm", "sbm_powerlaw", "rgg",
     "random_recursive_tree", "barabasi_albert", "largest_component",
-    "initial_layout", "graph_batch", "config_graph",
+    "initial_layout", "graph_batch", "config_graph", "bfs_ball",
 ]
 
 
@@ -283,3 +283,19 @@ def config_graph(name: str) -> Graph:
     if name == "ba4m":
         return barabasi_albert(4_000_000, 4, seed=5)
     raise KeyError(name)
+
+
+def bfs_ball(g: Graph, root: int, size: int) -> tuple[Graph, np.ndarray]:
+    """Induced subgraph on the first ``size`` vertices of a breadth-first
+    search from ``root`` (scipy's order), relabelled in that order; returns
+    (subgraph, original ids of its vertices)."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import breadth_first_order
+
+    A = csr_matrix((np.ones(g.col.shape[0]), g.col, g.row_ptr), shape=(g.n, g.n))
+    ball = breadth_first_order(A, root, directed=False, return_predecessors=False)[:size]
+    new = -np.ones(g.n, np.int64)
+    new[ball] = np.arange(ball.shape[0])
+    rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    keep = (new[rows] >= 0) & (new[g.col] >= 0)
+    return csr_from_edges(ball.shape[0], new[rows[keep]], new[g.col[keep]], name=f"{g.name}_ball{size}"), ball

@@ -439,20 +439,41 @@ def test_cost_autograd_rejects_exaggeration(ltlib, grid32, snapshots):
         F.apply(Y, P[2], P[0], P[1], ltlib.Stage(1, 1.0, 0.01, 0.0, 12.0, 0.5), ltlib.Params())
 
 
-def test_run_batched_equals_single_runs(ltlib):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_run_batched_equals_single_runs(ltlib, mode):
     """ltsnet_run_batched over graphs of several kinds and sizes, with fewer
-    workers than graphs, gives every graph exactly the layout ltsnet_run gives
-    it alone (deterministic kernels, nothing shared between graphs)."""
+    workers than graphs -- the one-launch form (every phase one launch over
+    all graphs, two launch shapes) and the per-graph form -- gives every
+    graph exactly the layout ltsnet_run gives it alone; the one-launch form
+    also reports each graph's largest box count, equal to its own run's."""
     import torch
 
     graphs = [synth.grid2d(20, 30), synth.random_recursive_tree(900, 5), synth.sbm([300, 250, 200], 9.5, 40, 7),
               synth.grid2d(9, 7), synth.rgg(1500, seed=9, lcc=True), synth.random_recursive_tree(150, 2)]
     Y0s = [synth.initial_layout(g.n, 11 + i) for i, g in enumerate(graphs)]
     params = ltlib.Params(stages=ltlib.default_stages(120))
-    Y, off = ltlib.run_batched(graphs, Y0s, params, workers=3)
-    for i, (g, y0) in enumerate(zip(graphs, Y0s)):
-        a, _ = ltlib.run(g.row_ptr, g.col, torch.from_numpy(y0), params)
-        assert torch.equal(Y[off[i]:off[i + 1]], a), i
+    single = [ltlib.run(g.row_ptr, g.col, torch.from_numpy(y0), params)[0] for g, y0 in zip(graphs, Y0s)]
+    shapes = [(0, 0), (1, 3)] if mode == 0 else [(0, 0)]
+    for fb, sb in shapes:
+        Y, off, boxes = ltlib.run_batched(graphs, Y0s, params, workers=3, mode=mode, fft_blocks=fb,
+                                          spread_blocks=sb, return_boxes=True)
+        for i in range(len(graphs)):
+            assert torch.equal(Y[off[i]:off[i + 1]], single[i]), (mode, fb, sb, i)
+        if mode == 0:
+            assert np.all(boxes >= params.min_boxes) and np.all(boxes <= params.max_boxes)
+        else:
+            assert np.all(boxes == -1)
+
+
+def test_run_batched_argument_checks(ltlib):
+    graphs = [synth.grid2d(6, 6), synth.grid2d(5, 7)]
+    Y0s = [synth.initial_layout(g.n, 1) for g in graphs]
+    for params in (ltlib.Params(stages=ltlib.default_stages(10), plain=True),
+                   ltlib.Params(stages=ltlib.default_stages(10), conv_mode=1)):
+        with pytest.raises(ltlib.LtsnetError):
+            ltlib.run_batched(graphs, Y0s, params, workers=2, mode=0)
+    # both forms accept what a single run accepts
+    ltlib.run_batched(graphs, Y0s, ltlib.Params(stages=ltlib.default_stages(10), plain=True), workers=2, mode=1)
 
 
 def test_run_step_rgg1m_matches_oracle(ltlib):
@@ -487,18 +508,7 @@ def test_run_step_rgg1m_matches_oracle(ltlib):
 
 
 def _bfs_ball(g, root: int, size: int):
-    """Induced subgraph on the first `size` vertices of a BFS from `root`,
-    relabelled in that order."""
-    from scipy.sparse import csr_matrix
-    from scipy.sparse.csgraph import breadth_first_order
-
-    A = csr_matrix((np.ones(g.col.shape[0]), g.col, g.row_ptr), shape=(g.n, g.n))
-    ball = breadth_first_order(A, root, directed=False, return_predecessors=False)[:size]
-    new = -np.ones(g.n, np.int64)
-    new[ball] = np.arange(ball.shape[0])
-    rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
-    keep = (new[rows] >= 0) & (new[g.col] >= 0)
-    return synth.csr_from_edges(ball.shape[0], new[rows[keep]], new[g.col[keep]])
+    return synth.bfs_ball(g, root, size)[0]
 
 
 @pytest.fixture(scope="module")
@@ -542,10 +552,10 @@ def test_cost_autograd_sbm100k_64_coordinates(ltlib):
     P = aff["P"]
     Pn = tuple(t.cpu().numpy() for t in P)
     rng = np.random.default_rng(64)
-    Y32 = (rng.standard_normal((g.n, 2)) * 20).astype(np.float32)
+    Y32 = (rng.standard_normal((g.n, 2)) * 8).astype(np.float32)
     st = ltlib.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
     params = ltlib.Params(perplexity=40.0)
-    gp = oracle.GridParams()
+    gp = oracle.GridParams(max_boxes=params.max_boxes)
     coords = [(int(i), int(d)) for i, d in zip(rng.choice(g.n, 64, replace=False), rng.integers(0, 2, 64))]
     _autograd_checks(ltlib, P, Pn, Y32, st, params, gp, coords, recompute=True)
 
@@ -575,3 +585,43 @@ def test_run_step_ba_ball_long_rows_match_oracle(ltlib, ba_ball):
              + np.linalg.norm(st.lambda_r / n ** 2 * pr["E"]))
     err = float(np.linalg.norm(step - (Yr - Y0)) / (lr * 1.2 * scale))
     assert err < 1e-5, err
+
+
+def test_rgg1m_ball20k_parity_both_forms_and_exact(ltlib, capsys):
+    """The benchmark graph's 20,000-vertex BFS ball (cfg 3's error on a
+    20k-vertex subsample), at iteration 300 of the oracle's own run on it:
+    every gradient term of both convolution forms against the oracle's
+    interpolation (1e-5), and the oracle's interpolation against the exact
+    O(n^2) sums (5e-3, the accuracy contract); the measured errors are
+    printed."""
+    import torch
+
+    g = synth.config_graph("rgg1m")
+    root = int(np.random.default_rng(31).integers(g.n))
+    sub, _ = synth.bfs_ball(g, root, 20_000)
+    aff = ltlib.affinities(sub.row_ptr, sub.col, 30.0)
+    P = aff["P"]
+    Pn = tuple(t.cpu().numpy() for t in P)
+    ref = oracle.preprocess(sub.row_ptr, sub.col, 30.0)
+    assert np.array_equal(Pn[0], ref.P_row) and np.array_equal(Pn[1], ref.P_col)
+    pv = Pn[2].astype(np.float64)
+    Y = oracle.run(synth.initial_layout(sub.n, 3), Pn[0], Pn[1], pv, oracle.default_stages(1000),
+                   oracle.GridParams(), iters=300).astype(np.float32)
+    st = ltlib.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+    out = {}
+    for conv in (0, 1):
+        errs = _compare(ltlib, P, Pn, Y, st, ltlib.Params(conv_mode=conv), oracle.GridParams())
+        out[conv] = errs
+        for key, v in errs.items():
+            assert v < TOL, f"conv {conv} {key}: {v:.3e} ({errs})"
+    ost = oracle.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+    Yd = Y.astype(np.float64)
+    A, R, E = oracle.exact_rows(Yd, Pn[0], Pn[1], pv, np.arange(sub.n, dtype=np.int32))
+    Z = oracle.exact_z(Yd)
+    _, pr = oracle.interp_gradient(Y, Pn[0], Pn[1], pv, ost, oracle.GridParams())
+    acc = dict(R=rel(pr["R"], R), E=rel(pr["E"], E), Z=abs(pr["Z"] - Z) / Z)
+    for key, v in acc.items():
+        assert v <= 5e-3, (key, acc)
+    with capsys.disabled():
+        print(f"\nrgg1m ball20k (extent {float(Y.max() - Y.min()):.1f}): fft {out[0]}\n  dft_gemm {out[1]}\n"
+              f"  interp vs exact {acc}")

@@ -47,11 +47,10 @@ GRAPHS = {
 def test_np_matches_oracle(ltlib, name):
     g = GRAPHS[name]()
     for lname, Y in layouts(g, 7):
-        npv, exc, b, c = ltlib.neighbourhood_preservation(g.row_ptr, g.col, Y, return_counts=True)
+        npv, b, c = ltlib.neighbourhood_preservation(g.row_ptr, g.col, Y, return_counts=True)
         npo, bo, co = quality.neighbourhood_preservation(g.row_ptr, g.col, Y)
         assert np.array_equal(b.cpu().numpy(), bo), lname
         assert np.array_equal(c.cpu().numpy(), co), lname
-        assert exc == int((bo < 0).sum())
         assert npv == pytest.approx(npo, rel=1e-12, abs=1e-15), lname
 
 
@@ -60,18 +59,47 @@ def test_np_is_one_on_the_lattice(ltlib):
     g = synth.grid2d(w, h)
     ids = np.arange(w * h)
     Y = np.stack([ids % w, ids // w], axis=1).astype(np.float32) * 0.25
-    npv, exc = ltlib.neighbourhood_preservation(g.row_ptr, g.col, Y)
-    assert npv == 1.0 and exc == 0
+    npv = ltlib.neighbourhood_preservation(g.row_ptr, g.col, Y)
+    assert npv == 1.0
 
 
-def test_np_hub_exclusion(ltlib):
+def test_np_hubs_in_the_global_pool(ltlib):
+    """A 20,000-vertex Barabasi-Albert graph: the vertices with more than 2048
+    two-hop candidates (hubs and their neighbours) go through the hash tables
+    in the workspace; per-vertex b and c on all of them and on 300 others
+    against the oracle, and a workspace too small for the largest table
+    reported as LTSNET_ERR_WORKSPACE."""
     g = synth.barabasi_albert(20000, 4, 3)
     Y = np.random.default_rng(1).normal(size=(g.n, 2)).astype(np.float32)
-    npv, exc, b, c = ltlib.neighbourhood_preservation(g.row_ptr, g.col, Y, return_counts=True)
+    npv, b, c = ltlib.neighbourhood_preservation(g.row_ptr, g.col, Y, return_counts=True)
+    b, c = b.cpu().numpy(), c.cpu().numpy()
     deg = np.diff(g.row_ptr)
     cand = deg + np.add.reduceat(deg[g.col], g.row_ptr[:-1]) * (deg > 0)
-    assert exc == int((cand > 2048).sum()) > 0
-    assert np.array_equal(b.cpu().numpy() < 0, cand > 2048)
+    big = np.flatnonzero(cand > 2048)
+    assert big.shape[0] > 20
+    rng = np.random.default_rng(4)
+    picks = np.concatenate([big, rng.choice(np.flatnonzero(cand <= 2048), 300, replace=False)])
+    for v in picks:
+        ball = quality.two_hop_ball(g.row_ptr, g.col, int(v))
+        assert b[v] == ball.shape[0], v
+        near = quality.nearest_in_drawing(Y, int(v), int(b[v]))
+        assert c[v] == np.intersect1d(ball, near).shape[0], v
+    assert np.all(b > 0)
+    assert np.isclose(npv, np.mean(c / (2 * b - c)), rtol=1e-12)
+    # the pool is the workspace beyond its fixed part: half the largest table
+    # short of it is too small
+    def pow2_slots(x):
+        s = 4096
+        while s < 2 * x:
+            s *= 2
+        return s
+
+    need = ltlib.lib().ltsnet_quality_workspace_size(g.n, g.col.shape[0])
+    fixed = need - 4 * pow2_slots(g.n + g.col.shape[0])
+    small = ltlib._workspace(fixed + 4 * pow2_slots(int(cand.max())) // 2)
+    with pytest.raises(ltlib.LtsnetError) as e:
+        ltlib.neighbourhood_preservation(g.row_ptr, g.col, Y, ws=small)
+    assert e.value.code == -2
 
 
 def test_np_rgg_full_size_sampled(ltlib):
@@ -81,9 +109,8 @@ def test_np_rgg_full_size_sampled(ltlib):
     g = synth.config_graph("rgg1m")
     Y, _, _ = ltlib.pivot_mds(g.row_ptr, g.col, 30)
     Y = Y.cpu().numpy()
-    npv, exc, b, c = ltlib.neighbourhood_preservation(g.row_ptr, g.col, Y, return_counts=True)
+    npv, b, c = ltlib.neighbourhood_preservation(g.row_ptr, g.col, Y, return_counts=True)
     b, c = b.cpu().numpy(), c.cpu().numpy()
-    assert exc == 0
     rng = np.random.default_rng(5)
     for v in rng.choice(g.n, 150, replace=False):
         ball = quality.two_hop_ball(g.row_ptr, g.col, int(v))
@@ -139,14 +166,14 @@ def test_quality_degenerate_graphs(ltlib):
     pairs are skipped by stress); a single source."""
     g = synth.csr_from_edges(2, np.array([0]), np.array([1]))
     Y = np.array([[0, 0], [2, 1]], np.float32)
-    npv, exc, b, c = ltlib.neighbourhood_preservation(g.row_ptr, g.col, Y, return_counts=True)
-    assert npv == 1.0 and exc == 0 and list(b.cpu().numpy()) == [1, 1]
+    npv, b, c = ltlib.neighbourhood_preservation(g.row_ptr, g.col, Y, return_counts=True)
+    assert npv == 1.0 and list(b.cpu().numpy()) == [1, 1]
     st, alpha, cnt, skipped = ltlib.stress(g.row_ptr, g.col, Y)
     assert abs(st) < 1e-15 and cnt == 2 and skipped == 0
     u = np.arange(5)
     g = synth.csr_from_edges(9, u, u + 1)  # path 0..5, vertices 6, 7, 8 isolated
     Y = np.random.default_rng(1).normal(size=(9, 2)).astype(np.float32)
-    npv, exc, b, c = ltlib.neighbourhood_preservation(g.row_ptr, g.col, Y, return_counts=True)
+    npv, b, c = ltlib.neighbourhood_preservation(g.row_ptr, g.col, Y, return_counts=True)
     npo, bo, co = quality.neighbourhood_preservation(g.row_ptr, g.col, Y)
     assert np.array_equal(b.cpu().numpy(), bo) and np.array_equal(c.cpu().numpy(), co)
     assert list(bo[6:]) == [0, 0, 0] and npv == pytest.approx(npo, rel=1e-12)
