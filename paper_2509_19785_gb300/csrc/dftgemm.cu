@@ -590,24 +590,20 @@ __global__ void __launch_bounds__(kProdThreads) k_dft_products(GridDev* G, DftWs
     }
 }
 
-// Kernel spectra of grid.cu (planes of L x H, ky major, 1/L^2 applied)
-// repacked for the S2 epilogue: for every (kx, ky) in [0, H)^2, 8 floats
-// (K2, Ke, K1, Kln, D2x, Dex, D2y, Dey) times the fold weights w_ky w_kx,
-// where D = -Im of the odd kernels' spectra and the y-odd ones are the
-// x-odd ones transposed.
-__global__ void k_dft_kpack(const GridDev* __restrict__ G, const float* __restrict__ khat, float4* __restrict__ kp)
+// Kernel spectrum records of grid.cu (for (kx, ky) in [0, H)^2: K2, Ke, K1,
+// Kln and D2x, Dex, D2y, Dey, 1/L^2 applied) repacked for the S2 epilogue:
+// times the fold weights w_ky w_kx, with D = -Im of the odd kernels' spectra.
+__global__ void k_dft_kpack(const GridDev* __restrict__ G, const float4* __restrict__ kc, float4* __restrict__ kp)
 {
     const DftDims d = dft_dims(G);
     const int H = d.H;
-    const int64_t LH = (int64_t)d.L * H;
     const int64_t tot = (int64_t)H * H;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < tot; u += (int64_t)gridDim.x * blockDim.x) {
         const int kx = (int)(u / H), ky = (int)(u - (int64_t)kx * H);
         const float w = ((ky == 0 || ky == H - 1) ? 1.0f : 2.0f) * ((kx == 0 || kx == H - 1) ? 1.0f : 2.0f);
-        const int64_t o = (int64_t)ky * H + kx, ot = (int64_t)kx * H + ky;
-        kp[2 * u] = make_float4(khat[o] * w, khat[LH + o] * w, khat[2 * LH + o] * w, khat[5 * LH + o] * w);
-        kp[2 * u + 1] = make_float4(-khat[3 * LH + o] * w, -khat[4 * LH + o] * w, -khat[3 * LH + ot] * w,
-                                    -khat[4 * LH + ot] * w);
+        const float4 a = kc[2 * u], b = kc[2 * u + 1];
+        kp[2 * u] = make_float4(a.x * w, a.y * w, a.z * w, a.w * w);
+        kp[2 * u + 1] = make_float4(-b.x * w, -b.y * w, -b.z * w, -b.w * w);
     }
 }
 
@@ -689,7 +685,7 @@ cudaError_t launch_dft_prep(const IterWs& w, cudaStream_t s)
 
 cudaError_t launch_dft_products(const IterWs& w, int32_t n, cudaStream_t s)
 {
-    k_dft_kpack<<<(unsigned)num_sms() * 4, 256, 0, s>>>(w.g, w.khat, (float4*)w.dft.kpack);
+    k_dft_kpack<<<(unsigned)num_sms() * 4, 256, 0, s>>>(w.g, w.kc, (float4*)w.dft.kpack);
     GemmArgs a;
     a.G = w.g;
     a.st = w.st;

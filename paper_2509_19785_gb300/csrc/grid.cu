@@ -189,6 +189,117 @@ __device__ float2* fft_lines(float2* a, float2* b, int nl, int ld, const GridDev
     return a;
 }
 
+// ---- in-place FFTs of interleaved line batches ----------------------------
+// nl lines of length L held interleaved in shared memory, element t of line
+// l at X[t * ld + l] (ld = nl rounded up to odd, so that both a walk along a
+// line and a walk across lines hit distinct banks).  Decimation in frequency
+// in place takes natural order to the digit-reversed order of the radix
+// sequence; decimation in time with the stages reversed takes that order back
+// to natural order.  A convolution therefore needs no permutation pass: the
+// products are formed in digit-reversed order, where the position p holds
+// frequency drev[p].
+//
+// Stage k (radix R, span N = R m): butterfly (b, j), b < L / N, j < m, on the
+// positions b N + j + r m.  DIF: R-point DFT, then multiply output q by
+// e^{-2 pi i j q / N}.  DIT: multiply input r by e^{-2 pi i j r / N}, then the
+// R-point DFT.  The twiddle of exponent j q (L / N) is tw[j q ts].
+struct LinePlan {
+    int32_t L, nst;
+    int32_t R[kMaxRadix];
+    int32_t m[kMaxRadix];
+    uint32_t mg[kMaxRadix];  // floor(2^32 / m) + 1: b = umulhi(beta, mg) exactly for beta, m < 2^12
+    int32_t ts[kMaxRadix];
+};
+
+// Thread 0 fills the plan from the grid's radix sequence; the caller syncs.
+__device__ __forceinline__ void make_line_plan(const GridDev& g, LinePlan& pl)
+{
+    if (threadIdx.x != 0) return;
+    pl.L = g.L;
+    pl.nst = g.nst;
+    int N = g.L;
+    for (int k = 0; k < g.nst; ++k) {
+        const int R = g.radix[k];
+        const int m = N / R;
+        pl.R[k] = R;
+        pl.m[k] = m;
+        pl.mg[k] = m > 1 ? (uint32_t)(4294967296ull / (unsigned)m) + 1u : 0u;
+        pl.ts[k] = g.L / N;
+        N = m;
+    }
+}
+
+// drev[p] = the frequency that DIF leaves at position p; pos_of is its
+// inverse.  Position p has digits q_k = (p / m_k) mod R_k and frequency
+// sum_k q_k R_1 ... R_{k-1}.
+__device__ __forceinline__ void make_digit_tables(const LinePlan& pl, uint16_t* drev, uint16_t* pos_of)
+{
+    for (int p = threadIdx.x; p < pl.L; p += blockDim.x) {
+        int k = 0, place = 1;
+        for (int st = 0; st < pl.nst; ++st) {
+            const int q = (p / pl.m[st]) % pl.R[st];
+            k += q * place;
+            place *= pl.R[st];
+        }
+        drev[p] = (uint16_t)k;
+        if (pos_of) pos_of[k] = (uint16_t)p;
+    }
+}
+
+template <int R, bool DIT>
+__device__ __forceinline__ void ip_stage(float2* X, int ld, int nl, const LinePlan& pl, int st, const float2* tw,
+                                         int tl, int tb, int nbp)
+{
+    const int m = pl.m[st];
+    const uint32_t mg = pl.mg[st];
+    const int ts = pl.ts[st];
+    const int nbf = pl.L / R;
+    for (int beta = tb; beta < nbf; beta += nbp) {
+        const int b = m > 1 ? (int)__umulhi((uint32_t)beta, mg) : beta;
+        const int j = beta - b * m;
+        float2* x = X + (int64_t)(b * R * m + j) * ld + tl;
+        const int step = m * ld;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = x[r * step];
+        if (DIT) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[j * r * ts]);
+        }
+        dft_small<R>(v);
+        if (!DIT) {
+#pragma unroll
+            for (int q = 1; q < R; ++q) v[q] = cmul(v[q], tw[j * q * ts]);
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q * step] = v[q];
+    }
+}
+
+// Forward DFT of the nl interleaved lines in place: DIF (natural order in,
+// digit-reversed out) or DIT (digit-reversed in, natural out).  All threads
+// of the block call it; it ends with a barrier.
+template <bool DIT>
+__device__ void ip_fft(float2* X, int ld, int nl, const LinePlan& pl, const float2* tw)
+{
+    const int nbp = (int)blockDim.x / nl;
+    const int tl = (int)threadIdx.x % nl;
+    const int tb = (int)threadIdx.x / nl;
+    const bool on = tb < nbp;
+    for (int k = 0; k < pl.nst; ++k) {
+        const int st = DIT ? pl.nst - 1 - k : k;
+        if (on) {
+            switch (pl.R[st]) {
+                case 4: ip_stage<4, DIT>(X, ld, nl, pl, st, tw, tl, tb, nbp); break;
+                case 2: ip_stage<2, DIT>(X, ld, nl, pl, st, tw, tl, tb, nbp); break;
+                case 3: ip_stage<3, DIT>(X, ld, nl, pl, st, tw, tl, tb, nbp); break;
+                default: ip_stage<5, DIT>(X, ld, nl, pl, st, tw, tl, tb, nbp); break;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 __device__ void compute_grid(const int32_t* bounds, float bwm, int min_boxes, int max_boxes, int P, int32_t n,
                              GridDev& g)
 {
@@ -853,54 +964,104 @@ __device__ __forceinline__ bool circ_offset(int a, int M, int L, int& d)
 constexpr float kEntScale = 0.125f;  // Ke is packed scaled by 1/8 to match K2's magnitude
 constexpr float kLnScale = 1.0f / 1024.0f;  // ln(eps + d^2) packed beside K1, scaled to K1's magnitude
 
-// Kernel spectra, pass 1: rows a in [0, L) of the circulant embeddings of
+// Shared-memory carve of the in-place line kernels: twiddles (unless they
+// are read from global memory), digit tables, then the line buffer.
+struct IpSmem {
+    const float2* tw;  // smem copy or the global table
+    uint16_t* drev;
+    uint16_t* pos_of;  // null unless requested
+    float2* X;
+    int avail;         // float2 slots left for X
+};
+
+__device__ __forceinline__ IpSmem ip_smem(float2* smf, int sm_f2, int L, bool pos_tab, bool tw_smem,
+                                          const float2* __restrict__ tw)
+{
+    IpSmem r;
+    const int tab = ((pos_tab ? 2 : 1) * L + 3) / 4;  // uint16 tables in float2 slots
+    float2* p = smf;
+    if (tw_smem) {
+        load_tw(p, tw, L);
+        r.tw = p;
+        p += L;
+    } else {
+        r.tw = tw;
+    }
+    r.drev = (uint16_t*)p;
+    r.pos_of = pos_tab ? r.drev + L : nullptr;
+    r.X = p + tab;
+    r.avail = sm_f2 - (int)(r.X - smf);
+    return r;
+}
+
+// Kernel spectrum records: for (kx, ky) in [0, H)^2 eight floats
+//   a = (K2^, Ke^, K1^, ln^),  b = (D2x, Dex, D2y, Dey)
+// (D = Im of the odd kernels' spectra, scaled like the even ones by 1/L^2).
+// The kernels depend on |dx| and |dy| only (times dx or dy for the odd ones),
+// so D?y(kx, ky) = D?x(ky, kx); the even spectra and D?x are even in ky and
+// D?y is odd in ky.  kc_at unfolds ky in [0, L).
+__device__ __forceinline__ void kc_at(const float4* __restrict__ kc, int kx, int ky, int L, int H, float4& a, float4& b)
+{
+    const bool up = ky >= H;
+    const float4* r = kc + 2 * ((int64_t)kx * H + (up ? L - ky : ky));
+    a = r[0];
+    b = r[1];
+    if (up) {
+        b.z = -b.z;
+        b.w = -b.w;
+    }
+}
+
+// Kernel spectra, pass 1: rows a in [0, H) of the circulant embeddings of
 // three packed complex kernels over node offsets (dx, dy), d^2 = s^2 |.|^2:
 //   q = 0: K2 + i Ke/8      q = 1: K1 + i ln(eps + d^2)/1024
 //   q = 2: K2 dx + i Ke dx / 8
-// transformed along x; columns kx in [0, L/2] are kept (all five kernels are
-// even or odd in x, so the other half follows by symmetry).
+// (rows a and L - a are equal, every kernel being even in dy), transformed
+// along x; columns kx in [0, L/2] are kept (the kernels are even or odd in
+// x), written column-major: krow[q][kx][a].
 __device__ __forceinline__ void k_spec_rows_body(const GridDev* __restrict__ Gp, const float2* __restrict__ tw, float eps,
                             float2* __restrict__ krow, int sm_f2)
 {
     extern __shared__ float2 smf[];
+    __shared__ LinePlan pl;
     const GridDev& G = *Gp;
     const int L = G.L, M = G.M, H = L / 2 + 1;
     const float s2 = G.s * G.s;
-    const int cap = line_cap(sm_f2, L, 2);
-    float2* stw = smf;
-    float2* A = smf + L;
-    float2* B = A + (size_t)cap * L;
-    load_tw(stw, tw, L);
-    int beg, end;
-    block_range(3 * L, beg, end);  // unit = (q, a)
-    for (int u0 = beg; u0 < end; u0 += cap) {
-        const int nl = min(cap, end - u0);
+    make_line_plan(G, pl);
+    const IpSmem sm = ip_smem(smf, sm_f2, L, true, true, tw);
+    __syncthreads();
+    make_digit_tables(pl, sm.drev, sm.pos_of);
+    const int units = 3 * H;  // (q, a)
+    int cap = sm.avail / L;
+    cap = min(cap - !(cap & 1), (units + (int)gridDim.x - 1) / (int)gridDim.x);  // odd cap: ld = cap
+    if (cap < 1) cap = 1;
+    for (int u0 = blockIdx.x * cap; u0 < units; u0 += gridDim.x * cap) {
+        const int nl = min(cap, units - u0), ld = nl | 1;
+        const int nbp = (int)blockDim.x / nl, tl = (int)threadIdx.x % nl, tb = (int)threadIdx.x / nl;
+        const int u = u0 + tl, q = u / H, a = u - q * H;
         __syncthreads();
-        for (int line = 0; line < nl; ++line) {
-            const int u = u0 + line, q = u / L, a = u - q * L;
+        if (tb < nbp) {
             int dy;
             const bool rowok = circ_offset(a, M, L, dy);
-            for (int b = threadIdx.x; b < L; b += blockDim.x) {
-            int dx;
-            float2 v = make_float2(0.f, 0.f);
-            if (rowok && circ_offset(b, M, L, dx)) {
-                const float d2 = s2 * (float)(dx * dx + dy * dy);
-                const float k1 = 1.0f / (1.0f + d2);
-                const float ke = kEntScale / (eps + d2);
-                if (q == 0) v = make_float2(k1 * k1, ke);
-                else if (q == 1) v = make_float2(k1, kLnScale * logf(eps + d2));
-                else v = make_float2(k1 * k1 * (float)dx, ke * (float)dx);
-            }
-            A[line * L + b] = v;
+            for (int b = tb; b < L; b += nbp) {
+                int dx;
+                float2 v = make_float2(0.f, 0.f);
+                if (rowok && circ_offset(b, M, L, dx)) {
+                    const float d2 = s2 * (float)(dx * dx + dy * dy);
+                    const float k1 = 1.0f / (1.0f + d2);
+                    const float ke = kEntScale / (eps + d2);
+                    if (q == 0) v = make_float2(k1 * k1, ke);
+                    else if (q == 1) v = make_float2(k1, kLnScale * logf(eps + d2));
+                    else v = make_float2(k1 * k1 * (float)dx, ke * (float)dx);
+                }
+                sm.X[(int64_t)b * ld + tl] = v;
             }
         }
         __syncthreads();
-        float2* R = fft_lines(A, B, nl, L, G, stw);
-        for (int line = 0; line < nl; ++line) {
-            const int u = u0 + line, q = u / L, a = u - q * L;
-            float2* dst = krow + ((int64_t)q * L + a) * H;
-            for (int k = threadIdx.x; k < H; k += blockDim.x) dst[k] = R[line * L + k];
-        }
+        ip_fft<false>(sm.X, ld, nl, pl, sm.tw);
+        if (tb < nbp)
+            for (int kx = tb; kx < H; kx += nbp)
+                krow[((int64_t)q * H + kx) * H + a] = sm.X[(int64_t)sm.pos_of[kx] * ld + tl];
     }
 }
 
@@ -910,60 +1071,64 @@ __global__ void __launch_bounds__(1024) k_spec_rows(const GridDev* __restrict__ 
     k_spec_rows_body(Gp, tw, eps, krow, sm_f2);
 }
 
-// Kernel spectra, pass 2: columns kx in [0, L/2], scaled by 1/L^2 (the inverse
-// transforms are unnormalised).  khat[f][ky][kx], f = 0: K2^, 1: Ke^, 2: K1^,
-// 5: (ln(eps + d^2))^ (real), 3: Im (K2 dx)^, 4: Im (Ke dx)^ (those two
-// spectra are imaginary).
+// Kernel spectra, pass 2: for tiles of columns kx, the three packed lines
+// over a in [0, L) (mirrored from the H stored rows) transformed along y and
+// unpacked into the records of kc_at, scaled by 1/L^2 (the inverse
+// transforms are unnormalised):
+//   FFT(K2 + i Ke/8) = K2^ + i Ke^/8,  FFT(K1 + i ln/1024) = K1^ + i ln^/1024,
+//   FFT(K2 dx + i Ke dx/8) = i D2x + i (i Dex/8) = -Dex/8 + i D2x.
+// Each column also supplies the transposed odd parts D?y of the records
+// (ky, kx).
 __device__ __forceinline__ void k_spec_cols_body(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
-                            const float2* __restrict__ krow, float* __restrict__ khat, int sm_f2)
+                            const float2* __restrict__ krow, float4* __restrict__ kc, int sm_f2)
 {
     extern __shared__ float2 smf[];
+    __shared__ LinePlan pl;
     const GridDev& G = *Gp;
     const int L = G.L, H = L / 2 + 1;
     const float scale = 1.0f / ((float)L * (float)L);
-    const int cap = line_cap(sm_f2, L, 2);
-    float2* stw = smf;
-    float2* A = smf + L;
-    float2* B = A + (size_t)cap * L;
-    load_tw(stw, tw, L);
-    const int64_t LH = (int64_t)L * H;
-    int beg, end;
-    block_range(3 * H, beg, end);  // unit = (q, kx)
-    for (int u0 = beg; u0 < end; u0 += cap) {
-        const int nl = min(cap, end - u0);
+    make_line_plan(G, pl);
+    const IpSmem sm = ip_smem(smf, sm_f2, L, true, true, tw);
+    __syncthreads();
+    make_digit_tables(pl, sm.drev, sm.pos_of);
+    int C = (sm.avail / L - 1) / 3;
+    C = min(C, (H + (int)gridDim.x - 1) / (int)gridDim.x);
+    if (C < 1) C = 1;
+    for (int t = blockIdx.x; t * C < H; t += gridDim.x) {
+        const int k0 = t * C, nc = min(C, H - k0), nl = 3 * nc;
+        const int ld = (nl | 1) * L <= sm.avail ? (nl | 1) : nl;
         __syncthreads();
         for (int line = 0; line < nl; ++line) {
-            const int u = u0 + line, q = u / H, kx = u - q * H;
-            const float2* src = krow + (int64_t)q * LH + kx;
-            for (int a = threadIdx.x; a < L; a += blockDim.x) A[line * L + a] = src[(int64_t)a * H];
+            const int q = line / nc, c = line - q * nc;
+            const float2* src = krow + ((int64_t)q * H + k0 + c) * H;
+#pragma unroll 4
+            for (int a = threadIdx.x; a < L; a += blockDim.x) sm.X[(int64_t)a * ld + line] = src[a < H ? a : L - a];
         }
         __syncthreads();
-        float2* R = fft_lines(A, B, nl, L, G, stw);
-        for (int line = 0; line < nl; ++line) {
-            const int u = u0 + line, q = u / H, kx = u - q * H;
-            for (int ky = threadIdx.x; ky < L; ky += blockDim.x) {
-            const float2 v = R[line * L + ky];
-            const int64_t o = (int64_t)ky * H + kx;
-            if (q == 0) {
-                khat[0 * LH + o] = v.x * scale;
-                khat[1 * LH + o] = v.y * scale / kEntScale;
-            } else if (q == 1) {
-                khat[2 * LH + o] = v.x * scale;
-                khat[5 * LH + o] = v.y * scale / kLnScale;
-            } else {
-                // FFT(K2dx + i Ke dx/8) = i b2 + i (i be/8) = -be/8 + i b2
-                khat[3 * LH + o] = v.y * scale;
-                khat[4 * LH + o] = -v.x * scale / kEntScale;
-            }
+        ip_fft<false>(sm.X, ld, nl, pl, sm.tw);
+        for (int c = 0; c < nc; ++c) {
+            float4* rec = kc + 2 * ((int64_t)(k0 + c) * H);
+            for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
+                const float2* x = sm.X + (int64_t)sm.pos_of[ky] * ld + c;
+                const float2 v0 = x[0], v1 = x[nc], v2 = x[2 * nc];
+                rec[2 * ky] = make_float4(v0.x * scale, v0.y * scale / kEntScale, v1.x * scale, v1.y * scale / kLnScale);
+                ((float2*)(rec + 2 * ky + 1))[0] = make_float2(v2.y * scale, -v2.x * scale / kEntScale);
             }
         }
+        const int nbp = (int)blockDim.x / nc, tl = (int)threadIdx.x % nc, tb = (int)threadIdx.x / nc;
+        if (tb < nbp)
+            for (int ky = tb; ky < H; ky += nbp) {
+                const float2 v2 = sm.X[(int64_t)sm.pos_of[ky] * ld + 2 * nc + tl];
+                ((float2*)(kc + 2 * ((int64_t)ky * H + k0 + tl) + 1))[1] =
+                    make_float2(v2.y * scale, -v2.x * scale / kEntScale);
+            }
     }
 }
 
 __global__ void __launch_bounds__(1024) k_spec_cols(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
-                            const float2* __restrict__ krow, float* __restrict__ khat, int sm_f2)
+                            const float2* __restrict__ krow, float4* __restrict__ kc, int sm_f2)
 {
-    k_spec_cols_body(Gp, tw, krow, khat, sm_f2);
+    k_spec_cols_body(Gp, tw, krow, kc, sm_f2);
 }
 
 // Row FFTs of the charge grids S0, S1x, S1y, S2 (node-local moments), packed
@@ -1021,24 +1186,20 @@ __global__ void __launch_bounds__(1024) k_conv_rows_fwd(const GridDev* __restric
     k_conv_rows_fwd_body(Gp, tw, wflt, srow, sm_f2);
 }
 
-// Column pass, kx in [0, L/2]: FFT along y of the four charge spectra, the
-// products with the kernel spectra (node-local form of the repulsion and
-// entropy sums), inverse FFTs along y (conjugation trick), rows < M kept:
+// Column pass, tiles of columns kx in [0, L/2]: FFT along y of the four
+// charge spectra (in place, digit-reversed out), the products with the kernel
+// spectra (node-local form of the repulsion and entropy sums), inverse FFTs
+// along y (conjugation trick, natural order out), rows < M kept:
 //   U0 = K2^ S0^                 (F0)
 //   U1 = Ke^ S0^                 (Fe0)
 //   U2 = (K2 dx)^ S0^ - K2^ S1x^ (Vx)     U3 = (K2 dy)^ S0^ - K2^ S1y^ (Vy)
 //   U4 = (Ke dx)^ S0^ - Ke^ S1x^ (Vex)    U5 = (Ke dy)^ S0^ - Ke^ S1y^ (Vey)
 // and, by Parseval over the half spectrum, the grid sum
 //   Z + n = sum [S0 (K1*S0) + 2 s^2 (S1 . (2 (K2 d)*S0 - K2*S1) + S2 (K2*S0))],
-// accumulated in FP64 and finished by the last block in a fixed order.
-__device__ __forceinline__ float odd_transposed(const float* __restrict__ Dh, int kx, int ky, int L, int H)
-{
-    // (K dy)^(kx, ky) = (K dx)^(ky, kx); stored half spectrum covers kx <= L/2,
-    // the rest by oddness in the first argument.
-    return ky <= L / 2 ? Dh[(int64_t)kx * H + ky] : -Dh[(int64_t)kx * H + (L - ky)];
-}
-
-// Z integrand at (kx, ky) from the four charge spectra (see k_conv_cols).
+// accumulated in FP64 per column in an order fixed by the column alone
+// (kColSlots warps, lanes over positions, a fixed tree), and finished by the
+// last block in column order.
+// Z integrand at (kx, ky) from the four charge spectra.
 __device__ __forceinline__ float z_term(float2 s0, float2 s1x, float2 s1y, float2 s2v, float k2, float k1, float d2x,
                                         float d2y, float s2)
 {
@@ -1049,29 +1210,10 @@ __device__ __forceinline__ float z_term(float2 s0, float2 s1x, float2 s1y, float
     return t + 2.0f * s2 * c;
 }
 
-// Product q at (kx, ky) for the inverse column transform (conjugated).
-__device__ __forceinline__ float2 conv_product(int q, float2 s0, float2 s1x, float2 s1y, const float* __restrict__ K2h,
-                                               const float* __restrict__ Keh, const float* __restrict__ D2h,
-                                               const float* __restrict__ Deh, int kx, int ky, int L, int H)
+// (K d)^ S0^ - K^ S1^ for an odd kernel spectrum i d (d real) and its even K.
+__device__ __forceinline__ float2 odd_product(float d, float k, float2 s0, float2 s1)
 {
-    const int64_t o = (int64_t)ky * H + kx;
-    float2 v;
-    if (q == 0) {
-        const float k = K2h[o];
-        v = make_float2(k * s0.x, k * s0.y);
-    } else if (q == 1) {
-        const float k = Keh[o];
-        v = make_float2(k * s0.x, k * s0.y);
-    } else {
-        const bool ent = q >= 4;
-        const bool ydir = (q & 1) != 0;
-        const float* Dh = ent ? Deh : D2h;
-        const float k = ent ? Keh[o] : K2h[o];
-        const float d = ydir ? odd_transposed(Dh, kx, ky, L, H) : Dh[o];
-        const float2 s1 = ydir ? s1y : s1x;
-        v = make_float2(-d * s0.y - k * s1.x, d * s0.x - k * s1.y);
-    }
-    return conj2(v);
+    return make_float2(-d * s0.y - k * s1.x, d * s0.x - k * s1.y);
 }
 
 // Sum of one double per thread over the block (blockDim.x a multiple of 32,
@@ -1096,144 +1238,103 @@ __device__ __forceinline__ double block_sum_double(double v, double* red)
     return r;
 }
 
-// Z + n and the entropy double sum's terms of one column kx (Parseval over
-// the half spectra, FP32 terms summed in FP64 by the block in a fixed order)
-// into zcol[kx] and zcol[H + kx].  All threads of the block call it.
-__device__ __forceinline__ void column_sums(const float2* S0, const float2* S1x, const float2* S1y, const float2* S2,
-                                            int kx, int L, int H, const float* __restrict__ K2h,
-                                            const float* __restrict__ K1h, const float* __restrict__ D2h,
-                                            const float* __restrict__ Klh, float s2, double* __restrict__ zcol,
-                                            double* red)
-{
-    const float wgt = (kx == 0 || 2 * kx == L) ? 1.0f : 2.0f;
-    double zp = 0.0, lp = 0.0;
-    for (int ky = threadIdx.x; ky < L; ky += blockDim.x) {
-        const int64_t o = (int64_t)ky * H + kx;
-        const float2 s0 = S0[ky];
-        zp += (double)(wgt * z_term(s0, S1x[ky], S1y[ky], S2[ky], K2h[o], K1h[o], D2h[o],
-                                    odd_transposed(D2h, kx, ky, L, H), s2));
-        lp += (double)(wgt * Klh[o] * (s0.x * s0.x + s0.y * s0.y));
-    }
-    const double zs = block_sum_double(zp, red);
-    const double ls = block_sum_double(lp, red);
-    if (threadIdx.x == 0) {
-        zcol[kx] = zs;
-        zcol[H + kx] = ls;
-    }
-}
-
-constexpr int kColThreads = 1024;  // the column pass runs 4 and then 6 lines of a column at once
+constexpr int kColThreads = 1024;
+constexpr int kColSlots = 8;                        // warps per column in the Z sums
+constexpr int kColPerRound = kColThreads / 32 / kColSlots;
+constexpr int kColMaxC = 16;                        // columns per tile
 
 __device__ __forceinline__ void k_conv_cols_body(GridDev* Gp, const float2* __restrict__ tw, const float2* __restrict__ srow,
-                            const float* __restrict__ khat, float2* __restrict__ ucol, double* __restrict__ zcol,
+                            const float4* __restrict__ kc, float2* __restrict__ ucol, double* __restrict__ zcol,
                             int32_t n, int sm_f2)
 {
     extern __shared__ float2 smf[];
+    __shared__ LinePlan pl;
+    __shared__ double wz[32], wl[32];
     __shared__ double red[33];
     __shared__ bool last;
     const GridDev& G = *Gp;
     const int L = G.L, M = G.M, H = L / 2 + 1;
     const float s2 = G.s * G.s;
-    float2* stw = smf;
-    load_tw(stw, tw, L);
-    const int64_t MH = (int64_t)M * H, LH = (int64_t)L * H;
-    const float* K2h = khat;
-    const float* Keh = khat + LH;
-    const float* K1h = khat + 2 * LH;
-    const float* D2h = khat + 3 * LH;
-    const float* Deh = khat + 4 * LH;
-    const float* Klh = khat + 5 * LH;
-    int beg, end;
-    block_range(H, beg, end);
-    // Batched: 4 spectra + 6 products + 6 work lines per column, two FFT calls.
-    const int capb = (sm_f2 - L) / (16 * L);
-    if (capb >= 1) {
-        for (int k0 = beg; k0 < end; k0 += capb) {
-            const int nc = min(capb, end - k0);
-            float2* SP = smf + L;
-            float2* PR = SP + (size_t)4 * nc * L;
-            float2* PP = PR + (size_t)6 * nc * L;
-            __syncthreads();
-            // SP[(g nc + c) L + y]: spectrum g of column k0 + c (rows y >= M are padding)
-            for (int y = threadIdx.x; y < L; y += blockDim.x) {
-                if (y < M) {
-                    const float2* src = srow + (int64_t)y * H + k0;
-                    for (int g = 0; g < 4; ++g)
-                        for (int c = 0; c < nc; ++c) SP[(g * nc + c) * L + y] = src[(int64_t)g * MH + c];
-                } else {
-                    for (int r = 0; r < 4 * nc; ++r) SP[r * L + y] = make_float2(0.f, 0.f);
-                }
-            }
-            __syncthreads();
-            float2* R = fft_lines(SP, PP, 4 * nc, L, G, stw);
-            if (R != SP) {
-                for (int idx = threadIdx.x; idx < 4 * nc * L; idx += blockDim.x) SP[idx] = R[idx];
-                __syncthreads();
-            }
-            for (int ky = threadIdx.x; ky < L; ky += blockDim.x) {
-                for (int c = 0; c < nc; ++c) {
-                    const int kx = k0 + c;
-                    const float2 s0 = SP[(0 * nc + c) * L + ky], s1x = SP[(1 * nc + c) * L + ky];
-                    const float2 s1y = SP[(2 * nc + c) * L + ky];
-#pragma unroll
-                    for (int q = 0; q < 6; ++q)
-                        PR[(q * nc + c) * L + ky] = conv_product(q, s0, s1x, s1y, K2h, Keh, D2h, Deh, kx, ky, L, H);
-                }
-            }
-            __syncthreads();
-            for (int c = 0; c < nc; ++c)
-                column_sums(SP + (0 * nc + c) * L, SP + (1 * nc + c) * L, SP + (2 * nc + c) * L,
-                            SP + (3 * nc + c) * L, k0 + c, L, H, K2h, K1h, D2h, Klh, s2, zcol, red);
-            float2* R2 = fft_lines(PR, PP, 6 * nc, L, G, stw);
-            for (int y = threadIdx.x; y < M; y += blockDim.x) {
-                float2* dst = ucol + (int64_t)y * H + k0;
-                for (int q = 0; q < 6; ++q)
-                    for (int c = 0; c < nc; ++c) dst[(int64_t)q * MH + c] = conj2(R2[(q * nc + c) * L + y]);
+    make_line_plan(G, pl);
+    // six lines per column; the twiddles move to global memory (L1) when
+    // one column with them does not fit
+    const bool tw_smem = 7 * L + L + (L + 3) / 4 <= sm_f2;
+    const IpSmem sm = ip_smem(smf, sm_f2, L, false, tw_smem, tw);
+    __syncthreads();
+    make_digit_tables(pl, sm.drev, nullptr);
+    int C = (sm.avail / L - 1) / 6;
+    C = min(min(C, kColMaxC), (H + (int)gridDim.x - 1) / (int)gridDim.x);
+    if (C < 1) C = 1;
+    const int64_t MH = (int64_t)M * H;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = blockIdx.x; t * C < H; t += gridDim.x) {
+        const int k0 = t * C, nc = min(C, H - k0);
+        const int ld = (6 * nc + 1) * L <= sm.avail ? 6 * nc + 1 : 6 * nc;
+        float2* X = sm.X;
+        __syncthreads();
+        {
+            // line g nc + c: spectrum g of column k0 + c along y (rows >= M zero)
+            const int nl = 4 * nc, nbp = kColThreads / nl, tl = (int)threadIdx.x % nl, tb = (int)threadIdx.x / nl;
+            if (tb < nbp) {
+                const int g = tl / nc, c = tl - g * nc;
+                const float2* src = srow + g * MH + k0 + c;
+                for (int y = tb; y < L; y += nbp)
+                    X[(int64_t)y * ld + tl] = y < M ? src[(int64_t)y * H] : make_float2(0.f, 0.f);
             }
         }
-    } else {
-        // Long lines: four kept spectra + two work lines per column.
-        const int cap = line_cap(sm_f2, L, 6);
-        float2* buf[6];
-        for (int i = 0; i < 6; ++i) buf[i] = smf + L + (size_t)i * cap * L;
-        for (int k0 = beg; k0 < end; k0 += cap) {
-            const int nl = min(cap, end - k0);
-            float2* spec[4];
-            float2* pool[6] = {buf[0], buf[1], buf[2], buf[3], buf[4], buf[5]};
-            for (int gsel = 0; gsel < 4; ++gsel) {
-                float2* a = pool[gsel];
-                float2* b = pool[gsel + 1];
-                __syncthreads();
-                for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
-                    const int y = idx / nl, line = idx - y * nl;
-                    a[line * L + y] =
-                        y < M ? srow[(int64_t)gsel * MH + (int64_t)y * H + k0 + line] : make_float2(0.f, 0.f);
+        __syncthreads();
+        ip_fft<false>(X, ld, 4 * nc, pl, sm.tw);
+        // products in place at every position p (frequency drev[p]): line
+        // q nc + c receives U_q of column k0 + c, conjugated for the inverse
+        for (int c0 = 0; c0 < nc; c0 += kColPerRound) {
+            const int c = c0 + warp / kColSlots, wg = warp % kColSlots;
+            double zp = 0.0, lp = 0.0;
+            if (c < nc) {
+                const int kx = k0 + c;
+                const float wgt = (kx == 0 || 2 * kx == L) ? 1.0f : 2.0f;
+                for (int p = lane + 32 * wg; p < L; p += 32 * kColSlots) {
+                    float4 a, b;
+                    kc_at(kc, kx, sm.drev[p], L, H, a, b);
+                    float2* x = X + (int64_t)p * ld + c;
+                    const float2 s0 = x[0], s1x = x[nc], s1y = x[2 * nc], s2v = x[3 * nc];
+                    zp += (double)(wgt * z_term(s0, s1x, s1y, s2v, a.x, a.z, b.x, b.z, s2));
+                    lp += (double)(wgt * a.w * (s0.x * s0.x + s0.y * s0.y));
+                    x[0] = conj2(make_float2(a.x * s0.x, a.x * s0.y));
+                    x[nc] = conj2(make_float2(a.y * s0.x, a.y * s0.y));
+                    x[2 * nc] = conj2(odd_product(b.x, a.x, s0, s1x));
+                    x[3 * nc] = conj2(odd_product(b.z, a.x, s0, s1y));
+                    x[4 * nc] = conj2(odd_product(b.y, a.y, s0, s1x));
+                    x[5 * nc] = conj2(odd_product(b.w, a.y, s0, s1y));
                 }
-                __syncthreads();
-                float2* r = fft_lines(a, b, nl, L, G, stw);
-                spec[gsel] = r;
-                pool[gsel] = r;
-                pool[gsel + 1] = (r == a) ? b : a;
             }
-            float2* wa = pool[4];
-            float2* wb = pool[5];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                zp += __shfl_xor_sync(FULL, zp, o);
+                lp += __shfl_xor_sync(FULL, lp, o);
+            }
+            if (lane == 0) {
+                wz[warp] = zp;
+                wl[warp] = lp;
+            }
             __syncthreads();
-            for (int line = 0; line < nl; ++line)
-                column_sums(spec[0] + line * L, spec[1] + line * L, spec[2] + line * L, spec[3] + line * L,
-                            k0 + line, L, H, K2h, K1h, D2h, Klh, s2, zcol, red);
-            for (int q = 0; q < 6; ++q) {
-                __syncthreads();
-                for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
-                    const int ky = idx / nl, line = idx - ky * nl;
-                    wa[line * L + ky] = conv_product(q, spec[0][line * L + ky], spec[1][line * L + ky],
-                                                     spec[2][line * L + ky], K2h, Keh, D2h, Deh, k0 + line, ky, L, H);
+            if ((int)threadIdx.x < kColPerRound && c0 + (int)threadIdx.x < nc) {
+                double zs = 0.0, ls = 0.0;
+                for (int w = 0; w < kColSlots; ++w) {
+                    zs += wz[threadIdx.x * kColSlots + w];
+                    ls += wl[threadIdx.x * kColSlots + w];
                 }
-                __syncthreads();
-                float2* r = fft_lines(wa, wb, nl, L, G, stw);
-                for (int idx = threadIdx.x; idx < nl * M; idx += blockDim.x) {
-                    const int y = idx / nl, line = idx - y * nl;
-                    ucol[(int64_t)q * MH + (int64_t)y * H + k0 + line] = conj2(r[line * L + y]);
-                }
+                zcol[k0 + c0 + threadIdx.x] = zs;
+                zcol[H + k0 + c0 + threadIdx.x] = ls;
+            }
+            __syncthreads();
+        }
+        ip_fft<true>(X, ld, 6 * nc, pl, sm.tw);
+        {
+            const int nl = 6 * nc, nbp = kColThreads / nl, tl = (int)threadIdx.x % nl, tb = (int)threadIdx.x / nl;
+            if (tb < nbp) {
+                const int q = tl / nc, c = tl - q * nc;
+                float2* dst = ucol + q * MH + k0 + c;
+                for (int y = tb; y < M; y += nbp) dst[(int64_t)y * H] = conj2(X[(int64_t)y * ld + tl]);
             }
         }
     }
@@ -1264,10 +1365,10 @@ __device__ __forceinline__ void k_conv_cols_body(GridDev* Gp, const float2* __re
 }
 
 __global__ void __launch_bounds__(kColThreads) k_conv_cols(GridDev* Gp, const float2* __restrict__ tw, const float2* __restrict__ srow,
-                            const float* __restrict__ khat, float2* __restrict__ ucol, double* __restrict__ zcol,
+                            const float4* __restrict__ kc, float2* __restrict__ ucol, double* __restrict__ zcol,
                             int32_t n, int sm_f2)
 {
-    k_conv_cols_body(Gp, tw, srow, khat, ucol, zcol, n, sm_f2);
+    k_conv_cols_body(Gp, tw, srow, kc, ucol, zcol, n, sm_f2);
 }
 
 // Inverse row FFTs, three packed lines per row (U0 + i U1, U2 + i U3,
@@ -1450,7 +1551,7 @@ __global__ void __launch_bounds__(1024) k_spec_rows_b(const BatchGraph* __restri
 __global__ void __launch_bounds__(1024) k_spec_cols_b(const BatchGraph* __restrict__ bg, int sm_f2)
 {
     const BatchGraph& b = bg[blockIdx.y];
-    k_spec_cols_body(b.w.g, b.w.tw, b.w.krow, b.w.khat, sm_f2);
+    k_spec_cols_body(b.w.g, b.w.tw, b.w.krow, b.w.kc, sm_f2);
 }
 
 __global__ void __launch_bounds__(1024) k_conv_rows_fwd_b(const BatchGraph* __restrict__ bg, int sm_f2)
@@ -1462,7 +1563,7 @@ __global__ void __launch_bounds__(1024) k_conv_rows_fwd_b(const BatchGraph* __re
 __global__ void __launch_bounds__(kColThreads) k_conv_cols_b(const BatchGraph* __restrict__ bg, int sm_f2)
 {
     const BatchGraph& b = bg[blockIdx.y];
-    k_conv_cols_body(b.w.g, b.w.tw, b.w.srow, b.w.khat, b.w.ucol, b.w.zcol, b.n, sm_f2);
+    k_conv_cols_body(b.w.g, b.w.tw, b.w.srow, b.w.kc, b.w.ucol, b.w.zcol, b.n, sm_f2);
 }
 
 __global__ void __launch_bounds__(1024) k_conv_rows_inv_b(const BatchGraph* __restrict__ bg, int sm_f2)
@@ -1474,7 +1575,11 @@ constexpr int kPsumBlocks = 304;
 
 // Room for the twiddles plus six lines of the longest length (the column
 // pass keeps four spectra and two work lines), at least 64 KB.
-size_t fft_smem_bytes(int Lmax) { return std::max<size_t>(64 * 1024, (size_t)7 * Lmax * 8); }
+// Dynamic shared memory of every FFT pass: the most a block may take less a
+// margin for the static arrays.  A fixed size makes every tiling decision a
+// function of the grid alone.
+constexpr size_t kFftSmemBytes = 230400;
+static_assert(kFftSmemBytes >= (size_t)(6 * kLMax + (kLMax + 3) / 4) * 8, "six FFT lines of kLMax must fit");
 
 }  // namespace
 
@@ -1514,10 +1619,10 @@ IterWs iter_carve(Carve& c, const IterShape& sh)
     w.bpre = c.take<int32_t>(kMaxScanChunks);
     w.su = c.take<float2>(sh.n);
     w.wflt = c.take<float4>(MM);
-    const int64_t LH = (int64_t)sh.Lmax * (sh.Lmax / 2 + 1);
+    const int64_t HH = (int64_t)(sh.Lmax / 2 + 1) * (sh.Lmax / 2 + 1);
     const int64_t MH = (int64_t)sh.Mmax * (sh.Lmax / 2 + 1);
-    w.krow = c.take<float2>(3 * LH);
-    w.khat = c.take<float>(6 * LH);
+    w.krow = c.take<float2>(3 * HH);
+    w.kc = c.take<float4>(2 * HH);
     w.srow = c.take<float2>(4 * MH);
     w.ucol = c.take<float2>(6 * MH);
     w.fields = c.take<float>(MM * kFieldStride);
@@ -1582,7 +1687,7 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
                                                       Y, w.bcnt, n, p->box_width_max, p->min_boxes, p->max_boxes, P,
                                                       plain ? 0 : 1);
     count_launches(1);
-    const size_t fsm = fft_smem_bytes(sh.Lmax);
+    const size_t fsm = kFftSmemBytes;
     const int f2 = (int)(fsm / sizeof(float2));
     const int fb = num_sms();  // FFT blocks: one per SM
     // The kernel spectra need only the grid parameters: unless kernels are
@@ -1595,7 +1700,7 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
         if ((e2 = cudaEventRecord(aux->fork, s)) != cudaSuccess) return e2;
         if ((e2 = cudaStreamWaitEvent(aux->branch, aux->fork, 0)) != cudaSuccess) return e2;
         k_spec_rows<<<fb, kFftThreads, fsm, aux->branch>>>(w.g, w.tw, p->eps, w.krow, f2);
-        k_spec_cols<<<fb, kFftThreads, fsm, aux->branch>>>(w.g, w.tw, w.krow, w.khat, f2);
+        k_spec_cols<<<fb, kFftThreads, fsm, aux->branch>>>(w.g, w.tw, w.krow, w.kc, f2);
         count_launches(2);
         if ((e2 = cudaEventRecord(aux->join, aux->branch)) != cudaSuccess) return e2;
     }
@@ -1639,7 +1744,7 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
     profile_start(LTSNET_KERNEL_CONV, s);
     if (!fork) {
         k_spec_rows<<<fb, kFftThreads, fsm, s>>>(w.g, w.tw, p->eps, w.krow, f2);
-        k_spec_cols<<<fb, kFftThreads, fsm, s>>>(w.g, w.tw, w.krow, w.khat, f2);
+        k_spec_cols<<<fb, kFftThreads, fsm, s>>>(w.g, w.tw, w.krow, w.kc, f2);
         count_launches(2);
     }
     if (sh.conv_mode == LTSNET_CONV_DFT_GEMM) {
@@ -1655,7 +1760,7 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
         cudaError_t e2 = cudaStreamWaitEvent(s, aux->join, 0);
         if (e2 != cudaSuccess) return e2;
     }
-    k_conv_cols<<<fb, kColThreads, fsm, s>>>(w.g, w.tw, w.srow, w.khat, w.ucol, w.zcol, n, f2);
+    k_conv_cols<<<fb, kColThreads, fsm, s>>>(w.g, w.tw, w.srow, w.kc, w.ucol, w.zcol, n, f2);
     k_conv_rows_inv<<<fb, kFftThreads, fsm, s>>>(w.g, w.tw, w.ucol, w.fields, w.wflt, w.bcnt, plain ? 1 : 0, f2);
     count_launches(3);
     profile_stop(LTSNET_KERNEL_CONV, s);
@@ -1664,7 +1769,7 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
 
 cudaError_t grid_set_smem_attrs()
 {
-    const int fsm = (int)fft_smem_bytes(kLMax);
+    const int fsm = (int)kFftSmemBytes;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_spec_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
     if ((e = cudaFuncSetAttribute(k_spec_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, fsm))) return e;
@@ -1692,7 +1797,7 @@ cudaError_t launch_grid_phase_batched(const BatchGraph* bg, int32_t ng, const Ba
     const dim3 gpt(tiles, (unsigned)ng);
     k_setup_b<<<gpt, kBoxThreads, 0, s>>>(bg, parity, p->box_width_max, p->min_boxes, p->max_boxes, P);
     count_launches(1);
-    const size_t fsm = fft_smem_bytes(sh.Lmax);
+    const size_t fsm = kFftSmemBytes;
     const int f2 = (int)(fsm / sizeof(float2));
     const dim3 gfft((unsigned)bs.fft_blocks, (unsigned)ng);
     AuxStreams* aux = nullptr;

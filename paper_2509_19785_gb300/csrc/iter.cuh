@@ -71,8 +71,8 @@ struct IterWs {
     int32_t* bpre;       // their exclusive scan
     float2* su;          // n local coordinates, box-sorted
     float4* wflt;        // M_max^2 float charges (plain form)
-    float2* krow;        // 3 * L_max * H kernel row transforms (H = L_max/2 + 1)
-    float* khat;         // 5 * L_max * H kernel spectra (K2, Ke, K1, Im K2dx, Im Kedx)
+    float2* krow;        // 3 * H * H kernel row transforms [q][kx][a] (H = L_max/2 + 1)
+    float4* kc;          // H * H records of 8 floats: kernel spectra (K2, Ke, K1, ln; D2x, Dex, D2y, Dey)
     float2* srow;        // 4 * M_max * H row half spectra of S0, S1x, S1y, S2
     float2* ucol;        // 6 * M_max * H column results
     float* fields;       // M_max^2 * 8
@@ -109,6 +109,12 @@ struct BatchGraph {
     float2* gains;
     Stage st;
     int32_t n;
+    // rows of P summed in chunks before the fused kernel (nchunks = 0: none)
+    const int32_t* hbase;
+    const int32_t* crow;
+    const int64_t* cstart;
+    float2* hpartial;
+    int32_t nchunks;
 };
 
 // Launch shape of the batched kernels (blocks per graph), chosen by the

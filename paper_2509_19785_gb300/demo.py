@@ -144,6 +144,7 @@ def run_batch(args):
     mode = lt.BATCH_ONE_LAUNCH if args.batch_form == "one" else lt.BATCH_PER_GRAPH
     times = []
     boxes = None
+    c0 = lt.launch_count()
     for _ in range(args.repeat):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -156,7 +157,8 @@ def run_batch(args):
     print(json.dumps({"graph": "batch", "graphs": len(gs), "vertices": int(sum(g.n for g in gs)),
                       "form": args.batch_form, "iters": args.iters,
                       "seconds": [round(t, 4) for t in times], "graphs_per_s": round(len(gs) / min(times), 2),
-                      "max_boxes_used": int(boxes.max()), "finite": bool(torch.isfinite(Yb).all())}))
+                      "max_boxes_used": int(boxes.max()), "graphs_at_cap": int((boxes >= params.max_boxes).sum()),
+                      "launches": lt.launch_count() - c0, "finite": bool(torch.isfinite(Yb).all())}))
 
 
 if __name__ == "__main__":
