@@ -29,7 +29,17 @@ const ltsnet_stage kDefaultStages[2] = {
 
 }  // namespace
 
-void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+namespace {
+thread_local int64_t t_launches = 0;  // this thread's share of g_launches
+}  // namespace
+
+void count_launches(int64_t k)
+{
+    g_launches.fetch_add(k, std::memory_order_relaxed);
+    t_launches += k;
+}
+
+int64_t thread_launch_count() { return t_launches; }
 
 namespace {
 constexpr int kMaxDev = 64;

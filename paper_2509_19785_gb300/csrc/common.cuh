@@ -63,6 +63,9 @@ enum OnceSlot { kOnceGridAttrs = 0, kOnceFusedAttrs, kOnceRadix, kOnceCalib, kOn
 cudaError_t once_per_device(int slot, cudaError_t (*f)());
 // Host: kernels launched by this library (instrumentation).
 void count_launches(int64_t k);
+// Launches counted by the calling thread (a capture on one thread measures
+// its own graph's size while other threads launch).
+int64_t thread_launch_count();
 // Host: remember the last failing CUDA call of this thread (ltsnet_last_cuda_error).
 void note_cuda_error(cudaError_t e, const char* where);
 // Host: internal streams/events of a device (abi.cu).

@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_fused_b(const BatchGraph* 
     const float2* cur = parity ? b.w.yalt : b.Y;
     float2* nxt = parity ? b.Y : b.w.yalt;
     k_fused_body<P, true, D16>(b.P_row, b.P_col, b.P_d16, b.P_val, b.n, cur, nxt, b.upd, b.gains, b.w.g, b.w.fields,
-                               b.st, b.w.bounds + 2 * (parity ^ 1), nullptr, nullptr, b.w.st, nullptr, nullptr);
+                               b.st, b.w.bounds + 2 * (parity ^ 1), nullptr, nullptr, b.w.st, b.hbase, b.hpartial);
 }
 
 constexpr size_t kFusedSmem = 0;  // the windows live in registers
@@ -447,13 +447,13 @@ constexpr size_t kFusedSmem = 0;  // the windows live in registers
 // Attraction sums of the chunks of the long rows: one warp per chunk of
 // kChunk entries of one row, lanes striding over the entries.
 template <bool D16>
-__global__ void __launch_bounds__(256) k_attr_chunks(const int64_t* __restrict__ P_row,
-                                                     const int32_t* __restrict__ P_col,
-                                                     const int16_t* __restrict__ P_d16,
-                                                     const float* __restrict__ P_val, int32_t n,
-                                                     const float2* __restrict__ Y, const int32_t* __restrict__ crow,
-                                                     const int64_t* __restrict__ cstart, int32_t nchunks,
-                                                     float2* __restrict__ partial)
+__device__ __forceinline__ void k_attr_chunks_body(const int64_t* __restrict__ P_row,
+                                                   const int32_t* __restrict__ P_col,
+                                                   const int16_t* __restrict__ P_d16,
+                                                   const float* __restrict__ P_val, int32_t n,
+                                                   const float2* __restrict__ Y, const int32_t* __restrict__ crow,
+                                                   const int64_t* __restrict__ cstart, int32_t nchunks,
+                                                   float2* __restrict__ partial)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -474,6 +474,28 @@ __global__ void __launch_bounds__(256) k_attr_chunks(const int64_t* __restrict__
         ay = warp_sum(ay);
         if (lane == 0) partial[c] = make_float2(ax, ay);
     }
+}
+
+template <bool D16>
+__global__ void __launch_bounds__(256) k_attr_chunks(const int64_t* __restrict__ P_row,
+                                                     const int32_t* __restrict__ P_col,
+                                                     const int16_t* __restrict__ P_d16,
+                                                     const float* __restrict__ P_val, int32_t n,
+                                                     const float2* __restrict__ Y, const int32_t* __restrict__ crow,
+                                                     const int64_t* __restrict__ cstart, int32_t nchunks,
+                                                     float2* __restrict__ partial)
+{
+    k_attr_chunks_body<D16>(P_row, P_col, P_d16, P_val, n, Y, crow, cstart, nchunks, partial);
+}
+
+// The long rows' chunk sums of every graph of a batch (graph = blockIdx.y).
+template <bool D16>
+__global__ void __launch_bounds__(256) k_attr_chunks_b(const BatchGraph* __restrict__ bg, int parity)
+{
+    const BatchGraph& b = bg[blockIdx.y];
+    if (b.nchunks == 0) return;
+    k_attr_chunks_body<D16>(b.P_row, b.P_col, b.P_d16, b.P_val, b.n, parity ? b.w.yalt : b.Y, b.crow, b.cstart,
+                            b.nchunks, b.hpartial);
 }
 
 // Chunks per row (0 for rows of at most kHeavyRow entries).
@@ -920,7 +942,7 @@ ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const in
         }
         const int32_t pairs = graphs ? (run - done) / 2 : 0;
         if (pairs >= 2) {
-            const int64_t c0 = ltsnet_launch_count();
+            const int64_t c0 = thread_launch_count();
             cudaGraph_t graph = nullptr;
             cudaGraphExec_t exec = nullptr;
             LT_CUDA(cudaStreamBeginCapture(aux->capture, cudaStreamCaptureModeThreadLocal));
@@ -935,7 +957,7 @@ ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const in
             e = cudaGraphInstantiate(&exec, graph, 0);
             cudaGraphDestroy(graph);
             LT_CUDA(e);
-            const int64_t per = ltsnet_launch_count() - c0;
+            const int64_t per = thread_launch_count() - c0;
             for (int32_t q = 0; q < pairs; ++q) {
                 e = cudaGraphLaunch(exec, s);
                 if (e != cudaSuccess) break;
@@ -1178,9 +1200,18 @@ ltsnet_status batched_loop(BatchGraph* const* bg, const std::vector<BatchGraph>&
     AuxStreams* aux = nullptr;
     const bool graphs = !profiling_active() && aux_streams(&aux) == cudaSuccess;
     const unsigned fblocks = (unsigned)std::max<int64_t>(1, ((int64_t)bs.max_n + kFusedWarps * 32 - 1) / (kFusedWarps * 32));
+    int64_t max_chunks = 0;
+    for (const BatchGraph& b : hg) max_chunks = std::max<int64_t>(max_chunks, b.nchunks);
+    const unsigned cblocks = (unsigned)std::min<int64_t>(num_sms() * 2, (max_chunks * 32 + 255) / 256);
     auto iteration = [&](const BatchGraph* dbg, int parity, cudaStream_t st) -> cudaError_t {
         cudaError_t e = launch_grid_phase_batched(dbg, ng, bs, sh, p, parity, st);
         if (e != cudaSuccess) return e;
+        if (max_chunks > 0) {
+            // chunk sums of the long rows (graphs without any return at once)
+            if (d16) k_attr_chunks_b<true><<<dim3(cblocks, (unsigned)ng), 256, 0, st>>>(dbg, parity);
+            else k_attr_chunks_b<false><<<dim3(cblocks, (unsigned)ng), 256, 0, st>>>(dbg, parity);
+            count_launches(1);
+        }
         profile_start(LTSNET_KERNEL_FUSED_UPDATE, st);
         const dim3 grid(fblocks, (unsigned)ng);
 #define LT_FB(PP)                                                                              \
@@ -1216,7 +1247,7 @@ ltsnet_status batched_loop(BatchGraph* const* bg, const std::vector<BatchGraph>&
         }
         const int64_t pairs = graphs ? (run - done) / 2 : 0;
         if (pairs >= 2) {
-            const int64_t c0 = ltsnet_launch_count();
+            const int64_t c0 = thread_launch_count();
             cudaGraph_t graph = nullptr;
             cudaGraphExec_t exec = nullptr;
             LT_CUDA(cudaStreamBeginCapture(aux->capture, cudaStreamCaptureModeThreadLocal));
@@ -1230,7 +1261,7 @@ ltsnet_status batched_loop(BatchGraph* const* bg, const std::vector<BatchGraph>&
             e = cudaGraphInstantiate(&exec, graph, 0);
             cudaGraphDestroy(graph);
             LT_CUDA(e);
-            const int64_t per = ltsnet_launch_count() - c0;
+            const int64_t per = thread_launch_count() - c0;
             for (int64_t q = 0; q < pairs; ++q) {
                 e = cudaGraphLaunch(exec, s);
                 if (e != cudaSuccess) break;
@@ -1531,11 +1562,8 @@ extern "C" ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx
     }
     // one launch per phase over all graphs
     cudaStream_t s = (cudaStream_t)stream;
-    bool d16 = true, heavy = false;
-    for (int32_t g = 0; g < n_graphs; ++g) {
-        d16 = d16 && prep[g].d16;
-        heavy = heavy || prep[g].hr.nchunks > 0;
-    }
+    bool d16 = true;
+    for (int32_t g = 0; g < n_graphs; ++g) d16 = d16 && prep[g].d16;
     const IterShape shmax = iter_shape((int32_t)max_n, p);
     std::vector<BatchGraph> hg(n_graphs);
     std::vector<RunWs> rws(n_graphs);
@@ -1557,16 +1585,15 @@ extern "C" ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx
         b.upd = r.upd;
         b.gains = r.gains;
         b.n = ng;
+        const HeavyRows& hr = prep[g].hr;
+        b.hbase = hr.hbase;
+        b.crow = hr.crow;
+        b.cstart = hr.cstart;
+        b.hpartial = hr.partial;
+        b.nchunks = hr.nchunks;
     }
     ltsnet_status rc = LTSNET_OK;
-    if (heavy) {
-        // rows of P longer than the fused kernel's groups take: each graph on
-        // its own (the one-launch kernels do not sum row chunks)
-        for (int32_t g = 0; g < n_graphs && rc == LTSNET_OK; ++g)
-            rc = optimize_core(hg[g].P_row, hg[g].P_col, hg[g].P_d16, hg[g].P_val, prep[g].hr, hg[g].n, p, hg[g].Y,
-                               hg[g].upd, hg[g].gains, 0, (int32_t)schedule_length(p), hg[g].w,
-                               iter_shape(hg[g].n, p), s);
-    } else {
+    {
         // descriptor arrays, one per schedule stage (the stage coefficients
         // depend on each graph's n)
         char* dbase = (char*)ws + one_launch_slices(n_graphs, vtx_off, edge_off, p, nullptr) -

@@ -445,11 +445,14 @@ def test_run_batched_equals_single_runs(ltlib, mode):
     workers than graphs -- the one-launch form (every phase one launch over
     all graphs, two launch shapes) and the per-graph form -- gives every
     graph exactly the layout ltsnet_run gives it alone; the one-launch form
-    also reports each graph's largest box count, equal to its own run's."""
+    also reports each graph's largest box count, equal to its own run's.
+    The star's centre has a row of P longer than the fused kernel's groups
+    take, summed in chunks in both forms."""
     import torch
 
+    star = synth.csr_from_edges(2501, np.zeros(2500, np.int64), np.arange(1, 2501, dtype=np.int64), "star2500")
     graphs = [synth.grid2d(20, 30), synth.random_recursive_tree(900, 5), synth.sbm([300, 250, 200], 9.5, 40, 7),
-              synth.grid2d(9, 7), synth.rgg(1500, seed=9, lcc=True), synth.random_recursive_tree(150, 2)]
+              synth.grid2d(9, 7), star, synth.rgg(1500, seed=9, lcc=True), synth.random_recursive_tree(150, 2)]
     Y0s = [synth.initial_layout(g.n, 11 + i) for i, g in enumerate(graphs)]
     params = ltlib.Params(stages=ltlib.default_stages(120))
     single = [ltlib.run(g.row_ptr, g.col, torch.from_numpy(y0), params)[0] for g, y0 in zip(graphs, Y0s)]
