@@ -112,84 +112,9 @@ __device__ __forceinline__ void dft_small<5>(float2* v)
     v[3] = csub(m2, n2);
 }
 
-// One radix-R Stockham stage on nl lines (stride ld): butterfly j of a line
-// reads a[j + r L/R] (r = 0..R-1), multiplies by the twiddles
-// e^{-2 pi i (j mod Ns) r / (Ns R)}, and writes b[(j - j mod Ns) R + j mod Ns
-// + q Ns].  When a line has fewer butterflies than the block has threads,
-// each thread keeps one j for several lines and loads its twiddles once.
-template <int R>
-__device__ __forceinline__ void fft_stage(const float2* a, float2* b, int nl, int ld, int L, int Ns,
-                                          const float2* tw)
-{
-    const int nbf = L / R;
-    const int ts = L / (Ns * R);
-    const int nt = blockDim.x;
-    if (nbf < nt) {
-        const int lpp = nt / nbf;
-        const int t0 = threadIdx.x / nbf;
-        if (t0 >= lpp) return;
-        const int j = threadIdx.x - t0 * nbf;
-        const int jm = j % Ns;
-        const int ob = (j - jm) * R + jm;
-        float2 w[R];
-#pragma unroll
-        for (int r = 1; r < R; ++r) w[r] = tw[jm * r * ts];
-        for (int line = t0; line < nl; line += lpp) {
-            const float2* in = a + line * ld;
-            float2* out = b + line * ld;
-            float2 v[R];
-            v[0] = in[j];
-#pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(in[j + r * nbf], w[r]);
-            dft_small<R>(v);
-#pragma unroll
-            for (int q = 0; q < R; ++q) out[ob + q * Ns] = v[q];
-        }
-    } else {
-        for (int line = 0; line < nl; ++line) {
-            const float2* in = a + line * ld;
-            float2* out = b + line * ld;
-            for (int j = threadIdx.x; j < nbf; j += nt) {
-                const int jm = j % Ns;
-                const int ob = (j - jm) * R + jm;
-                float2 v[R];
-                v[0] = in[j];
-#pragma unroll
-                for (int r = 1; r < R; ++r) v[r] = cmul(in[j + r * nbf], tw[jm * r * ts]);
-                dft_small<R>(v);
-#pragma unroll
-                for (int q = 0; q < R; ++q) out[ob + q * Ns] = v[q];
-            }
-        }
-    }
-}
-
-// Forward DFT (e^{-2 pi i jk/L}) of `nl` lines of length L (stride ld) held in
-// shared memory, mixed radix 4/2/3/5 Stockham autosort with ping-pong buffers
-// a, b.  Returns the buffer holding the result.  All threads of the block
-// must call it.
-__device__ float2* fft_lines(float2* a, float2* b, int nl, int ld, const GridDev& g, const float2* tw)
-{
-    const int L = g.L;
-    int Ns = 1;
-    for (int st = 0; st < g.nst; ++st) {
-        const int R = g.radix[st];
-        switch (R) {
-            case 4: fft_stage<4>(a, b, nl, ld, L, Ns, tw); break;
-            case 2: fft_stage<2>(a, b, nl, ld, L, Ns, tw); break;
-            case 3: fft_stage<3>(a, b, nl, ld, L, Ns, tw); break;
-            default: fft_stage<5>(a, b, nl, ld, L, Ns, tw); break;
-        }
-        __syncthreads();
-        float2* t = a;
-        a = b;
-        b = t;
-        Ns *= R;
-    }
-    return a;
-}
-
 // ---- in-place FFTs of interleaved line batches ----------------------------
+constexpr int kIpThreads = 512;  // threads of the in-place kernels (128 registers for two stages at once)
+
 // nl lines of length L held interleaved in shared memory, element t of line
 // l at X[t * ld + l] (ld = nl rounded up to odd, so that both a walk along a
 // line and a walk across lines hit distinct banks).  Decimation in frequency
@@ -209,6 +134,9 @@ struct LinePlan {
     int32_t m[kMaxRadix];
     uint32_t mg[kMaxRadix];  // floor(2^32 / m) + 1: b = umulhi(beta, mg) exactly for beta, m < 2^12
     int32_t ts[kMaxRadix];
+    int32_t np;                // register passes: stage ps[k], and ps[k] + 1 when pp[k]
+    int32_t ps[kMaxRadix];
+    int32_t pp[kMaxRadix];
 };
 
 // Thread 0 fills the plan from the grid's radix sequence; the caller syncs.
@@ -227,6 +155,17 @@ __device__ __forceinline__ void make_line_plan(const GridDev& g, LinePlan& pl)
         pl.ts[k] = g.L / N;
         N = m;
     }
+    // stages st, st + 1 share one register pass unless their product is above
+    // 16 or the first is 5 (registers at 1024 threads)
+    int np = 0;
+    for (int st = 0; st < g.nst;) {
+        const bool pair = st + 1 < g.nst && g.radix[st] * g.radix[st + 1] <= 16 && g.radix[st] != 5;
+        pl.ps[np] = st;
+        pl.pp[np] = pair ? 1 : 0;
+        ++np;
+        st += pair ? 2 : 1;
+    }
+    pl.np = np;
 }
 
 // drev[p] = the frequency that DIF leaves at position p; pos_of is its
@@ -276,9 +215,99 @@ __device__ __forceinline__ void ip_stage(float2* X, int ld, int nl, const LinePl
     }
 }
 
+// Stages st and st + 1 in registers: the R1 R2 positions b N + j' + r1 m +
+// r2 m2 (N = R1 m, m = R2 m2, j' < m2) are closed under both stages.  DIF:
+// stage st over r1 for each r2 (j = j' + r2 m2), then stage st + 1 over r2 for
+// each output q1 of the first.  DIT: the same two stages transposed, in the
+// reverse order.
+template <int R1, int R2, bool DIT>
+__device__ __forceinline__ void ip_stage2(float2* X, int ld, const LinePlan& pl, int st, const float2* tw, int tl,
+                                          int tb, int nbp)
+{
+    const int m = pl.m[st], m2 = pl.m[st + 1];
+    const uint32_t mg2 = pl.mg[st + 1];
+    const int ts1 = pl.ts[st], ts2 = pl.ts[st + 1];
+    const int nb = pl.L / (R1 * R2);
+    for (int beta = tb; beta < nb; beta += nbp) {
+        const int b = m2 > 1 ? (int)__umulhi((uint32_t)beta, mg2) : beta;
+        const int jp = beta - b * m2;
+        float2* x = X + (int64_t)(b * R1 * m + jp) * ld + tl;
+        float2 v[R1][R2];
+#pragma unroll
+        for (int r1 = 0; r1 < R1; ++r1)
+#pragma unroll
+            for (int r2 = 0; r2 < R2; ++r2) v[r1][r2] = x[(int64_t)(r1 * m + r2 * m2) * ld];
+        if (!DIT) {
+#pragma unroll
+            for (int r2 = 0; r2 < R2; ++r2) {
+                float2 u[R1];
+#pragma unroll
+                for (int r1 = 0; r1 < R1; ++r1) u[r1] = v[r1][r2];
+                dft_small<R1>(u);
+                const int j = jp + r2 * m2;
+#pragma unroll
+                for (int q1 = 0; q1 < R1; ++q1) v[q1][r2] = q1 ? cmul(u[q1], tw[j * q1 * ts1]) : u[0];
+            }
+#pragma unroll
+            for (int q1 = 0; q1 < R1; ++q1) {
+                dft_small<R2>(v[q1]);
+#pragma unroll
+                for (int q2 = 1; q2 < R2; ++q2) v[q1][q2] = cmul(v[q1][q2], tw[jp * q2 * ts2]);
+            }
+        } else {
+#pragma unroll
+            for (int r1 = 0; r1 < R1; ++r1) {
+#pragma unroll
+                for (int r2 = 1; r2 < R2; ++r2) v[r1][r2] = cmul(v[r1][r2], tw[jp * r2 * ts2]);
+                dft_small<R2>(v[r1]);
+            }
+#pragma unroll
+            for (int q2 = 0; q2 < R2; ++q2) {
+                const int j = jp + q2 * m2;
+                float2 u[R1];
+#pragma unroll
+                for (int r1 = 0; r1 < R1; ++r1) u[r1] = r1 ? cmul(v[r1][q2], tw[j * r1 * ts1]) : v[0][q2];
+                dft_small<R1>(u);
+#pragma unroll
+                for (int q1 = 0; q1 < R1; ++q1) v[q1][q2] = u[q1];
+            }
+        }
+#pragma unroll
+        for (int r1 = 0; r1 < R1; ++r1)
+#pragma unroll
+            for (int r2 = 0; r2 < R2; ++r2) x[(int64_t)(r1 * m + r2 * m2) * ld] = v[r1][r2];
+    }
+}
+
+// One pass over the lines: stages st (and st + 1 when pair) of the plan.
+template <bool DIT>
+__device__ __forceinline__ void ip_pass(float2* X, int ld, int nl, const LinePlan& pl, int st, bool pair,
+                                        const float2* tw, int tl, int tb, int nbp)
+{
+    if (!pair) {
+        switch (pl.R[st]) {
+            case 4: ip_stage<4, DIT>(X, ld, nl, pl, st, tw, tl, tb, nbp); break;
+            case 2: ip_stage<2, DIT>(X, ld, nl, pl, st, tw, tl, tb, nbp); break;
+            case 3: ip_stage<3, DIT>(X, ld, nl, pl, st, tw, tl, tb, nbp); break;
+            default: ip_stage<5, DIT>(X, ld, nl, pl, st, tw, tl, tb, nbp); break;
+        }
+        return;
+    }
+    switch (pl.R[st] * 8 + pl.R[st + 1]) {
+        case 4 * 8 + 4: ip_stage2<4, 4, DIT>(X, ld, pl, st, tw, tl, tb, nbp); break;
+        case 4 * 8 + 2: ip_stage2<4, 2, DIT>(X, ld, pl, st, tw, tl, tb, nbp); break;
+        case 4 * 8 + 3: ip_stage2<4, 3, DIT>(X, ld, pl, st, tw, tl, tb, nbp); break;
+        case 2 * 8 + 3: ip_stage2<2, 3, DIT>(X, ld, pl, st, tw, tl, tb, nbp); break;
+        case 2 * 8 + 5: ip_stage2<2, 5, DIT>(X, ld, pl, st, tw, tl, tb, nbp); break;
+        case 3 * 8 + 3: ip_stage2<3, 3, DIT>(X, ld, pl, st, tw, tl, tb, nbp); break;
+        default: ip_stage2<3, 5, DIT>(X, ld, pl, st, tw, tl, tb, nbp); break;  // 3 x 5
+    }
+}
+
 // Forward DFT of the nl interleaved lines in place: DIF (natural order in,
-// digit-reversed out) or DIT (digit-reversed in, natural out).  All threads
-// of the block call it; it ends with a barrier.
+// digit-reversed out) or DIT (digit-reversed in, natural out), in the
+// plan's register passes (DIT runs them in reverse).  All threads of the
+// block call it; it ends with a barrier.
 template <bool DIT>
 __device__ void ip_fft(float2* X, int ld, int nl, const LinePlan& pl, const float2* tw)
 {
@@ -286,16 +315,9 @@ __device__ void ip_fft(float2* X, int ld, int nl, const LinePlan& pl, const floa
     const int tl = (int)threadIdx.x % nl;
     const int tb = (int)threadIdx.x / nl;
     const bool on = tb < nbp;
-    for (int k = 0; k < pl.nst; ++k) {
-        const int st = DIT ? pl.nst - 1 - k : k;
-        if (on) {
-            switch (pl.R[st]) {
-                case 4: ip_stage<4, DIT>(X, ld, nl, pl, st, tw, tl, tb, nbp); break;
-                case 2: ip_stage<2, DIT>(X, ld, nl, pl, st, tw, tl, tb, nbp); break;
-                case 3: ip_stage<3, DIT>(X, ld, nl, pl, st, tw, tl, tb, nbp); break;
-                default: ip_stage<5, DIT>(X, ld, nl, pl, st, tw, tl, tb, nbp); break;
-            }
-        }
+    for (int k = 0; k < pl.np; ++k) {
+        const int q = DIT ? pl.np - 1 - k : k;
+        if (on) ip_pass<DIT>(X, ld, nl, pl, pl.ps[q], pl.pp[q] != 0, tw, tl, tb, nbp);
         __syncthreads();
     }
 }
@@ -933,24 +955,12 @@ __global__ void k_spread_atomic(const float2* __restrict__ Y, int32_t n, const G
 }
 
 // Work split: block b takes units [b*per, min(total, (b+1)*per)).
-__device__ __forceinline__ void block_range(int total, int& beg, int& end)
-{
-    const int per = (total + gridDim.x - 1) / gridDim.x;
-    beg = blockIdx.x * per;
-    end = min(total, beg + per);
-}
 
 __device__ __forceinline__ void load_tw(float2* stw, const float2* __restrict__ tw, int L)
 {
     for (int t = threadIdx.x; t < L; t += blockDim.x) stw[t] = tw[t];
 }
 
-// Lines of length L that fit `bufs` buffers next to the twiddles.
-__device__ __forceinline__ int line_cap(int sm_f2, int L, int bufs)
-{
-    const int c = (sm_f2 - L) / (bufs * L);
-    return c < 1 ? 1 : c;
-}
 
 // Signed node offset of circulant index a in [0, L): a for a < M, a - L for
 // a > L - M, none (the unused middle index) otherwise.
@@ -1065,7 +1075,7 @@ __device__ __forceinline__ void k_spec_rows_body(const GridDev* __restrict__ Gp,
     }
 }
 
-__global__ void __launch_bounds__(1024) k_spec_rows(const GridDev* __restrict__ Gp, const float2* __restrict__ tw, float eps,
+__global__ void __launch_bounds__(kIpThreads) k_spec_rows(const GridDev* __restrict__ Gp, const float2* __restrict__ tw, float eps,
                             float2* __restrict__ krow, int sm_f2)
 {
     k_spec_rows_body(Gp, tw, eps, krow, sm_f2);
@@ -1098,11 +1108,25 @@ __device__ __forceinline__ void k_spec_cols_body(const GridDev* __restrict__ Gp,
         const int k0 = t * C, nc = min(C, H - k0), nl = 3 * nc;
         const int ld = (nl | 1) * L <= sm.avail ? (nl | 1) : nl;
         __syncthreads();
-        for (int line = 0; line < nl; ++line) {
-            const int q = line / nc, c = line - q * nc;
-            const float2* src = krow + ((int64_t)q * H + k0 + c) * H;
-#pragma unroll 4
-            for (int a = threadIdx.x; a < L; a += blockDim.x) sm.X[(int64_t)a * ld + line] = src[a < H ? a : L - a];
+        // (line, a), a fastest: the mirrored rows, loads batched before the stores
+        const int tot = nl * L;
+        for (int i0 = threadIdx.x; i0 < tot; i0 += 8 * (int)blockDim.x) {
+            float2 v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int i = i0 + k * (int)blockDim.x;
+                const int line = i / L, a = i - line * L;
+                const int q = line / nc, c = line - q * nc;
+                v[k] = i < tot ? krow[((int64_t)q * H + k0 + c) * H + (a < H ? a : L - a)] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int i = i0 + k * (int)blockDim.x;
+                if (i < tot) {
+                    const int line = i / L, a = i - line * L;
+                    sm.X[(int64_t)a * ld + line] = v[k];
+                }
+            }
         }
         __syncthreads();
         ip_fft<false>(sm.X, ld, nl, pl, sm.tw);
@@ -1125,7 +1149,7 @@ __device__ __forceinline__ void k_spec_cols_body(const GridDev* __restrict__ Gp,
     }
 }
 
-__global__ void __launch_bounds__(1024) k_spec_cols(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
+__global__ void __launch_bounds__(kIpThreads) k_spec_cols(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
                             const float2* __restrict__ krow, float4* __restrict__ kc, int sm_f2)
 {
     k_spec_cols_body(Gp, tw, krow, kc, sm_f2);
@@ -1134,53 +1158,66 @@ __global__ void __launch_bounds__(1024) k_spec_cols(const GridDev* __restrict__ 
 // Row FFTs of the charge grids S0, S1x, S1y, S2 (node-local moments), packed
 // two real rows per complex line (S0 + i S1x, S1y + i S2) and separated by
 // Hermitian symmetry into half spectra srow[g][ty][kx], kx in [0, L/2].
+// Tiles of T rows, line 2 r + pair, transformed in place (DIF); the
+// Hermitian separation reads the digit-reversed positions of kx and L - kx.
 __device__ __forceinline__ void k_conv_rows_fwd_body(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
                                 const float4* __restrict__ wflt, float2* __restrict__ srow, int sm_f2)
 {
     extern __shared__ float2 smf[];
+    __shared__ LinePlan pl;
     const GridDev& G = *Gp;
     const int L = G.L, M = G.M, H = L / 2 + 1;
-    const int cap = line_cap(sm_f2, L, 2);
-    float2* stw = smf;
-    float2* A = smf + L;
-    float2* B = A + (size_t)cap * L;
-    load_tw(stw, tw, L);
+    make_line_plan(G, pl);
+    const IpSmem sm = ip_smem(smf, sm_f2, L, true, true, tw);
+    __syncthreads();
+    make_digit_tables(pl, sm.drev, sm.pos_of);
+    int T = (sm.avail / L - 1) / 2;
+    T = min(T, (M + (int)gridDim.x - 1) / (int)gridDim.x);
+    if (T < 1) T = 1;
     const int64_t MH = (int64_t)M * H;
-    int beg, end;
-    block_range(2 * M, beg, end);  // unit = (pair, row): pair 0 = (S0, S1x), 1 = (S1y, S2)
-    for (int u0 = beg; u0 < end; u0 += cap) {
-        const int nl = min(cap, end - u0);
+    for (int t = blockIdx.x; t * T < M; t += gridDim.x) {
+        const int r0 = t * T, nr = min(T, M - r0), nl = 2 * nr;
+        const int ld = (nl | 1) * L <= sm.avail ? (nl | 1) : nl;
         __syncthreads();
-        for (int line = 0; line < nl; ++line) {
-            const int u = u0 + line, pr = u / M, row = u - pr * M;
-            const float4* src = wflt + (int64_t)row * M;
-            for (int x = threadIdx.x; x < L; x += blockDim.x) {
-                float2 v = make_float2(0.f, 0.f);
-                if (x < M) {
-                    const float4 w = src[x];
-                    v = pr == 0 ? make_float2(w.x, w.y) : make_float2(w.z, w.w);
+        // (r, x) pairs, x fastest: one float4 of the charge grid feeds both
+        // lines of row r; loads batched before the stores
+        const int tot = nr * L;
+        for (int i0 = threadIdx.x; i0 < tot; i0 += 8 * (int)blockDim.x) {
+            float4 w[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int i = i0 + k * (int)blockDim.x;
+                const int r = i / L, x = i - r * L;
+                w[k] = (i < tot && x < M) ? wflt[(int64_t)(r0 + r) * M + x] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int i = i0 + k * (int)blockDim.x;
+                if (i < tot) {
+                    const int r = i / L, x = i - r * L;
+                    float2* dst = sm.X + (int64_t)x * ld + 2 * r;
+                    dst[0] = make_float2(w[k].x, w[k].y);
+                    dst[1] = make_float2(w[k].z, w[k].w);
                 }
-                A[line * L + x] = v;
             }
         }
         __syncthreads();
-        float2* R = fft_lines(A, B, nl, L, G, stw);
-        for (int line = 0; line < nl; ++line) {
-            const int u = u0 + line, pr = u / M, row = u - pr * M;
-            for (int k = threadIdx.x; k < H; k += blockDim.x) {
-            const float2 z = R[line * L + k];
-            const float2 zc = conj2(R[line * L + (k == 0 ? 0 : L - k)]);
+        ip_fft<false>(sm.X, ld, nl, pl, sm.tw);
+        for (int i = threadIdx.x; i < nl * H; i += blockDim.x) {
+            const int l = i / H, k = i - l * H;
+            const int r = l >> 1, pr = l & 1;
+            const float2 z = sm.X[(int64_t)sm.pos_of[k] * ld + l];
+            const float2 zc = conj2(sm.X[(int64_t)sm.pos_of[k == 0 ? 0 : L - k] * ld + l]);
             const float2 re = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y + zc.y));
-            const float2 df = make_float2(z.x - zc.x, z.y - zc.y);
-            const float2 im = make_float2(0.5f * df.y, -0.5f * df.x);  // (z - zc) / 2i
-            srow[(int64_t)(2 * pr) * MH + (int64_t)row * H + k] = re;
-            srow[(int64_t)(2 * pr + 1) * MH + (int64_t)row * H + k] = im;
-            }
+            const float2 im = make_float2(0.5f * (z.y - zc.y), -0.5f * (z.x - zc.x));  // (z - zc) / 2i
+            const int64_t o = (int64_t)(r0 + r) * H + k;
+            srow[(int64_t)(2 * pr) * MH + o] = re;
+            srow[(int64_t)(2 * pr + 1) * MH + o] = im;
         }
     }
 }
 
-__global__ void __launch_bounds__(1024) k_conv_rows_fwd(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
+__global__ void __launch_bounds__(kIpThreads) k_conv_rows_fwd(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
                                 const float4* __restrict__ wflt, float2* __restrict__ srow, int sm_f2)
 {
     k_conv_rows_fwd_body(Gp, tw, wflt, srow, sm_f2);
@@ -1238,7 +1275,7 @@ __device__ __forceinline__ double block_sum_double(double v, double* red)
     return r;
 }
 
-constexpr int kColThreads = 1024;
+constexpr int kColThreads = kIpThreads;
 constexpr int kColSlots = 8;                        // warps per column in the Z sums
 constexpr int kColPerRound = kColThreads / 32 / kColSlots;
 constexpr int kColMaxC = 16;                        // columns per tile
@@ -1278,8 +1315,19 @@ __device__ __forceinline__ void k_conv_cols_body(GridDev* Gp, const float2* __re
             if (tb < nbp) {
                 const int g = tl / nc, c = tl - g * nc;
                 const float2* src = srow + g * MH + k0 + c;
-                for (int y = tb; y < L; y += nbp)
-                    X[(int64_t)y * ld + tl] = y < M ? src[(int64_t)y * H] : make_float2(0.f, 0.f);
+                for (int y0 = tb; y0 < L; y0 += 8 * nbp) {
+                    float2 v[8];  // loads issued before the stores
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int y = y0 + q * nbp;
+                        v[q] = y < M ? src[(int64_t)y * H] : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int y = y0 + q * nbp;
+                        if (y < L) X[(int64_t)y * ld + tl] = v[q];
+                    }
+                }
             }
         }
         __syncthreads();
@@ -1292,9 +1340,20 @@ __device__ __forceinline__ void k_conv_cols_body(GridDev* Gp, const float2* __re
             if (c < nc) {
                 const int kx = k0 + c;
                 const float wgt = (kx == 0 || 2 * kx == L) ? 1.0f : 2.0f;
-                for (int p = lane + 32 * wg; p < L; p += 32 * kColSlots) {
-                    float4 a, b;
-                    kc_at(kc, kx, sm.drev[p], L, H, a, b);
+                constexpr int kStride = 32 * kColSlots;
+                for (int p0 = lane + 32 * wg; p0 < L; p0 += 4 * kStride) {
+                    // the records of four positions fetched together
+                    float4 ra[4], rb[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int p = p0 + q * kStride;
+                        if (p < L) kc_at(kc, kx, sm.drev[p], L, H, ra[q], rb[q]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                    const int p = p0 + q * kStride;
+                    if (p >= L) break;
+                    const float4 a = ra[q], b = rb[q];
                     float2* x = X + (int64_t)p * ld + c;
                     const float2 s0 = x[0], s1x = x[nc], s1y = x[2 * nc], s2v = x[3 * nc];
                     zp += (double)(wgt * z_term(s0, s1x, s1y, s2v, a.x, a.z, b.x, b.z, s2));
@@ -1305,6 +1364,7 @@ __device__ __forceinline__ void k_conv_cols_body(GridDev* Gp, const float2* __re
                     x[3 * nc] = conj2(odd_product(b.z, a.x, s0, s1y));
                     x[4 * nc] = conj2(odd_product(b.y, a.y, s0, s1x));
                     x[5 * nc] = conj2(odd_product(b.w, a.y, s0, s1y));
+                    }
                 }
             }
 #pragma unroll
@@ -1374,68 +1434,78 @@ __global__ void __launch_bounds__(kColThreads) k_conv_cols(GridDev* Gp, const fl
 // Inverse row FFTs, three packed lines per row (U0 + i U1, U2 + i U3,
 // U4 + i U5), each half spectrum extended by Hermitian symmetry.  Fields per
 // node: f0 = F0, f1 = Vx, f2 = Vy, f3 = Fe0, f4 = Vex, f5 = Vey, f6 = f7 = 0.
-// The plain (atomic) spread also needs the charge grid cleared for the next
-// iteration; its readers have finished, so that is done here.
+// Tiles of T rows, line 3 r + pair, loaded straight into digit-reversed
+// positions and transformed in place (DIT, conjugation trick), so each
+// node's eight fields leave as one 32-byte record.  The plain (atomic)
+// spread also needs the charge grid cleared for the next iteration; its
+// readers have finished, so that is done here.
 __device__ __forceinline__ void k_conv_rows_inv_body(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
                                 const float2* __restrict__ ucol, float* __restrict__ fields,
                                 float4* __restrict__ wflt, int32_t* __restrict__ bcnt, int plain, int sm_f2)
 {
     extern __shared__ float2 smf[];
+    __shared__ LinePlan pl;
     const GridDev& G = *Gp;
     const int L = G.L, M = G.M, H = L / 2 + 1;
-    const int cap = line_cap(sm_f2, L, 2);
-    float2* stw = smf;
-    float2* A = smf + L;
-    float2* B = A + (size_t)cap * L;
-    load_tw(stw, tw, L);
+    make_line_plan(G, pl);
+    const IpSmem sm = ip_smem(smf, sm_f2, L, true, true, tw);
+    __syncthreads();
+    make_digit_tables(pl, sm.drev, sm.pos_of);
+    int T = (sm.avail / L - 1) / 3;
+    T = min(T, (M + (int)gridDim.x - 1) / (int)gridDim.x);
+    if (T < 1) T = 1;
     const int64_t MH = (int64_t)M * H;
-    int beg, end;
-    block_range(3 * M, beg, end);  // unit = (pair, row)
-    for (int u0 = beg; u0 < end; u0 += cap) {
-        const int nl = min(cap, end - u0);
+    for (int t = blockIdx.x; t * T < M; t += gridDim.x) {
+        const int r0 = t * T, nr = min(T, M - r0), nl = 3 * nr;
+        const int ld = (nl | 1) * L <= sm.avail ? (nl | 1) : nl;
         __syncthreads();
-        for (int line = 0; line < nl; ++line) {
-            const int u = u0 + line, pr = u / M, row = u - pr * M;
-            const float2* ua = ucol + (int64_t)(2 * pr) * MH + (int64_t)row * H;
-            const float2* ub = ua + MH;
-            for (int k = threadIdx.x; k < L; k += blockDim.x) {
-            float2 a, b;
-            if (k < H) {
-                a = ua[k];
-                b = ub[k];
-            } else {
-                a = conj2(ua[L - k]);
-                b = conj2(ub[L - k]);
+        // (line, k) for k in [0, H), k fastest; k and L - k from one load pair
+        const int tot = nl * H;
+        for (int i0 = threadIdx.x; i0 < tot; i0 += 4 * (int)blockDim.x) {
+            float2 a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = i0 + q * (int)blockDim.x;
+                const int l = i / H, k = i - l * H;
+                const int r = l / 3, pr = l - 3 * r;
+                const float2* ua = ucol + (int64_t)(2 * pr) * MH + (int64_t)(r0 + r) * H + k;
+                a[q] = i < tot ? ua[0] : make_float2(0.f, 0.f);
+                b[q] = i < tot ? ua[MH] : make_float2(0.f, 0.f);
             }
-            A[line * L + k] = conj2(make_float2(a.x - b.y, a.y + b.x));  // conj(a + i b)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = i0 + q * (int)blockDim.x;
+                if (i < tot) {
+                    const int l = i / H, k = i - l * H;
+                    // conj(a + i b) at k; at L - k the half spectra are conjugated
+                    sm.X[(int64_t)sm.pos_of[k] * ld + l] = conj2(make_float2(a[q].x - b[q].y, a[q].y + b[q].x));
+                    if (k > 0 && 2 * k < L)
+                        sm.X[(int64_t)sm.pos_of[L - k] * ld + l] =
+                            conj2(make_float2(a[q].x + b[q].y, -a[q].y + b[q].x));
+                }
             }
         }
         __syncthreads();
-        float2* R = fft_lines(A, B, nl, L, G, stw);
-        for (int line = 0; line < nl; ++line) {
-            const int u = u0 + line, pr = u / M, row = u - pr * M;
-            float* frow = fields + (int64_t)row * M * kFieldStride;
-            for (int x = threadIdx.x; x < M; x += blockDim.x) {
-                const float2 v = conj2(R[line * L + x]);
-                float* f = frow + (int64_t)x * kFieldStride;
-                if (pr == 0) { f[0] = v.x; f[3] = v.y; f[6] = 0.f; f[7] = 0.f; }
-                else if (pr == 1) { f[1] = v.x; f[2] = v.y; }
-                else { f[4] = v.x; f[5] = v.y; }
-            }
+        ip_fft<true>(sm.X, ld, nl, pl, sm.tw);
+        for (int i = threadIdx.x; i < nr * M; i += blockDim.x) {
+            const int r = i / M, x = i - r * M;
+            const float2* s = sm.X + (int64_t)x * ld + 3 * r;
+            const float2 v0 = conj2(s[0]), v1 = conj2(s[1]), v2 = conj2(s[2]);
+            float4* f = (float4*)(fields + ((int64_t)(r0 + r) * M + x) * kFieldStride);
+            f[0] = make_float4(v0.x, v1.x, v1.y, v0.y);
+            f[1] = make_float4(v2.x, v2.y, 0.f, 0.f);
         }
+        if (plain)
+            for (int i = threadIdx.x; i < nr * M; i += blockDim.x)
+                wflt[(int64_t)r0 * M + i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     // the box counts of this iteration are used up: cleared for the next
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)G.I * G.I;
          t += (int64_t)gridDim.x * blockDim.x)
         bcnt[t] = 0;
-    if (!plain) return;
-    for (int u = beg; u < end; ++u) {
-        if (u >= M) break;  // units (0, row) cover every row once
-        for (int x = threadIdx.x; x < M; x += blockDim.x) wflt[(int64_t)u * M + x] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
 }
 
-__global__ void __launch_bounds__(1024) k_conv_rows_inv(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
+__global__ void __launch_bounds__(kIpThreads) k_conv_rows_inv(const GridDev* __restrict__ Gp, const float2* __restrict__ tw,
                                 const float2* __restrict__ ucol, float* __restrict__ fields,
                                 float4* __restrict__ wflt, int32_t* __restrict__ bcnt, int plain, int sm_f2)
 {
@@ -1508,7 +1578,6 @@ __global__ void k_psum(const float* __restrict__ v, const int64_t* __restrict__ 
     }
 }
 
-constexpr int kFftThreads = 1024;
 
 // ---- batched wrappers: graph = blockIdx.y (BatchGraph), each graph's work
 // split over gridDim.x blocks as in the single-graph launches ----
@@ -1542,19 +1611,19 @@ __global__ void __launch_bounds__(256) k_box_spread_b(const BatchGraph* __restri
                          b.w.wflt);
 }
 
-__global__ void __launch_bounds__(1024) k_spec_rows_b(const BatchGraph* __restrict__ bg, float eps, int sm_f2)
+__global__ void __launch_bounds__(kIpThreads) k_spec_rows_b(const BatchGraph* __restrict__ bg, float eps, int sm_f2)
 {
     const BatchGraph& b = bg[blockIdx.y];
     k_spec_rows_body(b.w.g, b.w.tw, eps, b.w.krow, sm_f2);
 }
 
-__global__ void __launch_bounds__(1024) k_spec_cols_b(const BatchGraph* __restrict__ bg, int sm_f2)
+__global__ void __launch_bounds__(kIpThreads) k_spec_cols_b(const BatchGraph* __restrict__ bg, int sm_f2)
 {
     const BatchGraph& b = bg[blockIdx.y];
     k_spec_cols_body(b.w.g, b.w.tw, b.w.krow, b.w.kc, sm_f2);
 }
 
-__global__ void __launch_bounds__(1024) k_conv_rows_fwd_b(const BatchGraph* __restrict__ bg, int sm_f2)
+__global__ void __launch_bounds__(kIpThreads) k_conv_rows_fwd_b(const BatchGraph* __restrict__ bg, int sm_f2)
 {
     const BatchGraph& b = bg[blockIdx.y];
     k_conv_rows_fwd_body(b.w.g, b.w.tw, b.w.wflt, b.w.srow, sm_f2);
@@ -1566,7 +1635,7 @@ __global__ void __launch_bounds__(kColThreads) k_conv_cols_b(const BatchGraph* _
     k_conv_cols_body(b.w.g, b.w.tw, b.w.srow, b.w.kc, b.w.ucol, b.w.zcol, b.n, sm_f2);
 }
 
-__global__ void __launch_bounds__(1024) k_conv_rows_inv_b(const BatchGraph* __restrict__ bg, int sm_f2)
+__global__ void __launch_bounds__(kIpThreads) k_conv_rows_inv_b(const BatchGraph* __restrict__ bg, int sm_f2)
 {
     const BatchGraph& b = bg[blockIdx.y];
     k_conv_rows_inv_body(b.w.g, b.w.tw, b.w.ucol, b.w.fields, b.w.wflt, b.w.bcnt, 0, sm_f2);
@@ -1699,8 +1768,8 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
         cudaError_t e2;
         if ((e2 = cudaEventRecord(aux->fork, s)) != cudaSuccess) return e2;
         if ((e2 = cudaStreamWaitEvent(aux->branch, aux->fork, 0)) != cudaSuccess) return e2;
-        k_spec_rows<<<fb, kFftThreads, fsm, aux->branch>>>(w.g, w.tw, p->eps, w.krow, f2);
-        k_spec_cols<<<fb, kFftThreads, fsm, aux->branch>>>(w.g, w.tw, w.krow, w.kc, f2);
+        k_spec_rows<<<fb, kIpThreads, fsm, aux->branch>>>(w.g, w.tw, p->eps, w.krow, f2);
+        k_spec_cols<<<fb, kIpThreads, fsm, aux->branch>>>(w.g, w.tw, w.krow, w.kc, f2);
         count_launches(2);
         if ((e2 = cudaEventRecord(aux->join, aux->branch)) != cudaSuccess) return e2;
     }
@@ -1743,8 +1812,8 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
 
     profile_start(LTSNET_KERNEL_CONV, s);
     if (!fork) {
-        k_spec_rows<<<fb, kFftThreads, fsm, s>>>(w.g, w.tw, p->eps, w.krow, f2);
-        k_spec_cols<<<fb, kFftThreads, fsm, s>>>(w.g, w.tw, w.krow, w.kc, f2);
+        k_spec_rows<<<fb, kIpThreads, fsm, s>>>(w.g, w.tw, p->eps, w.krow, f2);
+        k_spec_cols<<<fb, kIpThreads, fsm, s>>>(w.g, w.tw, w.krow, w.kc, f2);
         count_launches(2);
     }
     if (sh.conv_mode == LTSNET_CONV_DFT_GEMM) {
@@ -1755,13 +1824,13 @@ cudaError_t launch_grid_phase(const IterWs& w, const IterShape& sh, const ltsnet
         profile_stop(LTSNET_KERNEL_CONV, s);
         return cudaGetLastError();
     }
-    k_conv_rows_fwd<<<fb, kFftThreads, fsm, s>>>(w.g, w.tw, w.wflt, w.srow, f2);
+    k_conv_rows_fwd<<<fb, kIpThreads, fsm, s>>>(w.g, w.tw, w.wflt, w.srow, f2);
     if (fork) {
         cudaError_t e2 = cudaStreamWaitEvent(s, aux->join, 0);
         if (e2 != cudaSuccess) return e2;
     }
     k_conv_cols<<<fb, kColThreads, fsm, s>>>(w.g, w.tw, w.srow, w.kc, w.ucol, w.zcol, n, f2);
-    k_conv_rows_inv<<<fb, kFftThreads, fsm, s>>>(w.g, w.tw, w.ucol, w.fields, w.wflt, w.bcnt, plain ? 1 : 0, f2);
+    k_conv_rows_inv<<<fb, kIpThreads, fsm, s>>>(w.g, w.tw, w.ucol, w.fields, w.wflt, w.bcnt, plain ? 1 : 0, f2);
     count_launches(3);
     profile_stop(LTSNET_KERNEL_CONV, s);
     return cudaGetLastError();
@@ -1806,8 +1875,8 @@ cudaError_t launch_grid_phase_batched(const BatchGraph* bg, int32_t ng, const Ba
     if (fork) {
         if ((e = cudaEventRecord(aux->fork, s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(aux->branch, aux->fork, 0)) != cudaSuccess) return e;
-        k_spec_rows_b<<<gfft, kFftThreads, fsm, aux->branch>>>(bg, p->eps, f2);
-        k_spec_cols_b<<<gfft, kFftThreads, fsm, aux->branch>>>(bg, f2);
+        k_spec_rows_b<<<gfft, kIpThreads, fsm, aux->branch>>>(bg, p->eps, f2);
+        k_spec_cols_b<<<gfft, kIpThreads, fsm, aux->branch>>>(bg, f2);
         count_launches(2);
         if ((e = cudaEventRecord(aux->join, aux->branch)) != cudaSuccess) return e;
     }
@@ -1825,14 +1894,14 @@ cudaError_t launch_grid_phase_batched(const BatchGraph* bg, int32_t ng, const Ba
     count_launches(3);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (!fork) {
-        k_spec_rows_b<<<gfft, kFftThreads, fsm, s>>>(bg, p->eps, f2);
-        k_spec_cols_b<<<gfft, kFftThreads, fsm, s>>>(bg, f2);
+        k_spec_rows_b<<<gfft, kIpThreads, fsm, s>>>(bg, p->eps, f2);
+        k_spec_cols_b<<<gfft, kIpThreads, fsm, s>>>(bg, f2);
         count_launches(2);
     }
-    k_conv_rows_fwd_b<<<gfft, kFftThreads, fsm, s>>>(bg, f2);
+    k_conv_rows_fwd_b<<<gfft, kIpThreads, fsm, s>>>(bg, f2);
     if (fork && (e = cudaStreamWaitEvent(s, aux->join, 0)) != cudaSuccess) return e;
     k_conv_cols_b<<<gfft, kColThreads, fsm, s>>>(bg, f2);
-    k_conv_rows_inv_b<<<gfft, kFftThreads, fsm, s>>>(bg, f2);
+    k_conv_rows_inv_b<<<gfft, kIpThreads, fsm, s>>>(bg, f2);
     count_launches(3);
     return cudaGetLastError();
 }
