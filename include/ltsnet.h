@@ -339,9 +339,14 @@ ltsnet_status ltsnet_run_host(const int64_t* row_ptr_host, const int32_t* col_ho
  *    same way whatever the launch shape).
  *  LTSNET_BATCH_PER_GRAPH: ltsnet_run per graph on cfg->n_workers host
  *    threads, each with its own stream (largest graphs first).
+ * cfg->max_boxes (HOST int32[n_graphs], may be NULL): graph g runs with the
+ * grid cap max_boxes[g] in place of p->max_boxes where that entry is
+ * positive (the same bounds as p->max_boxes apply; an out-of-range cap
+ * returns LTSNET_ERR_INVALID_ARG), so a batch can give its large graphs
+ * large grids without sizing every graph's grid arrays for them.
  * cfg->max_boxes_used (HOST int32[n_graphs], may be NULL): the largest number
  * of boxes per dimension each graph's grid had during the run (-1 in the
- * per-graph mode): equal to max_boxes where that cap bound.  Synchronous
+ * per-graph mode): equal to the graph's cap where that cap bound.  Synchronous
  * (waits for `stream` first); returns the first error, else
  * LTSNET_WARN_NOT_CONVERGED if any graph had rows that missed the perplexity
  * target, else LTSNET_OK.
@@ -354,6 +359,10 @@ typedef struct {
     int32_t fft_blocks;      /* blocks per graph of the FFT passes, 0..64 (0: 4) */
     int32_t spread_blocks;   /* blocks per graph of the box spread, 0..64 (0: 8) */
     int32_t* max_boxes_used; /* HOST int32[n_graphs] or NULL */
+    const int32_t* max_boxes; /* HOST int32[n_graphs] or NULL: per-graph cap of
+                                 the boxes per dimension (an entry of 0 takes
+                                 p->max_boxes); each graph's grid arrays are
+                                 sized for its own cap */
 } ltsnet_batch_config;
 /* The batched calls (Alg. 3 on every graph; the batching itself has no
  * counterpart in the paper), as described above. */

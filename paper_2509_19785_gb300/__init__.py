@@ -67,7 +67,8 @@ class CParams(ctypes.Structure):
 
 class CBatchConfig(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("n_workers", ctypes.c_int32), ("fft_blocks", ctypes.c_int32),
-                ("spread_blocks", ctypes.c_int32), ("max_boxes_used", ctypes.c_void_p)]
+                ("spread_blocks", ctypes.c_int32), ("max_boxes_used", ctypes.c_void_p),
+                ("max_boxes", ctypes.c_void_p)]
 
 
 BATCH_ONE_LAUNCH = 0
@@ -660,13 +661,14 @@ def _batch_arrays(graphs, Y0s):
 
 
 def run_batched(graphs, Y0s, params: Params | None = None, workers: int = 16, mode: int = BATCH_ONE_LAUNCH,
-                fft_blocks: int = 0, spread_blocks: int = 0, return_boxes: bool = False):
+                fft_blocks: int = 0, spread_blocks: int = 0, return_boxes: bool = False, max_boxes=None):
     """The method on many independent graphs at once (ltsnet_run_batched).
     graphs: objects with row_ptr (int64 [n+1]) and col (int32) numpy arrays;
     Y0s: matching float32 [n,2] arrays.  mode BATCH_ONE_LAUNCH runs the loop
     with one launch per phase over all graphs (fft_blocks / spread_blocks
     blocks per graph, 0 = the library's defaults), BATCH_PER_GRAPH one
-    ltsnet_run per graph on `workers` host threads.  Returns (Y, vtx_off) --
+    ltsnet_run per graph on `workers` host threads.  max_boxes: optional
+    per-graph grid caps (0 = params.max_boxes).  Returns (Y, vtx_off) --
     all final layouts in one [sum n, 2] CUDA tensor, graph g in rows
     vtx_off[g]:vtx_off[g+1] -- and, if return_boxes, the largest box count
     per dimension of each graph's grid."""
@@ -675,8 +677,13 @@ def run_batched(graphs, Y0s, params: Params | None = None, workers: int = 16, mo
     vtx_off, edge_off, rp, col, Y = _batch_arrays(graphs, Y0s)
     cp = params.to_c()
     boxes = np.zeros(len(graphs), np.int32)
+    caps = None
+    if max_boxes is not None:
+        caps = np.ascontiguousarray(np.asarray(max_boxes, dtype=np.int32))
+        if caps.shape != (len(graphs),):
+            raise ValueError("max_boxes: one cap per graph")
     cfg = CBatchConfig(int(mode), max(1, min(int(workers), 64)), int(fft_blocks), int(spread_blocks),
-                       boxes.ctypes.data)
+                       boxes.ctypes.data, caps.ctypes.data if caps is not None else None)
     need = lib().ltsnet_run_batched_workspace_size(len(graphs), vtx_off.ctypes.data, edge_off.ctypes.data,
                                                     ctypes.byref(cp), ctypes.byref(cfg))
     if need == 0:
@@ -688,31 +695,35 @@ def run_batched(graphs, Y0s, params: Params | None = None, workers: int = 16, mo
     return (Y, vtx_off, boxes) if return_boxes else (Y, vtx_off)
 
 
-def _tune_key(graphs, params: Params) -> str:
+def _tune_key(graphs, params: Params, max_boxes=None) -> str:
     """Cache key of a batch: buckets of its median and largest graph size
-    (powers of 2), of its grid size (nodes per side at max_boxes) and of its
-    mean entries per row of the graph (powers of 2)."""
+    (powers of 2), of its largest grid (nodes per side at the largest cap) and
+    of its mean entries per row of the graph (powers of 2)."""
     import numpy as np
     ns = np.array([int(g.row_ptr.shape[0] - 1) for g in graphs])
     deg = float(np.mean([g.col.shape[0] / max(1, g.row_ptr.shape[0] - 1) for g in graphs]))
+    cap = params.max_boxes
+    if max_boxes is not None:
+        caps = np.asarray(max_boxes)
+        cap = int(np.where(caps > 0, caps, params.max_boxes).max())
     b = lambda x: int(np.ceil(np.log2(max(1.0, x))))  # noqa: E731
-    return (f"n{b(np.median(ns))}-{b(ns.max())}_M{params.nodes_per_box * params.max_boxes}_d{b(deg)}"
+    return (f"n{b(np.median(ns))}-{b(ns.max())}_M{params.nodes_per_box * cap}_d{b(deg)}"
             f"_p{params.perplexity:g}")
 
 
 def autotune_batched(graphs, Y0s, params: Params | None = None, cache: str | None = None, iters: int = 40,
-                     candidates=((2, 4), (4, 8), (8, 8), (8, 16), (16, 16)), workers: int = 16):
+                     candidates=((2, 4), (4, 8), (8, 8), (8, 16), (16, 16)), workers: int = 16, max_boxes=None):
     """Picks the launch shape (FFT blocks, spread blocks per graph) of the
     one-launch batched form by timing each candidate on the batch itself
-    (`iters` iterations of the default schedule's second stage) and keeps the
-    fastest in a JSON cache keyed by _tune_key.  Returns (fft_blocks,
-    spread_blocks, timings)."""
+    (`iters` iterations of the default schedule's second stage, per-graph grid
+    caps `max_boxes` as in run_batched) and keeps the fastest in a JSON cache
+    keyed by _tune_key.  Returns (fft_blocks, spread_blocks, timings)."""
     import json
     import os
     import time
     torch = _torch()
     params = params or Params()
-    key = _tune_key(graphs, params)
+    key = _tune_key(graphs, params, max_boxes)
     table = {}
     if cache and os.path.exists(cache):
         with open(cache) as f:
@@ -722,10 +733,11 @@ def autotune_batched(graphs, Y0s, params: Params | None = None, cache: str | Non
     probe = Params(**{**params.__dict__, "stages": [Stage(iters, 1.0, 0.01, 0.6, 1.0, 0.8)]})
     ms = {}
     for fb, sb in candidates:
-        run_batched(graphs, Y0s, probe, workers=workers, fft_blocks=fb, spread_blocks=sb)  # warm-up
+        run_batched(graphs, Y0s, probe, workers=workers, fft_blocks=fb, spread_blocks=sb,
+                    max_boxes=max_boxes)  # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        run_batched(graphs, Y0s, probe, workers=workers, fft_blocks=fb, spread_blocks=sb)
+        run_batched(graphs, Y0s, probe, workers=workers, fft_blocks=fb, spread_blocks=sb, max_boxes=max_boxes)
         torch.cuda.synchronize()
         ms[f"{fb},{sb}"] = round((time.perf_counter() - t0) * 1e3, 2)
     best = min(ms, key=ms.get)

@@ -1584,11 +1584,11 @@ __global__ void k_psum(const float* __restrict__ v, const int64_t* __restrict__ 
 __device__ __forceinline__ const float2* layout_of(const BatchGraph& b, int parity) { return parity ? b.w.yalt : b.Y; }
 
 __global__ void __launch_bounds__(kBoxThreads) k_setup_b(const BatchGraph* __restrict__ bg, int parity, float bwm,
-                                                         int min_boxes, int max_boxes, int P)
+                                                         int min_boxes, int P)
 {
     const BatchGraph& b = bg[blockIdx.y];
     k_setup_body(b.w.bounds + 2 * parity, b.w.bounds + 2 * (parity ^ 1), b.w.g, b.w.tw, layout_of(b, parity),
-                 b.w.bcnt, b.n, bwm, min_boxes, max_boxes, P, 1);
+                 b.w.bcnt, b.n, bwm, min_boxes, b.max_boxes, P, 1);
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_box_scan_b(const BatchGraph* __restrict__ bg)
@@ -1864,7 +1864,7 @@ cudaError_t launch_grid_phase_batched(const BatchGraph* bg, int32_t ng, const Ba
     const int P = sh.P;
     const unsigned tiles = (unsigned)std::max<int64_t>(1, ((int64_t)bs.max_n + kBoxTile - 1) / kBoxTile);
     const dim3 gpt(tiles, (unsigned)ng);
-    k_setup_b<<<gpt, kBoxThreads, 0, s>>>(bg, parity, p->box_width_max, p->min_boxes, p->max_boxes, P);
+    k_setup_b<<<gpt, kBoxThreads, 0, s>>>(bg, parity, p->box_width_max, p->min_boxes, P);
     count_launches(1);
     const size_t fsm = kFftSmemBytes;
     const int f2 = (int)(fsm / sizeof(float2));

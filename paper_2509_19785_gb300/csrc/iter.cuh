@@ -109,6 +109,7 @@ struct BatchGraph {
     float2* gains;
     Stage st;
     int32_t n;
+    int32_t max_boxes;  // this graph's grid cap
     // rows of P summed in chunks before the fused kernel (nchunks = 0: none)
     const int32_t* hbase;
     const int32_t* crow;

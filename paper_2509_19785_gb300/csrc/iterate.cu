@@ -1,9 +1,11 @@
 // The per-iteration gradient and the descent loop (Alg. 3 loop body).
 //
 // k_fused (optimised form): one warp per 32 consecutive vertices.
-//   Attraction (Eq. 6, first term): the warp walks the 32 CSR rows in turn,
-//   each lane reading 4 consecutive (col, p) entries with 16-byte loads, and
-//   the row sum is reduced across the warp and handed to the row's lane.
+//   Attraction (Eq. 6, first term): the warp walks the 32 rows of P four at a
+//   time, 8 lanes per row, each lane reading 4 entries (value, column) per
+//   vector load from the packed layout built by k_pack_rows (or from CSR
+//   with int32 columns), and the row sum is reduced across the 8 lanes and
+//   handed to the row's lane.
 //   Then every lane, for its own vertex: gathers the interpolated repulsion
 //   sum R_i (Sec. 2.3) and entropy sum E_i (Eq. 8, repulsive reading) from
 //   the P x P nodes of its box, adds the compression (lambda_c/n) X_i
@@ -236,12 +238,20 @@ __device__ __forceinline__ void window_cols(const Window& w, int u, int rowi, in
     }
 }
 
-// Window start: the row start rounded down so that every vector load is
-// aligned (4 int32 / float, or 8 int16 columns).
+// Window start: the row start, which the packed layout keeps a multiple of
+// 4 entries; for int32 columns the row start rounded down to a multiple of 4
+// so that every vector load is aligned.
+// Window end: the row's end, or its start for a long row (summed in chunks
+// beforehand), so that the window holds no entry of it.
+__device__ __forceinline__ int64_t window_end(const int32_t* hbase, int64_t s0, int64_t e0)
+{
+    return hbase != nullptr && e0 - s0 > kHeavyRow ? s0 : e0;
+}
+
 template <bool D16>
 __device__ __forceinline__ int64_t window_start(int64_t s0)
 {
-    return D16 ? (s0 & ~(int64_t)7) : (s0 & ~(int64_t)3);
+    return D16 ? s0 : (s0 & ~(int64_t)3);
 }
 
 // Load the lane's slots j = 32 u + 4 gl + q (u, q < 4) of the window starting
@@ -317,7 +327,8 @@ __device__ __forceinline__ void
         Window nxt;
         {
             const int64_t s0 = __shfl_sync(FULL, rs, grp), e0 = __shfl_sync(FULL, re, grp);
-            load_window<D16>(nxt, P_col, P_d16, P_val, nnz, window_start<D16>(s0), e0, (int)(g0 + grp), gl);
+            load_window<D16>(nxt, P_col, P_d16, P_val, nnz, window_start<D16>(s0), window_end(hbase, s0, e0),
+                             (int)(g0 + grp), gl);
         }
 #pragma unroll 1
         for (int rr = 0; rr < 8; ++rr) {
@@ -327,7 +338,8 @@ __device__ __forceinline__ void
             if (rr < 7) {
                 const int nsrc = src + 4;
                 const int64_t ns0 = __shfl_sync(FULL, rs, nsrc), ne0 = __shfl_sync(FULL, re, nsrc);
-                load_window<D16>(nxt, P_col, P_d16, P_val, nnz, window_start<D16>(ns0), ne0, rowi + 4, gl);
+                load_window<D16>(nxt, P_col, P_d16, P_val, nnz, window_start<D16>(ns0), window_end(hbase, ns0, ne0),
+                                 rowi + 4, gl);
             }
             const int64_t s0 = __shfl_sync(FULL, rs, src), e0r = __shfl_sync(FULL, re, src);
             const float xi = __shfl_sync(FULL, yi.x, src), yv = __shfl_sync(FULL, yi.y, src);
@@ -343,6 +355,22 @@ __device__ __forceinline__ void
             for (int u = 0; u < 4; ++u) {
                 const int j = 32 * u + 4 * gl;
                 const float vv[4] = {cur.v[u].x, cur.v[u].y, cur.v[u].z, cur.v[u].w};
+                if (D16) {
+                    // Packed rows: every slot gathers.  Slots past the row's
+                    // window (past its end, or a long row's) were loaded as
+                    // offset 0 and weight 0, like the pads of a packed row,
+                    // so they read the point itself and add nothing; and
+                    // k_pack_rows checked every column against [0, n).
+                    const float2* yr = Y + rowi;
+                    const int o[4] = {(int)(int16_t)(cur.c[u].x & 0xffff), cur.c[u].x >> 16,
+                                      (int)(int16_t)(cur.c[u].y & 0xffff), cur.c[u].y >> 16};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        yj[u][q] = __ldg(yr + o[q]);
+                        pv[u][q] = vv[q];
+                    }
+                    continue;
+                }
                 int cc[4];
                 window_cols<D16>(cur, u, rowi, cc);
 #pragma unroll
@@ -459,7 +487,7 @@ __device__ __forceinline__ void k_attr_chunks_body(const int64_t* __restrict__ P
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nw) {
         const int32_t row = crow[c];
-        const int64_t a = cstart[c], b = min(a + kChunk, P_row[row + 1]);
+        const int64_t a = P_row[row] + cstart[c], b = min(a + kChunk, P_row[row + 1]);
         const float2 yi = Y[row];
         float ax = 0.f, ay = 0.f;
         for (int64_t e = a + lane; e < b; e += 32) {
@@ -507,7 +535,10 @@ __global__ void k_heavy_count(const int64_t* __restrict__ P_row, int32_t n, uint
     }
 }
 
-// The chunk list of the long rows, their first chunks at base[row].
+// The chunk list of the long rows, their first chunks at base[row]; a
+// chunk's start is its offset in the row, so the list serves both the CSR
+// layout and the packed one (a chunk of kChunk entries covers whole 32-entry
+// blocks of a packed row: the same entries as in CSR order).
 __global__ void k_heavy_emit(const int64_t* __restrict__ P_row, int32_t n, const uint32_t* __restrict__ nch,
                              const uint32_t* __restrict__ base, int32_t* __restrict__ crow,
                              int64_t* __restrict__ cstart)
@@ -516,25 +547,63 @@ __global__ void k_heavy_emit(const int64_t* __restrict__ P_row, int32_t n, const
         const uint32_t m = nch[i];
         for (uint32_t c = 0; c < m; ++c) {
             crow[base[i] + c] = (int32_t)i;
-            cstart[base[i] + c] = P_row[i] + (int64_t)c * kChunk;
+            cstart[base[i] + c] = (int64_t)c * kChunk;
         }
     }
 }
 
-// P's columns as int16 offsets from their row, one warp per row; `far` is set
-// if any offset does not fit (the int32 columns are used then).
-__global__ void k_pack_d16(const int64_t* __restrict__ P_row, const int32_t* __restrict__ P_col, int32_t n,
-                           int16_t* __restrict__ d16, int32_t* __restrict__ far)
+// Packed layout of the library's own P for the point phase: every row padded
+// to a multiple of 4 entries (column offset 0, weight 0) and, inside each
+// block of 32 entries of a row (the last block: s = 4m entries), entry
+// t = a + m q (a < m, q < 4) of the block stored at slot 4 a + q.  A lane
+// that loads slots 4a .. 4a+3 of a block as one vector then holds entries
+// a, a + m, a + 2m, a + 3m, so the 8 lanes of a row gather the neighbours of
+// m consecutive (sorted) columns at a time: after the breadth-first
+// renumbering these lie close together, and each gather instruction touches
+// fewer cache lines.  Columns are int16 offsets from the row; `far` is set if
+// one does not fit, or a column is outside [0, n) or on the diagonal (the
+// CSR arrays with int32 columns, whose gathers are clamped, are used then).
+// Q_row[i] = P_row[i] + pads of the rows before i.
+__global__ void k_pad_count(const int64_t* __restrict__ P_row, int32_t n, uint32_t* __restrict__ pads)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        pads[i] = (uint32_t)((-(P_row[i + 1] - P_row[i])) & 3);
+}
+
+__global__ void k_pad_rows(const int64_t* __restrict__ P_row, int32_t n, const uint32_t* __restrict__ pads,
+                           const uint32_t* __restrict__ pad_before, int64_t* __restrict__ Q_row)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        Q_row[i] = P_row[i] + pad_before[i];
+        if (i == n - 1) Q_row[n] = P_row[n] + pad_before[i] + pads[i];
+    }
+}
+
+__global__ void k_pack_rows(const int64_t* __restrict__ P_row, const int32_t* __restrict__ P_col,
+                            const float* __restrict__ P_val, int32_t n, const int64_t* __restrict__ Q_row,
+                            int16_t* __restrict__ Q_d16, float* __restrict__ Q_val, int32_t* __restrict__ far)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += nw) {
-        const int64_t e1 = P_row[row + 1];
+        const int64_t p0 = P_row[row], len = P_row[row + 1] - p0;
+        const int64_t q0 = Q_row[row], lp = Q_row[row + 1] - q0;
         bool bad = false;
-        for (int64_t e = P_row[row] + lane; e < e1; e += 32) {
-            const int64_t d = (int64_t)P_col[e] - row;
-            bad |= d < -32767 || d > 32767;
-            d16[e] = (int16_t)d;
+        for (int64_t t = lane; t < lp; t += 32) {
+            const int64_t blk = t & ~(int64_t)31;
+            const int m = (int)(min(lp - blk, (int64_t)32) >> 2);
+            const int r = (int)(t - blk), a = r % m, q = r / m;
+            int16_t d = 0;
+            float v = 0.f;
+            if (t < len) {
+                const int32_t col = P_col[p0 + t];
+                const int64_t off = (int64_t)col - row;
+                bad |= off < -32767 || off > 32767 || off == 0 || col < 0 || col >= n;
+                d = (int16_t)off;
+                v = P_val[p0 + t];
+            }
+            Q_d16[q0 + blk + 4 * a + q] = d;
+            Q_val[q0 + blk + 4 * a + q] = v;
         }
         if (__any_sync(FULL, bad) && lane == 0) atomicExch(far, 1);
     }
@@ -982,7 +1051,9 @@ struct RunWs {
     int32_t* cnt;
     double* beta;
     double* pcond;
-    int16_t* d16;      // P's columns as offsets from their row (aliases pcond, dead by then)
+    int64_t* Q_row;    // packed layout of P for the point phase (k_pack_rows), in
+    int16_t* Q_d16;    // the symmetrisation's scratch, dead once P is built;
+    float* Q_val;      // null when it does not fit there (tiny graphs)
     int32_t* far;      // set when some |col - row| exceeds the int16 range
     uint32_t* hnch;    // chunks per long row of P
     uint32_t* hbase;   // first chunk of each long row
@@ -1027,7 +1098,6 @@ RunWs run_carve(Carve& c, int32_t n, int64_t m2, const ltsnet_params* p, bool ho
     r.cnt = c.take<int32_t>(n);
     r.beta = c.take<double>(n);
     r.pcond = c.take<double>(nk);
-    r.d16 = (int16_t*)r.pcond;  // 2 nnz <= 4 n k bytes <= 8 n k
     r.far = c.take<int32_t>(1);
     r.hnch = c.take<uint32_t>(n);
     r.hbase = c.take<uint32_t>(n);
@@ -1057,6 +1127,15 @@ RunWs run_carve(Carve& c, int32_t n, int64_t m2, const ltsnet_params* p, bool ho
     r.ord = c.take<char>(r.ord_bytes);
     r.sym_bytes = ltsnet_symmetrize_workspace_size(n, k);
     r.sym = c.take<char>(r.sym_bytes);
+    {
+        // padded rows: at most nnz + 3 n <= 2 n k + 3 n entries
+        const int64_t qcap = 2 * nk + 3 * (int64_t)n;
+        Carve q(r.sym, r.sym_bytes);
+        r.Q_row = q.take<int64_t>((int64_t)n + 1);
+        r.Q_d16 = q.take<int16_t>(qcap);
+        r.Q_val = q.take<float>(qcap);
+        if (!q.ok()) r.Q_row = nullptr, r.Q_d16 = nullptr, r.Q_val = nullptr;
+    }
     r.iter_bytes = iter_ws_bytes(n, p);
     r.iter = c.take<char>(r.iter_bytes);
     return r;
@@ -1068,7 +1147,7 @@ RunWs run_carve(Carve& c, int32_t n, int64_t m2, const ltsnet_params* p, bool ho
 // its renumbered copy in r.Y2).
 struct Prepared {
     bool reordered = false;
-    bool d16 = false;
+    bool d16 = false;  // P packed (k_pack_rows) in Q_row / Q_d16 / Q_val
     HeavyRows hr;
     int64_t nnz = 0;
     float2* Yw = nullptr;
@@ -1101,12 +1180,16 @@ ltsnet_status run_prepare(const int64_t* row_ptr, const int32_t* col, int32_t n,
                                r.sym, r.sym_bytes, s);
     }
     if (rc != LTSNET_OK) return rc;
-    // compact columns when every entry is within int16 range of its row
+    // packed layout with int16 columns when every entry is within int16
+    // range of its row
     bool d16 = false;
-    if (!(p->flags & LTSNET_FLAG_PLAIN) && nnz > 0) {
+    if (!(p->flags & LTSNET_FLAG_PLAIN) && nnz > 0 && r.Q_row) {
+        k_pad_count<<<flat_blocks(n), 256, 0, s>>>(r.P_row, n, r.hnch);
+        LT_CUDA(scan_u32_exclusive(r.hnch, r.hbase, n, r.htmp, s));
+        k_pad_rows<<<flat_blocks(n), 256, 0, s>>>(r.P_row, n, r.hnch, r.hbase, r.Q_row);
         LT_CUDA(cudaMemsetAsync(r.far, 0, sizeof(int32_t), s));
-        k_pack_d16<<<num_sms() * 8, 256, 0, s>>>(r.P_row, r.P_col, n, r.d16, r.far);
-        count_launches(1);
+        k_pack_rows<<<num_sms() * 8, 256, 0, s>>>(r.P_row, r.P_col, r.P_val, n, r.Q_row, r.Q_d16, r.Q_val, r.far);
+        count_launches(3);
         LT_CHECK_LAUNCH();
         int32_t far = 1;
         LT_CUDA(cudaMemcpyAsync(&far, r.far, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -1176,7 +1259,8 @@ ltsnet_status run_core(const int64_t* row_ptr, const int32_t* col, int32_t n, co
     const IterWs w = iter_carve(ic, sh);
     LT_CUDA(iter_reset(w, sh, s));
     const int64_t total = schedule_length(p);
-    rc = optimize_core(r.P_row, r.P_col, pr.d16 ? r.d16 : nullptr, r.P_val, pr.hr, n, p, pr.Yw, r.upd, r.gains, 0,
+    rc = optimize_core(pr.d16 ? r.Q_row : r.P_row, r.P_col, pr.d16 ? r.Q_d16 : nullptr, pr.d16 ? r.Q_val : r.P_val,
+                       pr.hr, n, p, pr.Yw, r.upd, r.gains, 0,
                        (int32_t)total, w, sh, s);
     if (rc != LTSNET_OK) return rc;
     return run_finish(n, Y, r, pr, w.st, s);
@@ -1443,6 +1527,15 @@ static bool batch_ok(int32_t n_graphs, const int64_t* vtx_off, const int64_t* ed
     return true;
 }
 
+// The parameters graph g of a batch runs with: p, with the graph's own grid
+// cap where cfg->max_boxes gives one.
+static ltsnet_params graph_params(const ltsnet_params* p, const ltsnet_batch_config* cfg, int32_t g)
+{
+    ltsnet_params q = *p;
+    if (cfg->max_boxes && cfg->max_boxes[g] > 0) q.max_boxes = cfg->max_boxes[g];
+    return q;
+}
+
 static bool batch_cfg_ok(const ltsnet_batch_config* cfg)
 {
     return cfg && (cfg->mode == LTSNET_BATCH_ONE_LAUNCH || cfg->mode == LTSNET_BATCH_PER_GRAPH) &&
@@ -1450,20 +1543,48 @@ static bool batch_cfg_ok(const ltsnet_batch_config* cfg)
            cfg->spread_blocks >= 0 && cfg->spread_blocks <= 64;
 }
 
+// Every graph's parameters are valid (the per-graph caps included).
+static bool batch_params_ok(int32_t n_graphs, const ltsnet_params* p, const ltsnet_batch_config* cfg)
+{
+    for (int32_t g = 0; g < n_graphs; ++g) {
+        const ltsnet_params q = graph_params(p, cfg, g);
+        if (!params_ok(&q)) return false;
+    }
+    return true;
+}
+
 // Workspace of the one-launch mode: a run workspace per graph (C0, P, state,
-// iteration workspace), then one descriptor array per schedule stage.
+// iteration workspace, sized for the graph's own grid cap), then one
+// descriptor array per schedule stage.
 static size_t one_launch_slices(int32_t n_graphs, const int64_t* vtx_off, const int64_t* edge_off,
-                                const ltsnet_params* p, std::vector<size_t>* offs)
+                                const ltsnet_params* p, const ltsnet_batch_config* cfg, std::vector<size_t>* offs)
 {
     size_t off = 0;
     for (int32_t g = 0; g < n_graphs; ++g) {
+        const ltsnet_params q = graph_params(p, cfg, g);
         const size_t one = ltsnet_run_workspace_size((int32_t)(vtx_off[g + 1] - vtx_off[g]),
-                                                     edge_off[g + 1] - edge_off[g], p);
+                                                     edge_off[g + 1] - edge_off[g], &q);
         if (one == 0) return 0;
         if (offs) offs->push_back(off);
         off += align_up(one, 256);
     }
     return off + align_up(sizeof(BatchGraph) * (size_t)n_graphs, 256) * (size_t)p->n_stages;
+}
+
+// Slice of one worker in the per-graph mode: the largest run workspace of
+// any graph of the batch.
+static size_t per_graph_slice(int32_t n_graphs, const int64_t* vtx_off, const int64_t* edge_off,
+                              const ltsnet_params* p, const ltsnet_batch_config* cfg)
+{
+    size_t slice = 0;
+    for (int32_t g = 0; g < n_graphs; ++g) {
+        const ltsnet_params q = graph_params(p, cfg, g);
+        const size_t one = ltsnet_run_workspace_size((int32_t)(vtx_off[g + 1] - vtx_off[g]),
+                                                     edge_off[g + 1] - edge_off[g], &q);
+        if (one == 0) return 0;
+        slice = std::max(slice, align_up(one, 256));
+    }
+    return slice;
 }
 
 extern "C" size_t ltsnet_run_batched_workspace_size(int32_t n_graphs, const int64_t* vtx_off,
@@ -1472,10 +1593,11 @@ extern "C" size_t ltsnet_run_batched_workspace_size(int32_t n_graphs, const int6
 {
     int64_t max_n, max_m;
     if (!params_ok(p) || !batch_cfg_ok(cfg) || !batch_ok(n_graphs, vtx_off, edge_off, max_n, max_m)) return 0;
-    if (cfg->mode == LTSNET_BATCH_ONE_LAUNCH) return one_launch_slices(n_graphs, vtx_off, edge_off, p, nullptr);
-    const size_t one = ltsnet_run_workspace_size((int32_t)max_n, max_m, p);
+    if (!batch_params_ok(n_graphs, p, cfg)) return 0;
+    if (cfg->mode == LTSNET_BATCH_ONE_LAUNCH) return one_launch_slices(n_graphs, vtx_off, edge_off, p, cfg, nullptr);
+    const size_t one = per_graph_slice(n_graphs, vtx_off, edge_off, p, cfg);
     if (one == 0) return 0;
-    return align_up(one, 256) * (size_t)std::min(cfg->n_workers, n_graphs);
+    return one * (size_t)std::min(cfg->n_workers, n_graphs);
 }
 
 extern "C" ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx_off, const int64_t* edge_off,
@@ -1486,6 +1608,7 @@ extern "C" ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx
     int64_t max_n, max_m;
     if (!row_ptr || !col || !Y || !ws || !params_ok(p) || !batch_cfg_ok(cfg)) return LTSNET_ERR_INVALID_ARG;
     if (!batch_ok(n_graphs, vtx_off, edge_off, max_n, max_m)) return LTSNET_ERR_INVALID_ARG;
+    if (!batch_params_ok(n_graphs, p, cfg)) return LTSNET_ERR_INVALID_ARG;
     if (k_of(p) > LTSNET_MAX_K) return LTSNET_ERR_INVALID_ARG;
     if ((uintptr_t)ws & 255) return LTSNET_ERR_WORKSPACE;
     const bool one = cfg->mode == LTSNET_BATCH_ONE_LAUNCH;
@@ -1494,10 +1617,10 @@ extern "C" ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx
     std::vector<size_t> offs;
     size_t slice = 0;
     if (one) {
-        const size_t need = one_launch_slices(n_graphs, vtx_off, edge_off, p, &offs);
+        const size_t need = one_launch_slices(n_graphs, vtx_off, edge_off, p, cfg, &offs);
         if (need == 0 || ws_bytes < need) return LTSNET_ERR_WORKSPACE;
     } else {
-        slice = align_up(ltsnet_run_workspace_size((int32_t)max_n, max_m, p), 256);
+        slice = per_graph_slice(n_graphs, vtx_off, edge_off, p, cfg);
         if (slice == 0 || ws_bytes < slice * (size_t)workers) return LTSNET_ERR_WORKSPACE;
     }
     int dev = 0;
@@ -1517,9 +1640,11 @@ extern "C" ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx
         while ((rc < 0 && cur >= 0) || (rc > 0 && cur == 0))
             if (first_err.compare_exchange_weak(cur, rc)) break;
     };
+    std::vector<ltsnet_params> gp(n_graphs);
+    for (int32_t g = 0; g < n_graphs; ++g) gp[g] = graph_params(p, cfg, g);
     auto carve_graph = [&](int32_t g, void* base, size_t bytes, RunWs* r) {
         Carve c(base, bytes);
-        *r = run_carve(c, (int32_t)(vtx_off[g + 1] - vtx_off[g]), 0, p, false);
+        *r = run_carve(c, (int32_t)(vtx_off[g + 1] - vtx_off[g]), 0, &gp[g], false);
         return c.ok();
     };
     // per-graph mode: every graph through run_core on the workers; one-launch
@@ -1536,16 +1661,16 @@ extern "C" ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx
             const int32_t ng = (int32_t)(vtx_off[g + 1] - vtx_off[g]);
             RunWs r;
             void* base = one ? (char*)ws + offs[g] : (char*)ws + slice * (size_t)wi;
-            const size_t bytes = one ? align_up(ltsnet_run_workspace_size(ng, edge_off[g + 1] - edge_off[g], p), 256)
-                                     : slice;
+            const size_t bytes =
+                one ? align_up(ltsnet_run_workspace_size(ng, edge_off[g + 1] - edge_off[g], &gp[g]), 256) : slice;
             ltsnet_status rc = LTSNET_OK;
             if (!carve_graph(g, base, bytes, &r)) rc = LTSNET_ERR_WORKSPACE;
             else if (cudaMemsetAsync(r.st, 0, sizeof(StatusBlock), s) != cudaSuccess) rc = LTSNET_ERR_CUDA;
             else if (one)
-                rc = run_prepare(row_ptr + vtx_off[g] + g, col + edge_off[g], ng, p, (float2*)Y + vtx_off[g], r, s,
-                                 &prep[g]);
+                rc = run_prepare(row_ptr + vtx_off[g] + g, col + edge_off[g], ng, &gp[g], (float2*)Y + vtx_off[g], r,
+                                 s, &prep[g]);
             else
-                rc = run_core(row_ptr + vtx_off[g] + g, col + edge_off[g], ng, p, (float2*)Y + vtx_off[g], r, s);
+                rc = run_core(row_ptr + vtx_off[g] + g, col + edge_off[g], ng, &gp[g], (float2*)Y + vtx_off[g], r, s);
             note(rc);
         }
         cudaStreamSynchronize(s);
@@ -1564,27 +1689,30 @@ extern "C" ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx
     cudaStream_t s = (cudaStream_t)stream;
     bool d16 = true;
     for (int32_t g = 0; g < n_graphs; ++g) d16 = d16 && prep[g].d16;
-    const IterShape shmax = iter_shape((int32_t)max_n, p);
+    ltsnet_params pmax = gp[0];  // the largest grid cap of the batch sizes the shared launch shapes
+    for (int32_t g = 1; g < n_graphs; ++g) pmax.max_boxes = std::max(pmax.max_boxes, gp[g].max_boxes);
+    const IterShape shmax = iter_shape((int32_t)max_n, &pmax);
     std::vector<BatchGraph> hg(n_graphs);
     std::vector<RunWs> rws(n_graphs);
     for (int32_t g = 0; g < n_graphs; ++g) {
         const int32_t ng = (int32_t)(vtx_off[g + 1] - vtx_off[g]);
-        carve_graph(g, (char*)ws + offs[g], align_up(ltsnet_run_workspace_size(ng, edge_off[g + 1] - edge_off[g], p), 256),
-                    &rws[g]);
+        carve_graph(g, (char*)ws + offs[g],
+                    align_up(ltsnet_run_workspace_size(ng, edge_off[g + 1] - edge_off[g], &gp[g]), 256), &rws[g]);
         const RunWs& r = rws[g];
-        const IterShape sh = iter_shape(ng, p);
+        const IterShape sh = iter_shape(ng, &gp[g]);
         Carve ic(r.iter, r.iter_bytes);
         BatchGraph& b = hg[g];
         b.w = iter_carve(ic, sh);
         LT_CUDA(iter_reset(b.w, sh, s));
-        b.P_row = r.P_row;
+        b.P_row = d16 ? r.Q_row : r.P_row;
         b.P_col = r.P_col;
-        b.P_d16 = d16 ? r.d16 : nullptr;
-        b.P_val = r.P_val;
+        b.P_d16 = d16 ? r.Q_d16 : nullptr;
+        b.P_val = d16 ? r.Q_val : r.P_val;
         b.Y = prep[g].Yw;
         b.upd = r.upd;
         b.gains = r.gains;
         b.n = ng;
+        b.max_boxes = gp[g].max_boxes;
         const HeavyRows& hr = prep[g].hr;
         b.hbase = hr.hbase;
         b.crow = hr.crow;
@@ -1596,7 +1724,7 @@ extern "C" ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx
     {
         // descriptor arrays, one per schedule stage (the stage coefficients
         // depend on each graph's n)
-        char* dbase = (char*)ws + one_launch_slices(n_graphs, vtx_off, edge_off, p, nullptr) -
+        char* dbase = (char*)ws + one_launch_slices(n_graphs, vtx_off, edge_off, p, cfg, nullptr) -
                       align_up(sizeof(BatchGraph) * (size_t)n_graphs, 256) * (size_t)p->n_stages;
         std::vector<BatchGraph*> dbg(p->n_stages);
         for (int32_t st = 0; st < p->n_stages; ++st) {

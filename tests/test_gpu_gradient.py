@@ -313,10 +313,11 @@ def test_run_with_and_without_reordering(ltlib, grid32):
 
 
 def test_run_compact_columns_match_int32_columns(ltlib, grid32):
-    """ltsnet_run streams P's columns as int16 offsets from their row when they
-    fit; one iteration must then agree with ltsnet_optimize on the same P with
-    int32 columns up to FP32 summation order (the two formats align the CSR
-    windows differently, so the lanes sum the entries in different groups)."""
+    """ltsnet_run streams P in its packed layout (int16 column offsets, rows
+    padded to multiples of 4 and interleaved within 32-entry blocks) when
+    the offsets fit; one iteration must then agree with ltsnet_optimize on
+    the same P in CSR form with int32 columns up to FP32 summation order (the
+    lanes sum the entries of a row in different groups)."""
     import torch
 
     g, P, Pn = grid32
@@ -466,6 +467,38 @@ def test_run_batched_equals_single_runs(ltlib, mode):
             assert np.all(boxes >= params.min_boxes) and np.all(boxes <= params.max_boxes)
         else:
             assert np.all(boxes == -1)
+
+
+def test_run_batched_per_graph_caps(ltlib):
+    """Per-graph grid caps (ltsnet_batch_config.max_boxes): each graph of the
+    batch runs exactly as ltsnet_run does with its own cap, in both forms,
+    whether the cap binds (small caps) or not; an entry of 0 takes the
+    parameters' cap; an out-of-range cap is rejected."""
+    import torch
+
+    graphs = [synth.grid2d(20, 30), synth.random_recursive_tree(900, 5), synth.sbm([300, 250, 200], 9.5, 40, 7),
+              synth.grid2d(9, 7)]
+    Y0s = [synth.initial_layout(g.n, 21 + i) for i, g in enumerate(graphs)]
+    base = dict(stages=ltlib.default_stages(120), min_boxes=4, max_boxes=96)
+    caps = [6, 0, 40, 9]
+    single = []
+    for g, y0, c in zip(graphs, Y0s, caps):
+        q = ltlib.Params(**{**base, "max_boxes": c if c > 0 else base["max_boxes"]})
+        single.append(ltlib.run(g.row_ptr, g.col, torch.from_numpy(y0), q)[0])
+    params = ltlib.Params(**base)
+    for mode in (0, 1):
+        Y, off, boxes = ltlib.run_batched(graphs, Y0s, params, workers=2, mode=mode, return_boxes=True,
+                                          max_boxes=caps)
+        for i in range(len(graphs)):
+            assert torch.equal(Y[off[i]:off[i + 1]], single[i]), (mode, i)
+        if mode == 0:
+            eff = np.where(np.array(caps) > 0, caps, base["max_boxes"])
+            assert np.all(boxes <= eff)
+            assert boxes[0] == 6 and boxes[3] == 9, boxes  # the small caps bind
+    with pytest.raises(ltlib.LtsnetError):
+        ltlib.run_batched(graphs, Y0s, params, workers=2, mode=0, max_boxes=[6, 0, 40, 100000])
+    with pytest.raises(ltlib.LtsnetError):
+        ltlib.run_batched(graphs, Y0s, params, workers=2, mode=0, max_boxes=[6, 0, 40, 2])  # below min_boxes
 
 
 def test_run_batched_argument_checks(ltlib):
