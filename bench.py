@@ -40,7 +40,20 @@ PERPLEXITY = 30.0
 ITERS = 1000
 BATCH_ITERS = 750
 BATCH_WORKERS = 16
-BATCH_MAX_BOXES = 128
+
+
+def batch_caps(ns):
+    """Per-graph grid caps of the batch (boxes per side): 1.5 times an
+    envelope of the box counts the batch recipe's graphs reach at the end of
+    their runs (grids, trees and SBMs of n in [200, 20000] reached at most 120
+    boxes below n = 500 and 180 near n = 20000, growing with log n), rounded
+    up to a multiple of 16.  Only memory depends on the cap: the grid itself
+    follows each layout's extent, so a cap that never binds leaves every
+    graph at the default box width."""
+    import numpy as np
+    ns = np.asarray(ns, dtype=np.float64)
+    env = 120.0 + 60.0 * np.log(np.maximum(ns, 200.0) / 200.0) / np.log(100.0)
+    return (np.ceil(1.5 * env / 16.0) * 16.0).astype(np.int32)
 FUSED_PROFILE = os.path.join(ROOT, "profiles", "fused_update_rgg1m.md")
 KERNEL_SOURCES = ("paper_2509_19785_gb300/csrc/iterate.cu", "paper_2509_19785_gb300/csrc/iter.cuh")
 
@@ -398,21 +411,24 @@ def bench_ltsnet(args):
     if not args.no_batched:
         gs = synth.graph_batch(512)
         y0s = [synth.initial_layout(gb.n, 100 + i) for i, gb in enumerate(gs)]
-        # grid capped at BATCH_MAX_BOXES per side (the per-graph grid arrays
-        # of the whole batch live side by side); max_boxes_used says whether
-        # the cap bound on any graph
+        # every graph's grid arrays sized for its own cap (the arrays of the
+        # whole batch live side by side); max_boxes_used says whether a cap
+        # bound on any graph
         import tempfile
 
-        bparams = lt.Params(perplexity=PERPLEXITY, stages=lt.default_stages(BATCH_ITERS), max_boxes=BATCH_MAX_BOXES)
+        caps = batch_caps([gb.n for gb in gs])
+        bparams = lt.Params(perplexity=PERPLEXITY, stages=lt.default_stages(BATCH_ITERS))
         tune_cache = os.path.join(tempfile.gettempdir(), "ltsnet_autotune.json")
-        fb, sb, tune_ms = lt.autotune_batched(gs, y0s, bparams, cache=tune_cache, workers=BATCH_WORKERS)
-        lt.run_batched(gs[:32], y0s[:32], bparams, workers=BATCH_WORKERS, fft_blocks=fb, spread_blocks=sb)
+        fb, sb, tune_ms = lt.autotune_batched(gs, y0s, bparams, cache=tune_cache, workers=BATCH_WORKERS,
+                                              max_boxes=caps)
+        lt.run_batched(gs[:32], y0s[:32], bparams, workers=BATCH_WORKERS, fft_blocks=fb, spread_blocks=sb,
+                       max_boxes=caps[:32])
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
         Yb, _, boxes = lt.run_batched(gs, y0s, bparams, workers=BATCH_WORKERS, fft_blocks=fb, spread_blocks=sb,
-                                      return_boxes=True)
+                                      return_boxes=True, max_boxes=caps)
         torch.cuda.synchronize()
         tb = max_over_ranks(time.perf_counter() - t0, world)
         if not bool(torch.isfinite(Yb).all()):
@@ -422,7 +438,7 @@ def bench_ltsnet(args):
         # the worker threads)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        Yp, _ = lt.run_batched(gs, y0s, bparams, workers=BATCH_WORKERS, mode=lt.BATCH_PER_GRAPH)
+        Yp, _ = lt.run_batched(gs, y0s, bparams, workers=BATCH_WORKERS, mode=lt.BATCH_PER_GRAPH, max_boxes=caps)
         torch.cuda.synchronize()
         tp = max_over_ranks(time.perf_counter() - t0, world)
         del Yp
@@ -436,8 +452,12 @@ def bench_ltsnet(args):
                                       "seconds": round(tp, 3), "workers": BATCH_WORKERS,
                                       "form": "ltsnet_run per graph on host worker threads, one stream each"},
                    "speedup_over_per_graph": round(tp / tb, 3),
-                   "max_boxes": BATCH_MAX_BOXES, "max_boxes_used": int(boxes.max()),
-                   "graphs_at_cap": int((boxes >= BATCH_MAX_BOXES).sum())}
+                   "max_boxes": {"rule": "per graph: 1.5 x an envelope of the box counts the recipe's graphs "
+                                         "reach, 120 + 13.0 ln(n / 200), rounded up to 16",
+                                 "min": int(caps.min()), "max": int(caps.max())},
+                   "max_boxes_used": int(boxes.max()),
+                   "max_used_over_cap": round(float((boxes / caps).max()), 3),
+                   "graphs_at_cap": int((boxes >= caps).sum())}
 
     # scale-free workload: Barabasi-Albert, n = 4e6, 4 edges per new vertex,
     # perplexity 50, 1000 iterations (whole run incl. C0, one step)
@@ -560,10 +580,62 @@ def bench_ltsnet(args):
         "gpu_launches": int(launches),
     }
     line["cpu_baseline"] = cpu_baseline(g)
+    line["parity_vs_oracle"] = oracle_parity(g, Y.cpu().numpy())
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return line
+
+
+def oracle_parity(g, Yf, size: int = 20_000):
+    """Part of the oracle leg: the error of the GPU path against the FP64
+    oracle on a 20,000-vertex sample of the workload -- the breadth-first
+    ball of vertex 0, drawn at the timed run's final layout.  C0 (neighbour
+    lists, hops, P) and, at the last stage's weights, every gradient term of
+    both convolution forms, relative L2 (the assembled gradient relative to
+    the sum of its terms' norms)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2509_19785_gb300 as lt
+    import synth
+
+    sub, ids = synth.bfs_ball(g, 0, size)
+    Y32 = np.ascontiguousarray(Yf[ids], dtype=np.float32)
+    ref = oracle.preprocess(sub.row_ptr, sub.col, PERPLEXITY)
+    aff = lt.affinities(sub.row_ptr, sub.col, PERPLEXITY)
+    torch.cuda.synchronize()
+    pv32 = aff["P"][2].cpu().numpy()
+    c0 = {"nbr_equal": bool(np.array_equal(aff["nbr"].cpu().numpy(), ref.nbr)),
+          "hop_equal": bool(np.array_equal(aff["hop"].cpu().numpy().astype(np.int32), ref.hop)),
+          "P_pattern_equal": bool(np.array_equal(aff["P"][0].cpu().numpy(), ref.P_row)
+                                  and np.array_equal(aff["P"][1].cpu().numpy(), ref.P_col)),
+          "P_val_equal_fp32_of_fp64": bool(np.array_equal(pv32, ref.P_val64.astype(np.float32)))}
+    pv = pv32.astype(np.float64)
+    st = lt.default_stages(ITERS)[-1]
+    ost = oracle.Stage(st.iters, st.lambda_kl, st.lambda_c, st.lambda_r, st.exaggeration, st.momentum)
+    gref, pr = oracle.interp_gradient(Y32, ref.P_row, ref.P_col, pv, ost, oracle.GridParams())
+    nn = sub.n
+    scale = (np.linalg.norm(4 * ost.lambda_kl * ost.exaggeration * pr["A"])
+             + np.linalg.norm(4 * ost.lambda_kl * pr["S"] / pr["Z"] * pr["R"])
+             + np.linalg.norm(ost.lambda_c / nn * Y32.astype(np.float64))
+             + np.linalg.norm(ost.lambda_r / nn ** 2 * pr["E"]))
+
+    def rel(a, b):
+        return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+    forms = {}
+    for name, conv in (("fft", 0), ("dft_gemm", 1)):
+        grad, parts, terms = lt.gradient(aff["P"], torch.from_numpy(Y32).cuda(), st,
+                                         lt.Params(perplexity=PERPLEXITY, conv_mode=conv), parts=True)
+        grad, parts, terms = grad.cpu().numpy(), parts.cpu().numpy(), terms.cpu().numpy()
+        forms[name] = {"A": rel(parts[:, 0:2], pr["A"]), "R": rel(parts[:, 2:4], pr["R"]),
+                       "E": rel(parts[:, 4:6], pr["E"]), "Z": float(abs(terms[0] - pr["Z"]) / pr["Z"]),
+                       "grad_vs_term_norms": float(np.linalg.norm(grad - gref) / scale)}
+    return {"sample": f"breadth-first ball of {sub.n} vertices around vertex 0, final layout of the timed run "
+                      f"(extent {float(Y32.max() - Y32.min()):.1f}, grid {pr['grid'].I} boxes per side)",
+            "c0": c0, "gradient_rel_l2": forms, "tolerance": 1e-5}
 
 
 def oracle_affinities(g):

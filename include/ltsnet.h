@@ -199,7 +199,7 @@ ltsnet_status ltsnet_symmetrize(const int32_t* nbr, const int32_t* cnt, const do
  * they need this step: plug-ins and embedded hosts handed a fixed
  * device-memory budget that forbid allocation, and loops that must not pay
  * for cudaMalloc's implicit synchronisation).  The scratch is a device array
- * built into the library (about 10.6 MB on every GPU that loads it, held until
+ * built into the library (about 5.2 MB on every GPU that loads it, held until
  * the process exits); nothing is allocated by the call.  Limit:
  * 2 * n * k <= ltsnet_symmetrize_static_max_entries() (2^18); larger inputs
  * return LTSNET_ERR_WORKSPACE without touching the GPU.  The first call on a

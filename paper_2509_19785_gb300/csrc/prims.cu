@@ -130,7 +130,10 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const uint64_t* __
 // memory, then the tile is written out in that order, so each digit's run
 // goes to global memory as consecutive addresses.
 constexpr size_t kScatterSmem = (size_t)kRadixTile * (sizeof(uint64_t) + sizeof(double));
+constexpr size_t kScatterSmemKeys = (size_t)kRadixTile * sizeof(uint64_t);  // keys alone
 
+// VALS: (key, value) pairs, else keys alone (vin, vout unused).
+template <bool VALS>
 __global__ void __launch_bounds__(kRadixThreads, 2)
     k_radix_scatter(const uint64_t* __restrict__ kin, const double* __restrict__ vin, uint64_t* __restrict__ kout,
                     double* __restrict__ vout, int64_t count, int shift, const uint32_t* __restrict__ offs,
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(kRadixThreads, 2)
         const int64_t e = base + i * 32 + lane;
         if (e < count) {
             kk[i] = kin[e];
-            vv[i] = vin[e];
+            if (VALS) vv[i] = vin[e];
         }
     }
     // per-warp digit counts over the warp's sub-tile
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(kRadixThreads, 2)
         if (valid) {
             const uint32_t lp = wh[w][d] + __popc(peers & ltm);
             sk[lp] = kk[i];
-            sv[lp] = vv[i];
+            if (VALS) sv[lp] = vv[i];
         }
         __syncwarp();
         if (valid && (peers & ltm) == 0) wh[w][d] += __popc(peers);
@@ -211,7 +214,7 @@ __global__ void __launch_bounds__(kRadixThreads, 2)
         const int d = (int)((key >> shift) & 0xffu);
         const uint32_t gp = gbase[d] + ((uint32_t)j - dstart[d]);
         kout[gp] = key;
-        vout[gp] = sv[j];
+        if (VALS) vout[gp] = sv[j];
     }
 }
 
@@ -248,7 +251,8 @@ cudaError_t radix_sort_u64_f64(uint64_t* k0, double* v0, uint64_t* k1, double* v
     const int64_t nb = (count + kRadixTile - 1) / kRadixTile;
     {
         cudaError_t e = once_per_device(kOnceRadix, [] {
-            return cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+            return cudaFuncSetAttribute(k_radix_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kScatterSmem);
         });
         if (e != cudaSuccess) return e;
     }
@@ -259,12 +263,36 @@ cudaError_t radix_sort_u64_f64(uint64_t* k0, double* v0, uint64_t* k1, double* v
         count_launches(1);
         cudaError_t e = scan_u32_exclusive(hist, hist, nb * kDigits, tmp, s);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<(unsigned)nb, kRadixThreads, kScatterSmem, s>>>(ka, va, kb, vb, count, shift, hist, nb);
+        k_radix_scatter<true><<<(unsigned)nb, kRadixThreads, kScatterSmem, s>>>(ka, va, kb, vb, count, shift, hist,
+                                                                                nb);
         count_launches(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         uint64_t* tk = ka; ka = kb; kb = tk;
         double* tv = va; va = vb; vb = tv;
+        *in_alt = !*in_alt;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t radix_sort_u64(uint64_t* k0, uint64_t* k1, int64_t count, int lo_bit, int bits, uint32_t* hist,
+                           uint32_t* tmp, cudaStream_t s, bool* in_alt)
+{
+    *in_alt = false;
+    if (count <= 1) return cudaSuccess;
+    const int64_t nb = (count + kRadixTile - 1) / kRadixTile;
+    uint64_t *ka = k0, *kb = k1;
+    for (int shift = lo_bit; shift < lo_bit + bits; shift += 8) {
+        k_radix_hist<<<(unsigned)nb, kRadixThreads, 0, s>>>(ka, count, shift, hist, nb);
+        count_launches(1);
+        cudaError_t e = scan_u32_exclusive(hist, hist, nb * kDigits, tmp, s);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<false><<<(unsigned)nb, kRadixThreads, kScatterSmemKeys, s>>>(ka, nullptr, kb, nullptr, count,
+                                                                                    shift, hist, nb);
+        count_launches(1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        uint64_t* tk = ka; ka = kb; kb = tk;
         *in_alt = !*in_alt;
     }
     return cudaSuccess;

@@ -18,6 +18,11 @@ size_t radix_hist_words(int64_t count);
 cudaError_t radix_sort_u64_f64(uint64_t* k0, double* v0, uint64_t* k1, double* v1, int64_t count, int bits,
                                uint32_t* hist, uint32_t* tmp, cudaStream_t s, bool* in_alt);
 
+// The same for keys alone, by bits [lo_bit, lo_bit + bits) of the key (the
+// bits below lo_bit travel with the key unsorted).
+cudaError_t radix_sort_u64(uint64_t* k0, uint64_t* k1, int64_t count, int lo_bit, int bits, uint32_t* hist,
+                           uint32_t* tmp, cudaStream_t s, bool* in_alt);
+
 size_t bfs_warp_bytes(int k, int* hlog2_out);
 
 }  // namespace lt

@@ -9,7 +9,7 @@
 // is loaded, on every GPU that loads it, and forwards to ltsnet_symmetrize.
 //
 // The array holds one call's sort buffers for at most kStaticEntries emitted
-// entries (2 n k <= 2^18, about 10.6 MB).  Every call uses the same array and
+// entries (2 n k <= 2^18, about 5.2 MB).  Every call uses the same array and
 // leaves its contents behind; ltsnet_symmetrize clears the status word and the
 // nnz counter it reads and writes everything else before reading it.  Calls
 // whose GPU work overlaps (other streams, other host threads) race on it.
@@ -21,10 +21,11 @@ namespace lt {
 namespace {
 
 constexpr int64_t kStaticEntries = (int64_t)1 << 18;
-// Workspace layout of ltsnet_symmetrize for 2 n k = kStaticEntries (status,
-// nnz, two key and two value buffers, head flags, indices, histograms, scan
-// temporaries), rounded up; checked against the exact size at every call.
-constexpr size_t kStaticBytes = (size_t)kStaticEntries * 40 + ((size_t)1 << 20);
+// Workspace layout of ltsnet_symmetrize for 2 n k = kStaticEntries, always
+// its compact form at these sizes (status, nnz, two 8-byte key buffers,
+// histograms, scan temporaries), rounded up; checked against the exact size
+// at every call.
+constexpr size_t kStaticBytes = (size_t)kStaticEntries * 16 + ((size_t)1 << 20);
 
 static __device__ __align__(256) unsigned char g_sym_scratch[kStaticBytes];
 

@@ -1,79 +1,92 @@
 // K3 -- symmetrisation (Eq. 2): p_ij = (p_{j|i} + p_{i|j}) / (2n).
 //
-// Every conditional entry (i, j, p_{j|i}) is emitted twice, as (row i, col j)
-// and as (row j, col i); padded slots get a sentinel key that sorts last.
-// A stable radix sort on the packed key (row, col) brings the (at most two)
-// copies of each pair together with rows and columns ascending; a head-flag
-// scan numbers the distinct pairs; the write pass adds the two copies in
-// FP64, scales by 1/(2n), rounds once to FP32 and fills the CSR row offsets
-// (including empty rows).
+// Every conditional entry (i, j, p_{j|i}) at slot s of row i's list is
+// emitted twice, as the 64-bit key (row i, col j, slot s, copy 0) and as
+// (row j, col i, slot s, copy 1); padded slots get the key ~0, which sorts
+// last.  A stable radix sort of the keys alone by their (row, col) bits
+// brings the (at most two) copies of each pair together with rows and
+// columns ascending; a head-flag scan numbers the distinct pairs; the write
+// pass reads each copy's p_{j|i} back from its source's conditional row (row
+// i for copy 0, column i for copy 1, slot s), adds the two in FP64, scales by
+// 1/(2n), rounds once to FP32 and fills the CSR row offsets (including empty
+// rows).  The key needs 2 ceil(log2(n + 1)) + ceil(log2 k) + 1 bits, which
+// is at most 64 whenever the 2 n k emitted entries have 32-bit offsets.
+// Scratch: two key buffers, 16 bytes per emitted entry; the head flags and
+// pair numbers go into the key buffer the sort has left free.
 #include "prims.cuh"
 
 namespace lt {
 namespace {
 
-__global__ void k_sym_emit(const int32_t* __restrict__ nbr, const int32_t* __restrict__ cnt,
-                           const double* __restrict__ pcond, int32_t n, int32_t k, int nbits,
-                           uint64_t* __restrict__ keys, double* __restrict__ vals, StatusBlock* st)
+__global__ void k_sym_emit(const int32_t* __restrict__ nbr, const int32_t* __restrict__ cnt, int32_t n, int32_t k,
+                             int nbits, int pb, uint64_t* __restrict__ keys, StatusBlock* st)
 {
     const int64_t nk = (int64_t)n * k;
-    const uint64_t sent = (nbits >= 32) ? ~0ull : ((1ull << (2 * nbits)) - 1ull);
+    const uint64_t tflag = 1ull << (pb - 1);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e / k;
         const int s = (int)(e - i * k);
-        uint64_t ko = sent, kt = sent;
-        double p = 0.0;
+        uint64_t ko = ~0ull, kt = ~0ull;
         if (s < cnt[i]) {
             const int32_t v = nbr[e];
             if ((unsigned)v < (unsigned)n) {
-                p = pcond[e];
-                ko = ((uint64_t)i << nbits) | (uint64_t)v;
-                kt = ((uint64_t)v << nbits) | (uint64_t)i;
+                ko = ((((uint64_t)i << nbits) | (uint64_t)v) << pb) | (uint64_t)s;
+                kt = ((((uint64_t)v << nbits) | (uint64_t)i) << pb) | tflag | (uint64_t)s;
             } else {
                 record_error(st, LTSNET_ERR_BAD_GRAPH, v);
             }
         }
         keys[e] = ko;
-        vals[e] = p;
         keys[nk + e] = kt;
-        vals[nk + e] = p;
     }
 }
 
-__global__ void k_sym_heads(const uint64_t* __restrict__ keys, int64_t E, uint64_t sent, uint32_t* __restrict__ flag)
+__global__ void k_sym_heads(const uint64_t* __restrict__ keys, int64_t E, int pb, uint32_t* __restrict__ flag)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t x = keys[e];
-        flag[e] = (x != sent && (e == 0 || keys[e - 1] != x)) ? 1u : 0u;
+        flag[e] = (x != ~0ull && (e == 0 || (keys[e - 1] >> pb) != (x >> pb))) ? 1u : 0u;
     }
 }
 
-__global__ void k_sym_write(const uint64_t* __restrict__ keys, const double* __restrict__ vals,
-                            const uint32_t* __restrict__ flag, const uint32_t* __restrict__ uidx, int64_t E,
-                            uint64_t sent, int nbits, int32_t n, int64_t cap, double inv2n,
-                            int64_t* __restrict__ P_row, int32_t* __restrict__ P_col, float* __restrict__ P_val,
-                            int64_t* __restrict__ nnz_out)
+// p_{j|i} of a key: slot s of the source's conditional row, the
+// source being the row, or the column for a transposed copy.
+__device__ __forceinline__ double pair_p(uint64_t x, const double* __restrict__ pcond, int32_t k, int nbits,
+                                            int pb)
+{
+    const uint64_t rc = x >> pb;
+    const uint64_t cmask = (1ull << nbits) - 1ull;
+    const bool tr = (x >> (pb - 1)) & 1ull;
+    const int64_t src = tr ? (int64_t)(rc & cmask) : (int64_t)(rc >> nbits);
+    const int64_t s = (int64_t)(x & ((1ull << (pb - 1)) - 1ull));
+    return pcond[src * k + s];
+}
+
+__global__ void k_sym_write(const uint64_t* __restrict__ keys, const double* __restrict__ pcond,
+                              const uint32_t* __restrict__ flag, const uint32_t* __restrict__ uidx, int64_t E,
+                              int nbits, int pb, int32_t n, int32_t k, int64_t cap, double inv2n,
+                              int64_t* __restrict__ P_row, int32_t* __restrict__ P_col, float* __restrict__ P_val,
+                              int64_t* __restrict__ nnz_out)
 {
     const uint64_t cmask = (1ull << nbits) - 1ull;
+    const int rs = nbits + pb;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
         if (!flag[e]) continue;
         const uint64_t x = keys[e];
         const int64_t u = uidx[e];
-        const int64_t row = (int64_t)(x >> nbits);
-        double v = vals[e];
-        const bool dup = (e + 1 < E) && keys[e + 1] == x;
-        if (dup) v = v + vals[e + 1];
+        const int64_t row = (int64_t)(x >> rs);
+        double v = pair_p(x, pcond, k, nbits, pb);
+        const bool dup = (e + 1 < E) && (keys[e + 1] >> pb) == (x >> pb);
+        if (dup) v = v + pair_p(keys[e + 1], pcond, k, nbits, pb);
         if (u < cap) {
-            P_col[u] = (int32_t)(x & cmask);
+            P_col[u] = (int32_t)((x >> pb) & cmask);
             P_val[u] = (float)(v * inv2n);
         }
-        // Row offsets: this head starts row `row`; rows between the previous
-        // head's row and this one are empty.
-        const int64_t prev_row = (e == 0) ? -1 : (int64_t)(keys[e - 1] >> nbits);
+        const int64_t prev_row = (e == 0) ? -1 : (int64_t)(keys[e - 1] >> rs);
         if (e == 0 || prev_row != row)
             for (int64_t r = prev_row + 1; r <= row; ++r) P_row[r] = u;
         const int64_t nxt = e + (dup ? 2 : 1);
-        if (nxt >= E || keys[nxt] == sent) {
+        if (nxt >= E || keys[nxt] == ~0ull) {
             for (int64_t r = row + 1; r <= n; ++r) P_row[r] = u + 1;
             *nnz_out = u + 1;
         }
@@ -93,11 +106,21 @@ int sym_nbits(int32_t n)
     return b;
 }
 
+// Bits of the key below (row, col): the slot in the source's list and the
+// transposed-copy flag.
+int sym_pbits(int32_t k)
+{
+    int b = 1;
+    while (((int64_t)1 << b) < (int64_t)k) ++b;
+    return b + 1;
+}
+
+bool sym_key_fits(int32_t n, int32_t k) { return 2 * sym_nbits(n) + sym_pbits(k) <= 64; }
+
 struct SymWs {
     StatusBlock* st;
     uint64_t *k0, *k1;
-    double *v0, *v1;
-    uint32_t *flag, *uidx, *hist, *tmp;
+    uint32_t *hist, *tmp;
     int64_t* nnz;
 };
 
@@ -109,10 +132,6 @@ SymWs sym_carve(Carve& c, int32_t n, int32_t k)
     w.nnz = c.take<int64_t>(1);
     w.k0 = c.take<uint64_t>(E);
     w.k1 = c.take<uint64_t>(E);
-    w.v0 = c.take<double>(E);
-    w.v1 = c.take<double>(E);
-    w.flag = c.take<uint32_t>(E);
-    w.uidx = c.take<uint32_t>(E);
     const size_t hw = radix_hist_words(E);
     w.hist = c.take<uint32_t>(hw);
     size_t tw = scan_tmp_words(E);
@@ -161,26 +180,29 @@ extern "C" ltsnet_status ltsnet_symmetrize(const int32_t* nbr, const int32_t* cn
     SymWs w = sym_carve(c, n, k);
     if (!c.ok()) return LTSNET_ERR_WORKSPACE;
     const int nbits = sym_nbits(n);
-    const uint64_t sent = (1ull << (2 * nbits)) - 1ull;
+    if (!sym_key_fits(n, k)) return LTSNET_ERR_INVALID_ARG;  // not reached while E < 2^32
     const unsigned grid = num_sms() * 8, block = 256;
     LT_CUDA(cudaMemsetAsync(w.st, 0, sizeof(StatusBlock), s));
     LT_CUDA(cudaMemsetAsync(w.nnz, 0, sizeof(int64_t), s));
-    k_sym_emit<<<grid, block, 0, s>>>(nbr, cnt, pcond, n, k, nbits, w.k0, w.v0, w.st);
+    const int pb = sym_pbits(k);
+    k_sym_emit<<<grid, block, 0, s>>>(nbr, cnt, n, k, nbits, pb, w.k0, w.st);
     LT_CHECK_LAUNCH();
     count_launches(1);
     bool alt = false;
-    LT_CUDA(radix_sort_u64_f64(w.k0, w.v0, w.k1, w.v1, E, 2 * nbits, w.hist, w.tmp, s, &alt));
+    LT_CUDA(radix_sort_u64(w.k0, w.k1, E, pb, 2 * nbits, w.hist, w.tmp, s, &alt));
     const uint64_t* ks = alt ? w.k1 : w.k0;
-    const double* vs = alt ? w.v1 : w.v0;
-    k_sym_heads<<<grid, block, 0, s>>>(ks, E, sent, w.flag);
+    // head flags and pair numbers in the other key buffer, free after the sort
+    uint32_t* flag = (uint32_t*)(alt ? w.k0 : w.k1);
+    uint32_t* uidx = flag + E;
+    k_sym_heads<<<grid, block, 0, s>>>(ks, E, pb, flag);
     LT_CHECK_LAUNCH();
     count_launches(1);
-    LT_CUDA(scan_u32_exclusive(w.flag, w.uidx, E, w.tmp, s));
+    LT_CUDA(scan_u32_exclusive(flag, uidx, E, w.tmp, s));
     k_fill_i64<<<64, 256, 0, s>>>(P_row, (int64_t)n + 1, 0);
     LT_CHECK_LAUNCH();
     count_launches(1);
-    k_sym_write<<<grid, block, 0, s>>>(ks, vs, w.flag, w.uidx, E, sent, nbits, n, cap, 1.0 / (2.0 * (double)n), P_row,
-                                       P_col, P_val, w.nnz);
+    k_sym_write<<<grid, block, 0, s>>>(ks, pcond, flag, uidx, E, nbits, pb, n, k, cap, 1.0 / (2.0 * (double)n),
+                                         P_row, P_col, P_val, w.nnz);
     LT_CHECK_LAUNCH();
     count_launches(1);
     int64_t nnz = 0;
