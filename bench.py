@@ -236,11 +236,14 @@ def bench_ltsnet(args):
     # its row (P has the same support as the graph's k-hop balls).
     order, inv, reordered = lt.bfs_order(g.row_ptr, g.col)
     col_bytes = 4
+    nnz_streamed = None
     if reordered:
         invn = inv.cpu().numpy().astype(np.int64)
         rows = np.repeat(np.arange(n), np.diff(aff["P"][0].cpu().numpy()))
         cols = aff["P"][1].cpu().numpy().astype(np.int64)
         col_bytes = 2 if int(np.max(np.abs(invn[cols] - invn[rows]))) <= 32767 else 4
+        # the packed layout pads every row to a multiple of 4 entries
+        nnz_streamed = int(np.sum((np.diff(aff["P"][0].cpu().numpy()) + 3) // 4 * 4)) if col_bytes == 2 else None
     torch.cuda.synchronize()
     c0 = []
     for _ in range(3):
@@ -317,7 +320,10 @@ def bench_ltsnet(args):
     # roofline of the fused gather + attraction + compression + update kernel
     peaks = measured_peaks()
     bytes_per_launch = 8 * nnz + 8 * (n + 1) + 48 * n  # the per-entry and per-vertex figures of the method
-    moved_per_launch = col_bytes * nnz + 4 * nnz + 8 * (n + 1) + 48 * n  # what this P format streams
+    # what this P format streams: entries (padded rows when packed), row
+    # pointers, and per vertex the layout read, the new layout, update and
+    # gains read and written
+    moved_per_launch = (col_bytes + 4) * (nnz_streamed or nnz) + 8 * (n + 1) + 48 * n
     fused_ms, fused_launches = prof
     avg_s = fused_ms / 1e3 / max(1, fused_launches)
     achieved = bytes_per_launch / avg_s / 1e9
@@ -325,7 +331,7 @@ def bench_ltsnet(args):
                 "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": ncu_traffic_per_launch(),
                 "algorithmic_bytes_per_launch": bytes_per_launch, "moved_bytes_per_launch": moved_per_launch,
-                "column_format": "int16 offsets from the row" if col_bytes == 2 else "int32",
+                "column_format": "packed rows, int16 offsets from the row" if col_bytes == 2 else "int32 (CSR)",
                 "avg_launch_us": round(avg_s * 1e6, 2),
                 "launches_timed": fused_launches, "peak_source": peaks["source"]}
 
@@ -489,12 +495,24 @@ def bench_ltsnet(args):
         del aff_ba
         nnz_ba = int(P_ba[1].numel())
         ba_bytes = 8 * nnz_ba + 8 * (gba.n + 1) + 48 * gba.n
+        # the format ltsnet_run streams P in on this graph (as for rgg1m above)
+        _, inv_ba, reo_ba = lt.bfs_order(rp_ba, cl_ba)
+        ba_fmt = "int32 columns (CSR)"
+        if reo_ba:
+            invb = inv_ba.cpu().numpy().astype(np.int64)
+            rows_b = np.repeat(np.arange(gba.n), np.diff(P_ba[0].cpu().numpy()))
+            far_b = int(np.max(np.abs(invb[P_ba[1].cpu().numpy().astype(np.int64)] - invb[rows_b])))
+            if far_b <= 32767:
+                ba_fmt = "packed, int16 offsets from the row"
+            del rows_b
+        del inv_ba
         f_s = fms / 1e3 / max(1, fcnt)
         ba = {"value": round(job_rate(world, ITERS, tba * 1e3), 2), "unit": "iters/s", "n": gba.n, "m": gba.m,
               "nnz_P": nnz_ba, "perplexity": 50, "iters": ITERS, "seconds_incl_C0": round(tba, 3),
               "workspace_bytes": int(ws_bytes_ba), "peak_device_bytes": int(peak - base_mem),
               "status": int(rc), "note": "status 1: rows whose perplexity target is unreachable (hubs) are flagged",
               "roofline": {"kernel": "k_fused (rows of more than 2048 entries summed beforehand in chunks)",
+                           "column_format": ba_fmt,
                            "bound": "hbm", "achieved": round(ba_bytes / f_s / 1e9, 1), "peak": peaks["hbm_gbs"],
                            "unit": "GB/s", "frac": round(ba_bytes / f_s / 1e9 / peaks["hbm_gbs"], 4),
                            "algorithmic_bytes_per_launch": ba_bytes, "avg_launch_us": round(f_s * 1e6, 2),

@@ -779,10 +779,33 @@ __device__ __forceinline__ void add_point_row_q(float2 u, int bb, const float* h
     }
 }
 
+// Totals of NV (16 or 32) per-lane values over the warp by reduce-scatter:
+// each level halves the values a lane holds, so lane l ends with the total
+// of value l (NV = 32) or l >> 1 (NV = 16, both lanes of a pair) after NV - 1
+// shuffles instead of 5 NV.  Sums modulo 2^32, so the order of the additions
+// does not matter.
+template <int NV>
+__device__ __forceinline__ unsigned warp_reduce_scatter(unsigned (&v)[NV], int lane)
+{
+#pragma unroll
+    for (int h = NV / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const unsigned send = up ? v[i] : v[i + h];
+            const unsigned keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(FULL, send, o);
+        }
+    }
+    if (NV == 16) v[0] += __shfl_xor_sync(FULL, v[0], 1);
+    return v[0];
+}
+
 // The charge grid from the box-sorted points, every node written once.
 // (1) Boxes of more than kLightMax points, one warp per segment of kSeg
 // points (held in registers), node row by node row: the lanes sum strided
-// points in 32-bit integers and the sums are reduced across the warp.  A box of one segment is written
+// points in 32-bit integers and the sums are reduced across the warp
+// (reduce-scatter).  A box of one segment is written
 // directly; for the others the segments add their sums to the box's 64-bit
 // accumulator, and the warp that finishes last (a ticket per box) converts
 // it, writes the box's nodes and clears the accumulator and the ticket for
@@ -838,28 +861,26 @@ __device__ __forceinline__ void k_box_spread_body(const float2* __restrict__ su,
             for (int k = 0; k < kSeg / 32; ++k)
                 if ((unsigned)k < m) add_point_row_q<P>(pts[k], bb, hf, ra);
             const unsigned bias = m * kMagicBits;
-            int mine = 0;
+            // value a * 4 + ch of the row, padded with zeros to NV values
+            constexpr int NV = P * 4 <= 16 ? 16 : 32;
+            unsigned vals[NV];
 #pragma unroll
-            for (int a = 0; a < P; ++a)
-#pragma unroll
-                for (int ch = 0; ch < 4; ++ch) {
-                    ra[a][ch] -= bias;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) ra[a][ch] += __shfl_xor_sync(FULL, ra[a][ch], o);
-                    if (lane == a * 4 + ch) mine = (int)ra[a][ch];
-                }
+            for (int v = 0; v < NV; ++v) vals[v] = v < P * 4 ? ra[v >> 2][v & 3] - bias : 0u;
+            const unsigned tot = warp_reduce_scatter<NV>(vals, lane);
+            const int vi = NV == 32 ? lane : lane >> 1;  // the value this lane now holds the total of
             if (nseg == 1) {
-                if (lane < P) {
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                // node a = lane < P gathers its four moments from their lanes
+                const int a = min(lane, P - 1);
+                unsigned c[4];
 #pragma unroll
-                    for (int a = 0; a < P; ++a)
-                        if (a == lane)
-                            v = make_float4((float)(int)ra[a][0] * ihf[0], (float)(int)ra[a][1] * ihf[1],
-                                            (float)(int)ra[a][2] * ihf[2], (float)(int)ra[a][3] * ihf[3]);
-                    wflt[(int64_t)(by * P + bb) * M + (int64_t)bx * P + lane] = v;
-                }
-            } else if (lane < P * 4 && mine != 0) {
-                atomicAdd((unsigned long long*)(acc + bb * P * 4 + lane), (unsigned long long)(long long)mine);
+                for (int ch = 0; ch < 4; ++ch)
+                    c[ch] = __shfl_sync(FULL, tot, NV == 32 ? 4 * a + ch : 2 * (4 * a + ch));
+                if (lane < P)
+                    wflt[(int64_t)(by * P + bb) * M + (int64_t)bx * P + lane] =
+                        make_float4((float)(int)c[0] * ihf[0], (float)(int)c[1] * ihf[1], (float)(int)c[2] * ihf[2],
+                                    (float)(int)c[3] * ihf[3]);
+            } else if ((NV == 32 || (lane & 1) == 0) && vi < P * 4 && tot != 0u) {
+                atomicAdd((unsigned long long*)(acc + bb * P * 4 + vi), (unsigned long long)(long long)(int)tot);
             }
         }
         if (nseg == 1) continue;

@@ -325,23 +325,23 @@ __device__ __forceinline__ void
         const int64_t re = has ? P_row[row + 1] : 0;
         float2 A = make_float2(0.f, 0.f);
         Window nxt;
-        {
-            const int64_t s0 = __shfl_sync(FULL, rs, grp), e0 = __shfl_sync(FULL, re, grp);
-            load_window<D16>(nxt, P_col, P_d16, P_val, nnz, window_start<D16>(s0), window_end(hbase, s0, e0),
-                             (int)(g0 + grp), gl);
-        }
+        // bounds of the next round's row, shuffled once and kept for its round
+        int64_t ns0 = __shfl_sync(FULL, rs, grp), ne0 = __shfl_sync(FULL, re, grp);
+        load_window<D16>(nxt, P_col, P_d16, P_val, nnz, window_start<D16>(ns0), window_end(hbase, ns0, ne0),
+                         (int)(g0 + grp), gl);
 #pragma unroll 1
         for (int rr = 0; rr < 8; ++rr) {
             const Window cur = nxt;
             const int src = rr * 4 + grp;
             const int rowi = (int)(g0 + src);
+            const int64_t s0 = ns0, e0r = ne0;
             if (rr < 7) {
                 const int nsrc = src + 4;
-                const int64_t ns0 = __shfl_sync(FULL, rs, nsrc), ne0 = __shfl_sync(FULL, re, nsrc);
+                ns0 = __shfl_sync(FULL, rs, nsrc);
+                ne0 = __shfl_sync(FULL, re, nsrc);
                 load_window<D16>(nxt, P_col, P_d16, P_val, nnz, window_start<D16>(ns0), window_end(hbase, ns0, ne0),
                                  rowi + 4, gl);
             }
-            const int64_t s0 = __shfl_sync(FULL, rs, src), e0r = __shfl_sync(FULL, re, src);
             const float xi = __shfl_sync(FULL, yi.x, src), yv = __shfl_sync(FULL, yi.y, src);
             const bool heavy = hbase != nullptr && e0r - s0 > kHeavyRow;  // summed in chunks already
             const int64_t e0 = heavy ? s0 : e0r;
