@@ -421,6 +421,57 @@ __device__ __forceinline__ int box_hash_slot(BoxHash& H, int box)
     return -1;
 }
 
+// Points per box, in tiles of kBoxTile consecutive points per block: the
+// boxes a tile touches are aggregated in the shared-memory hash table and
+// added to bcnt.  count_prefetch loads the block's first tile and clears the
+// table (it needs no grid, so it runs while the grid is being derived);
+// count_tiles then counts that tile and the block's later ones.
+__device__ __forceinline__ void count_prefetch(const float2* __restrict__ Y, int32_t n, BoxHash& H,
+                                               float2 (&pts)[kBoxRounds])
+{
+    const int64_t ntiles = ((int64_t)n + kBoxTile - 1) / kBoxTile;
+    if ((int64_t)blockIdx.x >= ntiles) return;
+#pragma unroll
+    for (int r = 0; r < kBoxRounds; ++r) {
+        const int64_t i = (int64_t)blockIdx.x * kBoxTile + r * kBoxThreads + threadIdx.x;
+        pts[r] = i < n ? Y[i] : make_float2(0.f, 0.f);
+    }
+    box_hash_clear(H);
+}
+
+__device__ __forceinline__ void count_tiles(const float2* __restrict__ Y, int32_t n, float lo, float h, float rh,
+                                            int I, int32_t* __restrict__ bcnt, BoxHash& H,
+                                            float2 (&pts)[kBoxRounds])
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t ntiles = ((int64_t)n + kBoxTile - 1) / kBoxTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (tile != (int64_t)blockIdx.x) {
+            box_hash_clear(H);
+#pragma unroll
+            for (int r = 0; r < kBoxRounds; ++r) {
+                const int64_t i = tile * kBoxTile + r * kBoxThreads + threadIdx.x;
+                pts[r] = i < n ? Y[i] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int r = 0; r < kBoxRounds; ++r) {
+            const int64_t i = tile * kBoxTile + r * kBoxThreads + threadIdx.x;
+            const int box = i < n ? box_of_r(pts[r].y, lo, h, rh, I) * I + box_of_r(pts[r].x, lo, h, rh, I) : -1;
+            const unsigned peers = __match_any_sync(FULL, box);
+            if (box >= 0 && lane == __ffs(peers) - 1) {
+                const int slot = box_hash_slot(H, box);
+                if (slot >= 0) atomicAdd(&H.val[slot], __popc(peers));
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < kBoxHash; k += blockDim.x)
+            if (H.key[k] >= 0) atomicAdd(&bcnt[H.key[k]], H.val[k]);
+        __syncthreads();
+    }
+}
+
 // Grid of this iteration (every block derives the same grid from the bounds;
 // block 0 publishes it), FFT twiddles, and -- unless the plain atomic spread
 // is in use -- the points per box, aggregated per tile of kBoxTile points in
@@ -434,6 +485,10 @@ __device__ __forceinline__ void k_setup_body(const int32_t* __restrict__ bounds_
 {
     __shared__ GridDev g;
     __shared__ BoxHash H;
+    // the first tile's points and the hash table are made ready while
+    // thread 0 derives the grid
+    float2 pts[kBoxRounds];
+    if (count) count_prefetch(Y, n, H, pts);
     if (threadIdx.x == 0) compute_grid(bounds_cur, bwm, min_boxes, max_boxes, P, n, g);
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -456,6 +511,7 @@ __device__ __forceinline__ void k_setup_body(const int32_t* __restrict__ bounds_
         bounds_next[0] = f2ord(INFINITY);
         bounds_next[1] = f2ord(-INFINITY);
     }
+    if (count) count_tiles(Y, n, g.lo, g.h, g.rh, g.I, bcnt, H, pts);
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = tid; t < g.L; t += nth) {
@@ -470,33 +526,6 @@ __device__ __forceinline__ void k_setup_body(const int32_t* __restrict__ bounds_
         else if (q == 2) v = make_float2(-cs, -sn);
         else v = make_float2(-sn, cs);
         tw[t] = v;
-    }
-    if (!count) return;
-    const float lo = g.lo, h = g.h, rh = g.rh;
-    const int I = g.I;
-    const int lane = threadIdx.x & 31;
-    const int64_t ntiles = ((int64_t)n + kBoxTile - 1) / kBoxTile;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        box_hash_clear(H);
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < kBoxRounds; ++r) {
-            const int64_t i = tile * kBoxTile + r * kBoxThreads + threadIdx.x;
-            int box = -1;
-            if (i < n) {
-                const float2 p = Y[i];
-                box = box_of_r(p.y, lo, h, rh, I) * I + box_of_r(p.x, lo, h, rh, I);
-            }
-            const unsigned peers = __match_any_sync(FULL, box);
-            if (box >= 0 && lane == __ffs(peers) - 1) {
-                const int slot = box_hash_slot(H, box);
-                if (slot >= 0) atomicAdd(&H.val[slot], __popc(peers));
-            }
-        }
-        __syncthreads();
-        for (int k = threadIdx.x; k < kBoxHash; k += blockDim.x)
-            if (H.key[k] >= 0) atomicAdd(&bcnt[H.key[k]], H.val[k]);
-        __syncthreads();
     }
 }
 

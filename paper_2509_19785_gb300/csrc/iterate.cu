@@ -201,6 +201,36 @@ struct HeavyRows {
     int32_t nchunks = 0;
 };
 
+// Paired FP32 arithmetic (sm_100 family): each half is the IEEE
+// round-to-nearest result of the scalar operation, so these give the same
+// bits as two scalar instructions in one issue.
+__device__ __forceinline__ unsigned long long pack2(float2 a)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long r)
+{
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+// a - b, componentwise
+__device__ __forceinline__ float2 sub_x2(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)));
+    return unpack2(r);
+}
+// (w, w) * d + c, componentwise
+__device__ __forceinline__ float2 fma_x2(float w, float2 d, float2 c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pack2(make_float2(w, w))), "l"(pack2(d)), "l"(pack2(c)));
+    return unpack2(r);
+}
+
 // 1/x to within about one unit in the last place (the SFU reciprocal);
 // x >= 1 here.
 __device__ __forceinline__ float rcp_approx(float x)
@@ -348,7 +378,7 @@ __device__ __forceinline__ void
             const int64_t eb = window_start<D16>(s0);
             const int off = (int)(s0 - eb);  // leading slots that belong to the previous row
             const int64_t len = e0 - eb;     // slots from len on belong to the next rows
-            float ax = 0.f, ay = 0.f;
+            float2 acc = make_float2(0.f, 0.f);
             float2 yj[4][4];
             float pv[4][4];
 #pragma unroll
@@ -388,29 +418,27 @@ __device__ __forceinline__ void
             for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float dx = xi - yj[u][q].x, dy = yv - yj[u][q].y;
-                    const float w = pv[u][q] * rcp_approx(__fmaf_rn(dy, dy, __fmaf_rn(dx, dx, 1.0f)));
-                    ax = __fmaf_rn(w, dx, ax);
-                    ay = __fmaf_rn(w, dy, ay);
+                    const float2 d = sub_x2(make_float2(xi, yv), yj[u][q]);
+                    const float w = pv[u][q] * rcp_approx(__fmaf_rn(d.y, d.y, __fmaf_rn(d.x, d.x, 1.0f)));
+                    acc = fma_x2(w, d, acc);
                 }
             for (int64_t e = eb + kWin + gl; e < e0; e += kRowLanes) {
                 const int ce = D16 ? rowi + (int)__ldg(P_d16 + e) : __ldg(P_col + e);
                 const unsigned c = min((unsigned)ce, (unsigned)(n - 1));
-                const float2 q = __ldg(Y + c);
-                const float dx = xi - q.x, dy = yv - q.y;
-                const float w = __ldg(P_val + e) * rcp_approx(__fmaf_rn(dy, dy, __fmaf_rn(dx, dx, 1.0f)));
-                ax = __fmaf_rn(w, dx, ax);
-                ay = __fmaf_rn(w, dy, ay);
+                const float2 d = sub_x2(make_float2(xi, yv), __ldg(Y + c));
+                const float w = __ldg(P_val + e) * rcp_approx(__fmaf_rn(d.y, d.y, __fmaf_rn(d.x, d.x, 1.0f)));
+                acc = fma_x2(w, d, acc);
             }
             if (heavy) {
                 const int b = hbase[rowi];
                 const int nc = (int)((e0r - s0 + kChunk - 1) / kChunk);
                 for (int c = gl; c < nc; c += kRowLanes) {
                     const float2 q = hpartial[b + c];
-                    ax += q.x;
-                    ay += q.y;
+                    acc.x += q.x;
+                    acc.y += q.y;
                 }
             }
+            float ax = acc.x, ay = acc.y;
 #pragma unroll
             for (int o = kRowLanes / 2; o > 0; o >>= 1) {
                 ax += __shfl_xor_sync(gmask, ax, o);
