@@ -502,6 +502,7 @@ constexpr size_t kFusedSmem = 0;  // the windows live in registers
 
 // Attraction sums of the chunks of the long rows: one warp per chunk of
 // kChunk entries of one row, lanes striding over the entries.
+constexpr int kChunkBatch = 8;
 template <bool D16>
 __device__ __forceinline__ void k_attr_chunks_body(const int64_t* __restrict__ P_row,
                                                    const int32_t* __restrict__ P_col,
@@ -517,17 +518,30 @@ __device__ __forceinline__ void k_attr_chunks_body(const int64_t* __restrict__ P
         const int32_t row = crow[c];
         const int64_t a = P_row[row] + cstart[c], b = min(a + kChunk, P_row[row + 1]);
         const float2 yi = Y[row];
-        float ax = 0.f, ay = 0.f;
-        for (int64_t e = a + lane; e < b; e += 32) {
-            const int ce = D16 ? row + (int)P_d16[e] : P_col[e];
-            const float2 q = __ldg(Y + min((unsigned)ce, (unsigned)(n - 1)));
-            const float dx = yi.x - q.x, dy = yi.y - q.y;
-            const float w = __ldg(P_val + e) * rcp_approx(__fmaf_rn(dy, dy, __fmaf_rn(dx, dx, 1.0f)));
-            ax = __fmaf_rn(w, dx, ax);
-            ay = __fmaf_rn(w, dy, ay);
+        float2 acc = make_float2(0.f, 0.f);
+        // kChunkBatch entries per lane at a time: the column and value loads,
+        // then the gathers, all issued before any is used
+        for (int64_t e0 = a + lane; e0 < b; e0 += 32 * kChunkBatch) {
+            int cc[kChunkBatch];
+            float pv[kChunkBatch];
+#pragma unroll
+            for (int t = 0; t < kChunkBatch; ++t) {
+                const int64_t e = e0 + 32 * t;
+                const bool ok = e < b;
+                cc[t] = ok ? (D16 ? row + (int)P_d16[e] : P_col[e]) : row;
+                pv[t] = ok ? __ldg(P_val + e) : 0.f;
+            }
+            float2 q[kChunkBatch];
+#pragma unroll
+            for (int t = 0; t < kChunkBatch; ++t) q[t] = __ldg(Y + min((unsigned)cc[t], (unsigned)(n - 1)));
+#pragma unroll
+            for (int t = 0; t < kChunkBatch; ++t) {
+                const float2 d = sub_x2(yi, q[t]);
+                const float w = pv[t] * rcp_approx(__fmaf_rn(d.y, d.y, __fmaf_rn(d.x, d.x, 1.0f)));
+                acc = fma_x2(w, d, acc);
+            }
         }
-        ax = warp_sum(ax);
-        ay = warp_sum(ay);
+        const float ax = warp_sum(acc.x), ay = warp_sum(acc.y);
         if (lane == 0) partial[c] = make_float2(ax, ay);
     }
 }
