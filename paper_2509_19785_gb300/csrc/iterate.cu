@@ -4,8 +4,8 @@
 //   Attraction (Eq. 6, first term): the warp walks the 32 rows of P four at a
 //   time, 8 lanes per row, each lane reading 4 entries (value, column) per
 //   vector load from the packed layout built by k_pack_rows (or from CSR
-//   with int32 columns), and the row sum is reduced across the 8 lanes and
-//   handed to the row's lane.
+//   with int32 columns); the lanes' partial sums go to shared memory and
+//   each row's lane adds its row's 8 partials.
 //   Then every lane, for its own vertex: gathers the interpolated repulsion
 //   sum R_i (Sec. 2.3) and entropy sum E_i (Eq. 8, repulsive reading) from
 //   the P x P nodes of its box, adds the compression (lambda_c/n) X_i
@@ -342,7 +342,8 @@ __device__ __forceinline__ void
 {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int grp = lane >> 3, gl = lane & 7;
-    const unsigned gmask = 0xffu << (grp * 8);
+    __shared__ float2 part_all[kFusedWarps][256];
+    float2* part = part_all[wib];
     const Coeffs k = coeffs(G, st);
     const int64_t nnz = P_row[n];
     float mn = INFINITY, mx = -INFINITY;
@@ -353,10 +354,14 @@ __device__ __forceinline__ void
         const float2 yi = has ? Y[row] : make_float2(0.f, 0.f);
         const int64_t rs = has ? P_row[row] : 0;
         const int64_t re = has ? P_row[row + 1] : 0;
+        // row bounds as 32-bit offsets from the group's first row (the
+        // arrays have fewer than 2^32 entries): one shuffle each
+        const int64_t base = __shfl_sync(FULL, rs, 0);
+        const uint32_t rs32 = has ? (uint32_t)(rs - base) : 0u, re32 = has ? (uint32_t)(re - base) : 0u;
         float2 A = make_float2(0.f, 0.f);
         Window nxt;
         // bounds of the next round's row, shuffled once and kept for its round
-        int64_t ns0 = __shfl_sync(FULL, rs, grp), ne0 = __shfl_sync(FULL, re, grp);
+        int64_t ns0 = base + __shfl_sync(FULL, rs32, grp), ne0 = base + __shfl_sync(FULL, re32, grp);
         load_window<D16>(nxt, P_col, P_d16, P_val, nnz, window_start<D16>(ns0), window_end(hbase, ns0, ne0),
                          (int)(g0 + grp), gl);
 #pragma unroll 1
@@ -367,8 +372,8 @@ __device__ __forceinline__ void
             const int64_t s0 = ns0, e0r = ne0;
             if (rr < 7) {
                 const int nsrc = src + 4;
-                ns0 = __shfl_sync(FULL, rs, nsrc);
-                ne0 = __shfl_sync(FULL, re, nsrc);
+                ns0 = base + __shfl_sync(FULL, rs32, nsrc);
+                ne0 = base + __shfl_sync(FULL, re32, nsrc);
                 load_window<D16>(nxt, P_col, P_d16, P_val, nnz, window_start<D16>(ns0), window_end(hbase, ns0, ne0),
                                  rowi + 4, gl);
             }
@@ -438,16 +443,24 @@ __device__ __forceinline__ void
                     acc.y += q.y;
                 }
             }
-            float ax = acc.x, ay = acc.y;
-#pragma unroll
-            for (int o = kRowLanes / 2; o > 0; o >>= 1) {
-                ax += __shfl_xor_sync(gmask, ax, o);
-                ay += __shfl_xor_sync(gmask, ay, o);
-            }
-            const float sx = __shfl_sync(FULL, ax, (lane & 3) * 8);
-            const float sy = __shfl_sync(FULL, ay, (lane & 3) * 8);
-            if ((lane >> 2) == rr) A = make_float2(sx, sy);
+            // lane (group g, gl) of round rr holds a partial sum of row
+            // rr * 4 + g: kept at slot row * 8 + gl = rr * 32 + lane
+            part[rr * 32 + lane] = acc;
         }
+        __syncwarp();
+        {
+            // row `lane` adds its 8 partials, starting at a slot that
+            // depends on the row so that the lanes spread over the banks
+            float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < kRowLanes; ++k) {
+                const float2 q = part[lane * 8 + ((k + lane) & 7)];
+                t.x += q.x;
+                t.y += q.y;
+            }
+            A = t;
+        }
+        __syncwarp();
         if (has) {
             const Sums F = gather_sums<P>(yi, G, fields);
             const PointOut o = point_gradient(yi, A, F, k);
