@@ -187,6 +187,7 @@ constexpr int kWin = 128;        // CSR entries of a row taken per round (longer
 constexpr int kFusedWarps = kFusedThreads / 32;
 constexpr int kHeavyRow = 2048;  // longer rows of P are summed in chunks by k_attr_chunks
 constexpr int kChunk = 2048;     // entries per chunk
+constexpr int kTailBatch = 8;    // entries per lane in flight past a row's window
 
 // Rows of P longer than kHeavyRow (hubs of scale-free graphs can sit in a
 // large part of all neighbour lists): their attraction sums are computed in
@@ -427,12 +428,27 @@ __device__ __forceinline__ void
                     const float w = pv[u][q] * rcp_approx(__fmaf_rn(d.y, d.y, __fmaf_rn(d.x, d.x, 1.0f)));
                     acc = fma_x2(w, d, acc);
                 }
-            for (int64_t e = eb + kWin + gl; e < e0; e += kRowLanes) {
-                const int ce = D16 ? rowi + (int)__ldg(P_d16 + e) : __ldg(P_col + e);
-                const unsigned c = min((unsigned)ce, (unsigned)(n - 1));
-                const float2 d = sub_x2(make_float2(xi, yv), __ldg(Y + c));
-                const float w = __ldg(P_val + e) * rcp_approx(__fmaf_rn(d.y, d.y, __fmaf_rn(d.x, d.x, 1.0f)));
-                acc = fma_x2(w, d, acc);
+            // entries past the window: kTailBatch per lane at a time, all
+            // loads, then all gathers, issued before any is used
+            for (int64_t eb2 = eb + kWin + gl; eb2 < e0; eb2 += kRowLanes * kTailBatch) {
+                int tc[kTailBatch];
+                float tv[kTailBatch];
+#pragma unroll
+                for (int t = 0; t < kTailBatch; ++t) {
+                    const int64_t e = eb2 + kRowLanes * t;
+                    const bool ok = e < e0;
+                    tc[t] = ok ? (D16 ? rowi + (int)__ldg(P_d16 + e) : __ldg(P_col + e)) : rowi;
+                    tv[t] = ok ? __ldg(P_val + e) : 0.f;
+                }
+                float2 tq[kTailBatch];
+#pragma unroll
+                for (int t = 0; t < kTailBatch; ++t) tq[t] = __ldg(Y + min((unsigned)tc[t], (unsigned)(n - 1)));
+#pragma unroll
+                for (int t = 0; t < kTailBatch; ++t) {
+                    const float2 d = sub_x2(make_float2(xi, yv), tq[t]);
+                    const float w = tv[t] * rcp_approx(__fmaf_rn(d.y, d.y, __fmaf_rn(d.x, d.x, 1.0f)));
+                    acc = fma_x2(w, d, acc);
+                }
             }
             if (heavy) {
                 const int b = hbase[rowi];
@@ -449,12 +465,13 @@ __device__ __forceinline__ void
         }
         __syncwarp();
         {
-            // row `lane` adds its 8 partials, starting at a slot that
-            // depends on the row so that the lanes spread over the banks
+            // row `lane` adds its 8 partials, starting at slot lane / 2 of
+            // its row: the 32 lanes of one step then hit 16 distinct pairs of
+            // banks (two lanes each, two wavefronts)
             float2 t = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < kRowLanes; ++k) {
-                const float2 q = part[lane * 8 + ((k + lane) & 7)];
+                const float2 q = part[lane * 8 + ((k + (lane >> 1)) & 7)];
                 t.x += q.x;
                 t.y += q.y;
             }
