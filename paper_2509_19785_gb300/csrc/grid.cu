@@ -862,76 +862,96 @@ __device__ __forceinline__ void k_box_spread_body(const float2* __restrict__ su,
     }
     const int lane = threadIdx.x & 31;
     const int nw = (int)(gridDim.x * blockDim.x) >> 5;
-    for (int it = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); it < nit; it += nw) {
-        const int2 item = items[it];
-        const int hb = item.x;
-        const int box = heavy[hb];
-        const int cnt = bcnt[box];
-        const int nseg = (cnt + kSeg - 1) / kSeg;
-        const int start = bpre[box / kScanBlock] + bcur[box] - cnt;
-        const int q0 = start + item.y * kSeg, q1 = min(start + cnt, q0 + kSeg);
-        const int by = box / I, bx = box - by * I;
-        // the segment's points, all loads issued before any is used
-        float2 pts[kSeg / 32];
-#pragma unroll
-        for (int k = 0; k < kSeg / 32; ++k) {
-            const int q = q0 + lane + 32 * k;
-            pts[k] = q < q1 ? su[q] : make_float2(0.f, 0.f);
-        }
-        const unsigned m = (unsigned)max(0, min(kSeg / 32, (q1 - q0 - lane + 31) / 32));  // points of this lane
-        long long* acc = hacc + (int64_t)hb * P * P * 4;
-        for (int bb = 0; bb < P; ++bb) {
-            unsigned ra[P][4];  // sums modulo 2^32; the true sums are below 2^31
-#pragma unroll
-            for (int a = 0; a < P; ++a)
-#pragma unroll
-                for (int ch = 0; ch < 4; ++ch) ra[a][ch] = 0u;
-#pragma unroll
-            for (int k = 0; k < kSeg / 32; ++k)
-                if ((unsigned)k < m) add_point_row_q<P>(pts[k], bb, hf, ra);
-            const unsigned bias = m * kMagicBits;
-            // value a * 4 + ch of the row, padded with zeros to NV values
-            constexpr int NV = P * 4 <= 16 ? 16 : 32;
-            unsigned vals[NV];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) vals[v] = v < P * 4 ? ra[v >> 2][v & 3] - bias : 0u;
-            const unsigned tot = warp_reduce_scatter<NV>(vals, lane);
-            const int vi = NV == 32 ? lane : lane >> 1;  // the value this lane now holds the total of
-            if (nseg == 1) {
-                // node a = lane < P gathers its four moments from their lanes
-                const int a = min(lane, P - 1);
-                unsigned c[4];
-#pragma unroll
-                for (int ch = 0; ch < 4; ++ch)
-                    c[ch] = __shfl_sync(FULL, tot, NV == 32 ? 4 * a + ch : 2 * (4 * a + ch));
-                if (lane < P)
-                    wflt[(int64_t)(by * P + bb) * M + (int64_t)bx * P + lane] =
-                        make_float4((float)(int)c[0] * ihf[0], (float)(int)c[1] * ihf[1], (float)(int)c[2] * ihf[2],
-                                    (float)(int)c[3] * ihf[3]);
-            } else if ((NV == 32 || (lane & 1) == 0) && vi < P * 4 && tot != 0u) {
-                atomicAdd((unsigned long long*)(acc + bb * P * 4 + vi), (unsigned long long)(long long)(int)tot);
+    const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    for (int base = wid; base < nit; base += nw * 32) {
+        // The warp's items are base, base + nw, ...: lane j fetches the box,
+        // count and first point of the j-th, so that the chain of dependent
+        // loads (item, heavy box, count and offsets) is paid once per 32
+        // items; the items are then summed one after the other as before.
+        int m_hb = 0, m_seg = 0, m_box = 0, m_cnt = 0, m_start = 0;
+        {
+            const int itj = base + lane * nw;
+            if (itj < nit) {
+                const int2 item = items[itj];
+                m_hb = item.x;
+                m_seg = item.y;
+                m_box = heavy[m_hb];
+                m_cnt = bcnt[m_box];
+                m_start = bpre[m_box / kScanBlock] + bcur[m_box] - m_cnt;
             }
         }
-        if (nseg == 1) continue;
-        __threadfence();
-        int last = 0;
-        if (lane == 0) last = atomicAdd(&hticket[hb], 1) == nseg - 1;
-        last = __shfl_sync(FULL, last, 0);
-        if (!last) continue;
-        __threadfence();
-        if (lane < P * P) {
-            const int nb = lane / P, a = lane - nb * P;
-            long long* q = acc + lane * 4;
-            const long long c0 = __ldcg(q + 0), c1 = __ldcg(q + 1), c2 = __ldcg(q + 2), c3 = __ldcg(q + 3);
-            wflt[(int64_t)(by * P + nb) * M + (int64_t)bx * P + a] =
-                make_float4(fix_to_float(c0, ihf[0]), fix_to_float(c1, ihf[1]), fix_to_float(c2, ihf[2]),
-                            fix_to_float(c3, ihf[3]));
-            q[0] = 0;
-            q[1] = 0;
-            q[2] = 0;
-            q[3] = 0;
+        const int nj = min(32, (nit - base + nw - 1) / nw);
+        for (int j = 0; j < nj; ++j) {
+            const int hb = __shfl_sync(FULL, m_hb, j);
+            const int box = __shfl_sync(FULL, m_box, j);
+            const int cnt = __shfl_sync(FULL, m_cnt, j);
+            const int start = __shfl_sync(FULL, m_start, j);
+            const int seg = __shfl_sync(FULL, m_seg, j);
+            const int nseg = (cnt + kSeg - 1) / kSeg;
+            const int q0 = start + seg * kSeg, q1 = min(start + cnt, q0 + kSeg);
+            const int by = box / I, bx = box - by * I;
+            // the segment's points, all loads issued before any is used
+            float2 pts[kSeg / 32];
+#pragma unroll
+            for (int k = 0; k < kSeg / 32; ++k) {
+                const int q = q0 + lane + 32 * k;
+                pts[k] = q < q1 ? su[q] : make_float2(0.f, 0.f);
+            }
+            const unsigned m = (unsigned)max(0, min(kSeg / 32, (q1 - q0 - lane + 31) / 32));  // points of this lane
+            long long* acc = hacc + (int64_t)hb * P * P * 4;
+            for (int bb = 0; bb < P; ++bb) {
+                unsigned ra[P][4];  // sums modulo 2^32; the true sums are below 2^31
+#pragma unroll
+                for (int a = 0; a < P; ++a)
+#pragma unroll
+                    for (int ch = 0; ch < 4; ++ch) ra[a][ch] = 0u;
+#pragma unroll
+                for (int k = 0; k < kSeg / 32; ++k)
+                    if ((unsigned)k < m) add_point_row_q<P>(pts[k], bb, hf, ra);
+                const unsigned bias = m * kMagicBits;
+                // value a * 4 + ch of the row, padded with zeros to NV values
+                constexpr int NV = P * 4 <= 16 ? 16 : 32;
+                unsigned vals[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) vals[v] = v < P * 4 ? ra[v >> 2][v & 3] - bias : 0u;
+                const unsigned tot = warp_reduce_scatter<NV>(vals, lane);
+                const int vi = NV == 32 ? lane : lane >> 1;  // the value this lane now holds the total of
+                if (nseg == 1) {
+                    // node a = lane < P gathers its four moments from their lanes
+                    const int a = min(lane, P - 1);
+                    unsigned c[4];
+#pragma unroll
+                    for (int ch = 0; ch < 4; ++ch)
+                        c[ch] = __shfl_sync(FULL, tot, NV == 32 ? 4 * a + ch : 2 * (4 * a + ch));
+                    if (lane < P)
+                        wflt[(int64_t)(by * P + bb) * M + (int64_t)bx * P + lane] =
+                            make_float4((float)(int)c[0] * ihf[0], (float)(int)c[1] * ihf[1], (float)(int)c[2] * ihf[2],
+                                        (float)(int)c[3] * ihf[3]);
+                } else if ((NV == 32 || (lane & 1) == 0) && vi < P * 4 && tot != 0u) {
+                    atomicAdd((unsigned long long*)(acc + bb * P * 4 + vi), (unsigned long long)(long long)(int)tot);
+                }
+            }
+            if (nseg == 1) continue;
+            __threadfence();
+            int last = 0;
+            if (lane == 0) last = atomicAdd(&hticket[hb], 1) == nseg - 1;
+            last = __shfl_sync(FULL, last, 0);
+            if (!last) continue;
+            __threadfence();
+            if (lane < P * P) {
+                const int nb = lane / P, a = lane - nb * P;
+                long long* q = acc + lane * 4;
+                const long long c0 = __ldcg(q + 0), c1 = __ldcg(q + 1), c2 = __ldcg(q + 2), c3 = __ldcg(q + 3);
+                wflt[(int64_t)(by * P + nb) * M + (int64_t)bx * P + a] =
+                    make_float4(fix_to_float(c0, ihf[0]), fix_to_float(c1, ihf[1]), fix_to_float(c2, ihf[2]),
+                                fix_to_float(c3, ihf[3]));
+                q[0] = 0;
+                q[1] = 0;
+                q[2] = 0;
+                q[3] = 0;
+            }
+            if (lane == 0) hticket[hb] = 0;
         }
-        if (lane == 0) hticket[hb] = 0;
     }
 
     float fx[4], ifx[4];

@@ -623,6 +623,42 @@ def test_run_step_ba_ball_long_rows_match_oracle(ltlib, ba_ball):
     assert err < 1e-5, err
 
 
+def test_run_step_far_columns_match_oracle(ltlib):
+    """ltsnet_run on a graph whose columns of P lie further than the int16
+    range from their rows even after the breadth-first renumbering (a star
+    with 40,000 leaves: the centre and the leaves every leaf lists have rows
+    of about 40,000 entries), so P is streamed as CSR with int32 columns and
+    the long rows are summed in chunks; one step agrees with the oracle's
+    gradient and update."""
+    import torch
+
+    leaves = 40_000
+    g = synth.csr_from_edges(leaves + 1, np.zeros(leaves, np.int64), np.arange(1, leaves + 1, dtype=np.int64),
+                             "star40000")
+    aff = ltlib.affinities(g.row_ptr, g.col, 30.0)
+    Pn = tuple(t.cpu().numpy() for t in aff["P"])
+    _, inv, reordered = ltlib.bfs_order(g.row_ptr, g.col)
+    invn = inv.cpu().numpy().astype(np.int64) if reordered else np.arange(g.n, dtype=np.int64)
+    rows = np.repeat(np.arange(g.n), np.diff(Pn[0]))
+    assert np.abs(invn[Pn[1].astype(np.int64)] - invn[rows]).max() > 32767  # int32 columns
+    assert np.diff(Pn[0]).max() > 2048  # long rows present
+    Y0 = (np.random.default_rng(17).standard_normal((g.n, 2)) * 8).astype(np.float32)
+    params = ltlib.Params(perplexity=30.0, stages=[ltlib.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)])
+    Y1, _ = ltlib.run(g.row_ptr, g.col, torch.from_numpy(Y0), params)
+    step = Y1.cpu().numpy().astype(np.float64) - Y0
+    st = oracle.Stage(1, 1.0, 0.01, 0.6, 1.0, 0.8)
+    gref, pr = oracle.interp_gradient(Y0, Pn[0], Pn[1], Pn[2].astype(np.float64), st, oracle.GridParams())
+    lr = oracle.auto_learning_rate(g.n)
+    Yr, _, _ = oracle.update(Y0.astype(np.float64), np.zeros_like(gref), np.ones_like(gref), gref, st.momentum, lr)
+    n = g.n
+    scale = (np.linalg.norm(4 * st.lambda_kl * st.exaggeration * pr["A"])
+             + np.linalg.norm(4 * st.lambda_kl * pr["S"] / pr["Z"] * pr["R"])
+             + np.linalg.norm(st.lambda_c / n * Y0.astype(np.float64))
+             + np.linalg.norm(st.lambda_r / n ** 2 * pr["E"]))
+    err = float(np.linalg.norm(step - (Yr - Y0)) / (lr * 1.2 * scale))
+    assert err < 1e-5, err
+
+
 def test_rgg1m_ball20k_parity_both_forms_and_exact(ltlib, capsys):
     """The benchmark graph's 20,000-vertex BFS ball (cfg 3's error on a
     20k-vertex subsample), at iteration 300 of the oracle's own run on it:
