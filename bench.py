@@ -497,7 +497,7 @@ def bench_ltsnet(args):
         ba_bytes = 8 * nnz_ba + 8 * (gba.n + 1) + 48 * gba.n
         # the format ltsnet_run streams P in on this graph (as for rgg1m above)
         _, inv_ba, reo_ba = lt.bfs_order(rp_ba, cl_ba)
-        ba_fmt = "int32 columns (CSR)"
+        ba_fmt = "packed rows, int32 columns"
         if reo_ba:
             invb = inv_ba.cpu().numpy().astype(np.int64)
             rows_b = np.repeat(np.arange(gba.n), np.diff(P_ba[0].cpu().numpy()))

@@ -202,6 +202,28 @@ struct HeavyRows {
     int32_t nchunks = 0;
 };
 
+// P as the point phase streams it: row pointers, int32 columns (CSR or the
+// int32 packed layout) or int16 offsets (the int16 packed layout), values,
+// the format (kFmt* below) and the long rows' chunk lists.
+struct PStream {
+    const int64_t* row = nullptr;
+    const int32_t* col = nullptr;
+    const int16_t* d16 = nullptr;
+    const float* val = nullptr;
+    int fmt = 0;
+    HeavyRows hr;
+};
+
+// A caller's P: CSR with int32 columns, no chunk lists.
+PStream csr_stream(const int64_t* P_row, const int32_t* P_col, const float* P_val)
+{
+    PStream sp;
+    sp.row = P_row;
+    sp.col = P_col;
+    sp.val = P_val;
+    return sp;
+}
+
 // Paired FP32 arithmetic (sm_100 family): each half is the IEEE
 // round-to-nearest result of the scalar operation, so these give the same
 // bits as two scalar instructions in one issue.
@@ -252,26 +274,22 @@ struct Window {
     float4 v[4];    // P values
 };
 
-template <bool D16>
-__device__ __forceinline__ void window_cols(const Window& w, int u, int rowi, int* cc)
+// Formats P is streamed in by the point phase: CSR with int32 columns (a
+// caller's P), or the packed layout of k_pack_rows with int16 column offsets
+// from the row or with int32 columns.
+constexpr int kFmtCsr = 0;
+constexpr int kFmtPk16 = 1;
+constexpr int kFmtPk32 = 2;
+
+// int32 columns of chunk u of a window (CSR form)
+__device__ __forceinline__ void window_cols(const Window& w, int u, int* cc)
 {
-    if (D16) {
-        const unsigned x = (unsigned)w.c[u].x, y = (unsigned)w.c[u].y;
-        cc[0] = rowi + (int)(int16_t)(x & 0xffffu);
-        cc[1] = rowi + (int)(int16_t)(x >> 16);
-        cc[2] = rowi + (int)(int16_t)(y & 0xffffu);
-        cc[3] = rowi + (int)(int16_t)(y >> 16);
-    } else {
-        cc[0] = w.c[u].x;
-        cc[1] = w.c[u].y;
-        cc[2] = w.c[u].z;
-        cc[3] = w.c[u].w;
-    }
+    cc[0] = w.c[u].x;
+    cc[1] = w.c[u].y;
+    cc[2] = w.c[u].z;
+    cc[3] = w.c[u].w;
 }
 
-// Window start: the row start, which the packed layout keeps a multiple of
-// 4 entries; for int32 columns the row start rounded down to a multiple of 4
-// so that every vector load is aligned.
 // Window end: the row's end, or its start for a long row (summed in chunks
 // beforehand), so that the window holds no entry of it.
 __device__ __forceinline__ int64_t window_end(const int32_t* hbase, int64_t s0, int64_t e0)
@@ -279,21 +297,25 @@ __device__ __forceinline__ int64_t window_end(const int32_t* hbase, int64_t s0, 
     return hbase != nullptr && e0 - s0 > kHeavyRow ? s0 : e0;
 }
 
-template <bool D16>
+// Window start: the row start, which the packed layouts keep a multiple of 4
+// entries; for CSR the row start rounded down to a multiple of 4 so that
+// every vector load is aligned.
+template <int FMT>
 __device__ __forceinline__ int64_t window_start(int64_t s0)
 {
-    return D16 ? s0 : (s0 & ~(int64_t)3);
+    return FMT != kFmtCsr ? s0 : (s0 & ~(int64_t)3);
 }
 
 // Load the lane's slots j = 32 u + 4 gl + q (u, q < 4) of the window starting
 // at eb: vector loads that bypass L1 (the stream is read once), scalar
 // loads where a vector would pass the end of the arrays (nnz), nothing past
 // the row's end e0.
-template <bool D16>
+template <int FMT>
 __device__ __forceinline__ void load_window(Window& w, const int32_t* __restrict__ P_col,
                                             const int16_t* __restrict__ P_d16, const float* __restrict__ P_val,
                                             int64_t nnz, int64_t eb, int64_t e0, int rowi, int gl)
 {
+    constexpr bool D16 = FMT == kFmtPk16;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int64_t e = eb + 32 * u + 4 * gl;
@@ -332,7 +354,7 @@ __device__ __forceinline__ void load_window(Window& w, const int32_t* __restrict
 // than it) are read directly.  Row r's sum goes to lane r, which then
 // finishes its vertex: interpolated repulsion and entropy (gather from the
 // grid), compression, gradient, momentum/gain step, bounds of the next grid.
-template <int P, bool UPDATE, bool D16>
+template <int P, bool UPDATE, int FMT>
 __device__ __forceinline__ void
     k_fused_body(const int64_t* __restrict__ P_row, const int32_t* __restrict__ P_col, const int16_t* __restrict__ P_d16,
             const float* __restrict__ P_val,
@@ -363,7 +385,7 @@ __device__ __forceinline__ void
         Window nxt;
         // bounds of the next round's row, shuffled once and kept for its round
         int64_t ns0 = base + __shfl_sync(FULL, rs32, grp), ne0 = base + __shfl_sync(FULL, re32, grp);
-        load_window<D16>(nxt, P_col, P_d16, P_val, nnz, window_start<D16>(ns0), window_end(hbase, ns0, ne0),
+        load_window<FMT>(nxt, P_col, P_d16, P_val, nnz, window_start<FMT>(ns0), window_end(hbase, ns0, ne0),
                          (int)(g0 + grp), gl);
 #pragma unroll 1
         for (int rr = 0; rr < 8; ++rr) {
@@ -375,13 +397,13 @@ __device__ __forceinline__ void
                 const int nsrc = src + 4;
                 ns0 = base + __shfl_sync(FULL, rs32, nsrc);
                 ne0 = base + __shfl_sync(FULL, re32, nsrc);
-                load_window<D16>(nxt, P_col, P_d16, P_val, nnz, window_start<D16>(ns0), window_end(hbase, ns0, ne0),
+                load_window<FMT>(nxt, P_col, P_d16, P_val, nnz, window_start<FMT>(ns0), window_end(hbase, ns0, ne0),
                                  rowi + 4, gl);
             }
             const float xi = __shfl_sync(FULL, yi.x, src), yv = __shfl_sync(FULL, yi.y, src);
             const bool heavy = hbase != nullptr && e0r - s0 > kHeavyRow;  // summed in chunks already
             const int64_t e0 = heavy ? s0 : e0r;
-            const int64_t eb = window_start<D16>(s0);
+            const int64_t eb = window_start<FMT>(s0);
             const int off = (int)(s0 - eb);  // leading slots that belong to the previous row
             const int64_t len = e0 - eb;     // slots from len on belong to the next rows
             float2 acc = make_float2(0.f, 0.f);
@@ -391,7 +413,7 @@ __device__ __forceinline__ void
             for (int u = 0; u < 4; ++u) {
                 const int j = 32 * u + 4 * gl;
                 const float vv[4] = {cur.v[u].x, cur.v[u].y, cur.v[u].z, cur.v[u].w};
-                if (D16) {
+                if (FMT == kFmtPk16) {
                     // Packed rows: every slot gathers.  Slots past the row's
                     // window (past its end, or a long row's) were loaded as
                     // offset 0 and weight 0, like the pads of a packed row,
@@ -407,8 +429,19 @@ __device__ __forceinline__ void
                     }
                     continue;
                 }
+                if (FMT == kFmtPk32) {
+                    // packed rows with int32 columns: as above, slots past
+                    // the window hold the row itself with weight 0
+                    const int cq[4] = {cur.c[u].x, cur.c[u].y, cur.c[u].z, cur.c[u].w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        yj[u][q] = __ldg(Y + cq[q]);
+                        pv[u][q] = vv[q];
+                    }
+                    continue;
+                }
                 int cc[4];
-                window_cols<D16>(cur, u, rowi, cc);
+                window_cols(cur, u, cc);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     // Slots of other rows get weight 0 and no gather (the
@@ -437,7 +470,7 @@ __device__ __forceinline__ void
                 for (int t = 0; t < kTailBatch; ++t) {
                     const int64_t e = eb2 + kRowLanes * t;
                     const bool ok = e < e0;
-                    tc[t] = ok ? (D16 ? rowi + (int)__ldg(P_d16 + e) : __ldg(P_col + e)) : rowi;
+                    tc[t] = ok ? (FMT == kFmtPk16 ? rowi + (int)__ldg(P_d16 + e) : __ldg(P_col + e)) : rowi;
                     tv[t] = ok ? __ldg(P_val + e) : 0.f;
                 }
                 float2 tq[kTailBatch];
@@ -503,7 +536,7 @@ __device__ __forceinline__ void
     if (UPDATE) block_bounds(mn, mx, bounds_next);
 }
 
-template <int P, bool UPDATE, bool D16>
+template <int P, bool UPDATE, int FMT>
 __global__ void __launch_bounds__(kFusedThreads, 2)
     k_fused(const int64_t* __restrict__ P_row, const int32_t* __restrict__ P_col, const int16_t* __restrict__ P_d16,
             const float* __restrict__ P_val,
@@ -512,19 +545,19 @@ __global__ void __launch_bounds__(kFusedThreads, 2)
             int32_t* __restrict__ bounds_next, float2* __restrict__ grad_out, float* __restrict__ parts,
             StatusBlock* status, const int32_t* __restrict__ hbase, const float2* __restrict__ hpartial)
 {
-    k_fused_body<P, UPDATE, D16>(P_row, P_col, P_d16, P_val, n, Y, Ynew, upd, gains, G, fields, st, bounds_next,
+    k_fused_body<P, UPDATE, FMT>(P_row, P_col, P_d16, P_val, n, Y, Ynew, upd, gains, G, fields, st, bounds_next,
                                  grad_out, parts, status, hbase, hpartial);
 }
 
 // The fused point phase of one iteration for every graph of a batch (graph =
 // blockIdx.y), layouts by parity as in one_iteration.
-template <int P, bool D16>
+template <int P, int FMT>
 __global__ void __launch_bounds__(kFusedThreads, 2) k_fused_b(const BatchGraph* __restrict__ bg, int parity)
 {
     const BatchGraph& b = bg[blockIdx.y];
     const float2* cur = parity ? b.w.yalt : b.Y;
     float2* nxt = parity ? b.Y : b.w.yalt;
-    k_fused_body<P, true, D16>(b.P_row, b.P_col, b.P_d16, b.P_val, b.n, cur, nxt, b.upd, b.gains, b.w.g, b.w.fields,
+    k_fused_body<P, true, FMT>(b.P_row, b.P_col, b.P_d16, b.P_val, b.n, cur, nxt, b.upd, b.gains, b.w.g, b.w.fields,
                                b.st, b.w.bounds + 2 * (parity ^ 1), nullptr, nullptr, b.w.st, b.hbase, b.hpartial);
 }
 
@@ -651,9 +684,13 @@ __global__ void k_pad_rows(const int64_t* __restrict__ P_row, int32_t n, const u
     }
 }
 
+// C32: int32 columns (pads: the row itself, weight 0); `far` is set only
+// for a column outside [0, n).  Else int16 offsets (pads: offset 0), `far`
+// set also for an offset outside the int16 range or on the diagonal.
+template <bool C32>
 __global__ void k_pack_rows(const int64_t* __restrict__ P_row, const int32_t* __restrict__ P_col,
                             const float* __restrict__ P_val, int32_t n, const int64_t* __restrict__ Q_row,
-                            int16_t* __restrict__ Q_d16, float* __restrict__ Q_val, int32_t* __restrict__ far)
+                            void* __restrict__ Q_col, float* __restrict__ Q_val, int32_t* __restrict__ far)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -665,17 +702,20 @@ __global__ void k_pack_rows(const int64_t* __restrict__ P_row, const int32_t* __
             const int64_t blk = t & ~(int64_t)31;
             const int m = (int)(min(lp - blk, (int64_t)32) >> 2);
             const int r = (int)(t - blk), a = r % m, q = r / m;
-            int16_t d = 0;
+            int32_t c = C32 ? (int32_t)row : 0;
             float v = 0.f;
             if (t < len) {
                 const int32_t col = P_col[p0 + t];
                 const int64_t off = (int64_t)col - row;
-                bad |= off < -32767 || off > 32767 || off == 0 || col < 0 || col >= n;
-                d = (int16_t)off;
+                bad |= col < 0 || col >= n;
+                if (!C32) bad |= off < -32767 || off > 32767 || off == 0;
+                c = C32 ? col : (int32_t)off;
                 v = P_val[p0 + t];
             }
-            Q_d16[q0 + blk + 4 * a + q] = d;
-            Q_val[q0 + blk + 4 * a + q] = v;
+            const int64_t dst = q0 + blk + 4 * a + q;
+            if (C32) ((int32_t*)Q_col)[dst] = c;
+            else ((int16_t*)Q_col)[dst] = (int16_t)c;
+            Q_val[dst] = v;
         }
         if (__any_sync(FULL, bad) && lane == 0) atomicExch(far, 1);
     }
@@ -876,17 +916,21 @@ int flat_blocks(int64_t n, int per_sm = 8)
 }
 
 template <bool UPDATE>
-cudaError_t launch_point_phase(const int64_t* P_row, const int32_t* P_col, const int16_t* P_d16, const float* P_val,
-                               const HeavyRows& hr, int32_t n, const float2* Y, float2* Ynew, float2* upd,
+cudaError_t launch_point_phase(const PStream& sp, int32_t n, const float2* Y, float2* Ynew, float2* upd,
                                float2* gains, const IterWs& w,
                                const IterShape& sh, const Stage& st, int parity, float2* grad, float* parts,
                                bool plain, cudaStream_t s)
 {
+    const int64_t* P_row = sp.row;
+    const int32_t* P_col = sp.col;
+    const int16_t* P_d16 = sp.d16;
+    const float* P_val = sp.val;
+    const HeavyRows& hr = sp.hr;
     int32_t* bn = w.bounds + 2 * (parity ^ 1);
     if (!plain && hr.nchunks > 0) {
         int64_t cb = ((int64_t)hr.nchunks * 32 + 255) / 256;
         if (cb > num_sms() * 8) cb = num_sms() * 8;
-        if (P_d16)
+        if (sp.fmt == kFmtPk16)
             k_attr_chunks<true><<<(unsigned)cb, 256, 0, s>>>(P_row, P_col, P_d16, P_val, n, Y, hr.crow, hr.cstart,
                                                              hr.nchunks, hr.partial);
         else
@@ -897,15 +941,14 @@ cudaError_t launch_point_phase(const int64_t* P_row, const int32_t* P_col, const
     profile_start(LTSNET_KERNEL_FUSED_UPDATE, s);
     if (!plain) {
         const int nb = fused_blocks(n);
-#define LT_FUSED(PP)                                                                                          \
-    if (P_d16)                                                                                                \
-        k_fused<PP, UPDATE, true><<<nb, kFusedThreads, kFusedSmem, s>>>(P_row, P_col, P_d16, P_val, n, Y, Ynew,  \
-                                                                        upd, gains, w.g, w.fields, st, bn, grad, \
-                                                                        parts, w.st, hr.hbase, hr.partial);      \
-    else                                                                                                      \
-        k_fused<PP, UPDATE, false><<<nb, kFusedThreads, kFusedSmem, s>>>(P_row, P_col, P_d16, P_val, n, Y, Ynew, \
-                                                                         upd, gains, w.g, w.fields, st, bn, grad, \
-                                                                         parts, w.st, hr.hbase, hr.partial)
+#define LT_FUSED_F(PP, FF)                                                                                   \
+    k_fused<PP, UPDATE, FF><<<nb, kFusedThreads, kFusedSmem, s>>>(P_row, P_col, P_d16, P_val, n, Y, Ynew, upd,  \
+                                                                  gains, w.g, w.fields, st, bn, grad, parts,   \
+                                                                  w.st, hr.hbase, hr.partial)
+#define LT_FUSED(PP)                                                   \
+    if (sp.fmt == kFmtPk16) LT_FUSED_F(PP, kFmtPk16);                  \
+    else if (sp.fmt == kFmtPk32) LT_FUSED_F(PP, kFmtPk32);             \
+    else LT_FUSED_F(PP, kFmtCsr)
         switch (sh.P) {
             case 2: LT_FUSED(2); break;
             case 3: LT_FUSED(3); break;
@@ -913,6 +956,7 @@ cudaError_t launch_point_phase(const int64_t* P_row, const int32_t* P_col, const
             default: LT_FUSED(5); break;
         }
 #undef LT_FUSED
+#undef LT_FUSED_F
         count_launches(1);
     } else {
         const int nb = flat_blocks(n);
@@ -1031,8 +1075,7 @@ ltsnet_status read_status(StatusBlock* st, cudaStream_t s)
 // The loop over iterations [t0, t0 + niter) on a carved iteration workspace.
 // One iteration i (local index; parity i & 1 picks the layout buffer and
 // the bounds slot): grid phase, then the point phase.
-cudaError_t one_iteration(const int64_t* P_row, const int32_t* P_col, const int16_t* P_d16, const float* P_val,
-                          const HeavyRows& hr, int32_t n,
+cudaError_t one_iteration(const PStream& sp, int32_t n,
                           const ltsnet_params* p, float2* Y, float2* upd, float2* gains, const IterWs& w,
                           const IterShape& sh, const Stage& st, int parity, bool plain, cudaStream_t s)
 {
@@ -1040,8 +1083,7 @@ cudaError_t one_iteration(const int64_t* P_row, const int32_t* P_col, const int1
     float2* nxt = parity ? Y : w.yalt;
     cudaError_t e = launch_grid_phase(w, sh, p, cur, parity, plain, s);
     if (e != cudaSuccess) return e;
-    return launch_point_phase<true>(P_row, P_col, P_d16, P_val, hr, n, cur, nxt, upd, gains, w, sh, st, parity,
-                                    nullptr, nullptr, plain, s);
+    return launch_point_phase<true>(sp, n, cur, nxt, upd, gains, w, sh, st, parity, nullptr, nullptr, plain, s);
 }
 
 bool same_stage(const ltsnet_stage& a, const ltsnet_stage& b)
@@ -1056,17 +1098,15 @@ bool same_stage(const ltsnet_stage& a, const ltsnet_stage& b)
 // graph's launches are counted as their kernels.  While kernels are being
 // timed one by one (ltsnet_profile_begin) every iteration is launched
 // directly.
-// P_d16, when not null, holds P's columns as int16 offsets from their row
-// (the fused kernel then streams 6 bytes per entry instead of 8).
-ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const int16_t* P_d16, const float* P_val,
-                            const HeavyRows& hr, int32_t n,
+// sp is P in the format the point phase streams (CSR or a packed layout).
+ltsnet_status optimize_core(const PStream& sp, int32_t n,
                             const ltsnet_params* p, float2* Y, float2* upd, float2* gains, int32_t t0, int32_t niter,
                             const IterWs& w, const IterShape& sh, cudaStream_t s)
 {
     const bool plain = (p->flags & LTSNET_FLAG_PLAIN) != 0;
     const float lr = learning_rate(p, n);
     LT_CUDA(ensure_attrs());
-    LT_CUDA(launch_psum(w, P_row, n, P_val, s));
+    LT_CUDA(launch_psum(w, sp.row, n, sp.val, s));
     LT_CUDA(launch_bounds_init(w, Y, n, 0, s));
     AuxStreams* aux = nullptr;
     const bool graphs = !profiling_active() && aux_streams(&aux) == cudaSuccess;
@@ -1078,7 +1118,7 @@ ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const in
         const Stage st = make_stage(sg, lr, n);
         int32_t done = 0;
         if ((i & 1) && run > 0) {  // align to an even iteration
-            LT_CUDA(one_iteration(P_row, P_col, P_d16, P_val, hr, n, p, Y, upd, gains, w, sh, st, 1, plain, s));
+            LT_CUDA(one_iteration(sp, n, p, Y, upd, gains, w, sh, st, 1, plain, s));
             done = 1;
         }
         const int32_t pairs = graphs ? (run - done) / 2 : 0;
@@ -1087,9 +1127,9 @@ ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const in
             cudaGraph_t graph = nullptr;
             cudaGraphExec_t exec = nullptr;
             LT_CUDA(cudaStreamBeginCapture(aux->capture, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = one_iteration(P_row, P_col, P_d16, P_val, hr, n, p, Y, upd, gains, w, sh, st, 0, plain, aux->capture);
+            cudaError_t e = one_iteration(sp, n, p, Y, upd, gains, w, sh, st, 0, plain, aux->capture);
             if (e == cudaSuccess)
-                e = one_iteration(P_row, P_col, P_d16, P_val, hr, n, p, Y, upd, gains, w, sh, st, 1, plain, aux->capture);
+                e = one_iteration(sp, n, p, Y, upd, gains, w, sh, st, 1, plain, aux->capture);
             cudaError_t e2 = cudaStreamEndCapture(aux->capture, &graph);
             if (e != cudaSuccess || e2 != cudaSuccess) {
                 if (graph) cudaGraphDestroy(graph);
@@ -1109,7 +1149,7 @@ ltsnet_status optimize_core(const int64_t* P_row, const int32_t* P_col, const in
             done += 2 * pairs;
         }
         for (; done < run; ++done)
-            LT_CUDA(one_iteration(P_row, P_col, P_d16, P_val, hr, n, p, Y, upd, gains, w, sh, st, (i + done) & 1, plain, s));
+            LT_CUDA(one_iteration(sp, n, p, Y, upd, gains, w, sh, st, (i + done) & 1, plain, s));
         i += run;
     }
     if (niter & 1) LT_CUDA(cudaMemcpyAsync(Y, w.yalt, sizeof(float2) * (size_t)n, cudaMemcpyDeviceToDevice, s));
@@ -1124,8 +1164,9 @@ struct RunWs {
     double* beta;
     double* pcond;
     int64_t* Q_row;    // packed layout of P for the point phase (k_pack_rows), in
-    int16_t* Q_d16;    // the symmetrisation's scratch, dead once P is built;
-    float* Q_val;      // null when it does not fit there (tiny graphs)
+    int32_t* Q_col;    // the symmetrisation's scratch, dead once P is built
+    float* Q_val;      // (int16 offsets or int32 columns in Q_col); null when
+                       // it does not fit there (tiny graphs)
     int32_t* far;      // set when some |col - row| exceeds the int16 range
     uint32_t* hnch;    // chunks per long row of P
     uint32_t* hbase;   // first chunk of each long row
@@ -1204,13 +1245,48 @@ RunWs run_carve(Carve& c, int32_t n, int64_t m2, const ltsnet_params* p, bool ho
         const int64_t qcap = 2 * nk + 3 * (int64_t)n;
         Carve q(r.sym, r.sym_bytes);
         r.Q_row = q.take<int64_t>((int64_t)n + 1);
-        r.Q_d16 = q.take<int16_t>(qcap);
+        r.Q_col = q.take<int32_t>(qcap);
         r.Q_val = q.take<float>(qcap);
-        if (!q.ok()) r.Q_row = nullptr, r.Q_d16 = nullptr, r.Q_val = nullptr;
+        if (!q.ok()) r.Q_row = nullptr, r.Q_col = nullptr, r.Q_val = nullptr;
     }
     r.iter_bytes = iter_ws_bytes(n, p);
     r.iter = c.take<char>(r.iter_bytes);
     return r;
+}
+
+// P of a prepared run in the packed layout (Q_row already holds the padded
+// row starts): int16 offsets (c32 false) or int32 columns; *fmt gets the
+// format, or kFmtCsr when a column does not fit it (CSR is streamed then).
+cudaError_t pack_rows(const RunWs& r, int32_t n, bool c32, cudaStream_t s, int* fmt)
+{
+    cudaError_t e = cudaMemsetAsync(r.far, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    if (c32)
+        k_pack_rows<true><<<num_sms() * 8, 256, 0, s>>>(r.P_row, r.P_col, r.P_val, n, r.Q_row, r.Q_col, r.Q_val, r.far);
+    else
+        k_pack_rows<false><<<num_sms() * 8, 256, 0, s>>>(r.P_row, r.P_col, r.P_val, n, r.Q_row, r.Q_col, r.Q_val,
+                                                         r.far);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int32_t far = 1;
+    if ((e = cudaMemcpyAsync(&far, r.far, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    *fmt = far != 0 ? kFmtCsr : (c32 ? kFmtPk32 : kFmtPk16);
+    return cudaSuccess;
+}
+
+// The P a prepared run streams.
+PStream stream_of(const RunWs& r, int fmt, const HeavyRows& hr)
+{
+    PStream sp;
+    const bool pk = fmt != kFmtCsr;
+    sp.row = pk ? r.Q_row : r.P_row;
+    sp.col = fmt == kFmtPk32 ? r.Q_col : r.P_col;
+    sp.d16 = fmt == kFmtPk16 ? (const int16_t*)r.Q_col : nullptr;
+    sp.val = pk ? r.Q_val : r.P_val;
+    sp.fmt = fmt;
+    sp.hr = hr;
+    return sp;
 }
 
 // C0 of one graph and the state the loop starts from: partial BFS,
@@ -1219,7 +1295,7 @@ RunWs run_carve(Carve& c, int32_t n, int64_t m2, const ltsnet_params* p, bool ho
 // its renumbered copy in r.Y2).
 struct Prepared {
     bool reordered = false;
-    bool d16 = false;  // P packed (k_pack_rows) in Q_row / Q_d16 / Q_val
+    int fmt = kFmtCsr;  // kFmtPk16 / kFmtPk32: P packed (k_pack_rows) in Q_row / Q_col / Q_val
     HeavyRows hr;
     int64_t nnz = 0;
     float2* Yw = nullptr;
@@ -1254,19 +1330,15 @@ ltsnet_status run_prepare(const int64_t* row_ptr, const int32_t* col, int32_t n,
     if (rc != LTSNET_OK) return rc;
     // packed layout with int16 columns when every entry is within int16
     // range of its row
-    bool d16 = false;
+    int fmt = kFmtCsr;
     if (!(p->flags & LTSNET_FLAG_PLAIN) && nnz > 0 && r.Q_row) {
         k_pad_count<<<flat_blocks(n), 256, 0, s>>>(r.P_row, n, r.hnch);
         LT_CUDA(scan_u32_exclusive(r.hnch, r.hbase, n, r.htmp, s));
         k_pad_rows<<<flat_blocks(n), 256, 0, s>>>(r.P_row, n, r.hnch, r.hbase, r.Q_row);
-        LT_CUDA(cudaMemsetAsync(r.far, 0, sizeof(int32_t), s));
-        k_pack_rows<<<num_sms() * 8, 256, 0, s>>>(r.P_row, r.P_col, r.P_val, n, r.Q_row, r.Q_d16, r.Q_val, r.far);
-        count_launches(3);
+        count_launches(2);
         LT_CHECK_LAUNCH();
-        int32_t far = 1;
-        LT_CUDA(cudaMemcpyAsync(&far, r.far, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        LT_CUDA(cudaStreamSynchronize(s));
-        d16 = far == 0;
+        LT_CUDA(pack_rows(r, n, false, s, &fmt));
+        if (fmt == kFmtCsr) LT_CUDA(pack_rows(r, n, true, s, &fmt));
     }
     // rows of P too long for one 8-lane group: chunk lists
     HeavyRows hr;
@@ -1301,7 +1373,7 @@ ltsnet_status run_prepare(const int64_t* row_ptr, const int32_t* col, int32_t n,
         Yw = r.Y2;
     }
     out->reordered = reordered;
-    out->d16 = d16;
+    out->fmt = fmt;
     out->hr = hr;
     out->nnz = nnz;
     out->Yw = Yw;
@@ -1331,8 +1403,7 @@ ltsnet_status run_core(const int64_t* row_ptr, const int32_t* col, int32_t n, co
     const IterWs w = iter_carve(ic, sh);
     LT_CUDA(iter_reset(w, sh, s));
     const int64_t total = schedule_length(p);
-    rc = optimize_core(pr.d16 ? r.Q_row : r.P_row, r.P_col, pr.d16 ? r.Q_d16 : nullptr, pr.d16 ? r.Q_val : r.P_val,
-                       pr.hr, n, p, pr.Yw, r.upd, r.gains, 0,
+    rc = optimize_core(stream_of(r, pr.fmt, pr.hr), n, p, pr.Yw, r.upd, r.gains, 0,
                        (int32_t)total, w, sh, s);
     if (rc != LTSNET_OK) return rc;
     return run_finish(n, Y, r, pr, w.st, s);
@@ -1345,7 +1416,7 @@ ltsnet_status run_core(const int64_t* row_ptr, const int32_t* col, int32_t n, co
 // schedule stage st; hg the host copy of stage 0's (for the per-graph
 // start and end steps).
 ltsnet_status batched_loop(BatchGraph* const* bg, const std::vector<BatchGraph>& hg, const BatchShape& bs,
-                           const IterShape& sh, const ltsnet_params* p, bool d16, cudaStream_t s)
+                           const IterShape& sh, const ltsnet_params* p, int fmt, cudaStream_t s)
 {
     const int32_t ng = (int32_t)hg.size();
     LT_CUDA(ensure_attrs());
@@ -1364,15 +1435,16 @@ ltsnet_status batched_loop(BatchGraph* const* bg, const std::vector<BatchGraph>&
         if (e != cudaSuccess) return e;
         if (max_chunks > 0) {
             // chunk sums of the long rows (graphs without any return at once)
-            if (d16) k_attr_chunks_b<true><<<dim3(cblocks, (unsigned)ng), 256, 0, st>>>(dbg, parity);
+            if (fmt == kFmtPk16) k_attr_chunks_b<true><<<dim3(cblocks, (unsigned)ng), 256, 0, st>>>(dbg, parity);
             else k_attr_chunks_b<false><<<dim3(cblocks, (unsigned)ng), 256, 0, st>>>(dbg, parity);
             count_launches(1);
         }
         profile_start(LTSNET_KERNEL_FUSED_UPDATE, st);
         const dim3 grid(fblocks, (unsigned)ng);
-#define LT_FB(PP)                                                                              \
-    if (d16) k_fused_b<PP, true><<<grid, kFusedThreads, kFusedSmem, st>>>(dbg, parity);        \
-    else k_fused_b<PP, false><<<grid, kFusedThreads, kFusedSmem, st>>>(dbg, parity)
+#define LT_FB(PP)                                                                                   \
+    if (fmt == kFmtPk16) k_fused_b<PP, kFmtPk16><<<grid, kFusedThreads, kFusedSmem, st>>>(dbg, parity);    \
+    else if (fmt == kFmtPk32) k_fused_b<PP, kFmtPk32><<<grid, kFusedThreads, kFusedSmem, st>>>(dbg, parity); \
+    else k_fused_b<PP, kFmtCsr><<<grid, kFusedThreads, kFusedSmem, st>>>(dbg, parity)
         switch (sh.P) {
             case 2: LT_FB(2); break;
             case 3: LT_FB(3); break;
@@ -1489,8 +1561,8 @@ extern "C" ltsnet_status ltsnet_gradient(const int64_t* P_row, const int32_t* P_
     LT_CUDA(launch_psum(w, P_row, n, P_val, s));
     LT_CUDA(launch_bounds_init(w, (const float2*)Y, n, 0, s));
     LT_CUDA(launch_grid_phase(w, sh, p, (const float2*)Y, 0, plain, s));
-    LT_CUDA(launch_point_phase<false>(P_row, P_col, nullptr, P_val, HeavyRows{}, n, (const float2*)Y, nullptr, nullptr, nullptr, w, sh, st,
-                                      0, (float2*)grad, parts, plain, s));
+    LT_CUDA(launch_point_phase<false>(csr_stream(P_row, P_col, P_val), n, (const float2*)Y, nullptr, nullptr, nullptr,
+                                      w, sh, st, 0, (float2*)grad, parts, plain, s));
     if (terms) {
         k_terms<<<1, 1, 0, s>>>(w.g, terms);
         count_launches(1);
@@ -1550,8 +1622,8 @@ extern "C" ltsnet_status ltsnet_optimize(const int64_t* P_row, const int32_t* P_
     ltsnet_status rc = prepare_iter(n, p, ws, ws_bytes, sh, w, s);
     if (rc != LTSNET_OK) return rc;
     LT_CUDA(launch_check_cols(P_row, P_col, n, w.st, s));
-    return optimize_core(P_row, P_col, nullptr, P_val, HeavyRows{}, n, p, (float2*)Y, (float2*)update, (float2*)gains, start_iter, n_iter,
-                         w, sh, s);
+    return optimize_core(csr_stream(P_row, P_col, P_val), n, p, (float2*)Y, (float2*)update, (float2*)gains,
+                         start_iter, n_iter, w, sh, s);
 }
 
 extern "C" size_t ltsnet_run_workspace_size(int32_t n, int64_t nnz_graph, const ltsnet_params* p)
@@ -1759,8 +1831,14 @@ extern "C" ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx
     }
     // one launch per phase over all graphs
     cudaStream_t s = (cudaStream_t)stream;
-    bool d16 = true;
-    for (int32_t g = 0; g < n_graphs; ++g) d16 = d16 && prep[g].d16;
+    // one format for the whole batch: int16 packed if every graph's P fits
+    // it, else int32 packed if every graph is packed (the int16 ones are
+    // packed again with int32 columns below), else CSR
+    int fmt = kFmtPk16;
+    for (int32_t g = 0; g < n_graphs; ++g) {
+        if (prep[g].fmt == kFmtCsr) fmt = kFmtCsr;
+        else if (prep[g].fmt == kFmtPk32 && fmt == kFmtPk16) fmt = kFmtPk32;
+    }
     ltsnet_params pmax = gp[0];  // the largest grid cap of the batch sizes the shared launch shapes
     for (int32_t g = 1; g < n_graphs; ++g) pmax.max_boxes = std::max(pmax.max_boxes, gp[g].max_boxes);
     const IterShape shmax = iter_shape((int32_t)max_n, &pmax);
@@ -1776,10 +1854,16 @@ extern "C" ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx
         BatchGraph& b = hg[g];
         b.w = iter_carve(ic, sh);
         LT_CUDA(iter_reset(b.w, sh, s));
-        b.P_row = d16 ? r.Q_row : r.P_row;
-        b.P_col = r.P_col;
-        b.P_d16 = d16 ? r.Q_d16 : nullptr;
-        b.P_val = d16 ? r.Q_val : r.P_val;
+        if (fmt == kFmtPk32 && prep[g].fmt == kFmtPk16) {
+            int f = kFmtCsr;
+            LT_CUDA(pack_rows(r, ng, true, s, &f));
+            if (f != kFmtPk32) return LTSNET_ERR_BAD_GRAPH;  // not reached: the int16 packing checked the columns
+        }
+        const PStream sp = stream_of(r, fmt, prep[g].hr);
+        b.P_row = sp.row;
+        b.P_col = sp.col;
+        b.P_d16 = sp.d16;
+        b.P_val = sp.val;
         b.Y = prep[g].Yw;
         b.upd = r.upd;
         b.gains = r.gains;
@@ -1812,7 +1896,7 @@ extern "C" ltsnet_status ltsnet_run_batched(int32_t n_graphs, const int64_t* vtx
         bs.fft_blocks = cfg->fft_blocks > 0 ? cfg->fft_blocks : 4;
         bs.spread_blocks = cfg->spread_blocks > 0 ? cfg->spread_blocks : 8;
         bs.max_n = (int32_t)max_n;
-        rc = batched_loop(dbg.data(), hg, bs, shmax, p, d16, s);
+        rc = batched_loop(dbg.data(), hg, bs, shmax, p, fmt, s);
     }
     if (rc != LTSNET_OK) return rc;
     for (int32_t g = 0; g < n_graphs; ++g) {

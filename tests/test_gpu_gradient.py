@@ -627,9 +627,9 @@ def test_run_step_far_columns_match_oracle(ltlib):
     """ltsnet_run on a graph whose columns of P lie further than the int16
     range from their rows even after the breadth-first renumbering (a star
     with 40,000 leaves: the centre and the leaves every leaf lists have rows
-    of about 40,000 entries), so P is streamed as CSR with int32 columns and
-    the long rows are summed in chunks; one step agrees with the oracle's
-    gradient and update."""
+    of about 40,000 entries), so P is streamed in the packed layout with
+    int32 columns and the long rows are summed in chunks; one step agrees
+    with the oracle's gradient and update."""
     import torch
 
     leaves = 40_000
