@@ -1290,9 +1290,9 @@ PStream stream_of(const RunWs& r, int fmt, const HeavyRows& hr)
 }
 
 // C0 of one graph and the state the loop starts from: partial BFS,
-// calibration, breadth-first renumbering, symmetrisation, int16 columns, long
-// row chunks, update/gains.  *Yw gets the layout the loop works on (Y, or
-// its renumbered copy in r.Y2).
+// calibration, breadth-first renumbering, symmetrisation, the packed layout
+// of P, long row chunks, update/gains.  *Yw gets the layout the loop works
+// on (Y, or its renumbered copy in r.Y2).
 struct Prepared {
     bool reordered = false;
     int fmt = kFmtCsr;  // kFmtPk16 / kFmtPk32: P packed (k_pack_rows) in Q_row / Q_col / Q_val
@@ -1328,8 +1328,8 @@ ltsnet_status run_prepare(const int64_t* row_ptr, const int32_t* col, int32_t n,
                                r.sym, r.sym_bytes, s);
     }
     if (rc != LTSNET_OK) return rc;
-    // packed layout with int16 columns when every entry is within int16
-    // range of its row
+    // packed layout: int16 column offsets when every entry is within int16
+    // range of its row, else int32 columns
     int fmt = kFmtCsr;
     if (!(p->flags & LTSNET_FLAG_PLAIN) && nnz > 0 && r.Q_row) {
         k_pad_count<<<flat_blocks(n), 256, 0, s>>>(r.P_row, n, r.hnch);

@@ -514,7 +514,7 @@ def test_run_batched_argument_checks(ltlib):
 
 def test_run_step_rgg1m_matches_oracle(ltlib):
     """The benchmark's workload at full size (RGG, n = 999,019) through
-    ltsnet_run -- breadth-first renumbering, int16 columns, the kernels the
+    ltsnet_run -- breadth-first renumbering, packed int16 P, the kernels the
     benchmark times -- for one iteration from a spread-out layout, against
     the oracle's interpolated gradient and update rule on the same P (the
     GPU's C0 in the original numbering, checked separately)."""
