@@ -1347,7 +1347,6 @@ __device__ __forceinline__ double block_sum_double(double v, double* red)
 
 constexpr int kColThreads = kIpThreads;
 constexpr int kColSlots = 8;                        // warps per column in the Z sums
-constexpr int kColPerRound = kColThreads / 32 / kColSlots;
 constexpr int kColMaxC = 16;                        // columns per tile
 
 __device__ __forceinline__ void k_conv_cols_body(GridDev* Gp, const float2* __restrict__ tw, const float2* __restrict__ srow,
@@ -1374,6 +1373,8 @@ __device__ __forceinline__ void k_conv_cols_body(GridDev* Gp, const float2* __re
     if (C < 1) C = 1;
     const int64_t MH = (int64_t)M * H;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nthr = (int)blockDim.x;                    // 256 or 512 threads
+    const int per_round = (nthr >> 5) / kColSlots;       // columns per round of products
     for (int t = blockIdx.x; t * C < H; t += gridDim.x) {
         const int k0 = t * C, nc = min(C, H - k0);
         const int ld = (6 * nc + 1) * L <= sm.avail ? 6 * nc + 1 : 6 * nc;
@@ -1381,7 +1382,7 @@ __device__ __forceinline__ void k_conv_cols_body(GridDev* Gp, const float2* __re
         __syncthreads();
         {
             // line g nc + c: spectrum g of column k0 + c along y (rows >= M zero)
-            const int nl = 4 * nc, nbp = kColThreads / nl, tl = (int)threadIdx.x % nl, tb = (int)threadIdx.x / nl;
+            const int nl = 4 * nc, nbp = nthr / nl, tl = (int)threadIdx.x % nl, tb = (int)threadIdx.x / nl;
             if (tb < nbp) {
                 const int g = tl / nc, c = tl - g * nc;
                 const float2* src = srow + g * MH + k0 + c;
@@ -1404,7 +1405,7 @@ __device__ __forceinline__ void k_conv_cols_body(GridDev* Gp, const float2* __re
         ip_fft<false>(X, ld, 4 * nc, pl, sm.tw);
         // products in place at every position p (frequency drev[p]): line
         // q nc + c receives U_q of column k0 + c, conjugated for the inverse
-        for (int c0 = 0; c0 < nc; c0 += kColPerRound) {
+        for (int c0 = 0; c0 < nc; c0 += per_round) {
             const int c = c0 + warp / kColSlots, wg = warp % kColSlots;
             double zp = 0.0, lp = 0.0;
             if (c < nc) {
@@ -1447,7 +1448,7 @@ __device__ __forceinline__ void k_conv_cols_body(GridDev* Gp, const float2* __re
                 wl[warp] = lp;
             }
             __syncthreads();
-            if ((int)threadIdx.x < kColPerRound && c0 + (int)threadIdx.x < nc) {
+            if ((int)threadIdx.x < per_round && c0 + (int)threadIdx.x < nc) {
                 double zs = 0.0, ls = 0.0;
                 for (int w = 0; w < kColSlots; ++w) {
                     zs += wz[threadIdx.x * kColSlots + w];
@@ -1460,7 +1461,7 @@ __device__ __forceinline__ void k_conv_cols_body(GridDev* Gp, const float2* __re
         }
         ip_fft<true>(X, ld, 6 * nc, pl, sm.tw);
         {
-            const int nl = 6 * nc, nbp = kColThreads / nl, tl = (int)threadIdx.x % nl, tb = (int)threadIdx.x / nl;
+            const int nl = 6 * nc, nbp = nthr / nl, tl = (int)threadIdx.x % nl, tb = (int)threadIdx.x / nl;
             if (tb < nbp) {
                 const int q = tl / nc, c = tl - q * nc;
                 float2* dst = ucol + q * MH + k0 + c;
@@ -1718,6 +1719,9 @@ constexpr int kPsumBlocks = 304;
 // margin for the static arrays.  A fixed size makes every tiling decision a
 // function of the grid alone.
 constexpr size_t kFftSmemBytes = 230400;
+// The batched FFT passes' half size: two blocks and their static shared
+// memory per SM.
+constexpr size_t kFftSmemHalf = 112640;
 static_assert(kFftSmemBytes >= (size_t)(6 * kLMax + (kLMax + 3) / 4) * 8, "six FFT lines of kLMax must fit");
 
 }  // namespace
@@ -1936,7 +1940,17 @@ cudaError_t launch_grid_phase_batched(const BatchGraph* bg, int32_t ng, const Ba
     const dim3 gpt(tiles, (unsigned)ng);
     k_setup_b<<<gpt, kBoxThreads, 0, s>>>(bg, parity, p->box_width_max, p->min_boxes, P);
     count_launches(1);
-    const size_t fsm = kFftSmemBytes;
+    // FFT blocks sized for the batch's largest grid cap: when half the
+    // shared memory holds one column of it (seven lines and the digit
+    // table), blocks of 256 threads and half the shared memory run two to
+    // an SM; every line is transformed the same way whatever the block, so
+    // each graph's result does not change.
+    size_t fsm = kFftSmemBytes;
+    unsigned fthr = kIpThreads;
+    if ((size_t)(15 * sh.Lmax / 2 + 64) * sizeof(float2) <= kFftSmemHalf) {
+        fsm = kFftSmemHalf;
+        fthr = kIpThreads / 2;
+    }
     const int f2 = (int)(fsm / sizeof(float2));
     const dim3 gfft((unsigned)bs.fft_blocks, (unsigned)ng);
     AuxStreams* aux = nullptr;
@@ -1945,8 +1959,8 @@ cudaError_t launch_grid_phase_batched(const BatchGraph* bg, int32_t ng, const Ba
     if (fork) {
         if ((e = cudaEventRecord(aux->fork, s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(aux->branch, aux->fork, 0)) != cudaSuccess) return e;
-        k_spec_rows_b<<<gfft, kIpThreads, fsm, aux->branch>>>(bg, p->eps, f2);
-        k_spec_cols_b<<<gfft, kIpThreads, fsm, aux->branch>>>(bg, f2);
+        k_spec_rows_b<<<gfft, fthr, fsm, aux->branch>>>(bg, p->eps, f2);
+        k_spec_cols_b<<<gfft, fthr, fsm, aux->branch>>>(bg, f2);
         count_launches(2);
         if ((e = cudaEventRecord(aux->join, aux->branch)) != cudaSuccess) return e;
     }
@@ -1964,14 +1978,14 @@ cudaError_t launch_grid_phase_batched(const BatchGraph* bg, int32_t ng, const Ba
     count_launches(3);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (!fork) {
-        k_spec_rows_b<<<gfft, kIpThreads, fsm, s>>>(bg, p->eps, f2);
-        k_spec_cols_b<<<gfft, kIpThreads, fsm, s>>>(bg, f2);
+        k_spec_rows_b<<<gfft, fthr, fsm, s>>>(bg, p->eps, f2);
+        k_spec_cols_b<<<gfft, fthr, fsm, s>>>(bg, f2);
         count_launches(2);
     }
-    k_conv_rows_fwd_b<<<gfft, kIpThreads, fsm, s>>>(bg, f2);
+    k_conv_rows_fwd_b<<<gfft, fthr, fsm, s>>>(bg, f2);
     if (fork && (e = cudaStreamWaitEvent(s, aux->join, 0)) != cudaSuccess) return e;
-    k_conv_cols_b<<<gfft, kColThreads, fsm, s>>>(bg, f2);
-    k_conv_rows_inv_b<<<gfft, kIpThreads, fsm, s>>>(bg, f2);
+    k_conv_cols_b<<<gfft, fthr, fsm, s>>>(bg, f2);
+    k_conv_rows_inv_b<<<gfft, fthr, fsm, s>>>(bg, f2);
     count_launches(3);
     return cudaGetLastError();
 }

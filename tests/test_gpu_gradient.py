@@ -469,6 +469,25 @@ def test_run_batched_equals_single_runs(ltlib, mode):
             assert np.all(boxes == -1)
 
 
+def test_run_batched_half_size_fft_blocks_equal_single_runs(ltlib):
+    """With grid caps small enough for one column of the largest grid to fit
+    in half of an SM's shared memory, the one-launch form runs its FFT passes
+    as two 256-thread blocks per SM; every graph still gets exactly the
+    layout ltsnet_run gives it alone (which uses one 512-thread block per SM),
+    the long row of a star included."""
+    import torch
+
+    star = synth.csr_from_edges(2501, np.zeros(2500, np.int64), np.arange(1, 2501, dtype=np.int64), "star2500")
+    graphs = [synth.grid2d(20, 30), synth.random_recursive_tree(900, 5), star, synth.sbm([300, 250, 200], 9.5, 40, 7)]
+    Y0s = [synth.initial_layout(g.n, 31 + i) for i, g in enumerate(graphs)]
+    params = ltlib.Params(stages=ltlib.default_stages(120), max_boxes=200)
+    single = [ltlib.run(g.row_ptr, g.col, torch.from_numpy(y0), params)[0] for g, y0 in zip(graphs, Y0s)]
+    for fb in (0, 3):
+        Y, off = ltlib.run_batched(graphs, Y0s, params, workers=2, mode=0, fft_blocks=fb)
+        for i in range(len(graphs)):
+            assert torch.equal(Y[off[i]:off[i + 1]], single[i]), (fb, i)
+
+
 def test_run_batched_per_graph_caps(ltlib):
     """Per-graph grid caps (ltsnet_batch_config.max_boxes): each graph of the
     batch runs exactly as ltsnet_run does with its own cap, in both forms,
